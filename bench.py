@@ -1,0 +1,332 @@
+"""Throughput of the full output distribution, m=20 modes, n=10 photons.
+
+One step = every amplitude and probability of the 20,030,010 outputs of a
+Haar-random 20x20 unitary with photons in modes 0..9 (Eq. eqperm, Sec. 4.2),
+computed by the CUDA library through its C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--algo factor|group]
+
+Prints one JSON line (rank 0).  `value` is amplitudes/s over all ranks with
+inputs resident in HBM; `e2e` is the same metric through the public API with
+host buffers (pinned H2D of U, D2H of probabilities and amplitudes inside the
+timed region).  Multi-GPU (torchrun) runs independent unitaries per rank
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N_PH = 20, 10
+WORKLOAD = ("full distribution m=20 n=10, photons in modes 0..9, Haar-random 20x20 complex128 "
+            "unitary (QR of seeded complex Gaussian, seed 2204006022 + 1000*rank), all 20,030,010 "
+            "outputs, complex FP64 amplitudes and probabilities")
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2, written between timed steps
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture, or None
+# when no capture of the current kernel exists.
+NCU_TRAFFIC_PER_LAUNCH = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="factor", choices=["factor", "group"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax = float(r[1])
+                for nm, v in zip(names, r[4:8]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev.index or 0)
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample(budget_s: float, rank_seed: int = 0):
+    """Time the CPU oracle (Ryser, all host threads) on the first outputs of the
+    canonical order until `budget_s` seconds of work are done."""
+    import numpy as np
+
+    import oracle
+    import pcv_inputs as pin
+    U = pin.haar_unitary(M, pin.BASE_SEED + 2 + rank_seed)
+    t = pin.single_photon_input(M, N_PH)
+    chunk = 20_000
+    outs = oracle.enumerate_outputs_prefix(M, N_PH, 2_000_000)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and done + chunk <= len(outs):
+        oracle.amplitudes(U, t, outs[done:done + chunk])
+        done += chunk
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "amplitudes/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {done} outputs in canonical order of the m=20 n=10 workload, "
+                      f"{dt:.1f} s of Ryser FP64 on the host"}, done, dt
+
+
+# --------------------------------------------------------------- ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2204_00602_gb300 as pcv
+    import pcv_inputs as pin
+    from paper_2204_00602_gb300 import abi
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    U_h = pin.haar_unitary(M, pin.BASE_SEED + 2 + 1000 * rank)
+    t = pin.single_photon_input(M, N_PH)
+    Ntot = pcv.num_outputs(M, N_PH)
+    algo = pcv.PCV_ALGO_FACTOR if args.algo == "factor" else pcv.PCV_ALGO_GROUP
+    param = 0 if args.algo == "factor" else 32
+    U = torch.from_numpy(U_h).to(dev)
+    prob = torch.empty(Ntot, dtype=torch.float64, device=dev)
+    amp = torch.empty(Ntot, dtype=torch.complex128, device=dev)
+    ws = pcv.workspace(pcv.distribution_workspace_bytes(M, N_PH, algo, param), dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        pcv.distribution(U, t, algo=algo, param=param, ws=ws, out=(prob, amp))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # FP64 probe: measured DFMA throughput of this GPU (context for the roofline)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    iters = 1 << 16
+    pr_blocks, pr_threads = sms * 8, 256
+    pcv.fp64_probe(pr_blocks, pr_threads, iters, device=dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pcv.fp64_probe(pr_blocks, pr_threads, iters, device=dev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    probe_tflops = pr_blocks * pr_threads * iters * 16 / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+    # ---------------- timed region (inputs resident in HBM)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    abi.pcv_profile_read()
+    abi.pcv_profile_enable(True)
+    launches0 = abi.pcv_launch_count()
+    clocks = ClockSampler(gpu_id_for(torch, dev))
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))                      # L2 flush between steps (untimed)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    launches = abi.pcv_launch_count() - launches0
+    abi.pcv_profile_enable(False)
+    stages = abi.pcv_profile_read()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_dev = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(tt.item())
+        torch.distributed.barrier()
+    value = Ntot * args.steps * world / t_dev
+
+    # ---------------- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        U_pin = torch.from_numpy(U_h).pin_memory()
+        prob_h = torch.empty(Ntot, dtype=torch.float64).pin_memory()
+        amp_h = torch.empty(Ntot, dtype=torch.complex128).pin_memory()
+        U_d = torch.empty_like(U)
+
+        def e2e_step():
+            U_d.copy_(U_pin, non_blocking=True)
+            pcv.distribution(U_d, t, algo=algo, param=param, ws=ws, out=(prob, amp))
+            prob_h.copy_(prob, non_blocking=True)
+            amp_h.copy_(amp, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        es.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        ee.record(stream)
+        torch.cuda.synchronize()
+        te = es.elapsed_time(ee) / 1e3
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": Ntot * args.steps * world / te, "unit": "amplitudes/s",
+               "h2d_bytes_per_step": U_pin.numel() * 16,
+               "d2h_bytes_per_step": prob_h.numel() * 8 + amp_h.numel() * 16}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---------------- roofline of the dominant kernel (FP64 ALU bound)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak_tflops = sms * 4 * sm_max * 1e6 / 1e12        # 2 DFMA/clk/SM x 2 flop
+    if args.algo == "factor":
+        ms, calls = stages["dist_products"]
+        flops_per_call = Ntot * (2 ** (N_PH - 1)) * 8     # one complex MAC per output and sign vector
+        kname = "gemm_kernel (factorised Glynn products)"
+        launches_per_call = N_PH + 1
+    else:
+        ms, calls = stages["glynn_plain"]
+        flops_per_call = Ntot * (2 ** (N_PH - 1)) * (8 * N_PH - 4)
+        kname = "glynn_group_kernel<10,32> (plain Glynn)"
+        launches_per_call = 1
+    achieved = flops_per_call * calls / (ms * 1e-3) / 1e12 if ms > 0 else None
+    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops if achieved else None,
+            "peak_source": f"derived: {sms} SMs x 2 DFMA/clk x 2 flop x {sm_max:.0f} MHz (FP64 ALU)",
+            "fp64_probe_tflops": probe_tflops,
+            "traffic": NCU_TRAFFIC_PER_LAUNCH,
+            "launches_per_step": launches_per_call,
+            "stage_ms_per_step": {k: (v[0] / v[1] if v[1] else None) for k, v in stages.items()}}
+
+    cpu = None
+    if world == 1 or rank == 0:
+        cpu, _, _ = oracle_sample(args.cpu_seconds)
+
+    line = {
+        "metric": "amplitudes/s (m=20 n=10 full distribution, complex FP64)",
+        "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N_PH, "outputs": Ntot, "algo": args.algo,
+                   "l2": "flushed between steps (256 MiB write, untimed)", "parallelism": f"replicas{world}"},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import pcv_inputs as pin
+    U = pin.haar_unitary(M, pin.BASE_SEED + 2)
+    t = pin.single_photon_input(M, N_PH)
+    per_step = 20_000
+    outs = oracle.enumerate_outputs_prefix(M, N_PH, per_step)
+    for _ in range(args.warmup):
+        oracle.amplitudes(U, t, outs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.amplitudes(U, t, outs)
+    dt = time.perf_counter() - t0
+    v = per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "amplitudes/s (m=20 n=10 full distribution, complex FP64)",
+        "value": v, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N_PH, "outputs": oracle.num_outputs(M, N_PH),
+                   "sample_per_step": per_step},
+        "cpu_baseline": {"value": v, "unit": "amplitudes/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"each step: the first {per_step} outputs in canonical order, CPU Ryser FP64"},
+        "e2e": {"value": v, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

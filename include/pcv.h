@@ -1,0 +1,175 @@
+/*
+ * pcv: GB300 (sm_103a) strong simulation of linear-optical interferometers.
+ *
+ * C ABI of the CUDA library libpcv.so.  Everything the library computes is
+ * defined by Eq. eqperm (Sec. 4.2 of the Perceval paper, arXiv 2204.00602):
+ * for an m x m matrix U (row = output mode, column = input mode), an input
+ * occupation t and an output occupation s with the same photon number n,
+ * U_{T,S} is the n x n matrix holding s_i copies of row i of U and then t_j
+ * copies of column j, and the output amplitude is
+ *
+ *     a(S) = Perm(U_{T,S}) / sqrt(s_1! ... s_m! t_1! ... t_m!),   P(S) = |a(S)|^2.
+ *
+ * The Naive back-end of Sec. 3.2.3 evaluates this per (input, output) pair
+ * ("prob", "probampli"); the SLOS back-end returns every output at once
+ * ("allstateprob_iterator").  pcv_amplitudes and pcv_distribution are the
+ * GPU counterparts of those two calls.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Complex numbers are pcv_c64 {re, im}, the layout of torch.complex128 and
+ *    C99 double complex.  Device arrays of pcv_c64 must be 16-byte aligned.
+ *  - U is row-major m x m, U[out_mode * m + in_mode].  It is not checked for
+ *    unitarity (the permanent is defined for any matrix).
+ *  - Pointers documented as "device" are CUDA device pointers owned by the
+ *    caller; the library never frees or keeps them after the call returns.
+ *    Pointers documented as "host" are read during the call only.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute
+ *    calls enqueue kernels on it and return without synchronising; results
+ *    are valid once the stream reaches that point.
+ *  - `workspace` is caller-owned device scratch of `workspace_bytes` bytes
+ *    (query the size with the matching *_workspace call).  The library
+ *    allocates no device memory itself.  A workspace may be reused by
+ *    consecutive calls on the same stream but not by calls that overlap.
+ *  - Every function returns PCV_OK (0) or a negative PCV_E* code; the message
+ *    of the last failure on the calling host thread is pcv_last_error().
+ *    Argument errors are reported before anything is enqueued.
+ *  - An output whose photon number differs from the input's has amplitude 0
+ *    (linear optics conserves photon number).  n = 0 gives amplitude 1 for
+ *    the empty output.
+ */
+#ifndef PCV_H
+#define PCV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } pcv_c64;
+
+enum {
+    PCV_OK = 0,
+    PCV_EINVAL = -1,      /* bad argument: sizes, null pointer, alignment       */
+    PCV_ERANGE = -2,      /* the output space or an index does not fit in int64 */
+    PCV_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed        */
+    PCV_ETIMEOUT = -4,    /* a bounded device loop gave up                      */
+    PCV_ENOMEM = -5,      /* the workspace passed is smaller than required      */
+};
+
+#define PCV_MAX_PHOTONS 30   /* n <= 30 (the paper's practical limit of Naive, Table 2) */
+#define PCV_MAX_MODES 1024
+
+/* ----------------------------------------------------------- host helpers */
+
+/* Message of the last error on this host thread ("" if none).  The pointer
+ * stays valid until the next failing call on the same thread. */
+const char* pcv_last_error(void);
+
+/* Library version string, e.g. "pcv 0.1 sm_103a". */
+const char* pcv_version(void);
+
+/* |S_{m,n}| = C(m+n-1, n), the number of n-photon output states over m modes
+ * (Sec. 4.2, the output space S_{m,n}).  Returns PCV_EINVAL for m < 1 or
+ * n < 0 and PCV_ERANGE if it exceeds 2^62. */
+int64_t pcv_num_outputs(int m, int n);
+
+/* Canonical order of S_{m,n}: lexicographic order of the non-decreasing list
+ * of occupied modes (one entry per photon).  pcv_unrank writes the occupation
+ * of output `idx` to occ_out[m] (host); pcv_rank returns the index of the
+ * occupation occ[m] (host) or a negative error. */
+int pcv_unrank(int m, int n, int64_t idx, uint8_t* occ_out);
+int64_t pcv_rank(int m, const uint8_t* occ);
+
+/* ------------------------------------------------------ amplitude kernels */
+
+/* Algorithm selectors for the *_ex calls. */
+enum {
+    PCV_ALGO_AUTO = 0,
+    PCV_ALGO_GROUP = 1,   /* plain Glynn, G threads per permanent (G = 1..32), n <= 16  */
+    PCV_ALGO_BLOCK = 2,   /* plain Glynn, one block (x splits) per permanent, n <= 30   */
+    PCV_ALGO_FACTOR = 3,  /* factorised Glynn sum over the whole output space           */
+};
+
+/* Workspace bytes pcv_amplitudes needs for these sizes (0 if none). */
+int64_t pcv_amplitudes_workspace(int m, int n, int64_t n_out);
+
+/* Amplitudes a(S) of explicit outputs (Eq. eqperm; the Naive back-end's
+ * probampli of Sec. 3.2.3).
+ *   U          device, m*m pcv_c64, row = output mode
+ *   m          1..PCV_MAX_MODES
+ *   input_occ  host, m uint8, photon number n = sum <= PCV_MAX_PHOTONS
+ *   output_occ device, n_out*m uint8, row-major (output o at output_occ + o*m)
+ *   n_out      >= 0 (0 = nothing to do)
+ *   amp        device, n_out pcv_c64 (written)
+ *   prob       device, n_out double (written) or NULL
+ * The permanent is Glynn's formula, Perm(A) = 2^{-(n-1)} sum over sign
+ * vectors d with d_1 = +1 of (prod_k d_k) prod_i sum_j d_j a_ij, with the
+ * sign vectors visited in reflected Gray-code order so each step updates the
+ * row sums by one column (Sec. 3.2.3 names Glynn's algorithm). */
+int pcv_amplitudes(const pcv_c64* U, int m, const uint8_t* input_occ,
+                   const uint8_t* output_occ, int64_t n_out,
+                   pcv_c64* amp, double* prob,
+                   void* workspace, int64_t workspace_bytes, void* stream);
+
+/* pcv_amplitudes with an explicit algorithm: algo = PCV_ALGO_GROUP with
+ * `param` threads per permanent (1, 2, 4, 8, 16 or 32), or PCV_ALGO_BLOCK
+ * with `param` blocks per permanent (>= 1); PCV_ALGO_AUTO ignores param. */
+int pcv_amplitudes_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
+                      const uint8_t* output_occ, int64_t n_out,
+                      pcv_c64* amp, double* prob, int algo, int param,
+                      void* workspace, int64_t workspace_bytes, void* stream);
+
+/* Workspace bytes pcv_distribution needs for m modes and n photons with the
+ * default plan.  A smaller workspace (>= pcv_distribution_workspace_min) is
+ * accepted and processed in more passes. */
+int64_t pcv_distribution_workspace(int m, int n);
+int64_t pcv_distribution_workspace_min(int m, int n);
+
+/* Every output of S_{m,n} in canonical order (the SLOS back-end's full
+ * distribution, Sec. 3.2.3, computed here from Eq. eqperm).
+ *   prob  device, C(m+n-1,n) doubles (written) or NULL
+ *   amp   device, C(m+n-1,n) pcv_c64 (written) or NULL; not both NULL
+ * The default algorithm factorises Glynn's sum: with sign vectors on the
+ * input photons, every output shares the per-mode row sums
+ * y_r(d) = sum_j d_j U[r][c_j], and a(S) = sum_d (sign, scale) prod_r y_r(d)^{s_r};
+ * the product splits into the modes below and above m/2, so each output costs
+ * one complex multiply-add per sign vector. */
+int pcv_distribution(const pcv_c64* U, int m, const uint8_t* input_occ,
+                     double* prob, pcv_c64* amp,
+                     void* workspace, int64_t workspace_bytes, void* stream);
+
+/* pcv_distribution with an explicit algorithm: PCV_ALGO_FACTOR (param
+ * ignored), PCV_ALGO_GROUP (param = threads per permanent; unranks each
+ * output), PCV_ALGO_BLOCK (param = blocks per permanent). */
+int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
+                        double* prob, pcv_c64* amp, int algo, int param,
+                        void* workspace, int64_t workspace_bytes, void* stream);
+
+/* -------------------------------------------------- measurement helpers */
+
+/* FP64 throughput probe: `blocks` x `threads` threads each run `iters`
+ * iterations of 8 independent DFMA chains and write one value to out[]
+ * (device, blocks*threads doubles).  FLOPs = blocks*threads*iters*16.
+ * Used to measure the FP64 roofline denominator. */
+int pcv_fp64_probe(double* out, int blocks, int threads, int iters, void* stream);
+
+/* Stage timing for measurement.  pcv_profile_enable(1) makes the library
+ * record CUDA events on the launching stream around each stage of a call
+ * (stage 0: factorised-distribution tables, 1: factorised-distribution
+ * products, 2: plain Glynn kernels).  pcv_profile_read waits for the recorded
+ * events, writes the accumulated milliseconds and call counts of the first
+ * `nstages` stages to ms[] and calls[] (host) and resets them.
+ * pcv_launch_count returns the number of kernels the library has launched
+ * since it was loaded.  No counterpart in the paper. */
+int pcv_profile_enable(int on);
+int pcv_profile_read(double* ms, int64_t* calls, int nstages);
+int64_t pcv_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCV_H */

@@ -143,6 +143,14 @@ def enumerate_outputs(m: int, n: int) -> np.ndarray:
     return occ
 
 
+def enumerate_outputs_prefix(m: int, n: int, count: int) -> np.ndarray:
+    """The first min(count, C(m+n-1,n)) outputs of the canonical order."""
+    N = min(count, num_outputs(m, n))
+    occ = np.zeros((N, m), dtype=np.uint8)
+    _L().oracle_enumerate(m, n, _u8(occ), N)
+    return occ
+
+
 def distribution(U, input_occ):
     """(prob float64[N], amp complex128[N]) over all outputs in canonical order."""
     U = _cmat(U)

@@ -1,0 +1,168 @@
+"""ctypes binding of libpcv.so (declarations in include/pcv.h).
+
+The functions named pcv_* take exactly the C arguments (device pointers may
+be given as torch tensors) and raise PcvError on a negative return code.
+There is no fallback: if libpcv.so is missing this module raises on import.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpcv.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -m paper_2204_00602_gb300.build)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+PCV_OK = 0
+PCV_EINVAL = -1
+PCV_ERANGE = -2
+PCV_ECUDA = -3
+PCV_ETIMEOUT = -4
+PCV_ENOMEM = -5
+PCV_ALGO_AUTO = 0
+PCV_ALGO_GROUP = 1
+PCV_ALGO_BLOCK = 2
+PCV_ALGO_FACTOR = 3
+PCV_MAX_PHOTONS = 30
+PCV_MAX_MODES = 1024
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+
+# name -> (restype, argtypes); every symbol include/pcv.h declares
+SIGNATURES = {
+    "pcv_last_error": (ctypes.c_char_p, []),
+    "pcv_version": (ctypes.c_char_p, []),
+    "pcv_num_outputs": (_i64, [_i, _i]),
+    "pcv_unrank": (_i, [_i, _i, _i64, _vp]),
+    "pcv_rank": (_i64, [_i, _vp]),
+    "pcv_amplitudes_workspace": (_i64, [_i, _i, _i64]),
+    "pcv_amplitudes": (_i, [_vp, _i, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp]),
+    "pcv_amplitudes_ex": (_i, [_vp, _i, _vp, _vp, _i64, _vp, _vp, _i, _i, _vp, _i64, _vp]),
+    "pcv_distribution_workspace": (_i64, [_i, _i]),
+    "pcv_distribution_workspace_min": (_i64, [_i, _i]),
+    "pcv_distribution": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "pcv_distribution_ex": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _vp, _i64, _vp]),
+    "pcv_fp64_probe": (_i, [_vp, _i, _i, _i, _vp]),
+    "pcv_profile_enable": (_i, [_i]),
+    "pcv_profile_read": (_i, [_vp, _vp, _i]),
+    "pcv_launch_count": (_i64, []),
+}
+
+for _name, (_res, _args) in SIGNATURES.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class PcvError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.pcv_last_error().decode()
+        super().__init__(f"{where} failed with code {code}: {msg}")
+        self.code = code
+
+
+def ptr(x):
+    """Address of a torch tensor / numpy array / int / None for the C call."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _check(rc, where):
+    if rc < 0:
+        raise PcvError(int(rc), where)
+    return rc
+
+
+def _call(name, *args):
+    return _check(getattr(_lib, name)(*args), name)
+
+
+def pcv_version() -> str:
+    return _lib.pcv_version().decode()
+
+
+def pcv_last_error() -> str:
+    return _lib.pcv_last_error().decode()
+
+
+def pcv_num_outputs(m, n) -> int:
+    return _call("pcv_num_outputs", m, n)
+
+
+def pcv_unrank(m, n, idx, occ_out):
+    return _call("pcv_unrank", m, n, idx, ptr(occ_out))
+
+
+def pcv_rank(m, occ) -> int:
+    return _call("pcv_rank", m, ptr(occ))
+
+
+def pcv_amplitudes_workspace(m, n, n_out) -> int:
+    return _call("pcv_amplitudes_workspace", m, n, n_out)
+
+
+def pcv_amplitudes(U, m, input_occ, output_occ, n_out, amp, prob, workspace, workspace_bytes, stream):
+    return _call("pcv_amplitudes", ptr(U), m, ptr(input_occ), ptr(output_occ), n_out, ptr(amp), ptr(prob),
+                 ptr(workspace), workspace_bytes, stream)
+
+
+def pcv_amplitudes_ex(U, m, input_occ, output_occ, n_out, amp, prob, algo, param, workspace, workspace_bytes, stream):
+    return _call("pcv_amplitudes_ex", ptr(U), m, ptr(input_occ), ptr(output_occ), n_out, ptr(amp), ptr(prob),
+                 algo, param, ptr(workspace), workspace_bytes, stream)
+
+
+def pcv_distribution_workspace(m, n) -> int:
+    return _call("pcv_distribution_workspace", m, n)
+
+
+def pcv_distribution_workspace_min(m, n) -> int:
+    return _call("pcv_distribution_workspace_min", m, n)
+
+
+def pcv_distribution(U, m, input_occ, prob, amp, workspace, workspace_bytes, stream):
+    return _call("pcv_distribution", ptr(U), m, ptr(input_occ), ptr(prob), ptr(amp), ptr(workspace),
+                 workspace_bytes, stream)
+
+
+def pcv_distribution_ex(U, m, input_occ, prob, amp, algo, param, workspace, workspace_bytes, stream):
+    return _call("pcv_distribution_ex", ptr(U), m, ptr(input_occ), ptr(prob), ptr(amp), algo, param,
+                 ptr(workspace), workspace_bytes, stream)
+
+
+def pcv_fp64_probe(out, blocks, threads, iters, stream):
+    return _call("pcv_fp64_probe", ptr(out), blocks, threads, iters, stream)
+
+
+STAGES = ("dist_tables", "dist_products", "glynn_plain")
+
+
+def pcv_profile_enable(on: bool):
+    return _call("pcv_profile_enable", 1 if on else 0)
+
+
+def pcv_profile_read():
+    """{stage name: (milliseconds, calls)} accumulated since the last read."""
+    import numpy as np
+    ms = np.zeros(len(STAGES))
+    calls = np.zeros(len(STAGES), dtype=np.int64)
+    _call("pcv_profile_read", ms.ctypes.data, calls.ctypes.data, len(STAGES))
+    return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(STAGES)}
+
+
+def pcv_launch_count() -> int:
+    return int(_lib.pcv_launch_count())

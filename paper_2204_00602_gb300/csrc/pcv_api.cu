@@ -1,0 +1,436 @@
+// C ABI of libpcv.so (declared in include/pcv.h): argument checks, planning
+// and dispatch to the kernels.  No device memory is allocated here; scratch
+// comes from the caller's workspace.
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pcv_common.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(PCV_ECUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+int64_t binom(int a, int b)
+{
+    if (b < 0 || a < 0 || b > a) return 0;
+    unsigned __int128 c = 1;
+    for (int i = 1; i <= b; ++i) {
+        c = c * (unsigned __int128)(a - b + i) / (unsigned __int128)i;
+        if (c > ((unsigned __int128)1 << 62)) return -1;
+    }
+    return (int64_t)c;
+}
+
+int64_t msets(int w, int k) { return k == 0 ? 1 : (w <= 0 ? 0 : binom(w + k - 1, k)); }
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int make_plan(const pcv_c64* U, int m, const uint8_t* input_occ, pcv::Plan* p)
+{
+    if (m < 1 || m > PCV_MAX_MODES) return fail(PCV_EINVAL, "m=%d outside [1, %d]", m, PCV_MAX_MODES);
+    if (!U) return fail(PCV_EINVAL, "U is NULL");
+    if (!aligned(U, 16)) return fail(PCV_EINVAL, "U is not 16-byte aligned");
+    if (!input_occ) return fail(PCV_EINVAL, "input_occ is NULL");
+    int n = 0;
+    double f = 1.0;
+    for (int j = 0; j < m; ++j) {
+        n += input_occ[j];
+        for (int q = 2; q <= input_occ[j]; ++q) f *= q;
+    }
+    if (n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "input has %d photons, more than %d", n, PCV_MAX_PHOTONS);
+    p->m = m;
+    p->n = n;
+    int c = 0;
+    for (int j = 0; j < m; ++j)
+        for (int q = 0; q < input_occ[j]; ++q) p->cols[c++] = j;
+    for (; c < PCV_MAX_PHOTONS; ++c) p->cols[c] = 0;
+    p->norm_t = 1.0 / std::sqrt(f);
+    return PCV_OK;
+}
+
+constexpr int kSMs = 152;
+
+// Threads per permanent for the group kernel: enough threads in flight to
+// cover the GPU, never more lanes than Gray steps.
+int auto_group(int n, int64_t n_out)
+{
+    int G = 1;
+    const int gmax = n >= 6 ? 32 : (1 << std::max(0, n - 1));
+    while (G < gmax && n_out * G < (int64_t)kSMs * 512) G *= 2;
+    return G;
+}
+
+// Blocks per permanent for the block kernel.
+int auto_splits(int n, int64_t n_out)
+{
+    const int64_t steps = 1ll << (n - 1);
+    int S = 1;
+    while ((int64_t)S * 2 * pcv::glynn_block_threads() <= steps && n_out * S < (int64_t)kSMs * 8) S *= 2;
+    return S;
+}
+
+struct AmpChoice { int algo, param; };
+
+AmpChoice choose_amp(int n, int64_t n_out, int algo, int param)
+{
+    if (algo == PCV_ALGO_AUTO) {
+        if (n <= 12 || (n <= 16 && n_out >= (int64_t)kSMs * 256)) return {PCV_ALGO_GROUP, auto_group(n, n_out)};
+        return {PCV_ALGO_BLOCK, auto_splits(n, n_out)};
+    }
+    return {algo, param};
+}
+
+int check_choice(const AmpChoice& c, int n)
+{
+    if (c.algo == PCV_ALGO_GROUP) {
+        if (n > 16) return fail(PCV_EINVAL, "group kernel supports n <= 16 (n=%d)", n);
+        const int G = c.param;
+        if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32)
+            return fail(PCV_EINVAL, "threads per permanent %d not in {1,2,4,8,16,32}", G);
+        if (n > 0 && (1ll << (n - 1)) < G) return fail(PCV_EINVAL, "threads per permanent %d exceed 2^(n-1)=%lld", G, 1ll << (n - 1));
+        return PCV_OK;
+    }
+    if (c.algo == PCV_ALGO_BLOCK) {
+        if (n < 9 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "block kernel supports 9 <= n <= 30 (n=%d)", n);
+        if (c.param < 1 || (int64_t)c.param * pcv::glynn_block_threads() > (1ll << (n - 1)))
+            return fail(PCV_EINVAL, "blocks per permanent %d invalid for n=%d", c.param, n);
+        return PCV_OK;
+    }
+    return fail(PCV_EINVAL, "unknown algorithm %d", c.algo);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int64_t amp_workspace(const AmpChoice& c, int64_t n_out)
+{
+    if (c.algo == PCV_ALGO_BLOCK && c.param > 1) return (int64_t)align256((size_t)n_out * c.param * sizeof(double2));
+    return 0;
+}
+
+// ------------------------------------------------------ stage timing
+struct StageTimer {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    struct Open { int stage; cudaEvent_t a; };
+    struct Done { int stage; cudaEvent_t a, b; };
+    std::vector<Open> open;
+    std::vector<Done> done;
+    double ms[pcv::kStageCount] = {};
+    int64_t calls[pcv::kStageCount] = {};
+    cudaEvent_t get()
+    {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+StageTimer g_timer;
+std::atomic<int64_t> g_launches{0};
+
+}  // namespace
+
+namespace pcv {
+void stage_begin(int stage, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    if (!g_timer.on) return;
+    cudaEvent_t e = g_timer.get();
+    cudaEventRecord(e, s);
+    g_timer.open.push_back({stage, e});
+}
+void stage_end(int stage, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    if (!g_timer.on) return;
+    for (size_t i = g_timer.open.size(); i-- > 0;) {
+        if (g_timer.open[i].stage != stage) continue;
+        cudaEvent_t b = g_timer.get();
+        cudaEventRecord(b, s);
+        g_timer.done.push_back({stage, g_timer.open[i].a, b});
+        g_timer.open.erase(g_timer.open.begin() + (long)i);
+        return;
+    }
+}
+void note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace pcv
+
+extern "C" {
+
+int pcv_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    g_timer.on = on != 0;
+    return PCV_OK;
+}
+
+int pcv_profile_read(double* ms, int64_t* calls, int nstages)
+{
+    if (nstages < 0 || (nstages > 0 && (!ms || !calls))) return fail(PCV_EINVAL, "bad profile buffers");
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    for (auto& d : g_timer.done) {
+        cudaError_t e = cudaEventSynchronize(d.b);
+        if (e != cudaSuccess) return cuda_fail(e, "profile event");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, d.a, d.b);
+        g_timer.ms[d.stage] += t;
+        g_timer.calls[d.stage] += 1;
+        g_timer.pool.push_back(d.a);
+        g_timer.pool.push_back(d.b);
+    }
+    g_timer.done.clear();
+    for (int i = 0; i < nstages && i < pcv::kStageCount; ++i) {
+        ms[i] = g_timer.ms[i];
+        calls[i] = g_timer.calls[i];
+        g_timer.ms[i] = 0;
+        g_timer.calls[i] = 0;
+    }
+    return PCV_OK;
+}
+
+int64_t pcv_launch_count(void) { return g_launches.load(); }
+
+const char* pcv_last_error(void) { return g_err.c_str(); }
+
+const char* pcv_version(void) { return "pcv 0.1 sm_103a"; }
+
+int64_t pcv_num_outputs(int m, int n)
+{
+    if (m < 1 || n < 0) return fail(PCV_EINVAL, "m=%d n=%d", m, n);
+    const int64_t c = msets(m, n);
+    if (c < 0) return fail(PCV_ERANGE, "C(m+n-1,n) exceeds 2^62 for m=%d n=%d", m, n);
+    return c;
+}
+
+int pcv_unrank(int m, int n, int64_t idx, uint8_t* occ_out)
+{
+    const int64_t N = pcv_num_outputs(m, n);
+    if (N < 0) return (int)N;
+    if (!occ_out) return fail(PCV_EINVAL, "occ_out is NULL");
+    if (idx < 0 || idx >= N) return fail(PCV_ERANGE, "index %lld outside [0, %lld)", (long long)idx, (long long)N);
+    for (int r = 0; r < m; ++r) occ_out[r] = 0;
+    int v = 0;
+    for (int p = 0; p < n; ++p) {
+        for (;;) {
+            const int64_t c = msets(m - v, n - p - 1);
+            if (idx < c) break;
+            idx -= c;
+            ++v;
+        }
+        occ_out[v]++;
+    }
+    return PCV_OK;
+}
+
+int64_t pcv_rank(int m, const uint8_t* occ)
+{
+    if (m < 1 || !occ) return fail(PCV_EINVAL, "bad arguments");
+    int n = 0;
+    for (int r = 0; r < m; ++r) n += occ[r];
+    if (msets(m, n) < 0) return fail(PCV_ERANGE, "output space too large");
+    int64_t rank = 0;
+    int p = 0, prev = 0;
+    for (int r = 0; r < m; ++r) {
+        for (int q = 0; q < occ[r]; ++q) {
+            for (int v = prev; v < r; ++v) rank += msets(m - v, n - p - 1);
+            prev = r;
+            ++p;
+        }
+    }
+    return rank;
+}
+
+int64_t pcv_amplitudes_workspace(int m, int n, int64_t n_out)
+{
+    if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS || n_out < 0) return fail(PCV_EINVAL, "bad sizes");
+    return amp_workspace(choose_amp(n, n_out, PCV_ALGO_AUTO, 0), n_out);
+}
+
+int pcv_amplitudes_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
+                      const uint8_t* output_occ, int64_t n_out,
+                      pcv_c64* amp, double* prob, int algo, int param,
+                      void* workspace, int64_t workspace_bytes, void* stream)
+{
+    pcv::Plan p;
+    int rc = make_plan(U, m, input_occ, &p);
+    if (rc) return rc;
+    if (n_out < 0) return fail(PCV_EINVAL, "n_out=%lld < 0", (long long)n_out);
+    if (n_out == 0) return PCV_OK;
+    if (!output_occ) return fail(PCV_EINVAL, "output_occ is NULL");
+    if (!amp && !prob) return fail(PCV_EINVAL, "amp and prob are both NULL");
+    if (amp && !aligned(amp, 16)) return fail(PCV_EINVAL, "amp is not 16-byte aligned");
+    if (prob && !aligned(prob, 8)) return fail(PCV_EINVAL, "prob is not 8-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p.n == 0) {
+        cudaError_t e = pcv::launch_glynn_group(p, (const double2*)U, output_occ, nullptr, 0, n_out,
+                                                (double2*)amp, prob, 1, s);
+        return e == cudaSuccess ? PCV_OK : cuda_fail(e, "n0 kernel");
+    }
+    AmpChoice c = choose_amp(p.n, n_out, algo, param);
+    if ((rc = check_choice(c, p.n))) return rc;
+    const int64_t need = amp_workspace(c, n_out);
+    if (need > 0 && (!workspace || workspace_bytes < need))
+        return fail(PCV_ENOMEM, "workspace of %lld bytes needed, %lld given", (long long)need, (long long)workspace_bytes);
+    if (need > 0 && !aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
+    if ((int64_t)n_out * (c.algo == PCV_ALGO_BLOCK ? c.param : 1) > INT32_MAX)
+        return fail(PCV_ERANGE, "too many permanents for one launch");
+    cudaError_t e;
+    pcv::stage_begin(pcv::kStagePlain, s);
+    if (c.algo == PCV_ALGO_GROUP)
+        e = pcv::launch_glynn_group(p, (const double2*)U, output_occ, nullptr, 0, n_out, (double2*)amp, prob, c.param, s);
+    else
+        e = pcv::launch_glynn_block(p, (const double2*)U, output_occ, nullptr, 0, n_out, (double2*)amp, prob,
+                                    c.param, (double2*)workspace, s);
+    pcv::stage_end(pcv::kStagePlain, s);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "glynn launch");
+}
+
+int pcv_amplitudes(const pcv_c64* U, int m, const uint8_t* input_occ,
+                   const uint8_t* output_occ, int64_t n_out,
+                   pcv_c64* amp, double* prob,
+                   void* workspace, int64_t workspace_bytes, void* stream)
+{
+    return pcv_amplitudes_ex(U, m, input_occ, output_occ, n_out, amp, prob, PCV_ALGO_AUTO, 0,
+                             workspace, workspace_bytes, stream);
+}
+
+static int64_t dist_ws(int m, int n, int algo, int param, bool need_acc, int64_t ws_bytes, pcv::DistPlan* dp)
+{
+    pcv::Plan p;
+    p.m = m;
+    p.n = n;
+    if (algo == PCV_ALGO_FACTOR || algo == PCV_ALGO_AUTO) {
+        if (n == 0) return 0;
+        pcv::DistPlan local;
+        pcv::DistPlan* d = dp ? dp : &local;
+        int64_t r = pcv::dist_plan(p, ws_bytes, need_acc, d);
+        if (r >= 0 && need_acc && d->kc == (1ll << (n - 1))) r = pcv::dist_plan(p, ws_bytes, false, d);
+        return r;
+    }
+    const int64_t N = msets(m, n);
+    int64_t bytes = (int64_t)align256((size_t)(m + 1) * (n + 1) * sizeof(int64_t));
+    if (algo == PCV_ALGO_BLOCK && param > 1) bytes += (int64_t)align256((size_t)N * param * sizeof(double2));
+    return bytes;
+}
+
+int64_t pcv_distribution_workspace(int m, int n)
+{
+    if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "bad sizes");
+    if (msets(m, n) < 0) return fail(PCV_ERANGE, "output space too large");
+    const int64_t r = dist_ws(m, n, PCV_ALGO_FACTOR, 0, true, -1, nullptr);
+    return r < 0 ? fail(PCV_ERANGE, "workspace size overflows") : r;
+}
+
+int64_t pcv_distribution_workspace_min(int m, int n)
+{
+    if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "bad sizes");
+    if (msets(m, n) < 0) return fail(PCV_ERANGE, "output space too large");
+    const int64_t r = dist_ws(m, n, PCV_ALGO_FACTOR, 0, true, 0, nullptr);
+    return r < 0 ? fail(PCV_ERANGE, "workspace size overflows") : r;
+}
+
+int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
+                        double* prob, pcv_c64* amp, int algo, int param,
+                        void* workspace, int64_t workspace_bytes, void* stream)
+{
+    pcv::Plan p;
+    int rc = make_plan(U, m, input_occ, &p);
+    if (rc) return rc;
+    if (!amp && !prob) return fail(PCV_EINVAL, "amp and prob are both NULL");
+    if (amp && !aligned(amp, 16)) return fail(PCV_EINVAL, "amp is not 16-byte aligned");
+    if (prob && !aligned(prob, 8)) return fail(PCV_EINVAL, "prob is not 8-byte aligned");
+    const int64_t N = msets(m, p.n);
+    if (N < 0) return fail(PCV_ERANGE, "output space C(%d,%d) too large", m + p.n - 1, p.n);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p.n == 0) {
+        cudaError_t e = pcv::launch_glynn_group(p, (const double2*)U, nullptr, nullptr, 0, 1, (double2*)amp, prob, 1, s);
+        return e == cudaSuccess ? PCV_OK : cuda_fail(e, "n0 kernel");
+    }
+    if (algo == PCV_ALGO_AUTO) algo = PCV_ALGO_FACTOR;
+    if (workspace && !aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
+    if (algo == PCV_ALGO_FACTOR) {
+        pcv::DistPlan dp;
+        const int64_t need = dist_ws(m, p.n, algo, 0, amp == nullptr, workspace_bytes, &dp);
+        if (need < 0) return fail(PCV_ERANGE, "workspace size overflows");
+        if (!workspace || need > workspace_bytes)
+            return fail(PCV_ENOMEM, "workspace of at least %lld bytes needed, %lld given",
+                        (long long)pcv_distribution_workspace_min(m, p.n), (long long)workspace_bytes);
+        cudaError_t e = pcv::launch_glynn_dist(p, dp, (const double2*)U, prob, (double2*)amp, workspace, s);
+        return e == cudaSuccess ? PCV_OK : cuda_fail(e, "factorised distribution");
+    }
+    AmpChoice c{algo, param};
+    if ((rc = check_choice(c, p.n))) return rc;
+    const int64_t need = dist_ws(m, p.n, algo, param, false, workspace_bytes, nullptr);
+    if (!workspace || need > workspace_bytes)
+        return fail(PCV_ENOMEM, "workspace of %lld bytes needed, %lld given", (long long)need, (long long)workspace_bytes);
+    if (N * (algo == PCV_ALGO_BLOCK ? param : 1) > INT32_MAX) return fail(PCV_ERANGE, "too many permanents for one launch");
+    int64_t* table = (int64_t*)workspace;
+    double2* partial = (double2*)((char*)workspace + align256((size_t)(m + 1) * (p.n + 1) * sizeof(int64_t)));
+    cudaError_t e = pcv::build_multiset_table(table, m, p.n, s);
+    if (e != cudaSuccess) return cuda_fail(e, "multiset table");
+    pcv::stage_begin(pcv::kStagePlain, s);
+    if (algo == PCV_ALGO_GROUP)
+        e = pcv::launch_glynn_group(p, (const double2*)U, nullptr, table, 0, N, (double2*)amp, prob, param, s);
+    else
+        e = pcv::launch_glynn_block(p, (const double2*)U, nullptr, table, 0, N, (double2*)amp, prob, param, partial, s);
+    pcv::stage_end(pcv::kStagePlain, s);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "glynn launch");
+}
+
+int pcv_distribution(const pcv_c64* U, int m, const uint8_t* input_occ,
+                     double* prob, pcv_c64* amp,
+                     void* workspace, int64_t workspace_bytes, void* stream)
+{
+    return pcv_distribution_ex(U, m, input_occ, prob, amp, PCV_ALGO_AUTO, 0, workspace, workspace_bytes, stream);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ FP64 probe
+
+namespace {
+__global__ void fp64_probe_kernel(double* out, int iters)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double a0 = 1e-9 * t, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+    const double b = 0.9999999, c = 1e-7;
+    for (int i = 0; i < iters; ++i) {
+        a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+        a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+    }
+    out[t] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+}  // namespace
+
+extern "C" int pcv_fp64_probe(double* out, int blocks, int threads, int iters, void* stream)
+{
+    if (!out || blocks < 1 || threads < 1 || threads > 1024 || iters < 1) return fail(PCV_EINVAL, "bad probe arguments");
+    fp64_probe_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(out, iters);
+    pcv::note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "fp64 probe");
+}

@@ -1,0 +1,128 @@
+// Shared device helpers of the CUDA path (complex FP64 arithmetic, multiset
+// ranking, launch plumbing).  Internal to the library; the C ABI is in
+// include/pcv.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pcv.h"
+
+namespace pcv {
+
+// ------------------------------------------------------------ complex FP64
+// Complex values are double2 (x = real, y = imaginary); pcv_c64 and
+// torch.complex128 have the same layout.
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+// a * b: 2 DMUL + 2 DFMA
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
+}
+
+// acc += a * b: 4 DFMA
+__device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b)
+{
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+
+// acc += s * a for a real scalar s: 2 DFMA
+__device__ __forceinline__ void caxpy(double2& acc, double s, double2 a)
+{
+    acc.x = fma(s, a.x, acc.x);
+    acc.y = fma(s, a.y, acc.y);
+}
+
+__device__ __forceinline__ double2 ld(const double2* p) { return __ldg(p); }
+
+// -------------------------------------------------------- output space
+// Multisets of size k over a modes: C(a+k-1, k).  The table MC[a*(kmax+1)+k]
+// is built on the device (build_multiset_table) for a <= amax, k <= kmax and
+// saturates at INT64_MAX.
+struct MultisetTable {
+    const int64_t* t;
+    int kmax;
+    __device__ __forceinline__ int64_t operator()(int a, int k) const { return t[a * (kmax + 1) + k]; }
+};
+
+// Canonical order of S_{w,k}: lexicographic order of the non-decreasing
+// photon->mode list.  Unrank `idx` into modes[0..k) (values in [0, w)).
+template <int KMAX>
+__device__ __forceinline__ void unrank_multiset(MultisetTable mc, int w, int k, int64_t idx, int* modes)
+{
+    int v = 0;
+    for (int p = 0; p < k; ++p) {
+        const int rest = k - p - 1;
+        for (;;) {
+            const int64_t c = mc(w - v, rest);     // lists with this position = v
+            if (idx < c) break;
+            idx -= c;
+            ++v;
+        }
+        modes[p] = v;
+    }
+}
+
+// Rank of a non-decreasing mode list of length k over w modes.
+__device__ __forceinline__ int64_t rank_multiset(MultisetTable mc, int w, int k, const int* modes)
+{
+    int64_t r = 0;
+    int prev = 0;
+    for (int p = 0; p < k; ++p) {
+        const int rest = k - p - 1;
+        for (int v = prev; v < modes[p]; ++v) r += mc(w - v, rest);
+        prev = modes[p];
+    }
+    return r;
+}
+
+__device__ __forceinline__ double inv_sqrt_int(int k) { return 1.0 / sqrt((double)k); }
+
+}  // namespace pcv
+
+// Launch helpers implemented in the .cu files (host side).
+namespace pcv {
+struct Plan {           // host-side description of one (U, input) problem
+    int m;
+    int n;
+    int cols[PCV_MAX_PHOTONS];     // input modes with repetition (photon -> input mode)
+    double norm_t;                 // 1 / sqrt(prod t_j!)
+};
+
+cudaError_t build_multiset_table(int64_t* t, int amax, int kmax, cudaStream_t s);
+
+// Per-stage timing (pcv_api.cu): when enabled, stage_begin/stage_end record
+// CUDA events on the launching stream around a group of launches; the times
+// are read back by pcv_profile_read.  note_launches counts kernel launches.
+enum Stage { kStageTables = 0, kStageGemm = 1, kStagePlain = 2, kStageCount = 8 };
+void stage_begin(int stage, cudaStream_t s);
+void stage_end(int stage, cudaStream_t s);
+void note_launches(int64_t k);
+
+// Plain Glynn kernels (glynn_plain.cu)
+cudaError_t launch_glynn_group(const Plan& p, const double2* U, const uint8_t* out_occ,
+                               const int64_t* mc_table, int64_t idx0, int64_t count,
+                               double2* amp, double* prob, int G, cudaStream_t s);
+cudaError_t launch_glynn_block(const Plan& p, const double2* U, const uint8_t* out_occ,
+                               const int64_t* mc_table, int64_t idx0, int64_t count,
+                               double2* amp, double* prob, int splits, double2* partial,
+                               cudaStream_t s);
+int glynn_block_threads();
+
+// Factorised full distribution (glynn_dist.cu)
+struct DistPlan {
+    int h;                    // modes [0,h) are the low side, [h,m) the high side
+    int kc;                   // Glynn sign vectors per chunk
+    int64_t wlow, whigh;      // entries of all levels per side: C(h+n, n), C(m-h+n, n)
+    int64_t lowoff[PCV_MAX_PHOTONS + 2], highoff[PCV_MAX_PHOTONS + 2];
+    size_t ws_table, ws_y, ws_T, ws_base, ws_acc, ws_total;
+};
+int64_t dist_plan(const Plan& p, int64_t ws_bytes, bool need_acc, DistPlan* dp);
+cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* U,
+                              double* prob, double2* amp, void* ws, cudaStream_t s);
+}  // namespace pcv

@@ -1,0 +1,139 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every symbol
+include/pcv.h declares, and its host-only helpers (output-space counting,
+ranking, argument validation) behave.  No compute call reaches the GPU."""
+import ctypes
+import itertools
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def load_build_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "pcv_build", os.path.join(ROOT, "paper_2204_00602_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    path = load_build_module().build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"\b(pcv_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for want in ("pcv_amplitudes", "pcv_distribution", "pcv_num_outputs", "pcv_unrank", "pcv_last_error"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol(lib):
+    from paper_2204_00602_gb300 import _abi
+    assert set(declared_functions()) <= set(_abi.SIGNATURES)
+
+
+def test_num_outputs_and_errors(lib):
+    from paper_2204_00602_gb300 import _abi
+    assert _abi.pcv_num_outputs(20, 10) == 20_030_010
+    assert _abi.pcv_num_outputs(6, 3) == 56
+    assert _abi.pcv_num_outputs(1, 30) == 1
+    assert _abi.pcv_num_outputs(5, 0) == 1
+    with pytest.raises(_abi.PcvError) as e:
+        _abi.pcv_num_outputs(0, 3)
+    assert e.value.code == _abi.PCV_EINVAL
+    with pytest.raises(_abi.PcvError) as e:
+        _abi.pcv_num_outputs(1024, 30)
+    assert e.value.code == _abi.PCV_ERANGE
+
+
+@pytest.mark.parametrize("m,n", [(6, 3), (4, 2), (5, 5), (7, 1), (3, 0)])
+def test_unrank_and_rank_follow_lexicographic_order(m, n):
+    import oracle
+    import paper_2204_00602_gb300 as pcv
+    occ = oracle.enumerate_outputs(m, n)
+    for i, o in enumerate(occ):
+        assert np.array_equal(pcv.unrank(m, n, i), o)
+        assert pcv.rank(o) == i
+
+
+def test_rank_of_a_large_space_round_trips():
+    import paper_2204_00602_gb300 as pcv
+    m, n = 20, 10
+    N = pcv.num_outputs(m, n)
+    for idx in (0, 1, 12345, N // 2, N - 2, N - 1):
+        assert pcv.rank(pcv.unrank(m, n, idx)) == idx
+    assert list(np.nonzero(pcv.unrank(m, n, N - 1))[0]) == [m - 1]
+    first = pcv.unrank(m, n, 0)
+    assert first[0] == n
+
+
+def test_unrank_out_of_range():
+    from paper_2204_00602_gb300 import _abi
+    occ = np.zeros(6, np.uint8)
+    with pytest.raises(_abi.PcvError) as e:
+        _abi.pcv_unrank(6, 3, 56, occ)
+    assert e.value.code == _abi.PCV_ERANGE
+
+
+def test_argument_errors_are_reported_before_any_launch():
+    from paper_2204_00602_gb300 import _abi
+    t = np.array([1, 1, 0], np.uint8)
+    fake = 1 << 40        # never dereferenced: validation fails first
+    cases = [
+        (dict(U=None, m=3), _abi.PCV_EINVAL),
+        (dict(U=fake, m=0), _abi.PCV_EINVAL),
+        (dict(U=fake + 8, m=3), _abi.PCV_EINVAL),          # misaligned U
+        (dict(U=fake, m=3, n_out=-1), _abi.PCV_EINVAL),
+        (dict(U=fake, m=3, amp=None, prob=None), _abi.PCV_EINVAL),
+        (dict(U=fake, m=3, algo=_abi.PCV_ALGO_GROUP, param=3), _abi.PCV_EINVAL),
+        (dict(U=fake, m=3, algo=_abi.PCV_ALGO_GROUP, param=4), _abi.PCV_EINVAL),   # 4 > 2^(n-1)
+        (dict(U=fake, m=3, algo=_abi.PCV_ALGO_BLOCK, param=1), _abi.PCV_EINVAL),   # n < 9
+    ]
+    for kw, code in cases:
+        a = dict(U=fake, m=3, input=t, out=fake, n_out=4, amp=fake, prob=None, algo=0, param=0)
+        a.update(kw)
+        with pytest.raises(_abi.PcvError) as e:
+            _abi.pcv_amplitudes_ex(a["U"], a["m"], a["input"], a["out"], a["n_out"], a["amp"], a["prob"],
+                                   a["algo"], a["param"], None, 0, None)
+        assert e.value.code == code, kw
+    many = np.ones(40, np.uint8)
+    with pytest.raises(_abi.PcvError) as e:
+        _abi.pcv_amplitudes(fake, 40, many, fake, 1, fake, None, None, 0, None)
+    assert e.value.code == _abi.PCV_EINVAL and "photons" in str(e.value)
+
+
+def test_distribution_workspace_sizes():
+    from paper_2204_00602_gb300 import _abi
+    full = _abi.pcv_distribution_workspace(20, 10)
+    small = _abi.pcv_distribution_workspace_min(20, 10)
+    assert 0 < small < full < 8 << 30
+    n = 10
+    lo = math.comb(10 + n, n)
+    assert full >= 512 * 2 * lo * 16      # alpha and beta tables for all 512 sign vectors
+    with pytest.raises(_abi.PcvError) as e:
+        fake = 1 << 40
+        _abi.pcv_distribution(fake, 20, np.array([1] * 10 + [0] * 10, np.uint8), fake, None, fake, small - 1024, None)
+    assert e.value.code in (_abi.PCV_ENOMEM, _abi.PCV_EINVAL)

@@ -1,0 +1,248 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerance (Eq. eqperm amplitudes, complex FP64): the relative amplitude error
+|a_gpu - a_ref| / max(|a_ref|, 1/sqrt(C(m+n-1,n))) must stay <= 1e-10 for
+n <= 12 and <= 1e-8 for n <= 30; the floor is the RMS amplitude of a unitary
+U (sum_S |a(S)|^2 = 1), so near-zero amplitudes (HOM-type zeros) are judged
+on an absolute scale.  Full distributions: TVD (Eq. bosonsampling) <= 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import golden_io
+import oracle
+import pcv_inputs as pin
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pcv():
+    import paper_2204_00602_gb300 as pcv
+    return pcv
+
+
+def tol(n):
+    return 1e-10 if n <= 12 else 1e-8
+
+
+def amp_err(got, want, m, n):
+    floor = 1.0 / math.sqrt(math.comb(m + n - 1, n))
+    return np.max(np.abs(got - want) / np.maximum(np.abs(want), floor))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run_amps(pcv, U, t, outs, **kw):
+    amp, prob = pcv.amplitudes(dev(U), t, dev(outs), **kw)
+    torch.cuda.synchronize()
+    return amp.cpu().numpy(), prob.cpu().numpy()
+
+
+# ------------------------------------------------------------ workload 1
+
+
+def test_m6_n3_full_distribution_all_algorithms(pcv):
+    m, n = 6, 3
+    U = pin.haar_unitary(m, pin.BASE_SEED + 1)
+    t = pin.single_photon_input(m, n)
+    p_ref, a_ref = oracle.distribution(U, t)
+    assert len(p_ref) == 56
+    variants = [dict(algo=pcv.PCV_ALGO_FACTOR)] + [dict(algo=pcv.PCV_ALGO_GROUP, param=g) for g in (1, 2, 4)]
+    for kw in variants:
+        prob, amp = pcv.distribution(dev(U), t, **kw)
+        torch.cuda.synchronize()
+        prob, amp = prob.cpu().numpy(), amp.cpu().numpy()
+        assert amp_err(amp, a_ref, m, n) <= tol(n), kw
+        assert oracle.tvd(prob, p_ref) <= 1e-12, kw
+        assert abs(prob.sum() - 1) < 1e-13
+
+
+# -------------------------------------------------- explicit outputs
+
+
+@pytest.mark.parametrize("n", list(range(1, 13)))
+def test_group_kernel_every_threads_per_permanent(pcv, n):
+    m = max(n + 2, 8)
+    U = pin.haar_unitary(m, 300 + n)
+    t = pin.single_photon_input(m, n)
+    outs = np.concatenate([pin.random_outputs(m, n, 40, 400 + n), pin.random_bunched_outputs(m, n, 40, 500 + n)])
+    a_ref = oracle.amplitudes(U, t, outs)
+    for G in (1, 2, 4, 8, 16, 32):
+        if G > 2 ** (n - 1):
+            continue
+        amp, prob = run_amps(pcv, U, t, outs, algo=pcv.PCV_ALGO_GROUP, param=G)
+        assert amp_err(amp, a_ref, m, n) <= tol(n), G
+        assert np.allclose(prob, np.abs(a_ref) ** 2, rtol=1e-9, atol=1e-300)
+
+
+@pytest.mark.parametrize("n,splits", [(9, 1), (10, 2), (12, 1), (13, 4), (14, 2), (16, 8)])
+def test_block_kernel_with_splits(pcv, n, splits):
+    m = 2 * n
+    U = pin.haar_unitary(m, 600 + n)
+    t = pin.single_photon_input(m, n)
+    outs = np.concatenate([pin.random_outputs(m, n, 6, 700 + n), pin.random_bunched_outputs(m, n, 6, 800 + n)])
+    a_ref = oracle.amplitudes(U, t, outs)
+    amp, _ = run_amps(pcv, U, t, outs, algo=pcv.PCV_ALGO_BLOCK, param=splits)
+    assert amp_err(amp, a_ref, m, n) <= tol(n)
+
+
+def test_auto_choice_and_ragged_counts(pcv):
+    for m, n, cnt in [(9, 4, 1), (9, 4, 33), (16, 7, 257), (24, 12, 3), (30, 14, 5)]:
+        U = pin.haar_unitary(m, 900 + cnt)
+        t = pin.single_photon_input(m, n)
+        outs = pin.random_bunched_outputs(m, n, cnt, 1000 + cnt)
+        a_ref = oracle.amplitudes(U, t, outs)
+        amp, _ = run_amps(pcv, U, t, outs)
+        assert amp_err(amp, a_ref, m, n) <= tol(n), (m, n, cnt)
+
+
+def test_photon_number_mismatch_and_bunched_input(pcv):
+    m = 7
+    U = pin.haar_unitary(m, 31)
+    t = np.array([2, 0, 1, 0, 0, 1, 0], np.uint8)         # bunched input, n = 4
+    outs = np.concatenate([pin.random_bunched_outputs(m, 4, 30, 32), pin.random_bunched_outputs(m, 3, 5, 33),
+                           pin.random_bunched_outputs(m, 5, 5, 34), np.zeros((1, m), np.uint8)])
+    a_ref = oracle.amplitudes(U, t, outs)
+    for G in (1, 4, 8):
+        amp, _ = run_amps(pcv, U, t, outs, algo=pcv.PCV_ALGO_GROUP, param=G)
+        assert amp_err(amp, a_ref, m, 4) <= tol(4)
+        assert np.all(amp[30:] == 0)
+
+
+def test_zero_photons_and_empty_batch(pcv):
+    m = 5
+    U = pin.haar_unitary(m, 41)
+    t = np.zeros(m, np.uint8)
+    outs = np.array([[0] * 5, [1, 0, 0, 0, 0]], np.uint8)
+    amp, prob = run_amps(pcv, U, t, outs)
+    assert amp[0] == 1 and amp[1] == 0 and prob[0] == 1
+    amp, prob = pcv.amplitudes(dev(U), pin.single_photon_input(m, 2), torch.zeros((0, m), dtype=torch.uint8, device="cuda"))
+    assert amp.numel() == 0
+    prob, amp = pcv.distribution(dev(U), t)
+    torch.cuda.synchronize()
+    assert prob.numel() == 1 and prob.item() == 1.0
+
+
+def test_hong_ou_mandel_and_cnot(pcv):
+    U = oracle.BS_RX_HALF
+    outs = np.array([[1, 1], [2, 0], [0, 2]], np.uint8)
+    amp, prob = run_amps(pcv, U, np.array([1, 1], np.uint8), outs)
+    assert abs(amp[0]) < 1e-16 and abs(prob[1] - 0.5) < 1e-15 and abs(prob[2] - 0.5) < 1e-15
+    C = golden_io.cnot_unitary()
+    logical = [[0, 1, 0, 1, 0, 0], [0, 1, 0, 0, 1, 0], [0, 0, 1, 1, 0, 0], [0, 0, 1, 0, 1, 0]]
+    expected = [[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]]
+    for i, tin in enumerate(logical):
+        _, prob = run_amps(pcv, C, np.array(tin, np.uint8), np.array(logical, np.uint8))
+        assert abs(prob.sum() - 1 / 9) < 1e-15
+        assert np.allclose(prob * 9, expected[i], atol=1e-14)
+
+
+def test_single_mode(pcv):
+    U = np.array([[0.6 + 0.8j]])
+    for n in (1, 3, 7):
+        prob, amp = pcv.distribution(dev(U), [n])
+        torch.cuda.synchronize()
+        assert abs(amp.cpu().numpy()[0] - U[0, 0] ** n) < 1e-15
+
+
+# --------------------------------------------------- full distributions
+
+
+@pytest.mark.parametrize("m,n,t", [(12, 6, None), (9, 5, [2, 0, 1, 0, 0, 1, 0, 1, 0]), (5, 7, [3, 1, 0, 2, 1]),
+                                   (2, 1, None), (11, 2, None)])
+def test_factorised_distribution_matches_oracle(pcv, m, n, t):
+    U = pin.haar_unitary(m, 1200 + m + n)
+    t = pin.single_photon_input(m, n) if t is None else np.array(t, np.uint8)
+    p_ref, a_ref = oracle.distribution(U, t)
+    prob, amp = pcv.distribution(dev(U), t)
+    torch.cuda.synchronize()
+    amp = amp.cpu().numpy()
+    assert amp_err(amp, a_ref, m, n) <= tol(n)
+    assert oracle.tvd(prob.cpu().numpy(), p_ref) <= 1e-12
+
+
+def test_factorised_distribution_in_several_chunks(pcv):
+    # a workspace below the default forces several passes over the sign vectors
+    m, n = 10, 7
+    U = pin.haar_unitary(m, 1301)
+    t = pin.single_photon_input(m, n)
+    p_ref, a_ref = oracle.distribution(U, t)
+    wsmin = pcv.abi.pcv_distribution_workspace_min(m, n)
+    for want_amp in (True, False):
+        ws = torch.empty(wsmin, dtype=torch.uint8, device="cuda")
+        prob, amp = pcv.distribution(dev(U), t, want_amp=want_amp, ws=ws)
+        torch.cuda.synchronize()
+        assert oracle.tvd(prob.cpu().numpy(), p_ref) <= 1e-12
+        if want_amp:
+            assert amp_err(amp.cpu().numpy(), a_ref, m, n) <= tol(n)
+
+
+def test_plain_kernels_in_distribution_mode(pcv):
+    m, n = 8, 9
+    U = pin.haar_unitary(m, 1401)
+    t = np.array([2, 1, 1, 1, 1, 1, 1, 1], np.uint8)
+    p_ref, a_ref = oracle.distribution(U, t)
+    for kw in (dict(algo=pcv.PCV_ALGO_GROUP, param=8), dict(algo=pcv.PCV_ALGO_BLOCK, param=1),
+               dict(algo=pcv.PCV_ALGO_BLOCK, param=2)):
+        prob, amp = pcv.distribution(dev(U), t, **kw)
+        torch.cuda.synchronize()
+        assert amp_err(amp.cpu().numpy(), a_ref, m, n) <= tol(n), kw
+
+
+# ---------------------------------------------- full-size workloads
+
+
+def test_m20_n10_full_distribution_sampled_and_invariants(pcv):
+    """The 20,030,010-output workload, in the launch configuration the bench
+    times: sampled outputs against the oracle one by one, the sum rule, and
+    the partial certificate P(K) (Eq. eqpk) against one Gram-matrix permanent."""
+    m, n = 20, 10
+    U = pin.haar_unitary(m, pin.BASE_SEED + 2)
+    t = pin.single_photon_input(m, n)
+    prob, amp = pcv.distribution(dev(U), t)
+    torch.cuda.synchronize()
+    assert prob.numel() == 20_030_010
+    assert abs(prob.sum().item() - 1.0) < 1e-12
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([[0, 1, prob.numel() - 1], rng.integers(0, prob.numel(), 1500)]))
+    occ = np.stack([pcv.unrank(m, n, int(i)) for i in idx])
+    a_ref = oracle.amplitudes(U, t, occ)
+    a_gpu = amp[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert amp_err(a_gpu, a_ref, m, n) <= tol(n)
+    # P(K) for the last K modes: those outputs are the last C(K+n-1, n) entries of
+    # the canonical order (their first photon is already in mode >= m-K); their
+    # total equals the permanent of the Gram matrix of those rows of U.
+    for K in (12, 16, 19):
+        cnt = math.comb(K + n - 1, n)
+        V = U[m - K:][:, :n]
+        want = oracle.perm_ryser(V.conj().T @ V).real
+        assert abs(prob[prob.numel() - cnt:].sum().item() - want) < 1e-12
+
+
+@pytest.mark.parametrize("n", [16, 20, 24])
+def test_large_n_sweep_sampled(pcv, n):
+    m = n * n
+    U = pin.haar_unitary(m, 1500 + n)
+    t = pin.single_photon_input(m, n)
+    outs = pin.random_outputs(m, n, 2 if n >= 24 else 4, 1600 + n)
+    a_ref = oracle.amplitudes(U, t, outs)
+    amp, _ = run_amps(pcv, U, t, outs)
+    assert amp_err(amp, a_ref, m, n) <= tol(n)
+
+
+def test_n30_single_output(pcv):
+    n = 30
+    m = n * n
+    U = pin.haar_unitary(m, 1530)
+    t = pin.single_photon_input(m, n)
+    outs = pin.random_outputs(m, n, 1, 1630)
+    a_ref = oracle.amplitudes(U, t, outs)
+    amp, _ = run_amps(pcv, U, t, outs, algo=pcv.PCV_ALGO_BLOCK, param=64)
+    assert amp_err(amp, a_ref, m, n) <= tol(n)

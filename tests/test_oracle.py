@@ -12,6 +12,7 @@ import os
 import numpy as np
 import pytest
 
+import golden_io
 import oracle
 import pcv_inputs as pin
 
@@ -153,17 +154,8 @@ def test_photon_number_mismatch_gives_zero():
     assert oracle.amplitude(U, [1, 1, 0, 0], [1, 0, 0, 0]) == 0
 
 
-def _parse_cnot():
-    rows = []
-    for line in open(os.path.join(GOLD, "cnot_unitary.txt")):
-        if line.startswith("#") or not line.strip():
-            continue
-        rows.append([complex(eval(e.strip(), {"sqrt": math.sqrt, "j": 1j})) for e in line.split("|")])
-    return np.array(rows)
-
-
 def test_cnot_truth_table_and_performance():
-    U = _parse_cnot()
+    U = golden_io.cnot_unitary()
     assert np.abs(U.conj().T @ U - np.eye(6)).max() < 1e-15
     logical = {"00": [0, 1, 0, 1, 0, 0], "01": [0, 1, 0, 0, 1, 0],
                "10": [0, 0, 1, 1, 0, 0], "11": [0, 0, 1, 0, 1, 0]}
