@@ -91,6 +91,7 @@ enum {
     PCV_ALGO_GROUP = 1,   /* plain Glynn, G threads per permanent (G = 1..32), n <= 16  */
     PCV_ALGO_BLOCK = 2,   /* plain Glynn, one block (x splits) per permanent, n <= 30   */
     PCV_ALGO_FACTOR = 3,  /* factorised Glynn sum over the whole output space           */
+    PCV_ALGO_TILE = 4,    /* shared row sums, one block per tile of outputs, m <= 128   */
 };
 
 /* Workspace bytes pcv_amplitudes needs for these sizes (0 if none). */
@@ -115,12 +116,43 @@ int pcv_amplitudes(const pcv_c64* U, int m, const uint8_t* input_occ,
                    void* workspace, int64_t workspace_bytes, void* stream);
 
 /* pcv_amplitudes with an explicit algorithm: algo = PCV_ALGO_GROUP with
- * `param` threads per permanent (1, 2, 4, 8, 16 or 32), or PCV_ALGO_BLOCK
- * with `param` blocks per permanent (>= 1); PCV_ALGO_AUTO ignores param. */
+ * `param` threads per permanent (1, 2, 4, 8, 16 or 32), PCV_ALGO_BLOCK with
+ * `param` blocks per permanent (>= 1), or PCV_ALGO_TILE (m <= 128; the row
+ * sums y_r(d) = sum_j d_j U[r][c_j] of each sign vector are formed once per
+ * block and shared by its 32..256 outputs); PCV_ALGO_AUTO ignores param. */
 int pcv_amplitudes_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                       const uint8_t* output_occ, int64_t n_out,
                       pcv_c64* amp, double* prob, int algo, int param,
                       void* workspace, int64_t workspace_bytes, void* stream);
+
+/* One circuit of a batched call.  All pointers are device pointers; the
+ * descriptor array itself lives in device memory and is only read. */
+typedef struct {
+    const pcv_c64* U;        /* m*m, row = output mode                               */
+    const uint8_t* outputs;  /* n_out*m output occupations                           */
+    pcv_c64* amp;            /* n_out amplitudes (written), or NULL                  */
+    double* prob;            /* n_out probabilities (written), or NULL               */
+    int64_t n_out;           /* >= 0                                                 */
+    int32_t m;               /* 1..128                                               */
+    int32_t n;               /* 1..PCV_MAX_PHOTONS photons                           */
+    int32_t cols[PCV_MAX_PHOTONS];  /* photon -> input mode, non-decreasing, < m    */
+} pcv_batch_desc;
+
+/* Workspace bytes of pcv_amplitudes_batched for n_circ circuits holding
+ * total_outputs outputs in all. */
+int64_t pcv_amplitudes_batched_workspace(int n_circ, int64_t total_outputs);
+
+/* Amplitudes of many circuits of uneven size in one persistent launch
+ * (Eq. eqperm per circuit).  A planning kernel sorts the circuits by photon
+ * number (largest first) and expands them into work items (circuit, tile of
+ * 32..256 outputs); one block per SM slot then pulls items from a device
+ * counter until the queue is empty.  No block waits on another.
+ *   descs          device, n_circ descriptors (see pcv_batch_desc)
+ *   total_outputs  sum of n_out over the circuits (sizes the work queue)
+ * A descriptor with n or m out of range, or input modes outside [0, m) or
+ * out of order, is skipped (its outputs are not written). */
+int pcv_amplitudes_batched(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs,
+                           void* workspace, int64_t workspace_bytes, void* stream);
 
 /* Workspace bytes pcv_distribution needs for m modes and n photons with the
  * default plan.  A smaller workspace (>= pcv_distribution_workspace_min) is

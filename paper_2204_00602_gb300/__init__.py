@@ -15,10 +15,11 @@ import torch
 
 from . import _abi as abi
 from ._abi import (PCV_ALGO_AUTO, PCV_ALGO_BLOCK, PCV_ALGO_FACTOR, PCV_ALGO_GROUP,  # noqa: F401
-                   PCV_MAX_MODES, PCV_MAX_PHOTONS, PcvError)
+                   PCV_ALGO_TILE, PCV_MAX_MODES, PCV_MAX_PHOTONS, PcvError)
 
-__all__ = ["amplitudes", "distribution", "num_outputs", "unrank", "rank", "fp64_probe", "PcvError",
-           "PCV_ALGO_AUTO", "PCV_ALGO_GROUP", "PCV_ALGO_BLOCK", "PCV_ALGO_FACTOR", "abi"]
+__all__ = ["amplitudes", "amplitudes_batched", "BatchPlan", "distribution", "num_outputs", "unrank", "rank",
+           "fp64_probe", "PcvError", "PCV_ALGO_AUTO", "PCV_ALGO_GROUP", "PCV_ALGO_BLOCK", "PCV_ALGO_FACTOR",
+           "PCV_ALGO_TILE", "abi"]
 
 
 def _stream(device) -> int:
@@ -87,6 +88,62 @@ def amplitudes(U: torch.Tensor, input_occ, outputs: torch.Tensor, *, algo: int =
     abi.pcv_amplitudes_ex(U, m, t, outputs, n_out, amp, prob, algo, param, ws,
                           0 if ws is None else ws.numel(), _stream(U.device))
     return amp, prob
+
+
+class BatchPlan:
+    """Device-resident descriptors, outputs and workspace of one batched call.
+
+    circuits: list of (U complex128 [m, m] CUDA, input_occ (host), outputs uint8 [n_out, m] CUDA).
+    Keeps references to every tensor the descriptors point at.
+    """
+
+    def __init__(self, circuits, want_prob: bool = True):
+        if not circuits:
+            raise ValueError("empty batch")
+        dev = circuits[0][0].device
+        arr = (abi.pcv_batch_desc * len(circuits))()
+        self.keep, self.amps, self.probs = [], [], []
+        total = 0
+        for i, (U, t, outs) in enumerate(circuits):
+            m = _check_U(U)
+            if m > 128:
+                raise ValueError("batched circuits support m <= 128")
+            t = _host_occ(t, m)
+            n = int(t.sum())
+            if not 1 <= n <= PCV_MAX_PHOTONS:
+                raise ValueError(f"circuit {i}: n={n} outside [1, {PCV_MAX_PHOTONS}]")
+            if not (outs.is_cuda and outs.dtype == torch.uint8 and outs.dim() == 2 and outs.shape[1] == m):
+                raise TypeError(f"circuit {i}: outputs must be uint8 CUDA [n_out, {m}]")
+            U, outs = U.contiguous(), outs.contiguous()
+            amp = torch.empty(outs.shape[0], dtype=torch.complex128, device=dev)
+            prob = torch.empty(outs.shape[0], dtype=torch.float64, device=dev) if want_prob else None
+            d = arr[i]
+            d.U, d.outputs, d.amp = U.data_ptr(), outs.data_ptr(), amp.data_ptr()
+            d.prob = prob.data_ptr() if prob is not None else None
+            d.n_out, d.m, d.n = outs.shape[0], m, n
+            cols = np.repeat(np.arange(m), t)
+            for j, c in enumerate(cols):
+                d.cols[j] = int(c)
+            self.keep += [U, outs]
+            self.amps.append(amp)
+            self.probs.append(prob)
+            total += outs.shape[0]
+        raw = np.frombuffer(bytes(arr), dtype=np.uint8)
+        self.descs = torch.from_numpy(raw.copy()).to(dev)
+        self.n_circ, self.total = len(circuits), total
+        self.ws = workspace(abi.pcv_amplitudes_batched_workspace(self.n_circ, total), dev)
+        self.device = dev
+
+    def run(self):
+        abi.pcv_amplitudes_batched(self.descs, self.n_circ, self.total, self.ws,
+                                   0 if self.ws is None else self.ws.numel(), _stream(self.device))
+        return self.amps, self.probs
+
+
+def amplitudes_batched(circuits, want_prob: bool = True):
+    """Amplitudes of many circuits of uneven size in one persistent launch.
+    Returns (list of amp tensors, list of prob tensors or None)."""
+    return BatchPlan(circuits, want_prob).run()
 
 
 def distribution_workspace_bytes(m: int, n: int, algo: int = PCV_ALGO_AUTO, param: int = 0) -> int:

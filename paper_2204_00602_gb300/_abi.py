@@ -29,6 +29,7 @@ PCV_ALGO_AUTO = 0
 PCV_ALGO_GROUP = 1
 PCV_ALGO_BLOCK = 2
 PCV_ALGO_FACTOR = 3
+PCV_ALGO_TILE = 4
 PCV_MAX_PHOTONS = 30
 PCV_MAX_MODES = 1024
 
@@ -51,6 +52,8 @@ SIGNATURES = {
     "pcv_distribution": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
     "pcv_distribution_ex": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _vp, _i64, _vp]),
     "pcv_fp64_probe": (_i, [_vp, _i, _i, _i, _vp]),
+    "pcv_amplitudes_batched_workspace": (_i64, [_i, _i64]),
+    "pcv_amplitudes_batched": (_i, [_vp, _i, _i64, _vp, _i64, _vp]),
     "pcv_profile_enable": (_i, [_i]),
     "pcv_profile_read": (_i, [_vp, _vp, _i]),
     "pcv_launch_count": (_i64, []),
@@ -142,6 +145,20 @@ def pcv_distribution(U, m, input_occ, prob, amp, workspace, workspace_bytes, str
 def pcv_distribution_ex(U, m, input_occ, prob, amp, algo, param, workspace, workspace_bytes, stream):
     return _call("pcv_distribution_ex", ptr(U), m, ptr(input_occ), ptr(prob), ptr(amp), algo, param,
                  ptr(workspace), workspace_bytes, stream)
+
+
+class pcv_batch_desc(ctypes.Structure):
+    """Mirror of the C struct pcv_batch_desc (include/pcv.h)."""
+    _fields_ = [("U", _vp), ("outputs", _vp), ("amp", _vp), ("prob", _vp), ("n_out", _i64),
+                ("m", ctypes.c_int32), ("n", ctypes.c_int32), ("cols", ctypes.c_int32 * PCV_MAX_PHOTONS)]
+
+
+def pcv_amplitudes_batched_workspace(n_circ, total_outputs) -> int:
+    return _call("pcv_amplitudes_batched_workspace", n_circ, total_outputs)
+
+
+def pcv_amplitudes_batched(descs, n_circ, total_outputs, workspace, workspace_bytes, stream):
+    return _call("pcv_amplitudes_batched", ptr(descs), n_circ, total_outputs, ptr(workspace), workspace_bytes, stream)
 
 
 def pcv_fp64_probe(out, blocks, threads, iters, stream):

@@ -1,0 +1,336 @@
+// Shared-row-sum Glynn kernels for explicit outputs: one block computes a tile
+// of outputs of one (U, input) pair, and a persistent variant pulls tiles of
+// many circuits of uneven size from a device work queue.
+//
+// With Glynn's sign vector d on the input photons (columns of U_{T,S}, Eq.
+// eqperm), the row sum of output row i depends only on its output mode:
+// y_r(d) = sum_j d_j U[r][c_j].  A block therefore keeps y_r(d) for all m modes
+// in shared memory, advancing it one Gray step at a time (2 DFMA per mode and
+// step, shared by the whole tile), and each output only forms its product
+//     a(S) += sigma(d) prod_i y_{r_i}(d):  4(n-1) + 2 FP64 instructions per
+// output and sign vector instead of the 6n - 2 of the plain per-output kernel.
+//
+// Block layout: TILE = 256 / S outputs x S contiguous ranges of sign vectors
+// ("splits"); split s owns sign vectors [s L, (s+1) L), L = 2^{n-1} / S, and
+// walks them in chunks of C steps whose row sums are staged in shared memory.
+// The S partial sums of an output are added in a fixed order at the end, so
+// results are deterministic.
+
+#include "pcv_common.cuh"
+
+namespace pcv {
+
+// Splits per block as a function of n: more sign-vector parallelism for
+// larger permanents, whole tiles of 256 outputs for small ones.
+__host__ __device__ inline int tile_splits(int n)
+{
+    if (n <= 10) return 1;
+    if (n <= 13) return 2;
+    if (n <= 16) return 4;
+    return 8;
+}
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChunk = 4;            // Gray steps staged per split and pass
+constexpr int kMaxModes = 128;       // modes kept in shared memory
+
+struct TileShared {
+    double2 y[8 * kChunk * kMaxModes];   // [split][step][mode] staged row sums
+    double2 yrun[8 * kMaxModes];         // [split][mode] running row sums
+    double2 acc[kThreads];
+    uint8_t rows[kThreads * PCV_MAX_PHOTONS];
+    int cols[PCV_MAX_PHOTONS];
+};
+
+// One tile (outputs [out0, out0 + TILE)) of circuit c.
+__device__ void tile_item(const pcv_batch_desc& c, int64_t tile, TileShared& sh)
+{
+    const int n = c.n, m = c.m;
+    const int S = tile_splits(n);
+    const int TILE = kThreads / S;
+    const int tid = threadIdx.x;
+    const int ol = tid % TILE, s = tid / TILE;
+    const int64_t o = tile * TILE + ol;
+    const bool live = o < c.n_out;
+
+    if (tid < n) sh.cols[tid] = c.cols[tid];
+    double norm_t = 1.0;                  // 1/sqrt(prod t!) from the sorted photon -> input-mode list
+    {
+        double f = 1.0;
+        int run = 1;
+        for (int j = 1; j < n; ++j) {
+            run = (c.cols[j] == c.cols[j - 1]) ? run + 1 : 1;
+            f *= run;
+        }
+        norm_t = 1.0 / sqrt(f);
+    }
+    // decode the output: rows (output modes, non-decreasing) and 1/sqrt(prod s!)
+    bool ok = live;
+    double norm = 1.0;
+    if (live && s == 0) {
+        const uint8_t* occ = c.outputs + o * m;
+        int cnt = 0;
+        double f = 1.0;
+        for (int r = 0; r < m; ++r) {
+            const int k = occ[r];
+            for (int q = 1; q <= k; ++q) {
+                if (cnt < PCV_MAX_PHOTONS) sh.rows[tid * PCV_MAX_PHOTONS + cnt] = (uint8_t)r;
+                ++cnt;
+                f *= q;
+            }
+        }
+        ok = cnt == n;
+        norm = 1.0 / sqrt(f);
+    }
+    __syncthreads();
+    // every split of this output reads the rows decoded by split 0
+    const uint8_t* myrows = sh.rows + ol * PCV_MAX_PHOTONS;
+    if (live && s != 0) {
+        int cnt = 0;
+        const uint8_t* occ = c.outputs + o * m;
+        for (int r = 0; r < m; ++r) cnt += occ[r];
+        ok = cnt == n;
+    }
+
+    const int64_t L = (1ll << (n - 1)) / S;
+    const int C = L < kChunk ? (int)L : kChunk;
+    // running row sums of every split at its first sign vector
+    for (int q = tid; q < S * m; q += kThreads) {
+        const int ss = q / m, r = q % m;
+        const int64_t k0 = (int64_t)ss * L;
+        const uint64_t g = (uint64_t)k0 ^ ((uint64_t)k0 >> 1);
+        const double2* Ur = (const double2*)c.U + (size_t)r * m;
+        double2 y = Ur[sh.cols[0]];
+        for (int j = 1; j < n; ++j) caxpy(y, ((g >> (j - 1)) & 1u) ? -1.0 : 1.0, Ur[sh.cols[j]]);
+        sh.yrun[ss * kMaxModes + r] = y;
+    }
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t base = 0; base < L; base += C) {
+        __syncthreads();
+        // stage C steps of row sums for every split; advance the running sums
+        for (int q = tid; q < S * m; q += kThreads) {
+            const int ss = q / m, r = q % m;
+            double2 y = sh.yrun[ss * kMaxModes + r];
+            const double2* Ur = (const double2*)c.U + (size_t)r * m;
+            for (int st = 0; st < C; ++st) {
+                sh.y[(ss * kChunk + st) * kMaxModes + r] = y;
+                const int64_t kk = (int64_t)ss * L + base + st + 1;
+                if (base + st + 1 < L) {
+                    const int b = __ffsll(kk) - 1;
+                    const double sd = ((kk >> (b + 1)) & 1) ? 2.0 : -2.0;
+                    caxpy(y, sd, Ur[sh.cols[b + 1]]);
+                }
+            }
+            sh.yrun[ss * kMaxModes + r] = y;
+        }
+        __syncthreads();
+        if (ok) {
+            for (int st = 0; st < C; ++st) {
+                const int64_t k = (int64_t)s * L + base + st;
+                const uint64_t g = (uint64_t)k ^ ((uint64_t)k >> 1);
+                const double sg = (__popcll(g) & 1) ? -1.0 : 1.0;
+                const double2* ys = sh.y + (s * kChunk + st) * kMaxModes;
+                double2 p = ys[myrows[0]];
+                for (int i = 1; i < n; ++i) p = cmul(p, ys[myrows[i]]);
+                caxpy(acc, sg, p);
+            }
+        }
+    }
+    sh.acc[tid] = acc;
+    __syncthreads();
+    if (s == 0 && live) {
+        double2 t = acc;
+        for (int ss = 1; ss < S; ++ss) t = cadd(t, sh.acc[ss * TILE + ol]);
+        double2 v = make_double2(0.0, 0.0);
+        if (ok) {
+            const double sc = ldexp(norm * norm_t, -(n - 1));
+            v = make_double2(t.x * sc, t.y * sc);
+        }
+        if (c.amp) ((double2*)c.amp)[o] = v;
+        if (c.prob) c.prob[o] = fma(v.x, v.x, v.y * v.y);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) glynn_tile_kernel(const pcv_batch_desc c)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    TileShared& sh = *reinterpret_cast<TileShared*>(smem);
+    tile_item(c, blockIdx.x, sh);
+}
+
+// Work queue of the batched launch: items (circuit, tile) in order of
+// decreasing photon number; blocks pull the next item with one atomicAdd and
+// never wait for another block.
+struct Queue {
+    int* counter;
+    int* total;
+    int* item_circ;
+    int* item_tile;
+};
+
+__global__ void __launch_bounds__(kThreads) glynn_persistent_kernel(const pcv_batch_desc* descs, Queue q)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    TileShared& sh = *reinterpret_cast<TileShared*>(smem);
+    __shared__ int s_item;
+    const int total = *q.total;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(q.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= total) break;
+        tile_item(descs[q.item_circ[it]], q.item_tile[it], sh);
+    }
+}
+
+// Builds the work queue on the device (one block): per-circuit photon number
+// and norm, a counting sort by n (descending), and the expanded item list.
+// A descriptor the kernels cannot run (n or m out of range, an input mode
+// outside [0, m) or out of order) gets no work items; the binding checks
+// descriptors before they reach the device.
+__device__ bool desc_ok(const pcv_batch_desc& d)
+{
+    if (d.n < 1 || d.n > PCV_MAX_PHOTONS || d.m < 1 || d.m > kMaxModes || d.n_out < 0) return false;
+    for (int j = 0; j < d.n; ++j)
+        if (d.cols[j] < 0 || d.cols[j] >= d.m || (j > 0 && d.cols[j] < d.cols[j - 1])) return false;
+    return true;
+}
+
+__device__ int desc_items(const pcv_batch_desc& d)
+{
+    if (!desc_ok(d) || d.n_out == 0) return 0;
+    const int tilesz = kThreads / tile_splits(d.n);
+    return (int)((d.n_out + tilesz - 1) / tilesz);
+}
+
+__global__ void __launch_bounds__(1024) plan_kernel(const pcv_batch_desc* descs, int n_circ, Queue q, int* order,
+                                                    int* item_off, int max_items)
+{
+    __shared__ int bucket[PCV_MAX_PHOTONS + 2];
+    __shared__ int cursor[PCV_MAX_PHOTONS + 2];
+    __shared__ int carry;
+    const int tid = threadIdx.x;
+    if (tid < PCV_MAX_PHOTONS + 2) bucket[tid] = 0;
+    __syncthreads();
+    for (int c = tid; c < n_circ; c += blockDim.x)
+        atomicAdd(&bucket[desc_ok(descs[c]) ? descs[c].n : 0], 1);
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int n = PCV_MAX_PHOTONS; n >= 0; --n) { cursor[n] = acc; acc += bucket[n]; }
+        carry = 0;
+    }
+    __syncthreads();
+    for (int c = tid; c < n_circ; c += blockDim.x)
+        order[atomicAdd(&cursor[desc_ok(descs[c]) ? descs[c].n : 0], 1)] = c;
+    __syncthreads();
+    // exclusive scan of item counts over the sorted order, 1024 circuits at a time
+    __shared__ int scan[1024];
+    for (int b0 = 0; b0 < n_circ; b0 += 1024) {
+        const int p = b0 + tid;
+        const int cnt = p < n_circ ? desc_items(descs[order[p]]) : 0;
+        scan[tid] = cnt;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int v = tid >= off ? scan[tid - off] : 0;
+            __syncthreads();
+            scan[tid] += v;
+            __syncthreads();
+        }
+        if (p < n_circ) item_off[p] = carry + scan[tid] - cnt;
+        __syncthreads();
+        if (tid == 1023) carry += scan[1023];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        *q.total = carry < max_items ? carry : max_items;
+        *q.counter = 0;
+    }
+    __syncthreads();
+    for (int p = 0; p < n_circ; ++p) {
+        const int c = order[p];
+        const int cnt = desc_items(descs[c]);
+        for (int t = tid; t < cnt; t += blockDim.x) {
+            const int it = item_off[p] + t;
+            if (it < max_items) {
+                q.item_circ[it] = c;
+                q.item_tile[it] = t;
+            }
+        }
+    }
+}
+
+uint64_t g_attr_set = 0;     // bit d: attributes set on device d
+
+cudaError_t ensure_smem_attr()
+{
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (g_attr_set & bit) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(glynn_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileShared));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(glynn_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileShared));
+    if (e != cudaSuccess) return e;
+    g_attr_set |= bit;
+    return cudaSuccess;
+}
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+int tile_max_modes() { return kMaxModes; }
+
+cudaError_t launch_glynn_tile(const pcv_batch_desc& d, cudaStream_t s)
+{
+    if (d.n_out == 0) return cudaSuccess;
+    cudaError_t e = ensure_smem_attr();
+    if (e != cudaSuccess) return e;
+    const int tilesz = kThreads / tile_splits(d.n);
+    const int64_t tiles = (d.n_out + tilesz - 1) / tilesz;
+    glynn_tile_kernel<<<(unsigned)tiles, kThreads, sizeof(TileShared), s>>>(d);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+int64_t batched_workspace(int n_circ, int64_t total_outputs)
+{
+    const int64_t max_items = total_outputs / 32 + n_circ + 1;
+    return (int64_t)(al256(2 * sizeof(int)) + 3 * al256((size_t)n_circ * sizeof(int)) +
+                     2 * al256((size_t)max_items * sizeof(int)));
+}
+
+cudaError_t launch_glynn_batched(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs, void* ws,
+                                 int sms, cudaStream_t s)
+{
+    cudaError_t e = ensure_smem_attr();
+    if (e != cudaSuccess) return e;
+    const int64_t max_items = total_outputs / 32 + n_circ + 1;
+    char* w = (char*)ws;
+    Queue q;
+    q.counter = (int*)w;
+    q.total = q.counter + 1;                          w += al256(2 * sizeof(int));
+    int* order = (int*)w;                             w += al256((size_t)n_circ * sizeof(int));
+    int* item_off = (int*)w;                          w += al256((size_t)n_circ * sizeof(int));
+    w += al256((size_t)n_circ * sizeof(int));
+    q.item_circ = (int*)w;                            w += al256((size_t)max_items * sizeof(int));
+    q.item_tile = (int*)w;
+    plan_kernel<<<1, 1024, 0, s>>>(descs, n_circ, q, order, item_off, (int)max_items);
+    note_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, glynn_persistent_kernel, kThreads, sizeof(TileShared));
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    glynn_persistent_kernel<<<sms * per_sm, kThreads, sizeof(TileShared), s>>>(descs, q);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace pcv

@@ -105,6 +105,10 @@ AmpChoice choose_amp(int n, int64_t n_out, int algo, int param)
 
 int check_choice(const AmpChoice& c, int n)
 {
+    if (c.algo == PCV_ALGO_TILE) {
+        if (n < 1) return fail(PCV_EINVAL, "tile kernel needs n >= 1");
+        return PCV_OK;
+    }
     if (c.algo == PCV_ALGO_GROUP) {
         if (n > 16) return fail(PCV_EINVAL, "group kernel supports n <= 16 (n=%d)", n);
         const int G = c.param;
@@ -298,6 +302,22 @@ int pcv_amplitudes_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
     if (need > 0 && !aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
     if ((int64_t)n_out * (c.algo == PCV_ALGO_BLOCK ? c.param : 1) > INT32_MAX)
         return fail(PCV_ERANGE, "too many permanents for one launch");
+    if (c.algo == PCV_ALGO_TILE) {
+        if (m > pcv::tile_max_modes()) return fail(PCV_EINVAL, "tile kernel supports m <= %d (m=%d)", pcv::tile_max_modes(), m);
+        pcv_batch_desc d;
+        d.U = U;
+        d.outputs = output_occ;
+        d.amp = amp;
+        d.prob = prob;
+        d.n_out = n_out;
+        d.m = m;
+        d.n = p.n;
+        for (int j = 0; j < PCV_MAX_PHOTONS; ++j) d.cols[j] = p.cols[j];
+        pcv::stage_begin(pcv::kStagePlain, s);
+        cudaError_t e = pcv::launch_glynn_tile(d, s);
+        pcv::stage_end(pcv::kStagePlain, s);
+        return e == cudaSuccess ? PCV_OK : cuda_fail(e, "tile launch");
+    }
     cudaError_t e;
     pcv::stage_begin(pcv::kStagePlain, s);
     if (c.algo == PCV_ALGO_GROUP)
@@ -316,6 +336,34 @@ int pcv_amplitudes(const pcv_c64* U, int m, const uint8_t* input_occ,
 {
     return pcv_amplitudes_ex(U, m, input_occ, output_occ, n_out, amp, prob, PCV_ALGO_AUTO, 0,
                              workspace, workspace_bytes, stream);
+}
+
+int64_t pcv_amplitudes_batched_workspace(int n_circ, int64_t total_outputs)
+{
+    if (n_circ < 0 || total_outputs < 0) return fail(PCV_EINVAL, "bad sizes");
+    return pcv::batched_workspace(n_circ, total_outputs);
+}
+
+int pcv_amplitudes_batched(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs,
+                           void* workspace, int64_t workspace_bytes, void* stream)
+{
+    if (n_circ < 0 || total_outputs < 0) return fail(PCV_EINVAL, "n_circ=%d total_outputs=%lld", n_circ, (long long)total_outputs);
+    if (n_circ == 0) return PCV_OK;
+    if (!descs) return fail(PCV_EINVAL, "descs is NULL");
+    if ((total_outputs / 32 + n_circ + 1) > INT32_MAX) return fail(PCV_ERANGE, "too many outputs for one launch");
+    const int64_t need = pcv::batched_workspace(n_circ, total_outputs);
+    if (!workspace || workspace_bytes < need)
+        return fail(PCV_ENOMEM, "workspace of %lld bytes needed, %lld given", (long long)need, (long long)workspace_bytes);
+    if (!aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    cudaStream_t s = (cudaStream_t)stream;
+    pcv::stage_begin(pcv::kStagePlain, s);
+    e = pcv::launch_glynn_batched(descs, n_circ, total_outputs, workspace, sms, s);
+    pcv::stage_end(pcv::kStagePlain, s);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "batched launch");
 }
 
 static int64_t dist_ws(int m, int n, int algo, int param, bool need_acc, int64_t ws_bytes, pcv::DistPlan* dp)

@@ -114,6 +114,14 @@ cudaError_t launch_glynn_block(const Plan& p, const double2* U, const uint8_t* o
                                cudaStream_t s);
 int glynn_block_threads();
 
+// Shared-row-sum tile kernels (glynn_tile.cu)
+__host__ __device__ int tile_splits(int n);
+int tile_max_modes();
+cudaError_t launch_glynn_tile(const pcv_batch_desc& d, cudaStream_t s);
+int64_t batched_workspace(int n_circ, int64_t total_outputs);
+cudaError_t launch_glynn_batched(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs, void* ws,
+                                 int sms, cudaStream_t s);
+
 // Factorised full distribution (glynn_dist.cu)
 struct DistPlan {
     int h;                    // modes [0,h) are the low side, [h,m) the high side
