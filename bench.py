@@ -251,9 +251,9 @@ def run_ours(args):
     peak_tflops = sms * 4 * sm_max * 1e6 / 1e12        # 2 DFMA/clk/SM x 2 flop
     if args.algo == "factor":
         ms, calls = stages["dist_products"]
-        flops_per_call = Ntot * (2 ** (N_PH - 1)) * 8     # one complex MAC per output and sign vector
-        kname = "gemm_kernel (factorised Glynn products)"
-        launches_per_call = N_PH + 1
+        flops_per_call = Ntot * (2 ** (N_PH - 1)) * 6     # 3 DFMA per output and sign vector
+        kname = "gemm_kernel (factorised Glynn products, 3 DFMA per output and sign vector)"
+        launches_per_call = 1
     else:
         ms, calls = stages["glynn_plain"]
         flops_per_call = Ntot * (2 ** (N_PH - 1)) * (8 * N_PH - 4)

@@ -173,12 +173,76 @@ int pcv_distribution(const pcv_c64* U, int m, const uint8_t* input_occ,
                      double* prob, pcv_c64* amp,
                      void* workspace, int64_t workspace_bytes, void* stream);
 
+/* Full distributions of B unitaries with the same input state (the
+ * factorised algorithm of pcv_distribution, all B in the same launches).
+ *   U     device, B*m*m pcv_c64 (entry b at U + b*m*m)
+ *   B     1..65535
+ *   prob  device, B*C(m+n-1,n) doubles or NULL; amp likewise pcv_c64 or NULL
+ *         (entry b's outputs start at b*C(m+n-1,n)). */
+int64_t pcv_distribution_batched_workspace(int B, int m, int n);
+int pcv_distribution_batched(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
+                             double* prob, pcv_c64* amp,
+                             void* workspace, int64_t workspace_bytes, void* stream);
+
 /* pcv_distribution with an explicit algorithm: PCV_ALGO_FACTOR (param
  * ignored), PCV_ALGO_GROUP (param = threads per permanent; unranks each
  * output), PCV_ALGO_BLOCK (param = blocks per permanent). */
 int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                         double* prob, pcv_c64* amp, int algo, int param,
                         void* workspace, int64_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------ gradients */
+
+/* dL/dU from dL/da for explicit outputs of one U (n <= 8).
+ *   grad_amp  device, n_out pcv_c64: dL/dRe a + i dL/dIm a per output
+ *   grad_U    device, m*m pcv_c64 (overwritten): dL/dRe U + i dL/dIm U
+ * a(S) is holomorphic in U, so grad_U = sum_S grad_amp_S * conj(da_S/dU), and
+ * da_S/dU[k][l] = norm_S * sum over (i, j) with r_i = k, c_j = l of the
+ * permanent of the minor of (i, j) (the Laplace expansion of Eq. eqperm's
+ * permanent), each minor computed as a Glynn sum over the forward kernel's
+ * Gray-code row sums.  The order in which per-output contributions are added
+ * is not fixed (FP64 atomics), so repeated calls may differ in the last bits. */
+int pcv_amplitudes_backward(const pcv_c64* U, int m, const uint8_t* input_occ,
+                            const uint8_t* output_occ, int64_t n_out, const pcv_c64* grad_amp,
+                            pcv_c64* grad_U, void* stream);
+
+/* The same for every output of the distributions of B unitaries (grad_amp
+ * [B][C(m+n-1,n)] in canonical order, grad_U [B][m][m]); the workspace holds
+ * the multiset-count table used to unrank outputs. */
+int64_t pcv_distribution_backward_workspace(int m, int n);
+int pcv_distribution_backward(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
+                              const pcv_c64* grad_amp, pcv_c64* grad_U,
+                              void* workspace, int64_t workspace_bytes, void* stream);
+
+/* Clements rectangular MZI mesh (Sec. 2 cites the square decomposition;
+ * components of Eq. bs and Table 1): m columns, column c holds MZIs on modes
+ * (k, k+1), k = c mod 2, c mod 2 + 2, ...; MZI q uses phases[2q] (phase
+ * shifter inside, on the upper mode) and phases[2q+1] (phase shifter after,
+ * on the lower mode): MZI = diag(1, e^{i phi_b}) BS diag(e^{i phi_a}, 1) BS,
+ * BS = (1/sqrt2)[[1, i], [i, 1]]; later MZIs multiply on the left.
+ *   phases  device, B * m(m-1) doubles;  U device, B*m*m pcv_c64;  2 <= m <= 64.
+ * pcv_mesh_backward takes U = pcv_mesh_unitary's output and grad_U = dL/dU
+ * (dL/dRe + i dL/dIm) and writes dL/dphases [B][m(m-1)]. */
+int pcv_mesh_unitary(const double* phases, int B, int m, pcv_c64* U, void* stream);
+int pcv_mesh_backward(const double* phases, int B, int m, const pcv_c64* U, const pcv_c64* grad_U,
+                      double* grad_phases, void* stream);
+
+/* Per distribution b of B (p [B][N], q [N] or [B][N] when q_batched):
+ * out[3b] = sum_S p(S), out[3b+1] = TVD(p, q) = 1/2 sum |p - q| (Eq.
+ * bosonsampling), out[3b+2] = KL(q || p) = sum_{q>0} q log(q/p); q may be NULL
+ * (sum only).  Deterministic (fixed reduction order). */
+int64_t pcv_dist_stats_workspace(int B);
+int pcv_dist_stats(const double* p, const double* q, int64_t N, int B, int q_batched, double* out,
+                   void* workspace, int64_t workspace_bytes, void* stream);
+
+/* Gradient of L = sum_b scale * w_b * KL(q || p_b) with respect to the
+ * amplitudes: grad_amp = 2 a dL/dp, dL/dp = -scale w_b q / p (0 where q = 0);
+ * batch_scale = w (device, B doubles) or NULL for w_b = 1. */
+int pcv_kl_grad(const double* p, const double* q, const pcv_c64* amp, int64_t N, int B, int q_batched,
+                const double* batch_scale, double scale, pcv_c64* grad_amp, void* stream);
+
+/* grad_amp = 2 a grad_prob for p = |a|^2 (count elements). */
+int pcv_prob_grad_to_amp(const double* grad_prob, const pcv_c64* amp, int64_t count, pcv_c64* grad_amp, void* stream);
 
 /* -------------------------------------------------- measurement helpers */
 

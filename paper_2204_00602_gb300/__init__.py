@@ -17,7 +17,7 @@ from . import _abi as abi
 from ._abi import (PCV_ALGO_AUTO, PCV_ALGO_BLOCK, PCV_ALGO_FACTOR, PCV_ALGO_GROUP,  # noqa: F401
                    PCV_ALGO_TILE, PCV_MAX_MODES, PCV_MAX_PHOTONS, PcvError)
 
-__all__ = ["amplitudes", "amplitudes_batched", "BatchPlan", "distribution", "num_outputs", "unrank", "rank",
+__all__ = ["amplitudes", "amplitudes_batched", "BatchPlan", "distribution", "distribution_batched", "num_outputs", "unrank", "rank",
            "fp64_probe", "PcvError", "PCV_ALGO_AUTO", "PCV_ALGO_GROUP", "PCV_ALGO_BLOCK", "PCV_ALGO_FACTOR",
            "PCV_ALGO_TILE", "abi"]
 
@@ -176,6 +176,28 @@ def distribution(U: torch.Tensor, input_occ, *, want_amp: bool = True, algo: int
         ws = workspace(distribution_workspace_bytes(m, n, algo, param), U.device)
     abi.pcv_distribution_ex(U, m, t, prob, amp, algo, param, ws, 0 if ws is None else ws.numel(),
                             _stream(U.device))
+    return prob, amp
+
+
+def distribution_batched(U: torch.Tensor, input_occ, *, want_amp: bool = True, ws: torch.Tensor | None = None,
+                         out=None):
+    """Full distributions of a batch of unitaries U [B, m, m] with one input.
+    Returns (prob [B, N], amp [B, N] or None)."""
+    if not (U.is_cuda and U.dtype == torch.complex128 and U.dim() == 3 and U.shape[1] == U.shape[2]):
+        raise TypeError("U must be a complex128 CUDA tensor [B, m, m]")
+    B, m = U.shape[0], U.shape[1]
+    t = _host_occ(input_occ, m)
+    n = int(t.sum())
+    N = num_outputs(m, n)
+    U = U.contiguous()
+    if out is not None:
+        prob, amp = out
+    else:
+        prob = torch.empty(B, N, dtype=torch.float64, device=U.device)
+        amp = torch.empty(B, N, dtype=torch.complex128, device=U.device) if want_amp else None
+    if ws is None:
+        ws = workspace(abi.pcv_distribution_batched_workspace(B, m, n), U.device)
+    abi.pcv_distribution_batched(U, B, m, t, prob, amp, ws, 0 if ws is None else ws.numel(), _stream(U.device))
     return prob, amp
 
 

@@ -51,6 +51,17 @@ SIGNATURES = {
     "pcv_distribution_workspace_min": (_i64, [_i, _i]),
     "pcv_distribution": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
     "pcv_distribution_ex": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _vp, _i64, _vp]),
+    "pcv_distribution_batched_workspace": (_i64, [_i, _i, _i]),
+    "pcv_distribution_batched": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "pcv_amplitudes_backward": (_i, [_vp, _i, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "pcv_distribution_backward_workspace": (_i64, [_i, _i]),
+    "pcv_distribution_backward": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "pcv_mesh_unitary": (_i, [_vp, _i, _i, _vp, _vp]),
+    "pcv_mesh_backward": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp]),
+    "pcv_dist_stats_workspace": (_i64, [_i]),
+    "pcv_dist_stats": (_i, [_vp, _vp, _i64, _i, _i, _vp, _vp, _i64, _vp]),
+    "pcv_kl_grad": (_i, [_vp, _vp, _vp, _i64, _i, _i, _vp, ctypes.c_double, _vp, _vp]),
+    "pcv_prob_grad_to_amp": (_i, [_vp, _vp, _i64, _vp, _vp]),
     "pcv_fp64_probe": (_i, [_vp, _i, _i, _i, _vp]),
     "pcv_amplitudes_batched_workspace": (_i64, [_i, _i64]),
     "pcv_amplitudes_batched": (_i, [_vp, _i, _i64, _vp, _i64, _vp]),
@@ -159,6 +170,54 @@ def pcv_amplitudes_batched_workspace(n_circ, total_outputs) -> int:
 
 def pcv_amplitudes_batched(descs, n_circ, total_outputs, workspace, workspace_bytes, stream):
     return _call("pcv_amplitudes_batched", ptr(descs), n_circ, total_outputs, ptr(workspace), workspace_bytes, stream)
+
+
+def pcv_distribution_batched_workspace(B, m, n) -> int:
+    return _call("pcv_distribution_batched_workspace", B, m, n)
+
+
+def pcv_distribution_batched(U, B, m, input_occ, prob, amp, workspace, workspace_bytes, stream):
+    return _call("pcv_distribution_batched", ptr(U), B, m, ptr(input_occ), ptr(prob), ptr(amp), ptr(workspace),
+                 workspace_bytes, stream)
+
+
+def pcv_amplitudes_backward(U, m, input_occ, output_occ, n_out, grad_amp, grad_U, stream):
+    return _call("pcv_amplitudes_backward", ptr(U), m, ptr(input_occ), ptr(output_occ), n_out, ptr(grad_amp),
+                 ptr(grad_U), stream)
+
+
+def pcv_distribution_backward_workspace(m, n) -> int:
+    return _call("pcv_distribution_backward_workspace", m, n)
+
+
+def pcv_distribution_backward(U, B, m, input_occ, grad_amp, grad_U, workspace, workspace_bytes, stream):
+    return _call("pcv_distribution_backward", ptr(U), B, m, ptr(input_occ), ptr(grad_amp), ptr(grad_U),
+                 ptr(workspace), workspace_bytes, stream)
+
+
+def pcv_mesh_unitary(phases, B, m, U, stream):
+    return _call("pcv_mesh_unitary", ptr(phases), B, m, ptr(U), stream)
+
+
+def pcv_mesh_backward(phases, B, m, U, grad_U, grad_phases, stream):
+    return _call("pcv_mesh_backward", ptr(phases), B, m, ptr(U), ptr(grad_U), ptr(grad_phases), stream)
+
+
+def pcv_dist_stats_workspace(B) -> int:
+    return _call("pcv_dist_stats_workspace", B)
+
+
+def pcv_dist_stats(p, q, N, B, q_batched, out, workspace, workspace_bytes, stream):
+    return _call("pcv_dist_stats", ptr(p), ptr(q), N, B, q_batched, ptr(out), ptr(workspace), workspace_bytes, stream)
+
+
+def pcv_kl_grad(p, q, amp, N, B, q_batched, batch_scale, scale, grad_amp, stream):
+    return _call("pcv_kl_grad", ptr(p), ptr(q), ptr(amp), N, B, q_batched, ptr(batch_scale), scale, ptr(grad_amp),
+                 stream)
+
+
+def pcv_prob_grad_to_amp(grad_prob, amp, count, grad_amp, stream):
+    return _call("pcv_prob_grad_to_amp", ptr(grad_prob), ptr(amp), count, ptr(grad_amp), stream)
 
 
 def pcv_fp64_probe(out, blocks, threads, iters, stream):

@@ -1,4 +1,5 @@
-// Full output distribution by a factorised Glynn sum.
+// Full output distribution by a factorised Glynn sum, for a batch of B
+// unitaries sharing one input state.
 //
 // Put Glynn's sign vector on the input photons (columns of U_{T,S}, Eq.
 // eqperm).  The row sum of output row i then depends only on the output mode
@@ -8,23 +9,28 @@
 // Split the modes at h: S = (P on modes [0,h), Q on modes [h,m)).  With
 //     alpha_P(d) = sigma(d) 2^{-(n-1)} norm_t prod_{r<h} y_r^{P_r}/sqrt(P_r!),
 //     beta_Q(d)  = prod_{r>=h} y_r^{Q_r}/sqrt(Q_r!),
-// every output is a(S) = sum_d alpha_P(d) beta_Q(d): for each k = |P| this is
-// a complex matrix product over the sign vectors, one complex multiply-add
-// (4 DFMA) per output and sign vector, instead of the 6n-2 FP64 instructions
-// of a Gray step of the plain per-output kernel.
+// every output is a(S) = sum_d alpha_P(d) beta_Q(d): for each k = |P| a
+// complex matrix product over the sign vectors.  The product uses three real
+// multiply-adds per output and sign vector (Gauss's three-multiplication
+// form, with alpha_re + alpha_im and beta_re + beta_im stored beside the
+// tables):
+//     t1 += a_re b_re,  t2 += a_im b_im,  t3 += (a_re + a_im)(b_re + b_im),
+//     Re a(S) = t1 - t2,  Im a(S) = t3 - t1 - t2,
+// 3 DFMA instead of the 6n - 2 FP64 instructions of a Gray step of the plain
+// per-output kernel.
 //
-// Pipeline per chunk of KC sign vectors (all vectors at once when the
-// workspace allows):
-//   row_sums_kernel y_r(d) by Gray-code row-sum updates (one column per step)
-//   level_kernel   alpha/beta tables level by level: entry(P) = entry(P minus
-//                  its last mode) * y_last / sqrt(multiplicity)
-//   gemm_kernel    a(S) = sum_d alpha_P(d) beta_Q(d), written at the
-//                  canonical index lowbase(P) + rank(Q)
+// Pipeline per chunk of KC sign vectors (all of them when the workspace
+// allows):
+//   row_sums_kernel  y_r(d) by Gray-code row-sum updates (one column per step)
+//   level_kernel     alpha/beta tables level by level: entry(P) = entry(P minus
+//                    its last mode) * y_last / sqrt(multiplicity)
+//   gemm_kernel      one launch over every k: a(S) = sum_d alpha_P beta_Q,
+//                    written at the canonical index lowbase(P) + rank(Q)
 //
 // The canonical index of S (lexicographic order of the non-decreasing mode
 // list) splits as lowbase(P) + rank of Q among the (n-k)-multisets over
-// [h, m), because all outputs whose first k photons are P and whose others
-// lie in [h, m) are contiguous in that order.
+// [h, m): all outputs whose first k photons are P and whose other photons lie
+// in [h, m) are contiguous in that order.
 
 #include <algorithm>
 
@@ -34,22 +40,27 @@ namespace pcv {
 namespace {
 
 constexpr int kYRun = 32;          // sign vectors per row_sums_kernel thread
+constexpr int kLevelGroup = 8;     // sign vectors per level_kernel thread
+constexpr int kStrip = 4;          // outputs per gemm_kernel thread
+constexpr int kWarps = 8;          // rows of a gemm block tile
 
 struct ColList { int c[PCV_MAX_PHOTONS]; };
 
-__global__ void row_sums_kernel(const double2* __restrict__ U, int m, int n, ColList cols,
-                                int64_t d0, int kc, double2* __restrict__ Y)
+__global__ void row_sums_kernel(const double2* __restrict__ Ub, int m, int n, ColList cols,
+                                int64_t d0, int kc, double2* __restrict__ Yb, int64_t ystride)
 {
-    // thread -> (row r, run of kYRun consecutive sign vectors)
+    // thread -> (row r, run of kYRun consecutive sign vectors); blockIdx.y = batch entry
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int runs = (kc + kYRun - 1) / kYRun;
     if (t >= (int64_t)m * runs) return;
+    const double2* U = Ub + (size_t)blockIdx.y * m * m;
+    double2* Y = Yb + (size_t)blockIdx.y * ystride;
     const int r = (int)(t % m);
     const int run = (int)(t / m);
     const double2* Ur = U + (size_t)r * m;
     const int64_t dstart = d0 + (int64_t)run * kYRun;
     const int len = min(kYRun, kc - run * kYRun);
-    uint64_t g = (uint64_t)dstart ^ ((uint64_t)dstart >> 1);
+    const uint64_t g = (uint64_t)dstart ^ ((uint64_t)dstart >> 1);
     double2 y = __ldg(Ur + cols.c[0]);
     for (int j = 1; j < n; ++j) caxpy(y, ((g >> (j - 1)) & 1u) ? -1.0 : 1.0, __ldg(Ur + cols.c[j]));
     for (int q = 0; q < len; ++q) {
@@ -74,35 +85,44 @@ struct LevelArgs {
     int kc;
     int64_t d0;
     double lead;           // low side level 0: 2^{-(n-1)} norm_t
-    const double2* Y;
-    double2* T;
-    int64_t* lowbase;      // low side: canonical base index of each P (level k == n - |Q| pairing)
+    const double2* Y;      // [batch][kc][m]
+    int64_t ystride;
+    double2* T;            // [batch][kc][width]
+    double* Tsum;          // [batch][kc][width]: re + im of T
+    int64_t tstride;
+    int64_t* lowbase;      // low side: canonical base index of each P (written once)
 };
 
 __global__ void level_kernel(const LevelArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.count) return;
-    const int w = a.side == 0 ? a.h : a.m - a.h;
-    const int shift = a.side == 0 ? 0 : a.h;
+    const int q0 = blockIdx.y * kLevelGroup;
+    const int q1 = min(a.kc, q0 + kLevelGroup);
+    const int b = blockIdx.z;
+    double2* T = a.T + (size_t)b * a.tstride;
+    double* Ts = a.Tsum + (size_t)b * a.tstride;
+    const double2* Y = a.Y + (size_t)b * a.ystride;
+    const bool write_base = a.side == 0 && a.lowbase && blockIdx.y == 0 && b == 0;
     if (a.k == 0) {
-        for (int q = 0; q < a.kc; ++q) {
+        for (int q = q0; q < q1; ++q) {
             double v = 1.0;
             if (a.side == 0) {
                 const uint64_t d = (uint64_t)(a.d0 + q);
                 v = (__popcll(d ^ (d >> 1)) & 1) ? -a.lead : a.lead;
             }
-            a.T[(int64_t)q * a.width] = make_double2(v, 0.0);
+            T[(int64_t)q * a.width] = make_double2(v, 0.0);
+            Ts[(int64_t)q * a.width] = v;
         }
-        if (a.side == 0 && a.lowbase) {
+        if (write_base) {
             int64_t r = 0;
             if (a.n > 0) for (int v = 0; v < a.h; ++v) r += a.mc(a.m - v, a.n - 1);
             a.lowbase[0] = r;
         }
         return;
     }
-    // Level-local multiset tables count C(w' + k - 1, k) for w' <= w; the global
-    // table (a <= m) covers them.
+    const int w = a.side == 0 ? a.h : a.m - a.h;
+    const int shift = a.side == 0 ? 0 : a.h;
     int modes[PCV_MAX_PHOTONS];
     {
         int64_t idx = i;
@@ -125,7 +145,7 @@ __global__ void level_kernel(const LevelArgs a)
     const double sc = mult > 1 ? inv_sqrt_int(mult) : 1.0;
     const int r = last + shift;
 
-    if (a.side == 0 && a.lowbase) {
+    if (write_base) {
         // canonical index of the first output with prefix P and the rest in [h, m)
         int64_t base = 0;
         int prev = 0;
@@ -138,94 +158,103 @@ __global__ void level_kernel(const LevelArgs a)
         a.lowbase[a.off + i] = base;
     }
 
-    const double2* __restrict__ Tp = a.T + a.poff + parent;
-    const double2* __restrict__ Yr = a.Y + r;
-    double2* __restrict__ Tout = a.T + a.off + i;
-    if (mult > 1) {
-        for (int q = 0; q < a.kc; ++q) {
-            double2 y = Yr[(int64_t)q * a.m];
-            y.x *= sc;
-            y.y *= sc;
-            Tout[(int64_t)q * a.width] = cmul(Tp[(int64_t)q * a.width], y);
-        }
-    } else {
-        for (int q = 0; q < a.kc; ++q)
-            Tout[(int64_t)q * a.width] = cmul(Tp[(int64_t)q * a.width], Yr[(int64_t)q * a.m]);
+    for (int q = q0; q < q1; ++q) {
+        double2 y = Y[(int64_t)q * a.m + r];
+        if (mult > 1) { y.x *= sc; y.y *= sc; }
+        const double2 v = cmul(T[(int64_t)q * a.width + a.poff + parent], y);
+        T[(int64_t)q * a.width + a.off + i] = v;
+        Ts[(int64_t)q * a.width + a.off + i] = v.x + v.y;
     }
 }
 
 struct GemmArgs {
-    const double2* Tlow;   // [kc][wlow], level k at column lowoff
-    const double2* Thigh;  // [kc][whigh], level n-k at column highoff
-    int64_t wlow, whigh, lowoff, highoff;
-    int64_t M, N;          // entries of the two levels
+    const double2* Tlow;   // [batch][kc][wlow]
+    const double* Slow;
+    const double2* Thigh;  // [batch][kc][whigh]
+    const double* Shigh;
+    int64_t wlow, whigh, tstride_low, tstride_high;
+    int64_t lowoff[PCV_MAX_PHOTONS + 1], highoff[PCV_MAX_PHOTONS + 1];  // per k: level k low, level n-k high
+    int64_t M[PCV_MAX_PHOTONS + 1], N[PCV_MAX_PHOTONS + 1];
+    int64_t tile0[PCV_MAX_PHOTONS + 2];   // first tile of each k
+    int nk;
     const int64_t* lowbase;
     int kc;
     int first, last;       // first / last chunk of sign vectors
-    double2* acc;          // running sums (= amp when the caller wants amplitudes)
+    int64_t out_stride;    // outputs per batch entry
+    double2* acc;          // running sums between chunks (= amp when amplitudes are wanted)
     double2* amp;
     double* prob;
 };
 
-constexpr int kStrip = 4;               // outputs per thread
-constexpr int kWarps = 8;               // rows of a block tile
-
-// QSTRIP: a warp owns one P (alpha broadcast); its lanes own 4 Q's each
-// (strided by 32 so loads and stores coalesce).  !QSTRIP: the same with the
-// roles of P and Q exchanged.
-template <bool QSTRIP>
+// A warp owns one "fixed" entry (P if N >= M, else Q: the shorter side, so
+// the strip side fills whole warps); its lanes own 4 strip entries each,
+// strided by 32 so loads and stores coalesce.
 __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs a)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t nfixed = QSTRIP ? a.M : a.N;
-    const int64_t nstrip = QSTRIP ? a.N : a.M;
-    const int64_t strip_tiles = (nstrip + 32 * kStrip - 1) / (32 * kStrip);
     const int64_t tile = blockIdx.x;
-    const int64_t fixed = (tile / strip_tiles) * kWarps + warp;     // P (QSTRIP) or Q
+    int k = 0;
+    while (k + 1 < a.nk && a.tile0[k + 1] <= tile) ++k;
+    const int64_t M = a.M[k], N = a.N[k];
+    const bool qstrip = N >= M;
+    const int64_t nfixed = qstrip ? M : N, nstrip = qstrip ? N : M;
+    const int64_t strip_tiles = (nstrip + 32 * kStrip - 1) / (32 * kStrip);
+    const int64_t lt = tile - a.tile0[k];
+    const int64_t fixed = (lt / strip_tiles) * kWarps + warp;
     if (fixed >= nfixed) return;
-    const int64_t s0 = (tile % strip_tiles) * (32 * kStrip) + lane;
-    int64_t sidx[kStrip];
+    const int64_t s0 = (lt % strip_tiles) * (32 * kStrip) + lane;
+    const int b = blockIdx.y;
+
+    const double2* Tl = a.Tlow + (size_t)b * a.tstride_low + a.lowoff[k];
+    const double* Sl = a.Slow + (size_t)b * a.tstride_low + a.lowoff[k];
+    const double2* Th = a.Thigh + (size_t)b * a.tstride_high + a.highoff[k];
+    const double* Sh = a.Shigh + (size_t)b * a.tstride_high + a.highoff[k];
+    const double2* __restrict__ F = qstrip ? Tl + fixed : Th + fixed;
+    const double* __restrict__ Fs = qstrip ? Sl + fixed : Sh + fixed;
+    const double2* __restrict__ S = qstrip ? Th : Tl;
+    const double* __restrict__ Ss = qstrip ? Sh : Sl;
+    const int64_t wF = qstrip ? a.wlow : a.whigh;
+    const int64_t wS = qstrip ? a.whigh : a.wlow;
+
+    int64_t sidx[kStrip], oidx[kStrip];
     bool sv[kStrip];
 #pragma unroll
     for (int t = 0; t < kStrip; ++t) {
         sidx[t] = s0 + 32 * t;
         sv[t] = sidx[t] < nstrip;
+        if (!sv[t]) sidx[t] = 0;
+        oidx[t] = qstrip ? a.lowbase[a.lowoff[k] + fixed] + sidx[t] : a.lowbase[a.lowoff[k] + sidx[t]] + fixed;
     }
-    int64_t oidx[kStrip];
+    double t1[kStrip], t2[kStrip], t3[kStrip];
 #pragma unroll
-    for (int t = 0; t < kStrip; ++t) {
-        if (!sv[t]) { oidx[t] = 0; continue; }
-        oidx[t] = QSTRIP ? a.lowbase[a.lowoff + fixed] + sidx[t]
-                         : a.lowbase[a.lowoff + sidx[t]] + fixed;
-    }
-    double2 acc[kStrip];
-#pragma unroll
-    for (int t = 0; t < kStrip; ++t)
-        acc[t] = (a.first || !sv[t]) ? make_double2(0.0, 0.0) : a.acc[oidx[t]];
-
-    const double2* __restrict__ F = QSTRIP ? a.Tlow + a.lowoff + fixed : a.Thigh + a.highoff + fixed;
-    const double2* __restrict__ S = QSTRIP ? a.Thigh + a.highoff : a.Tlow + a.lowoff;
-    const int64_t wF = QSTRIP ? a.wlow : a.whigh;
-    const int64_t wS = QSTRIP ? a.whigh : a.wlow;
-    int64_t sclamp[kStrip];
-#pragma unroll
-    for (int t = 0; t < kStrip; ++t) sclamp[t] = sv[t] ? sidx[t] : 0;
+    for (int t = 0; t < kStrip; ++t) t1[t] = t2[t] = t3[t] = 0.0;
 
 #pragma unroll 2
     for (int q = 0; q < a.kc; ++q) {
         const double2 f = __ldg(F + (int64_t)q * wF);
+        const double fs = __ldg(Fs + (int64_t)q * wF);
         const double2* __restrict__ Sq = S + (int64_t)q * wS;
+        const double* __restrict__ Ssq = Ss + (int64_t)q * wS;
 #pragma unroll
         for (int t = 0; t < kStrip; ++t) {
-            if (sv[t]) cmac(acc[t], f, __ldg(Sq + sclamp[t]));
+            const double2 v = __ldg(Sq + sidx[t]);
+            const double vs = __ldg(Ssq + sidx[t]);
+            t1[t] = fma(f.x, v.x, t1[t]);
+            t2[t] = fma(f.y, v.y, t2[t]);
+            t3[t] = fma(fs, vs, t3[t]);
         }
     }
+    double2* acc = a.acc ? a.acc + (size_t)b * a.out_stride : nullptr;
+    double2* amp = a.amp ? a.amp + (size_t)b * a.out_stride : nullptr;
+    double* prob = a.prob ? a.prob + (size_t)b * a.out_stride : nullptr;
 #pragma unroll
     for (int t = 0; t < kStrip; ++t) {
         if (!sv[t]) continue;
-        if (!a.last) { a.acc[oidx[t]] = acc[t]; continue; }
-        if (a.amp) a.amp[oidx[t]] = acc[t];
-        if (a.prob) a.prob[oidx[t]] = fma(acc[t].x, acc[t].x, acc[t].y * acc[t].y);
+        double2 v = make_double2(t1[t] - t2[t], t3[t] - t1[t] - t2[t]);
+        if (!a.first) v = cadd(v, acc[oidx[t]]);
+        if (!a.last) { acc[oidx[t]] = v; continue; }
+        if (amp) amp[oidx[t]] = v;
+        if (prob) prob[oidx[t]] = fma(v.x, v.x, v.y * v.y);
     }
 }
 
@@ -245,14 +274,35 @@ int64_t mset(int w, int k) { return k == 0 ? 1 : (w <= 0 ? 0 : binom_host(w + k 
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+struct Layout {
+    size_t table, base, acc, y, tl, sl, th, sh, total;
+};
+
+Layout layout(int m, int n, int B, int64_t lo, int64_t hi, int64_t total, bool need_acc, int64_t kc)
+{
+    Layout L;
+    L.table = align256((size_t)(m + 1) * (n + 1) * sizeof(int64_t));
+    L.base = align256((size_t)lo * sizeof(int64_t));
+    L.acc = need_acc ? align256((size_t)B * total * sizeof(double2)) : 0;
+    L.y = align256((size_t)B * kc * m * sizeof(double2));
+    L.tl = align256((size_t)B * kc * lo * sizeof(double2));
+    L.sl = align256((size_t)B * kc * lo * sizeof(double));
+    L.th = align256((size_t)B * kc * hi * sizeof(double2));
+    L.sh = align256((size_t)B * kc * hi * sizeof(double));
+    L.total = L.table + L.base + L.acc + L.y + L.tl + L.sl + L.th + L.sh;
+    return L;
+}
+
 }  // namespace
 
-// Plan the workspace: fixed parts, then the largest power-of-two chunk of
-// sign vectors whose tables fit.  Returns the bytes used (or -1 on overflow).
-int64_t dist_plan(const Plan& p, int64_t ws_bytes, bool need_acc, DistPlan* dp)
+// Plan the workspace: the largest power-of-two chunk of sign vectors whose
+// tables fit into ws_bytes (ws_bytes < 0: the default budget of 8 GiB).
+// Returns the bytes used, or -1 on overflow.
+int64_t dist_plan(const Plan& p, int B, int64_t ws_bytes, bool need_acc, DistPlan* dp)
 {
     const int m = p.m, n = p.n;
     dp->h = std::max(1, m / 2);
+    dp->B = B;
     const int wl = dp->h, wh = m - dp->h;
     int64_t lo = 0, hi = 0;
     for (int k = 0; k <= n + 1; ++k) {
@@ -269,34 +319,38 @@ int64_t dist_plan(const Plan& p, int64_t ws_bytes, bool need_acc, DistPlan* dp)
     dp->whigh = hi;
     const int64_t total = mset(m, n);
     if (total < 0) return -1;
-    dp->ws_table = align256((size_t)(m + 1) * (n + 1) * sizeof(int64_t));
-    dp->ws_base = align256((size_t)lo * sizeof(int64_t));
-    dp->ws_acc = need_acc ? align256((size_t)total * sizeof(double2)) : 0;
-    const size_t fixed = dp->ws_table + dp->ws_base + dp->ws_acc;
-    const size_t per_d = (size_t)(m + lo + hi) * sizeof(double2);
+    dp->total = total;
     const int64_t dmax = n > 0 ? (1ll << (n - 1)) : 1;
-    // default plan: all sign vectors if the tables stay under 4 GiB
-    const size_t cap = ws_bytes < 0 ? ((size_t)4 << 30) : (size_t)std::max<int64_t>(0, ws_bytes - (int64_t)fixed - 3 * 256);
+    const size_t budget = ws_bytes < 0 ? ((size_t)8 << 30) : (size_t)ws_bytes;
     int64_t kc = dmax;
-    while (kc > 1 && (size_t)kc * per_d > cap) kc >>= 1;
+    while (kc > 1 && layout(m, n, B, lo, hi, total, need_acc && kc < dmax, kc).total > budget) kc >>= 1;
+    const Layout L = layout(m, n, B, lo, hi, total, need_acc && kc < dmax, kc);
     dp->kc = (int)kc;
-    dp->ws_y = align256((size_t)kc * m * sizeof(double2));
-    dp->ws_T = align256((size_t)kc * lo * sizeof(double2)) + align256((size_t)kc * hi * sizeof(double2));
-    dp->ws_total = fixed + dp->ws_y + dp->ws_T;
-    return (int64_t)dp->ws_total;
+    dp->ws_table = L.table;
+    dp->ws_base = L.base;
+    dp->ws_acc = L.acc;
+    dp->ws_y = L.y;
+    dp->ws_tl = L.tl;
+    dp->ws_sl = L.sl;
+    dp->ws_th = L.th;
+    dp->ws_sh = L.sh;
+    dp->ws_total = L.total;
+    return (int64_t)L.total;
 }
 
 cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* U,
                               double* prob, double2* amp, void* ws, cudaStream_t s)
 {
-    const int m = p.m, n = p.n;
+    const int m = p.m, n = p.n, B = dp.B;
     char* w = (char*)ws;
     int64_t* table = (int64_t*)w;            w += dp.ws_table;
     int64_t* lowbase = (int64_t*)w;          w += dp.ws_base;
     double2* accbuf = dp.ws_acc ? (double2*)w : amp;  w += dp.ws_acc;
     double2* Y = (double2*)w;                w += dp.ws_y;
-    double2* Tlow = (double2*)w;             w += align256((size_t)dp.kc * dp.wlow * sizeof(double2));
-    double2* Thigh = (double2*)w;
+    double2* Tlow = (double2*)w;             w += dp.ws_tl;
+    double* Slow = (double*)w;               w += dp.ws_sl;
+    double2* Thigh = (double2*)w;            w += dp.ws_th;
+    double* Shigh = (double*)w;
 
     cudaError_t e = build_multiset_table(table, m, n, s);
     if (e != cudaSuccess) return e;
@@ -307,13 +361,45 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
     const int64_t dtot = 1ll << (n - 1);
     const int nchunks = (int)(dtot / dp.kc);
     const double lead = ldexp(p.norm_t, -(n - 1));
+    const int64_t ystride = (int64_t)dp.kc * m;
+    const int64_t tl_stride = (int64_t)dp.kc * dp.wlow, th_stride = (int64_t)dp.kc * dp.whigh;
+
+    GemmArgs g;
+    g.Tlow = Tlow; g.Slow = Slow; g.Thigh = Thigh; g.Shigh = Shigh;
+    g.wlow = dp.wlow; g.whigh = dp.whigh;
+    g.tstride_low = tl_stride; g.tstride_high = th_stride;
+    g.lowbase = lowbase;
+    g.kc = dp.kc;
+    g.out_stride = dp.total;
+    g.acc = accbuf;
+    g.amp = amp;
+    g.prob = prob;
+    g.nk = 0;
+    int64_t tiles = 0;
+    for (int k = 0; k <= n; ++k) {
+        const int64_t M = mset(dp.h, k), N = mset(m - dp.h, n - k);
+        if (M == 0 || N == 0) continue;
+        const bool qstrip = N >= M;
+        const int64_t nstrip = qstrip ? N : M, nfixed = qstrip ? M : N;
+        g.lowoff[g.nk] = dp.lowoff[k];
+        g.highoff[g.nk] = dp.highoff[n - k];
+        g.M[g.nk] = M;
+        g.N[g.nk] = N;
+        g.tile0[g.nk] = tiles;
+        tiles += ((nstrip + 32 * kStrip - 1) / (32 * kStrip)) * ((nfixed + kWarps - 1) / kWarps);
+        g.nk++;
+    }
+    g.tile0[g.nk] = tiles;
+    if (tiles > INT32_MAX) return cudaErrorInvalidConfiguration;
+
     for (int ch = 0; ch < nchunks; ++ch) {
         const int64_t d0 = (int64_t)ch * dp.kc;
         stage_begin(kStageTables, s);
         {
             const int runs = (dp.kc + kYRun - 1) / kYRun;
             const int64_t th = (int64_t)m * runs;
-            row_sums_kernel<<<(unsigned)((th + 127) / 128), 128, 0, s>>>(U, m, n, cols, d0, dp.kc, Y);
+            dim3 grid((unsigned)((th + 127) / 128), (unsigned)B);
+            row_sums_kernel<<<grid, 128, 0, s>>>(U, m, n, cols, d0, dp.kc, Y, ystride);
             note_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
@@ -334,40 +420,25 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
                 la.d0 = d0;
                 la.lead = lead;
                 la.Y = Y;
+                la.ystride = ystride;
                 la.T = side == 0 ? Tlow : Thigh;
+                la.Tsum = side == 0 ? Slow : Shigh;
+                la.tstride = side == 0 ? tl_stride : th_stride;
                 la.lowbase = (side == 0 && ch == 0) ? lowbase : nullptr;
-                level_kernel<<<(unsigned)((la.count + 127) / 128), 128, 0, s>>>(la);
+                dim3 grid((unsigned)((la.count + 127) / 128), (unsigned)((dp.kc + kLevelGroup - 1) / kLevelGroup),
+                          (unsigned)B);
+                level_kernel<<<grid, 128, 0, s>>>(la);
                 note_launches(1);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
             }
         }
         stage_end(kStageTables, s);
         stage_begin(kStageGemm, s);
-        for (int k = 0; k <= n; ++k) {
-            GemmArgs g;
-            g.M = mset(dp.h, k);
-            g.N = mset(m - dp.h, n - k);
-            if (g.M == 0 || g.N == 0) continue;
-            g.Tlow = Tlow; g.Thigh = Thigh;
-            g.wlow = dp.wlow; g.whigh = dp.whigh;
-            g.lowoff = dp.lowoff[k]; g.highoff = dp.highoff[n - k];
-            g.lowbase = lowbase;
-            g.kc = dp.kc;
-            g.first = ch == 0;
-            g.last = ch == nchunks - 1;
-            g.acc = accbuf;
-            g.amp = amp;
-            g.prob = prob;
-            const bool qstrip = g.N >= g.M;
-            const int64_t nstrip = qstrip ? g.N : g.M, nfixed = qstrip ? g.M : g.N;
-            const int64_t tiles = ((nstrip + 32 * kStrip - 1) / (32 * kStrip)) * ((nfixed + kWarps - 1) / kWarps);
-            if (tiles > INT32_MAX) return cudaErrorInvalidConfiguration;
-            const unsigned grid = (unsigned)tiles;
-            if (qstrip) gemm_kernel<true><<<grid, 256, 0, s>>>(g);
-            else        gemm_kernel<false><<<grid, 256, 0, s>>>(g);
-            note_launches(1);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
+        g.first = ch == 0;
+        g.last = ch == nchunks - 1;
+        gemm_kernel<<<dim3((unsigned)tiles, (unsigned)B), 256, 0, s>>>(g);
+        note_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         stage_end(kStageGemm, s);
     }
     return cudaSuccess;

@@ -366,7 +366,7 @@ int pcv_amplitudes_batched(const pcv_batch_desc* descs, int n_circ, int64_t tota
     return e == cudaSuccess ? PCV_OK : cuda_fail(e, "batched launch");
 }
 
-static int64_t dist_ws(int m, int n, int algo, int param, bool need_acc, int64_t ws_bytes, pcv::DistPlan* dp)
+static int64_t dist_ws(int B, int m, int n, int algo, int param, bool need_acc, int64_t ws_bytes, pcv::DistPlan* dp)
 {
     pcv::Plan p;
     p.m = m;
@@ -374,10 +374,7 @@ static int64_t dist_ws(int m, int n, int algo, int param, bool need_acc, int64_t
     if (algo == PCV_ALGO_FACTOR || algo == PCV_ALGO_AUTO) {
         if (n == 0) return 0;
         pcv::DistPlan local;
-        pcv::DistPlan* d = dp ? dp : &local;
-        int64_t r = pcv::dist_plan(p, ws_bytes, need_acc, d);
-        if (r >= 0 && need_acc && d->kc == (1ll << (n - 1))) r = pcv::dist_plan(p, ws_bytes, false, d);
-        return r;
+        return pcv::dist_plan(p, B, ws_bytes, need_acc, dp ? dp : &local);
     }
     const int64_t N = msets(m, n);
     int64_t bytes = (int64_t)align256((size_t)(m + 1) * (n + 1) * sizeof(int64_t));
@@ -385,26 +382,63 @@ static int64_t dist_ws(int m, int n, int algo, int param, bool need_acc, int64_t
     return bytes;
 }
 
-int64_t pcv_distribution_workspace(int m, int n)
+int64_t pcv_distribution_batched_workspace(int B, int m, int n)
 {
-    if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "bad sizes");
+    if (B < 1 || m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "bad sizes");
     if (msets(m, n) < 0) return fail(PCV_ERANGE, "output space too large");
-    const int64_t r = dist_ws(m, n, PCV_ALGO_FACTOR, 0, true, -1, nullptr);
+    const int64_t r = dist_ws(B, m, n, PCV_ALGO_FACTOR, 0, true, -1, nullptr);
     return r < 0 ? fail(PCV_ERANGE, "workspace size overflows") : r;
 }
+
+int64_t pcv_distribution_workspace(int m, int n) { return pcv_distribution_batched_workspace(1, m, n); }
 
 int64_t pcv_distribution_workspace_min(int m, int n)
 {
     if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "bad sizes");
     if (msets(m, n) < 0) return fail(PCV_ERANGE, "output space too large");
-    const int64_t r = dist_ws(m, n, PCV_ALGO_FACTOR, 0, true, 0, nullptr);
+    const int64_t r = dist_ws(1, m, n, PCV_ALGO_FACTOR, 0, true, 0, nullptr);
     return r < 0 ? fail(PCV_ERANGE, "workspace size overflows") : r;
+}
+
+int pcv_distribution_batched(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
+                             double* prob, pcv_c64* amp,
+                             void* workspace, int64_t workspace_bytes, void* stream)
+{
+    pcv::Plan p;
+    int rc = make_plan(U, m, input_occ, &p);
+    if (rc) return rc;
+    if (B < 1 || B > 65535) return fail(PCV_EINVAL, "batch %d outside [1, 65535]", B);
+    if (!amp && !prob) return fail(PCV_EINVAL, "amp and prob are both NULL");
+    if (amp && !aligned(amp, 16)) return fail(PCV_EINVAL, "amp is not 16-byte aligned");
+    if (prob && !aligned(prob, 8)) return fail(PCV_EINVAL, "prob is not 8-byte aligned");
+    if (workspace && !aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
+    const int64_t N = msets(m, p.n);
+    if (N < 0) return fail(PCV_ERANGE, "output space C(%d,%d) too large", m + p.n - 1, p.n);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p.n == 0) {
+        for (int b = 0; b < B; ++b) {
+            cudaError_t e = pcv::launch_glynn_group(p, (const double2*)U, nullptr, nullptr, 0, 1,
+                                                    amp ? (double2*)amp + b : nullptr, prob ? prob + b : nullptr, 1, s);
+            if (e != cudaSuccess) return cuda_fail(e, "n0 kernel");
+        }
+        return PCV_OK;
+    }
+    pcv::DistPlan dp;
+    const int64_t need = dist_ws(B, m, p.n, PCV_ALGO_FACTOR, 0, amp == nullptr, workspace_bytes, &dp);
+    if (need < 0) return fail(PCV_ERANGE, "workspace size overflows");
+    if (!workspace || need > workspace_bytes)
+        return fail(PCV_ENOMEM, "workspace of at least %lld bytes needed, %lld given",
+                    (long long)dist_ws(B, m, p.n, PCV_ALGO_FACTOR, 0, amp == nullptr, 0, nullptr), (long long)workspace_bytes);
+    cudaError_t e = pcv::launch_glynn_dist(p, dp, (const double2*)U, prob, (double2*)amp, workspace, s);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "factorised distribution");
 }
 
 int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                         double* prob, pcv_c64* amp, int algo, int param,
                         void* workspace, int64_t workspace_bytes, void* stream)
 {
+    if (algo == PCV_ALGO_AUTO || algo == PCV_ALGO_FACTOR)
+        return pcv_distribution_batched(U, 1, m, input_occ, prob, amp, workspace, workspace_bytes, stream);
     pcv::Plan p;
     int rc = make_plan(U, m, input_occ, &p);
     if (rc) return rc;
@@ -418,21 +452,11 @@ int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
         cudaError_t e = pcv::launch_glynn_group(p, (const double2*)U, nullptr, nullptr, 0, 1, (double2*)amp, prob, 1, s);
         return e == cudaSuccess ? PCV_OK : cuda_fail(e, "n0 kernel");
     }
-    if (algo == PCV_ALGO_AUTO) algo = PCV_ALGO_FACTOR;
     if (workspace && !aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
-    if (algo == PCV_ALGO_FACTOR) {
-        pcv::DistPlan dp;
-        const int64_t need = dist_ws(m, p.n, algo, 0, amp == nullptr, workspace_bytes, &dp);
-        if (need < 0) return fail(PCV_ERANGE, "workspace size overflows");
-        if (!workspace || need > workspace_bytes)
-            return fail(PCV_ENOMEM, "workspace of at least %lld bytes needed, %lld given",
-                        (long long)pcv_distribution_workspace_min(m, p.n), (long long)workspace_bytes);
-        cudaError_t e = pcv::launch_glynn_dist(p, dp, (const double2*)U, prob, (double2*)amp, workspace, s);
-        return e == cudaSuccess ? PCV_OK : cuda_fail(e, "factorised distribution");
-    }
     AmpChoice c{algo, param};
     if ((rc = check_choice(c, p.n))) return rc;
-    const int64_t need = dist_ws(m, p.n, algo, param, false, workspace_bytes, nullptr);
+    if (algo == PCV_ALGO_TILE) return fail(PCV_EINVAL, "the tile kernel takes explicit outputs");
+    const int64_t need = dist_ws(1, m, p.n, algo, param, false, workspace_bytes, nullptr);
     if (!workspace || need > workspace_bytes)
         return fail(PCV_ENOMEM, "workspace of %lld bytes needed, %lld given", (long long)need, (long long)workspace_bytes);
     if (N * (algo == PCV_ALGO_BLOCK ? param : 1) > INT32_MAX) return fail(PCV_ERANGE, "too many permanents for one launch");
@@ -454,6 +478,109 @@ int pcv_distribution(const pcv_c64* U, int m, const uint8_t* input_occ,
                      void* workspace, int64_t workspace_bytes, void* stream)
 {
     return pcv_distribution_ex(U, m, input_occ, prob, amp, PCV_ALGO_AUTO, 0, workspace, workspace_bytes, stream);
+}
+
+// ------------------------------------------------------------- adjoint
+
+int pcv_amplitudes_backward(const pcv_c64* U, int m, const uint8_t* input_occ,
+                            const uint8_t* output_occ, int64_t n_out, const pcv_c64* grad_amp,
+                            pcv_c64* grad_U, void* stream)
+{
+    pcv::Plan p;
+    int rc = make_plan(U, m, input_occ, &p);
+    if (rc) return rc;
+    if (p.n > pcv::adjoint_max_photons()) return fail(PCV_EINVAL, "adjoint supports n <= %d (n=%d)", pcv::adjoint_max_photons(), p.n);
+    if (n_out < 0) return fail(PCV_EINVAL, "n_out < 0");
+    if (!grad_U || !aligned(grad_U, 16)) return fail(PCV_EINVAL, "grad_U is NULL or misaligned");
+    if (n_out > 0 && (!output_occ || !grad_amp || !aligned(grad_amp, 16))) return fail(PCV_EINVAL, "bad output or gradient pointer");
+    if ((n_out + 127) / 128 > INT32_MAX) return fail(PCV_ERANGE, "too many outputs");
+    cudaError_t e = pcv::launch_adjoint(p, (const double2*)U, 1, output_occ, nullptr, n_out, (const double2*)grad_amp,
+                                        (double2*)grad_U, (cudaStream_t)stream);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "adjoint");
+}
+
+int64_t pcv_distribution_backward_workspace(int m, int n)
+{
+    if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "bad sizes");
+    return (int64_t)align256((size_t)(m + 1) * (n + 1) * sizeof(int64_t));
+}
+
+int pcv_distribution_backward(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
+                              const pcv_c64* grad_amp, pcv_c64* grad_U,
+                              void* workspace, int64_t workspace_bytes, void* stream)
+{
+    pcv::Plan p;
+    int rc = make_plan(U, m, input_occ, &p);
+    if (rc) return rc;
+    if (B < 1 || B > 65535) return fail(PCV_EINVAL, "batch %d outside [1, 65535]", B);
+    if (p.n > pcv::adjoint_max_photons()) return fail(PCV_EINVAL, "adjoint supports n <= %d (n=%d)", pcv::adjoint_max_photons(), p.n);
+    if (!grad_U || !aligned(grad_U, 16) || !grad_amp || !aligned(grad_amp, 16)) return fail(PCV_EINVAL, "bad gradient pointer");
+    const int64_t N = msets(m, p.n);
+    if (N < 0 || (N + 127) / 128 > INT32_MAX) return fail(PCV_ERANGE, "output space too large");
+    const int64_t need = pcv_distribution_backward_workspace(m, p.n);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(PCV_ENOMEM, "workspace of %lld bytes (256-byte aligned) needed", (long long)need);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = pcv::build_multiset_table((int64_t*)workspace, m, p.n, s);
+    if (e == cudaSuccess)
+        e = pcv::launch_adjoint(p, (const double2*)U, B, nullptr, (const int64_t*)workspace, N,
+                                (const double2*)grad_amp, (double2*)grad_U, s);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "distribution adjoint");
+}
+
+// --------------------------------------------------------------- mesh
+
+int pcv_mesh_unitary(const double* phases, int B, int m, pcv_c64* U, void* stream)
+{
+    if (B < 1 || m < 2 || m > pcv::mesh_max_modes() || !phases || !U || !aligned(U, 16))
+        return fail(PCV_EINVAL, "mesh: B=%d m=%d", B, m);
+    cudaError_t e = pcv::launch_mesh_forward(phases, B, m, (double2*)U, (cudaStream_t)stream);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "mesh forward");
+}
+
+int pcv_mesh_backward(const double* phases, int B, int m, const pcv_c64* U, const pcv_c64* grad_U,
+                      double* grad_phases, void* stream)
+{
+    if (B < 1 || m < 2 || m > pcv::mesh_max_modes() || !phases || !U || !grad_U || !grad_phases)
+        return fail(PCV_EINVAL, "mesh backward: B=%d m=%d", B, m);
+    cudaError_t e = pcv::launch_mesh_backward(phases, B, m, (const double2*)U, (const double2*)grad_U, grad_phases,
+                                              (cudaStream_t)stream);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "mesh backward");
+}
+
+// ---------------------------------------------------------- reductions
+
+int64_t pcv_dist_stats_workspace(int B)
+{
+    if (B < 1) return fail(PCV_EINVAL, "B < 1");
+    return pcv::stats_workspace(B);
+}
+
+int pcv_dist_stats(const double* p, const double* q, int64_t N, int B, int q_batched, double* out,
+                   void* workspace, int64_t workspace_bytes, void* stream)
+{
+    if (!p || !out || N < 1 || B < 1 || B > 65535) return fail(PCV_EINVAL, "dist_stats: bad arguments");
+    if (!workspace || workspace_bytes < pcv::stats_workspace(B) || !aligned(workspace, 8))
+        return fail(PCV_ENOMEM, "dist_stats: workspace of %lld bytes needed", (long long)pcv::stats_workspace(B));
+    cudaError_t e = pcv::launch_stats(p, q, N, B, q_batched, out, (double*)workspace, (cudaStream_t)stream);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "dist_stats");
+}
+
+int pcv_kl_grad(const double* p, const double* q, const pcv_c64* amp, int64_t N, int B, int q_batched,
+                const double* batch_scale, double scale, pcv_c64* grad_amp, void* stream)
+{
+    if (!p || !q || !amp || !grad_amp || N < 1 || B < 1 || B > 65535) return fail(PCV_EINVAL, "kl_grad: bad arguments");
+    cudaError_t e = pcv::launch_kl_grad(p, q, (const double2*)amp, N, B, q_batched, batch_scale, scale, (double2*)grad_amp,
+                                        (cudaStream_t)stream);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "kl_grad");
+}
+
+int pcv_prob_grad_to_amp(const double* grad_prob, const pcv_c64* amp, int64_t count, pcv_c64* grad_amp, void* stream)
+{
+    if (count < 0 || (count > 0 && (!grad_prob || !amp || !grad_amp))) return fail(PCV_EINVAL, "prob_grad: bad arguments");
+    if (count == 0) return PCV_OK;
+    cudaError_t e = pcv::launch_prob_grad(grad_prob, (const double2*)amp, count, (double2*)grad_amp, (cudaStream_t)stream);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "prob_grad");
 }
 
 }  // extern "C"

@@ -122,15 +122,32 @@ int64_t batched_workspace(int n_circ, int64_t total_outputs);
 cudaError_t launch_glynn_batched(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs, void* ws,
                                  int sms, cudaStream_t s);
 
+// Adjoint (adjoint.cu), mesh (mesh.cu), reductions (reduce.cu)
+int adjoint_max_photons();
+cudaError_t launch_adjoint(const Plan& p, const double2* U, int B, const uint8_t* out_occ, const int64_t* mc_table,
+                           int64_t count, const double2* gbar, double2* gradU, cudaStream_t s);
+int mesh_max_modes();
+cudaError_t launch_mesh_forward(const double* phases, int B, int m, double2* U, cudaStream_t s);
+cudaError_t launch_mesh_backward(const double* phases, int B, int m, const double2* U, const double2* G,
+                                 double* gphi, cudaStream_t s);
+int64_t stats_workspace(int B);
+cudaError_t launch_stats(const double* p, const double* q, int64_t N, int B, int q_batched, double* out,
+                         double* ws, cudaStream_t s);
+cudaError_t launch_kl_grad(const double* p, const double* q, const double2* amp, int64_t N, int B, int q_batched,
+                           const double* bscale, double scale, double2* grad, cudaStream_t s);
+cudaError_t launch_prob_grad(const double* gp, const double2* amp, int64_t count, double2* gamp, cudaStream_t s);
+
 // Factorised full distribution (glynn_dist.cu)
 struct DistPlan {
     int h;                    // modes [0,h) are the low side, [h,m) the high side
+    int B;                    // batch entries (unitaries)
     int kc;                   // Glynn sign vectors per chunk
+    int64_t total;            // outputs per batch entry
     int64_t wlow, whigh;      // entries of all levels per side: C(h+n, n), C(m-h+n, n)
     int64_t lowoff[PCV_MAX_PHOTONS + 2], highoff[PCV_MAX_PHOTONS + 2];
-    size_t ws_table, ws_y, ws_T, ws_base, ws_acc, ws_total;
+    size_t ws_table, ws_base, ws_acc, ws_y, ws_tl, ws_sl, ws_th, ws_sh, ws_total;
 };
-int64_t dist_plan(const Plan& p, int64_t ws_bytes, bool need_acc, DistPlan* dp);
+int64_t dist_plan(const Plan& p, int B, int64_t ws_bytes, bool need_acc, DistPlan* dp);
 cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* U,
                               double* prob, double2* amp, void* ws, cudaStream_t s);
 }  // namespace pcv

@@ -272,3 +272,90 @@ def test_n30_block_diagonal_factorises(pcv):
     outs = np.concatenate([s1, s2])[None, :]
     amp, _ = run_amps(pcv, U, t, outs, algo=pcv.PCV_ALGO_BLOCK, param=64)
     assert abs(amp[0] - want) <= tol(30) * max(abs(want), 1 / math.sqrt(math.comb(m1 + 13, 14) * math.comb(m2 + 15, 16)))
+
+
+# ------------------------------------------- shared-row-sum tile kernel
+
+
+@pytest.mark.parametrize("m,n,cnt", [(8, 1, 5), (8, 3, 300), (12, 6, 257), (20, 10, 513), (24, 12, 70),
+                                     (30, 14, 33), (40, 17, 9), (64, 20, 3), (128, 8, 40)])
+def test_tile_kernel(pcv, m, n, cnt):
+    U = pin.haar_unitary(m, 2000 + m + n)
+    t = pin.single_photon_input(m, n)
+    outs = np.concatenate([pin.random_outputs(m, n, cnt, 2100 + n), pin.random_bunched_outputs(m, n, 3, 2200 + n),
+                           pin.random_bunched_outputs(m, max(n - 1, 0), 2, 2300 + n)])
+    a_ref = oracle.amplitudes(U, t, outs)
+    amp, prob = run_amps(pcv, U, t, outs, algo=pcv.PCV_ALGO_TILE)
+    assert amp_err(amp, a_ref, m, n) <= tol(n)
+    assert np.all(amp[-2:] == 0)
+
+
+def test_tile_kernel_bunched_input(pcv):
+    m = 16
+    U = pin.haar_unitary(m, 2401)
+    t = np.zeros(m, np.uint8); t[[0, 3, 7]] = [3, 2, 4]        # n = 9
+    outs = pin.random_bunched_outputs(m, 9, 100, 2402)
+    a_ref = oracle.amplitudes(U, t, outs)
+    amp, _ = run_amps(pcv, U, t, outs, algo=pcv.PCV_ALGO_TILE)
+    assert amp_err(amp, a_ref, m, 9) <= tol(9)
+
+
+# ------------------------------------------------- batched persistent
+
+
+def test_batched_uneven_circuits(pcv):
+    """Uneven batch (m in [8, 64], n in [4, min(16, m)]) in one persistent launch;
+    every circuit's amplitudes against the oracle."""
+    circs = pin.batched_circuits(24, 8, 64, 4, 16, 37, seed=2500)
+    batch = [(dev(c["U"]), c["input_occ"], dev(c["outputs"])) for c in circs]
+    amps, probs = pcv.amplitudes_batched(batch)
+    torch.cuda.synchronize()
+    for c, a, p in zip(circs, amps, probs):
+        a_ref = oracle.amplitudes(c["U"], c["input_occ"], c["outputs"])
+        assert amp_err(a.cpu().numpy(), a_ref, c["m"], c["n"]) <= tol(c["n"]), (c["m"], c["n"])
+        assert np.allclose(p.cpu().numpy(), np.abs(a_ref) ** 2, rtol=1e-9, atol=1e-300)
+
+
+def test_batched_repeat_is_deterministic(pcv):
+    circs = pin.batched_circuits(12, 8, 40, 4, 12, 300, seed=2600)
+    plan = pcv.BatchPlan([(dev(c["U"]), c["input_occ"], dev(c["outputs"])) for c in circs])
+    first = [a.clone() for a in plan.run()[0]]
+    second = plan.run()[0]
+    torch.cuda.synchronize()
+    for x, y in zip(first, second):
+        assert torch.equal(x, y)
+
+
+def test_batched_skips_invalid_descriptor(pcv):
+    # a descriptor with an input mode outside [0, m) gets no work; the others run
+    circs = pin.batched_circuits(3, 8, 12, 3, 5, 10, seed=2700)
+    plan = pcv.BatchPlan([(dev(c["U"]), c["input_occ"], dev(c["outputs"])) for c in circs])
+    raw = plan.descs.cpu().numpy().copy()
+    arr = (pcv.abi.pcv_batch_desc * 3).from_buffer_copy(raw.tobytes())
+    arr[1].cols[0] = 200
+    plan.descs = torch.from_numpy(np.frombuffer(bytes(arr), np.uint8).copy()).cuda()
+    plan.amps[1].fill_(7)
+    amps, _ = plan.run()
+    torch.cuda.synchronize()
+    assert torch.all(amps[1] == 7)
+    for i in (0, 2):
+        a_ref = oracle.amplitudes(circs[i]["U"], circs[i]["input_occ"], circs[i]["outputs"])
+        assert amp_err(amps[i].cpu().numpy(), a_ref, circs[i]["m"], circs[i]["n"]) <= tol(circs[i]["n"])
+
+
+def test_batched_distribution(pcv):
+    m, n, B = 12, 6, 5
+    Us = np.stack([pin.haar_unitary(m, 1700 + b) for b in range(B)])
+    t = pin.single_photon_input(m, n)
+    prob, amp = pcv.distribution_batched(dev(Us), t)
+    torch.cuda.synchronize()
+    for b in range(B):
+        p_ref, a_ref = oracle.distribution(Us[b], t)
+        assert amp_err(amp[b].cpu().numpy(), a_ref, m, n) <= tol(n)
+        assert oracle.tvd(prob[b].cpu().numpy(), p_ref) <= 1e-12
+    # a small workspace forces several passes over the sign vectors, per batch entry
+    wsmin = pcv.abi.pcv_distribution_batched_workspace(B, m, n) // 4
+    ws = torch.empty(wsmin, dtype=torch.uint8, device="cuda")
+    prob2, _ = pcv.distribution_batched(dev(Us), t, want_amp=False, ws=ws)
+    torch.cuda.synchronize()
+    assert torch.allclose(prob2, prob, rtol=1e-12, atol=1e-18)
