@@ -244,6 +244,37 @@ int pcv_kl_grad(const double* p, const double* q, const pcv_c64* amp, int64_t N,
 /* grad_amp = 2 a grad_prob for p = |a|^2 (count elements). */
 int pcv_prob_grad_to_amp(const double* grad_prob, const pcv_c64* amp, int64_t count, pcv_c64* grad_amp, void* stream);
 
+/* ------------------------------------------- distribution without allocation */
+
+/* Size of the scratch array pcv_distribution_static uses: 32 MiB. */
+#define PCV_STATIC_SCRATCH_BYTES (32ll << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc, and it computes exactly what
+ * pcv_distribution computes, with the same kernels.  Such callers include
+ * plugins whose host application owns all device memory through its own
+ * pool, and services that allow no allocation after start-up, so that no
+ * call can fail for lack of memory or stall the device while it allocates.
+ * They pass U and the output arrays as usual (device pointers they own) and
+ * no workspace: the scratch is a 32 MiB array in the library's device code,
+ * which every GPU that loads the library holds until the process exits.
+ *   - The first call on a device looks up that device's address of the array
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - Problems whose scratch would exceed PCV_STATIC_SCRATCH_BYTES are
+ *     rejected with PCV_ENOMEM (for example amp == NULL with an output space
+ *     larger than about a million states).  The sign vectors are processed in
+ *     as many passes as the array requires.
+ *   - Every call, from every host thread and stream, shares the one array.
+ *     Calls whose work overlaps on the GPU (different streams, or the same
+ *     array used concurrently from several threads) race and give wrong
+ *     results; serialise them on one stream.  Nothing in the array needs to
+ *     start at zero: each call writes all it reads.
+ *   - n must be >= 1.  Other arguments and errors as pcv_distribution. */
+int pcv_distribution_static(const pcv_c64* U, int m, const uint8_t* input_occ,
+                            double* prob, pcv_c64* amp, void* stream);
+int64_t pcv_distribution_static_max_bytes(void);
+
 /* -------------------------------------------------- measurement helpers */
 
 /* FP64 throughput probe: `blocks` x `threads` threads each run `iters`

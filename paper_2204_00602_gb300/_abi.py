@@ -62,6 +62,8 @@ SIGNATURES = {
     "pcv_dist_stats": (_i, [_vp, _vp, _i64, _i, _i, _vp, _vp, _i64, _vp]),
     "pcv_kl_grad": (_i, [_vp, _vp, _vp, _i64, _i, _i, _vp, ctypes.c_double, _vp, _vp]),
     "pcv_prob_grad_to_amp": (_i, [_vp, _vp, _i64, _vp, _vp]),
+    "pcv_distribution_static": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "pcv_distribution_static_max_bytes": (_i64, []),
     "pcv_fp64_probe": (_i, [_vp, _i, _i, _i, _vp]),
     "pcv_amplitudes_batched_workspace": (_i64, [_i, _i64]),
     "pcv_amplitudes_batched": (_i, [_vp, _i, _i64, _vp, _i64, _vp]),
@@ -218,6 +220,14 @@ def pcv_kl_grad(p, q, amp, N, B, q_batched, batch_scale, scale, grad_amp, stream
 
 def pcv_prob_grad_to_amp(grad_prob, amp, count, grad_amp, stream):
     return _call("pcv_prob_grad_to_amp", ptr(grad_prob), ptr(amp), count, ptr(grad_amp), stream)
+
+
+def pcv_distribution_static(U, m, input_occ, prob, amp, stream):
+    return _call("pcv_distribution_static", ptr(U), m, ptr(input_occ), ptr(prob), ptr(amp), stream)
+
+
+def pcv_distribution_static_max_bytes() -> int:
+    return _call("pcv_distribution_static_max_bytes")
 
 
 def pcv_fp64_probe(out, blocks, threads, iters, stream):

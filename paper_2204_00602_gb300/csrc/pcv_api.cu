@@ -181,6 +181,7 @@ void stage_end(int stage, cudaStream_t s)
     }
 }
 void note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void set_error(const char* msg) { g_err = msg; }
 }  // namespace pcv
 
 extern "C" {

@@ -103,6 +103,7 @@ enum Stage { kStageTables = 0, kStageGemm = 1, kStagePlain = 2, kStageCount = 8 
 void stage_begin(int stage, cudaStream_t s);
 void stage_end(int stage, cudaStream_t s);
 void note_launches(int64_t k);
+void set_error(const char* msg);      // message returned by pcv_last_error
 
 // Plain Glynn kernels (glynn_plain.cu)
 cudaError_t launch_glynn_group(const Plan& p, const double2* U, const uint8_t* out_occ,
