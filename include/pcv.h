@@ -191,6 +191,13 @@ int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                         double* prob, pcv_c64* amp, int algo, int param,
                         void* workspace, int64_t workspace_bytes, void* stream);
 
+/* The same explicit outputs for B unitaries with one input state (the tile
+ * kernel of PCV_ALGO_TILE with a batch dimension; m <= 128, n >= 1).
+ *   U       device, B*m*m pcv_c64;  output_occ device, n_out*m uint8
+ *   amp     device, B*n_out pcv_c64 or NULL;  prob device, B*n_out doubles or NULL */
+int pcv_amplitudes_multi(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
+                         const uint8_t* output_occ, int64_t n_out, pcv_c64* amp, double* prob, void* stream);
+
 /* ------------------------------------------------------------ gradients */
 
 /* dL/dU from dL/da for explicit outputs of one U (n <= 8).
@@ -205,6 +212,11 @@ int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
 int pcv_amplitudes_backward(const pcv_c64* U, int m, const uint8_t* input_occ,
                             const uint8_t* output_occ, int64_t n_out, const pcv_c64* grad_amp,
                             pcv_c64* grad_U, void* stream);
+
+/* The same explicit outputs for B unitaries: grad_amp [B][n_out], grad_U [B][m][m]. */
+int pcv_amplitudes_backward_multi(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
+                                  const uint8_t* output_occ, int64_t n_out, const pcv_c64* grad_amp,
+                                  pcv_c64* grad_U, void* stream);
 
 /* The same for every output of the distributions of B unitaries (grad_amp
  * [B][C(m+n-1,n)] in canonical order, grad_U [B][m][m]); the workspace holds
@@ -243,6 +255,51 @@ int pcv_kl_grad(const double* p, const double* q, const pcv_c64* amp, int64_t N,
 
 /* grad_amp = 2 a grad_prob for p = |a|^2 (count elements). */
 int pcv_prob_grad_to_amp(const double* grad_prob, const pcv_c64* amp, int64_t count, pcv_c64* grad_amp, void* stream);
+
+/* ------------------------------------------------------ BF16 MLP surrogate */
+/* No counterpart in the paper: kernels of the learned surrogate that maps
+ * mesh phases to log-probabilities of a fixed output set.  All pointers are
+ * device pointers; bf16 arrays are row-major with the given leading
+ * dimensions (elements).
+ *
+ * pcv_gemm_bf16: C[M x N] = A[M x K] . B[N x K]^T on the tensor cores (BF16
+ * operands, FP32 accumulation); K a multiple of 32, lda/ldb multiples of 8,
+ * operands 16-byte aligned.  Epilogue `mode`:
+ *   0  outf = C (fp32)
+ *   1  pre = C + bias -> outf (fp32, optional), outb = bf16(GELU(pre)),
+ *      GELU(x) = x/2 (1 + erf(x / sqrt 2))
+ *   2  outf = C + bias (fp32)
+ *   3  outb = bf16(C * GELU'(pre)), pre = the forward layer's pre-activation */
+int pcv_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int mode,
+                  const float* bias, float* outf, int ldo, void* outb, int ldob, const float* pre, int ldp,
+                  void* stream);
+/* out[C x R] = in[R x C]^T (bf16). */
+int pcv_transpose_bf16(const void* in, int R, int C, int ldi, void* out, int ldo, void* stream);
+/* db[n] = sum_m dY[m][n] (bf16 in, fp32 out, fixed summation order). */
+int pcv_colsum_bf16(const void* dY, int M, int N, int ld, float* db, void* stream);
+/* X[b] = (sin phi_b, cos phi_b, 1, 0 ...) as bf16 rows of length ldx >= 2P+1;
+ * the constant 1 carries the first layer's bias. */
+int pcv_phase_features(const double* phases, int B, int P, void* X, int ldx, void* stream);
+/* dL/dphi from dL/dX (fp32 [B][ldx]): dX_sin cos(phi) - dX_cos sin(phi). */
+int pcv_phase_features_grad(const double* phases, int B, int P, const float* dX, int ldx, double* grad_phases,
+                            void* stream);
+/* loss = mean (pred - target)^2 over count elements (fp32); grad_pred_bf16 =
+ * 2 (pred - target) / count as bf16, or NULL. */
+int64_t pcv_mse_workspace(void);
+int pcv_mse(const float* pred, const float* target, int64_t count, float* loss, void* grad_pred_bf16,
+            void* workspace, int64_t workspace_bytes, void* stream);
+/* Adam on fp32 master weights (bias-corrected with `step` >= 1); writes the
+ * bf16 copy of the updated weights to w_bf16 when it is not NULL. */
+int pcv_adam(float* w, float* m, float* v, const float* g, int64_t count, float lr, float beta1, float beta2,
+             float eps, int step, void* w_bf16, void* stream);
+int pcv_f32_to_bf16(const float* in, int64_t count, void* out, void* stream);
+/* Adam on FP64 parameters (the mesh phases of the optimisation loops). */
+int pcv_adam_f64(double* w, double* m, double* v, const double* g, int64_t count, double lr, double beta1,
+                 double beta2, double eps, int step, void* stream);
+/* out = (float) log(in) elementwise: log-probability targets of the surrogate. */
+int pcv_log_f64_to_f32(const double* in, int64_t count, float* out, void* stream);
+/* out = exp(in) elementwise in FP64: the surrogate's probabilities. */
+int pcv_exp_f32_to_f64(const float* in, int64_t count, double* out, void* stream);
 
 /* ------------------------------------------- distribution without allocation */
 

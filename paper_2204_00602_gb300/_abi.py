@@ -64,6 +64,22 @@ SIGNATURES = {
     "pcv_prob_grad_to_amp": (_i, [_vp, _vp, _i64, _vp, _vp]),
     "pcv_distribution_static": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "pcv_distribution_static_max_bytes": (_i64, []),
+    "pcv_amplitudes_multi": (_i, [_vp, _i, _i, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "pcv_gemm_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _i, _vp]),
+    "pcv_transpose_bf16": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
+    "pcv_colsum_bf16": (_i, [_vp, _i, _i, _i, _vp, _vp]),
+    "pcv_phase_features": (_i, [_vp, _i, _i, _vp, _i, _vp]),
+    "pcv_phase_features_grad": (_i, [_vp, _i, _i, _vp, _i, _vp, _vp]),
+    "pcv_mse_workspace": (_i64, []),
+    "pcv_mse": (_i, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp]),
+    "pcv_adam": (_i, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _i,
+                      _vp, _vp]),
+    "pcv_f32_to_bf16": (_i, [_vp, _i64, _vp, _vp]),
+    "pcv_log_f64_to_f32": (_i, [_vp, _i64, _vp, _vp]),
+    "pcv_exp_f32_to_f64": (_i, [_vp, _i64, _vp, _vp]),
+    "pcv_adam_f64": (_i, [_vp, _vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                          ctypes.c_double, _i, _vp]),
+    "pcv_amplitudes_backward_multi": (_i, [_vp, _i, _i, _vp, _vp, _i64, _vp, _vp, _vp]),
     "pcv_fp64_probe": (_i, [_vp, _i, _i, _i, _vp]),
     "pcv_amplitudes_batched_workspace": (_i64, [_i, _i64]),
     "pcv_amplitudes_batched": (_i, [_vp, _i, _i64, _vp, _i64, _vp]),
@@ -228,6 +244,66 @@ def pcv_distribution_static(U, m, input_occ, prob, amp, stream):
 
 def pcv_distribution_static_max_bytes() -> int:
     return _call("pcv_distribution_static_max_bytes")
+
+
+def pcv_amplitudes_multi(U, B, m, input_occ, output_occ, n_out, amp, prob, stream):
+    return _call("pcv_amplitudes_multi", ptr(U), B, m, ptr(input_occ), ptr(output_occ), n_out, ptr(amp), ptr(prob),
+                 stream)
+
+
+def pcv_gemm_bf16(A, lda, B, ldb, M, N, K, mode, bias, outf, ldo, outb, ldob, pre, ldp, stream):
+    return _call("pcv_gemm_bf16", ptr(A), lda, ptr(B), ldb, M, N, K, mode, ptr(bias), ptr(outf), ldo, ptr(outb),
+                 ldob, ptr(pre), ldp, stream)
+
+
+def pcv_transpose_bf16(inp, R, C, ldi, out, ldo, stream):
+    return _call("pcv_transpose_bf16", ptr(inp), R, C, ldi, ptr(out), ldo, stream)
+
+
+def pcv_colsum_bf16(dY, M, N, ld, db, stream):
+    return _call("pcv_colsum_bf16", ptr(dY), M, N, ld, ptr(db), stream)
+
+
+def pcv_phase_features(phases, B, P, X, ldx, stream):
+    return _call("pcv_phase_features", ptr(phases), B, P, ptr(X), ldx, stream)
+
+
+def pcv_phase_features_grad(phases, B, P, dX, ldx, grad_phases, stream):
+    return _call("pcv_phase_features_grad", ptr(phases), B, P, ptr(dX), ldx, ptr(grad_phases), stream)
+
+
+def pcv_mse_workspace() -> int:
+    return _call("pcv_mse_workspace")
+
+
+def pcv_mse(pred, target, count, loss, grad_pred_bf16, workspace, workspace_bytes, stream):
+    return _call("pcv_mse", ptr(pred), ptr(target), count, ptr(loss), ptr(grad_pred_bf16), ptr(workspace),
+                 workspace_bytes, stream)
+
+
+def pcv_adam(w, m, v, g, count, lr, beta1, beta2, eps, step, w_bf16, stream):
+    return _call("pcv_adam", ptr(w), ptr(m), ptr(v), ptr(g), count, lr, beta1, beta2, eps, step, ptr(w_bf16), stream)
+
+
+def pcv_f32_to_bf16(inp, count, out, stream):
+    return _call("pcv_f32_to_bf16", ptr(inp), count, ptr(out), stream)
+
+
+def pcv_log_f64_to_f32(inp, count, out, stream):
+    return _call("pcv_log_f64_to_f32", ptr(inp), count, ptr(out), stream)
+
+
+def pcv_exp_f32_to_f64(inp, count, out, stream):
+    return _call("pcv_exp_f32_to_f64", ptr(inp), count, ptr(out), stream)
+
+
+def pcv_adam_f64(w, m, v, g, count, lr, beta1, beta2, eps, step, stream):
+    return _call("pcv_adam_f64", ptr(w), ptr(m), ptr(v), ptr(g), count, lr, beta1, beta2, eps, step, stream)
+
+
+def pcv_amplitudes_backward_multi(U, B, m, input_occ, output_occ, n_out, grad_amp, grad_U, stream):
+    return _call("pcv_amplitudes_backward_multi", ptr(U), B, m, ptr(input_occ), ptr(output_occ), n_out,
+                 ptr(grad_amp), ptr(grad_U), stream)
 
 
 def pcv_fp64_probe(out, blocks, threads, iters, stream):

@@ -161,6 +161,20 @@ __global__ void __launch_bounds__(kThreads) glynn_tile_kernel(const pcv_batch_de
     tile_item(c, blockIdx.x, sh);
 }
 
+// Same outputs for B unitaries: blockIdx.y selects U + b*ustride and the
+// output arrays + b*ostride.
+__global__ void __launch_bounds__(kThreads) glynn_tile_multi_kernel(const pcv_batch_desc c0, int64_t ustride, int64_t ostride)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    TileShared& sh = *reinterpret_cast<TileShared*>(smem);
+    pcv_batch_desc c = c0;
+    const int64_t b = blockIdx.y;
+    c.U = c0.U + b * ustride;
+    if (c0.amp) c.amp = c0.amp + b * ostride;
+    if (c0.prob) c.prob = c0.prob + b * ostride;
+    tile_item(c, blockIdx.x, sh);
+}
+
 // Work queue of the batched launch: items (circuit, tile) in order of
 // decreasing photon number; blocks pull the next item with one atomicAdd and
 // never wait for another block.
@@ -277,6 +291,8 @@ cudaError_t ensure_smem_attr()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(glynn_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileShared));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(glynn_tile_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileShared));
+    if (e != cudaSuccess) return e;
     g_attr_set |= bit;
     return cudaSuccess;
 }
@@ -295,6 +311,19 @@ cudaError_t launch_glynn_tile(const pcv_batch_desc& d, cudaStream_t s)
     const int tilesz = kThreads / tile_splits(d.n);
     const int64_t tiles = (d.n_out + tilesz - 1) / tilesz;
     glynn_tile_kernel<<<(unsigned)tiles, kThreads, sizeof(TileShared), s>>>(d);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_glynn_tile_multi(const pcv_batch_desc& d, int B, cudaStream_t s)
+{
+    if (d.n_out == 0 || B == 0) return cudaSuccess;
+    cudaError_t e = ensure_smem_attr();
+    if (e != cudaSuccess) return e;
+    const int tilesz = kThreads / tile_splits(d.n);
+    const int64_t tiles = (d.n_out + tilesz - 1) / tilesz;
+    glynn_tile_multi_kernel<<<dim3((unsigned)tiles, (unsigned)B), kThreads, sizeof(TileShared), s>>>(
+        d, (int64_t)d.m * d.m, d.n_out);
     note_launches(1);
     return cudaGetLastError();
 }

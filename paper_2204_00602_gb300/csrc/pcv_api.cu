@@ -339,6 +339,35 @@ int pcv_amplitudes(const pcv_c64* U, int m, const uint8_t* input_occ,
                              workspace, workspace_bytes, stream);
 }
 
+int pcv_amplitudes_multi(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
+                         const uint8_t* output_occ, int64_t n_out, pcv_c64* amp, double* prob, void* stream)
+{
+    pcv::Plan p;
+    int rc = make_plan(U, m, input_occ, &p);
+    if (rc) return rc;
+    if (B < 1 || B > 65535) return fail(PCV_EINVAL, "batch %d outside [1, 65535]", B);
+    if (m > pcv::tile_max_modes()) return fail(PCV_EINVAL, "m=%d above %d", m, pcv::tile_max_modes());
+    if (p.n < 1) return fail(PCV_EINVAL, "n must be >= 1");
+    if (n_out < 0) return fail(PCV_EINVAL, "n_out < 0");
+    if (n_out == 0) return PCV_OK;
+    if (!output_occ || (!amp && !prob)) return fail(PCV_EINVAL, "bad output pointers");
+    if (amp && !aligned(amp, 16)) return fail(PCV_EINVAL, "amp is not 16-byte aligned");
+    pcv_batch_desc d;
+    d.U = U;
+    d.outputs = output_occ;
+    d.amp = amp;
+    d.prob = prob;
+    d.n_out = n_out;
+    d.m = m;
+    d.n = p.n;
+    for (int j = 0; j < PCV_MAX_PHOTONS; ++j) d.cols[j] = p.cols[j];
+    cudaStream_t s = (cudaStream_t)stream;
+    pcv::stage_begin(pcv::kStagePlain, s);
+    cudaError_t e = pcv::launch_glynn_tile_multi(d, B, s);
+    pcv::stage_end(pcv::kStagePlain, s);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "tile multi launch");
+}
+
 int64_t pcv_amplitudes_batched_workspace(int n_circ, int64_t total_outputs)
 {
     if (n_circ < 0 || total_outputs < 0) return fail(PCV_EINVAL, "bad sizes");
@@ -496,6 +525,24 @@ int pcv_amplitudes_backward(const pcv_c64* U, int m, const uint8_t* input_occ,
     if (n_out > 0 && (!output_occ || !grad_amp || !aligned(grad_amp, 16))) return fail(PCV_EINVAL, "bad output or gradient pointer");
     if ((n_out + 127) / 128 > INT32_MAX) return fail(PCV_ERANGE, "too many outputs");
     cudaError_t e = pcv::launch_adjoint(p, (const double2*)U, 1, output_occ, nullptr, n_out, (const double2*)grad_amp,
+                                        (double2*)grad_U, (cudaStream_t)stream);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "adjoint");
+}
+
+int pcv_amplitudes_backward_multi(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
+                                  const uint8_t* output_occ, int64_t n_out, const pcv_c64* grad_amp,
+                                  pcv_c64* grad_U, void* stream)
+{
+    pcv::Plan p;
+    int rc = make_plan(U, m, input_occ, &p);
+    if (rc) return rc;
+    if (B < 1 || B > 65535) return fail(PCV_EINVAL, "batch %d outside [1, 65535]", B);
+    if (p.n > pcv::adjoint_max_photons()) return fail(PCV_EINVAL, "adjoint supports n <= %d (n=%d)", pcv::adjoint_max_photons(), p.n);
+    if (n_out < 0) return fail(PCV_EINVAL, "n_out < 0");
+    if (!grad_U || !aligned(grad_U, 16)) return fail(PCV_EINVAL, "grad_U is NULL or misaligned");
+    if (n_out > 0 && (!output_occ || !grad_amp || !aligned(grad_amp, 16))) return fail(PCV_EINVAL, "bad output or gradient pointer");
+    if ((n_out + 127) / 128 > INT32_MAX) return fail(PCV_ERANGE, "too many outputs");
+    cudaError_t e = pcv::launch_adjoint(p, (const double2*)U, B, output_occ, nullptr, n_out, (const double2*)grad_amp,
                                         (double2*)grad_U, (cudaStream_t)stream);
     return e == cudaSuccess ? PCV_OK : cuda_fail(e, "adjoint");
 }

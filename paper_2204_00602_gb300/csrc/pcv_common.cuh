@@ -119,6 +119,7 @@ int glynn_block_threads();
 __host__ __device__ int tile_splits(int n);
 int tile_max_modes();
 cudaError_t launch_glynn_tile(const pcv_batch_desc& d, cudaStream_t s);
+cudaError_t launch_glynn_tile_multi(const pcv_batch_desc& d, int B, cudaStream_t s);
 int64_t batched_workspace(int n_circ, int64_t total_outputs);
 cudaError_t launch_glynn_batched(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs, void* ws,
                                  int sms, cudaStream_t s);

@@ -1,0 +1,203 @@
+"""Phase optimisation of Clements meshes with exact gradients, and with the
+learned surrogate in the loop (not in the paper; its Sec. 4.4 trains circuit
+parameters with an optimiser over exact output distributions).
+
+Problem: B independent m=12 meshes, n=6 photons in modes 0..5, a fixed set of
+512 outputs and a target q (Dirichlet(1) over the set).  Each mesh minimises
+L(phi) = KL(q || p(phi)) restricted to the set (= -sum q log p + const).
+
+* exact loop: mesh kernel -> tile kernel (512 amplitudes) -> KL gradient
+  kernel -> adjoint kernel -> mesh backward kernel -> FP64 Adam kernel.
+* surrogate loop: the MLP predicts log p; dL/dlog p = -q is constant, so one
+  MLP backward to its inputs and the sin/cos chain give dL/dphi.  Every
+  `check_every` steps the exact probabilities of the set are computed and the
+  surrogate's TVD on the set, 1/2 sum |p_hat - p|, is checked; above `tvd_tol`
+  the loop uses exact gradients for the next `check_every` steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+import time
+
+import numpy as np
+import torch
+
+from . import _abi as abi
+from . import _stream
+from .autograd import dist_stats, mesh_backward, mesh_unitary
+from .surrogate import MLP, exact_log_probs, init_weights, output_set
+
+
+class MeshProblem:
+    def __init__(self, B: int = 64, m: int = 12, n: int = 6, n_set: int = 512, seed: int = 2204006025,
+                 device="cuda"):
+        self.B, self.m, self.n = B, m, n
+        self.dev = torch.device(device)
+        self.t = np.zeros(m, np.uint8)
+        self.t[:n] = 1
+        self.outs_host = output_set(m, n, n_set, seed)
+        self.outs = torch.from_numpy(self.outs_host).to(self.dev)
+        self.n_set = n_set
+        self.q = torch.from_numpy(np.random.default_rng(seed + 1).dirichlet(np.ones(n_set))).to(self.dev)
+        self.P = m * (m - 1)
+        self.amp = torch.empty(B, n_set, dtype=torch.complex128, device=self.dev)
+        self.prob = torch.empty(B, n_set, dtype=torch.float64, device=self.dev)
+        self.gamp = torch.empty_like(self.amp)
+        self.gU = torch.empty(B, m, m, dtype=torch.complex128, device=self.dev)
+
+    @property
+    def stream(self):
+        return _stream(self.dev)
+
+    def probs(self, phases):
+        U = mesh_unitary(phases, self.m)
+        abi.pcv_amplitudes_multi(U, phases.shape[0], self.m, self.t, self.outs, self.n_set, self.amp, self.prob,
+                                 self.stream)
+        return U, self.prob
+
+    def loss(self, phases):
+        _, p = self.probs(phases)
+        return dist_stats(p, self.q)[:, 2]
+
+    def loss_and_grad(self, phases):
+        U, p = self.probs(phases)
+        B = phases.shape[0]
+        abi.pcv_kl_grad(p, self.q, self.amp, self.n_set, B, 0, None, 1.0, self.gamp, self.stream)
+        abi.pcv_amplitudes_backward_multi(U, B, self.m, self.t, self.outs, self.n_set, self.gamp, self.gU, self.stream)
+        return mesh_backward(phases, U, self.gU)
+
+
+class Adam64:
+    def __init__(self, params: torch.Tensor, lr: float):
+        self.p, self.lr = params, lr
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.t = 0
+
+    def step(self, g: torch.Tensor):
+        self.t += 1
+        abi.pcv_adam_f64(self.p, self.m, self.v, g, self.p.numel(), self.lr, 0.9, 0.999, 1e-8, self.t,
+                         _stream(self.p.device))
+
+
+def exact_loop(problem: MeshProblem, phases0: torch.Tensor, steps: int, lr: float = 0.02):
+    phases = phases0.clone()
+    opt = Adam64(phases, lr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        opt.step(problem.loss_and_grad(phases))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return phases, wall
+
+
+def surrogate_loop(problem: MeshProblem, net: MLP, phases0: torch.Tensor, steps: int, lr: float = 0.02,
+                   check_every: int = 50, tvd_tol: float = 1e-3):
+    phases = phases0.clone()
+    opt = Adam64(phases, lr)
+    B = phases.shape[0]
+    dy = torch.empty(B, problem.n_set, dtype=torch.bfloat16, device=phases.device)
+    negq = (-problem.q).to(torch.float32)
+    abi.pcv_f32_to_bf16(negq.repeat(B).contiguous(), B * problem.n_set, dy, problem.stream)
+    phat = torch.empty(B, problem.n_set, dtype=torch.float64, device=phases.device)
+    exact_steps, checks, tvds = 0, 0, []
+    use_exact_until = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(steps):
+        if s % check_every == 0:
+            checks += 1
+            _, p = problem.probs(phases)
+            y = net.predict_phases(phases)
+            abi.pcv_exp_f32_to_f64(y, y.numel(), phat, problem.stream)
+            tvd = float(dist_stats(p, phat)[:, 1].max().item())      # host read once per check
+            tvds.append(tvd)
+            if tvd > tvd_tol:
+                use_exact_until = s + check_every
+        if s < use_exact_until:
+            g = problem.loss_and_grad(phases)
+            exact_steps += 1
+        else:
+            net.predict_phases(phases)
+            g = net.grad_phases(phases, dy)
+        opt.step(g)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return phases, wall, {"exact_steps": exact_steps, "checks": checks, "max_tvd_seen": max(tvds),
+                          "min_tvd_seen": min(tvds), "tvd_tol": tvd_tol}
+
+
+def make_dataset(problem: MeshProblem, n_samples: int, seed: int):
+    """Uniform phases and exact log-probabilities of the set (fp32)."""
+    g = np.random.default_rng(seed)
+    phases = torch.from_numpy(g.uniform(0, 2 * np.pi, size=(n_samples, problem.P))).to(problem.dev)
+    targets = exact_log_probs(phases, problem.m, problem.t, problem.outs)
+    return phases, targets
+
+
+def train(net: MLP, phases: torch.Tensor, targets: torch.Tensor, epochs: int, batch: int = 4096):
+    n = phases.shape[0] - phases.shape[0] % batch
+    losses = []
+    for _ in range(epochs):
+        for s in range(0, n, batch):
+            X = net.features(phases[s:s + batch])
+            loss = net.train_step(X, targets[s:s + batch])
+        losses.append(float(loss.item()))
+    return losses
+
+
+def validate(net: MLP, problem: MeshProblem, phases: torch.Tensor):
+    """Per phase set: TVD on the set between exp(prediction) and the exact p."""
+    _, p = problem.probs(phases)
+    y = net.predict_phases(phases)
+    phat = torch.empty_like(p)
+    abi.pcv_exp_f32_to_f64(y, y.numel(), phat, problem.stream)
+    return dist_stats(p, phat)[:, 1]
+
+
+def run(samples: int, epochs: int, steps: int, B: int, seed: int = 2204006025, lr_net: float = 1e-3):
+    problem = MeshProblem(B=B, seed=seed)
+    t0 = time.perf_counter()
+    ph_train, y_train = make_dataset(problem, samples, seed + 10)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    Ws, bs = init_weights(seed + 20)
+    net = MLP(Ws, bs, lr=lr_net)
+    t0 = time.perf_counter()
+    losses = train(net, ph_train, y_train, epochs)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    val_ph = torch.from_numpy(np.random.default_rng(seed + 30).uniform(0, 2 * np.pi, (B, problem.P))).to(problem.dev)
+    val_tvd = validate(net, problem, val_ph)
+    phases0 = torch.from_numpy(np.random.default_rng(seed + 40).uniform(0, 2 * np.pi, (B, problem.P))).to(problem.dev)
+    loss0 = problem.loss(phases0).clone()
+    ph_e, wall_e = exact_loop(problem, phases0, steps)
+    loss_e = problem.loss(ph_e).clone()
+    ph_s, wall_s, info = surrogate_loop(problem, net, phases0, steps)
+    loss_s = problem.loss(ph_s).clone()
+    return {
+        "samples": samples, "epochs": epochs, "steps": steps, "batch_phase_sets": B,
+        "t_data_s": t_data, "t_train_s": t_train, "train_mse_per_epoch": losses,
+        "val_tvd_median": float(val_tvd.median().item()), "val_tvd_max": float(val_tvd.max().item()),
+        "loss_initial_mean": float(loss0.mean().item()),
+        "exact": {"wall_s": wall_e, "loss_mean": float(loss_e.mean().item())},
+        "surrogate": {"wall_s": wall_s, "loss_mean": float(loss_s.mean().item()), **info},
+        "speedup_wall": wall_e / wall_s,
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--samples", type=int, default=2_000_000)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--batch", type=int, default=64)
+    a = ap.parse_args(argv)
+    print(json.dumps(run(a.samples, a.epochs, a.steps, a.batch)), flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

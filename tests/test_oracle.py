@@ -331,3 +331,61 @@ def test_tvd_and_kl_basics():
     assert oracle.tvd(p, p) == 0 and 0 < oracle.tvd(p, q) <= 1
     assert abs(oracle.tvd(np.eye(2)[0], np.eye(2)[1]) - 1.0) < 1e-15
     assert abs(oracle.kl(p, p)) < 1e-15 and oracle.kl(q, p) > 0
+
+
+# ------------------------------------------------ surrogate MLP reference
+
+
+def test_mlp_oracle_bf16_rounding_matches_torch():
+    import torch
+    from oracle import mlp
+    x = np.random.default_rng(3).standard_normal(10000) * np.logspace(-30, 30, 10000)
+    want = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16(x), want)
+    bits = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(mlp.bf16_bits_to_f64(bits), want)
+
+
+def test_mlp_oracle_gelu_and_derivative():
+    import torch
+    from oracle import mlp
+    x = np.linspace(-8, 8, 2001)
+    assert np.abs(mlp.gelu(x) - torch.nn.functional.gelu(torch.from_numpy(x)).numpy()).max() < 1e-15
+    h = 1e-6
+    fd = (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h)
+    assert np.abs(mlp.gelu_grad(x) - fd).max() < 1e-8
+
+
+def test_mlp_oracle_adam_matches_torch_optimizer():
+    import torch
+    from oracle import mlp
+    g = np.random.default_rng(4)
+    w0 = g.standard_normal(50)
+    p = torch.nn.Parameter(torch.from_numpy(w0.copy()))
+    opt = torch.optim.Adam([p], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    w, m, v = w0.copy(), np.zeros(50), np.zeros(50)
+    for step in range(1, 6):
+        grad = g.standard_normal(50)
+        p.grad = torch.from_numpy(grad.copy())
+        opt.step()
+        w, m, v = mlp.adam(w, m, v, grad, 1e-2, 0.9, 0.999, 1e-8, step)
+    assert np.abs(w - p.detach().numpy()).max() < 1e-12
+
+
+def test_mlp_oracle_forward_backward_by_finite_differences():
+    # the oracle's layer recursion without bf16 rounding equals the network's
+    # function; its gradient (chain rule written out) matches differences
+    from oracle import mlp
+    g = np.random.default_rng(5)
+    X = g.standard_normal((3, 8))
+    Ws = [g.standard_normal((6, 8)) / 3, g.standard_normal((4, 6)) / 3]
+    bs = [g.standard_normal(6) / 3, g.standard_normal(4) / 3]
+    f = lambda W0: float(np.sum(mlp.gelu(X @ W0.T + bs[0]) @ Ws[1].T + bs[1]))
+    pre = X @ Ws[0].T + bs[0]
+    dpre = (np.ones((3, 4)) @ Ws[1]) * mlp.gelu_grad(pre)
+    gW0 = dpre.T @ X
+    h = 1e-6
+    for i in range(6):
+        for j in range(8):
+            E = np.zeros_like(Ws[0]); E[i, j] = h
+            assert abs((f(Ws[0] + E) - f(Ws[0] - E)) / (2 * h) - gW0[i, j]) < 1e-7
