@@ -28,8 +28,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 M, N_PH = 20, 10
-WORKLOAD = ("full distribution m=20 n=10, photons in modes 0..9, Haar-random 20x20 complex128 "
-            "unitary (QR of seeded complex Gaussian, seed 2204006022 + 1000*rank), all 20,030,010 "
+
+
+def workload_text(m, n, count):
+    return (f"full distribution m={m} n={n}, photons in modes 0..{n - 1}, Haar-random {m}x{m} complex128 "
+            f"unitary (QR of seeded complex Gaussian, seed 2204006022 + 1000*rank), all {count:,} "
             "outputs, complex FP64 amplitudes and probabilities")
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2, written between timed steps
 
@@ -47,7 +50,13 @@ def parse():
     ap.add_argument("--algo", default="factor", choices=["factor", "group"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
-    return ap.parse_args()
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--m", type=int, default=20, help="modes (default: the m=20 n=10 workload)")
+    ap.add_argument("--n", type=int, default=10, help="photons")
+    args = ap.parse_args()
+    global M, N_PH
+    M, N_PH = args.m, args.n
+    return args
 
 
 def dist_env():
@@ -269,15 +278,15 @@ def run_ours(args):
             "stage_ms_per_step": {k: (v[0] / v[1] if v[1] else None) for k, v in stages.items()}}
 
     cpu = None
-    if world == 1 or rank == 0:
+    if not args.no_cpu and (world == 1 or rank == 0):
         cpu, _, _ = oracle_sample(args.cpu_seconds)
 
     line = {
-        "metric": "amplitudes/s (m=20 n=10 full distribution, complex FP64)",
+        "metric": f"amplitudes/s (m={M} n={N_PH} full distribution, complex FP64)",
         "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": M, "n": N_PH, "outputs": Ntot, "algo": args.algo,
+        "config": {"workload": workload_text(M, N_PH, Ntot), "m": M, "n": N_PH, "outputs": Ntot, "algo": args.algo,
                    "l2": "flushed between steps (256 MiB write, untimed)", "parallelism": f"replicas{world}"},
         "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "wall_s_timed_region": wall,
@@ -307,11 +316,12 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = per_step * args.steps / dt
     line = {
-        "impl": "reference", "metric": "amplitudes/s (m=20 n=10 full distribution, complex FP64)",
+        "impl": "reference", "metric": f"amplitudes/s (m={M} n={N_PH} full distribution, complex FP64)",
         "value": v, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": M, "n": N_PH, "outputs": oracle.num_outputs(M, N_PH),
+        "config": {"workload": workload_text(M, N_PH, oracle.num_outputs(M, N_PH)), "m": M, "n": N_PH,
+                   "outputs": oracle.num_outputs(M, N_PH),
                    "sample_per_step": per_step},
         "cpu_baseline": {"value": v, "unit": "amplitudes/s", "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": f"each step: the first {per_step} outputs in canonical order, CPU Ryser FP64"},

@@ -83,6 +83,7 @@ class Adam64:
 
 
 def exact_loop(problem: MeshProblem, phases0: torch.Tensor, steps: int, lr: float = 0.02):
+    problem.loss_and_grad(phases0.clone())          # untimed: loads every kernel of the loop once
     phases = phases0.clone()
     opt = Adam64(phases, lr)
     torch.cuda.synchronize()
@@ -103,6 +104,12 @@ def surrogate_loop(problem: MeshProblem, net: MLP, phases0: torch.Tensor, steps:
     negq = (-problem.q).to(torch.float32)
     abi.pcv_f32_to_bf16(negq.repeat(B).contiguous(), B * problem.n_set, dy, problem.stream)
     phat = torch.empty(B, problem.n_set, dtype=torch.float64, device=phases.device)
+    warm = phases0.clone()                           # untimed: loads every kernel of the loop once
+    problem.loss_and_grad(warm)
+    net.predict_phases(warm)
+    net.grad_phases(warm, dy)
+    abi.pcv_exp_f32_to_f64(net.predict_phases(warm), B * problem.n_set, phat, problem.stream)
+    dist_stats(phat, phat)
     exact_steps, checks, tvds = 0, 0, []
     use_exact_until = 0
     torch.cuda.synchronize()

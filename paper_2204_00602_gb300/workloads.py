@@ -1,0 +1,138 @@
+"""Secondary throughput workloads (the headline m=20 n=10 distribution is bench.py).
+
+    python -m paper_2204_00602_gb300.workloads batched [--circuits 512] [--outputs 4096]
+    python -m paper_2204_00602_gb300.workloads sweep [--nmin 16] [--nmax 30] [--outputs 256]
+    python -m paper_2204_00602_gb300.workloads mesh   [--batch 64]
+
+batched: uneven circuits (m ~ U{8..64}, n ~ U{4..min(24, m)}, Haar U, photons in
+modes 0..n-1, 4096 seeded random outputs each, collision-free for n <= 16) in
+one persistent launch of the shared-row-sum tile kernel.
+sweep: one Haar unitary per n = 16..30 at m = n^2, 256 collision-free outputs,
+plain Glynn block kernel (m is too large for the shared-row-sum tiles).
+mesh: the differentiable m=12 n=6 mesh, 64 phase sets, forward (all 12,376
+outputs) + KL + backward per step.
+
+Each prints one JSON line: amplitudes/s, FP64 work per the kernel's
+instruction count, and the fraction of the FP64 peak (152 SMs x 2 DFMA/clk x
+2 flop x clock).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+import pcv_inputs as pin
+
+from . import BatchPlan, amplitudes
+
+SEED = pin.BASE_SEED + 3
+
+
+def _peak_flops():
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return sms * 2 * 2 * 2070e6
+
+
+def _events():
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def batched(n_circ: int, n_out: int, reps: int = 1):
+    g = np.random.default_rng(SEED)
+    circs = []
+    work_fp64_instr = 0.0   # per output and sign vector: (n-1) complex products (4 each) + signed add (2)
+    fl = 0.0                # the same in flops: 6 per complex product, 2 per complex add
+    for c in range(n_circ):
+        m = int(g.integers(8, 65))
+        n = int(g.integers(4, min(24, m) + 1))
+        U = torch.from_numpy(pin.haar_unitary(m, SEED + 1000 + c)).cuda()
+        outs = torch.from_numpy(pin.random_outputs(m, n, n_out, SEED + 5000 + c)).cuda()
+        circs.append((U, pin.single_photon_input(m, n), outs))
+        work_fp64_instr += n_out * 2 ** (n - 1) * (4 * n - 2)
+        fl += n_out * 2 ** (n - 1) * (6 * (n - 1) + 2)
+    plan = BatchPlan(circs, want_prob=True)
+    plan.run()
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    for _ in range(reps):
+        plan.run()
+    b.record()
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3 / reps
+    amps = n_circ * n_out
+    return {"workload": f"batched {n_circ} uneven circuits x {n_out} outputs (m~U[8,64], n~U[4,24])",
+            "amplitudes_per_s": amps / sec, "seconds": sec, "amplitudes": amps,
+            "fp64_tflops": fl / sec / 1e12, "frac_of_fp64_peak": fl / sec / _peak_flops(),
+            "fp64_instr_per_s": work_fp64_instr / sec}
+
+
+def sweep(nmin: int, nmax: int, n_out: int):
+    rows = []
+    for n in range(nmin, nmax + 1):
+        m = n * n
+        U = torch.from_numpy(pin.haar_unitary(m, SEED + 100 + n)).cuda()
+        t = pin.single_photon_input(m, n)
+        outs = torch.from_numpy(pin.random_outputs(m, n, n_out, SEED + 200 + n)).cuda()
+        amplitudes(U, t, outs[:1])
+        torch.cuda.synchronize()
+        a, b = _events()
+        a.record()
+        amplitudes(U, t, outs)
+        b.record()
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        fl = n_out * 2 ** (n - 1) * (8 * n - 4)
+        rows.append({"n": n, "m": m, "outputs": n_out, "seconds": sec, "amplitudes_per_s": n_out / sec,
+                     "fp64_tflops_algorithmic": fl / sec / 1e12, "frac_of_fp64_peak": fl / sec / _peak_flops()})
+        print(json.dumps(rows[-1]), flush=True)
+    return {"workload": f"sweep n={nmin}..{nmax} at m=n^2, {n_out} outputs each", "rows": rows}
+
+
+def mesh(batch: int, steps: int = 20):
+    from .autograd import mesh_kl
+    m, n = 12, 6
+    t = pin.single_photon_input(m, n)
+    N = math.comb(m + n - 1, n)
+    q = torch.from_numpy(pin.dirichlet_target(N, SEED + 7)).cuda()
+    ph = torch.from_numpy(pin.mesh_phases(batch, m * (m - 1), SEED + 8)).cuda().requires_grad_(True)
+    for _ in range(2):
+        mesh_kl(ph, m, t, q).sum().backward()
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    for _ in range(steps):
+        ph.grad = None
+        mesh_kl(ph, m, t, q).sum().backward()
+    b.record()
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3 / steps
+    return {"workload": f"mesh m=12 n=6, {batch} phase sets, all {N} outputs, KL forward+backward",
+            "ms_per_step": sec * 1e3, "amplitudes_per_s_forward": batch * N / sec}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("which", choices=["batched", "sweep", "mesh"])
+    ap.add_argument("--circuits", type=int, default=512)
+    ap.add_argument("--outputs", type=int, default=None)
+    ap.add_argument("--nmin", type=int, default=16)
+    ap.add_argument("--nmax", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=64)
+    a = ap.parse_args()
+    if a.which == "batched":
+        r = batched(a.circuits, a.outputs or 4096)
+    elif a.which == "sweep":
+        r = sweep(a.nmin, a.nmax, a.outputs or 256)
+    else:
+        r = mesh(a.batch)
+    print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()

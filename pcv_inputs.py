@@ -65,14 +65,16 @@ def random_outputs(m: int, n: int, count: int, seed: int) -> np.ndarray:
     """
     g = rng(seed)
     out = np.zeros((count, m), dtype=np.uint8)
-    for c in range(count):
-        if n <= 16 and n <= m:
-            modes = g.choice(m, size=n, replace=False)
-            out[c, modes] = 1
-        else:
-            slots = np.sort(g.choice(m + n - 1, size=n, replace=False))
-            modes = slots - np.arange(n)
-            np.add.at(out[c], modes, 1)
+    if count == 0 or n == 0:
+        return out
+    rows = np.repeat(np.arange(count), n)
+    if n <= 16 and n <= m:
+        modes = np.argsort(g.random((count, m)), axis=1)[:, :n]          # uniform n-subsets
+        out[rows, modes.reshape(-1)] = 1
+    else:
+        slots = np.sort(np.argsort(g.random((count, m + n - 1)), axis=1)[:, :n], axis=1)
+        modes = slots - np.arange(n)[None, :]                               # stars and bars
+        np.add.at(out, (rows, modes.reshape(-1)), 1)
     return out
 
 
@@ -80,9 +82,10 @@ def random_bunched_outputs(m: int, n: int, count: int, seed: int) -> np.ndarray:
     """uint8[count, m]: uniform random multisets (bunched outputs allowed) for any n."""
     g = rng(seed)
     out = np.zeros((count, m), dtype=np.uint8)
-    for c in range(count):
-        slots = np.sort(g.choice(m + n - 1, size=n, replace=False))
-        np.add.at(out[c], slots - np.arange(n), 1)
+    if count == 0 or n == 0:
+        return out
+    slots = np.sort(np.argsort(g.random((count, m + n - 1)), axis=1)[:, :n], axis=1)
+    np.add.at(out, (np.repeat(np.arange(count), n), (slots - np.arange(n)[None, :]).reshape(-1)), 1)
     return out
 
 
