@@ -273,6 +273,16 @@ int pcv_prob_grad_to_amp(const double* grad_prob, const pcv_c64* amp, int64_t co
 int pcv_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int mode,
                   const float* bias, float* outf, int ldo, void* outb, int ldob, const float* pre, int ldp,
                   void* stream);
+/* The same product on the 5th-generation tensor cores: TMA loads of 128 x 64
+ * bf16 tiles (128-byte swizzle) into a 4-stage shared-memory ring,
+ * tcgen05.mma (M = N = 128, K = 16) accumulating FP32 in tensor memory,
+ * tcgen05.ld epilogue with the same `mode`s.  K must be a multiple of 8 (no
+ * multiple of 32 needed: TMA zero-fills beyond K).  `error` (device int, may
+ * be NULL) is set nonzero if a pipeline wait gave up (bounded polling); the
+ * result is then invalid. */
+int pcv_gemm_bf16_tc(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int mode,
+                     const float* bias, float* outf, int ldo, void* outb, int ldob, const float* pre, int ldp,
+                     int* error, void* stream);
 /* out[C x R] = in[R x C]^T (bf16). */
 int pcv_transpose_bf16(const void* in, int R, int C, int ldi, void* out, int ldo, void* stream);
 /* db[n] = sum_m dY[m][n] (bf16 in, fp32 out, fixed summation order). */

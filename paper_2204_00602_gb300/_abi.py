@@ -66,6 +66,7 @@ SIGNATURES = {
     "pcv_distribution_static_max_bytes": (_i64, []),
     "pcv_amplitudes_multi": (_i, [_vp, _i, _i, _vp, _vp, _i64, _vp, _vp, _vp]),
     "pcv_gemm_bf16": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _i, _vp]),
+    "pcv_gemm_bf16_tc": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _i, _vp, _vp]),
     "pcv_transpose_bf16": (_i, [_vp, _i, _i, _i, _vp, _i, _vp]),
     "pcv_colsum_bf16": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     "pcv_phase_features": (_i, [_vp, _i, _i, _vp, _i, _vp]),
@@ -254,6 +255,11 @@ def pcv_amplitudes_multi(U, B, m, input_occ, output_occ, n_out, amp, prob, strea
 def pcv_gemm_bf16(A, lda, B, ldb, M, N, K, mode, bias, outf, ldo, outb, ldob, pre, ldp, stream):
     return _call("pcv_gemm_bf16", ptr(A), lda, ptr(B), ldb, M, N, K, mode, ptr(bias), ptr(outf), ldo, ptr(outb),
                  ldob, ptr(pre), ldp, stream)
+
+
+def pcv_gemm_bf16_tc(A, lda, B, ldb, M, N, K, mode, bias, outf, ldo, outb, ldob, pre, ldp, error, stream):
+    return _call("pcv_gemm_bf16_tc", ptr(A), lda, ptr(B), ldb, M, N, K, mode, ptr(bias), ptr(outf), ldo, ptr(outb),
+                 ldob, ptr(pre), ldp, ptr(error), stream)
 
 
 def pcv_transpose_bf16(inp, R, C, ldi, out, ldo, stream):

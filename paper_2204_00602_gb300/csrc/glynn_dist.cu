@@ -24,7 +24,7 @@
 //   row_sums_kernel  y_r(d) by Gray-code row-sum updates (one column per step)
 //   level_kernel     alpha/beta tables level by level: entry(P) = entry(P minus
 //                    its last mode) * y_last / sqrt(multiplicity)
-//   gemm_kernel      two launches over every k: a(S) = sum_d alpha_P beta_Q,
+//   gemm_kernel      one launch over every k: a(S) = sum_d alpha_P beta_Q,
 //                    written at the canonical index lowbase(P) + rank(Q)
 //
 // The canonical index of S (lexicographic order of the non-decreasing mode
@@ -186,13 +186,9 @@ struct GemmArgs {
     double* prob;
 };
 
-// A warp owns RF "fixed" entries (P if N >= M, else Q: the shorter side, so
-// the strip side fills whole warps) and its lanes own 4 strip entries each,
-// strided by 32 so loads and stores coalesce: an RF x 4 register tile of
-// outputs per thread, 3 accumulators each.  RF = 4 for the large levels (one
-// load per 3 DFMA and a quarter of the strip re-reads of RF = 1), RF = 1 for
-// levels whose fixed side has fewer than 32 entries.
-template <int RF>
+// A warp owns one "fixed" entry (P if N >= M, else Q: the shorter side, so
+// the strip side fills whole warps); its lanes own 4 strip entries each,
+// strided by 32 so loads and stores coalesce.
 __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs a)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -204,8 +200,8 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs a)
     const int64_t nfixed = qstrip ? M : N, nstrip = qstrip ? N : M;
     const int64_t strip_tiles = (nstrip + 32 * kStrip - 1) / (32 * kStrip);
     const int64_t lt = tile - a.tile0[k];
-    const int64_t fbase = (lt / strip_tiles) * (kWarps * RF) + (int64_t)warp * RF;
-    if (fbase >= nfixed) return;
+    const int64_t fixed = (lt / strip_tiles) * kWarps + warp;
+    if (fixed >= nfixed) return;
     const int64_t s0 = (lt % strip_tiles) * (32 * kStrip) + lane;
     const int b = blockIdx.y;
 
@@ -213,77 +209,52 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs a)
     const double* Sl = a.Slow + (size_t)b * a.tstride_low + a.lowoff[k];
     const double2* Th = a.Thigh + (size_t)b * a.tstride_high + a.highoff[k];
     const double* Sh = a.Shigh + (size_t)b * a.tstride_high + a.highoff[k];
-    const double2* __restrict__ F = qstrip ? Tl : Th;
-    const double* __restrict__ Fs = qstrip ? Sl : Sh;
+    const double2* __restrict__ F = qstrip ? Tl + fixed : Th + fixed;
+    const double* __restrict__ Fs = qstrip ? Sl + fixed : Sh + fixed;
     const double2* __restrict__ S = qstrip ? Th : Tl;
     const double* __restrict__ Ss = qstrip ? Sh : Sl;
     const int64_t wF = qstrip ? a.wlow : a.whigh;
     const int64_t wS = qstrip ? a.whigh : a.wlow;
 
-    int64_t fidx[RF], sidx[kStrip];
-    bool fv[RF], sv[kStrip];
-#pragma unroll
-    for (int r = 0; r < RF; ++r) {
-        fidx[r] = fbase + r;
-        fv[r] = fidx[r] < nfixed;
-        if (!fv[r]) fidx[r] = fbase;
-    }
+    int64_t sidx[kStrip], oidx[kStrip];
+    bool sv[kStrip];
 #pragma unroll
     for (int t = 0; t < kStrip; ++t) {
         sidx[t] = s0 + 32 * t;
         sv[t] = sidx[t] < nstrip;
         if (!sv[t]) sidx[t] = 0;
+        oidx[t] = qstrip ? a.lowbase[a.lowoff[k] + fixed] + sidx[t] : a.lowbase[a.lowoff[k] + sidx[t]] + fixed;
     }
-    double t1[RF][kStrip], t2[RF][kStrip], t3[RF][kStrip];
+    double t1[kStrip], t2[kStrip], t3[kStrip];
 #pragma unroll
-    for (int r = 0; r < RF; ++r)
-#pragma unroll
-        for (int t = 0; t < kStrip; ++t) t1[r][t] = t2[r][t] = t3[r][t] = 0.0;
+    for (int t = 0; t < kStrip; ++t) t1[t] = t2[t] = t3[t] = 0.0;
 
 #pragma unroll 2
     for (int q = 0; q < a.kc; ++q) {
-        const double2* __restrict__ Fq = F + (int64_t)q * wF;
-        const double* __restrict__ Fsq = Fs + (int64_t)q * wF;
+        const double2 f = __ldg(F + (int64_t)q * wF);
+        const double fs = __ldg(Fs + (int64_t)q * wF);
         const double2* __restrict__ Sq = S + (int64_t)q * wS;
         const double* __restrict__ Ssq = Ss + (int64_t)q * wS;
-        double2 f[RF], v[kStrip];
-        double fs[RF], vs[kStrip];
-#pragma unroll
-        for (int r = 0; r < RF; ++r) {
-            f[r] = __ldg(Fq + fidx[r]);
-            fs[r] = __ldg(Fsq + fidx[r]);
-        }
 #pragma unroll
         for (int t = 0; t < kStrip; ++t) {
-            v[t] = __ldg(Sq + sidx[t]);
-            vs[t] = __ldg(Ssq + sidx[t]);
+            const double2 v = __ldg(Sq + sidx[t]);
+            const double vs = __ldg(Ssq + sidx[t]);
+            t1[t] = fma(f.x, v.x, t1[t]);
+            t2[t] = fma(f.y, v.y, t2[t]);
+            t3[t] = fma(fs, vs, t3[t]);
         }
-#pragma unroll
-        for (int r = 0; r < RF; ++r)
-#pragma unroll
-            for (int t = 0; t < kStrip; ++t) {
-                t1[r][t] = fma(f[r].x, v[t].x, t1[r][t]);
-                t2[r][t] = fma(f[r].y, v[t].y, t2[r][t]);
-                t3[r][t] = fma(fs[r], vs[t], t3[r][t]);
-            }
     }
     double2* acc = a.acc ? a.acc + (size_t)b * a.out_stride : nullptr;
     double2* amp = a.amp ? a.amp + (size_t)b * a.out_stride : nullptr;
     double* prob = a.prob ? a.prob + (size_t)b * a.out_stride : nullptr;
 #pragma unroll
-    for (int r = 0; r < RF; ++r) {
-        if (!fv[r]) continue;
-        const int64_t fb = qstrip ? a.lowbase[a.lowoff[k] + fidx[r]] : 0;
-#pragma unroll
-        for (int t = 0; t < kStrip; ++t) {
-            if (!sv[t]) continue;
-            const int64_t o = qstrip ? fb + sidx[t] : a.lowbase[a.lowoff[k] + sidx[t]] + fidx[r];
-            double2 val = make_double2(t1[r][t] - t2[r][t], t3[r][t] - t1[r][t] - t2[r][t]);
-            if (!a.first) val = cadd(val, acc[o]);
-            if (!a.last) { acc[o] = val; continue; }
-            if (amp) amp[o] = val;
-            if (prob) prob[o] = fma(val.x, val.x, val.y * val.y);
-        }
+    for (int t = 0; t < kStrip; ++t) {
+        if (!sv[t]) continue;
+        double2 v = make_double2(t1[t] - t2[t], t3[t] - t1[t] - t2[t]);
+        if (!a.first) v = cadd(v, acc[oidx[t]]);
+        if (!a.last) { acc[oidx[t]] = v; continue; }
+        if (amp) amp[oidx[t]] = v;
+        if (prob) prob[oidx[t]] = fma(v.x, v.x, v.y * v.y);
     }
 }
 
@@ -393,43 +364,33 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
     const int64_t ystride = (int64_t)dp.kc * m;
     const int64_t tl_stride = (int64_t)dp.kc * dp.wlow, th_stride = (int64_t)dp.kc * dp.whigh;
 
-    // Two product launches: levels whose fixed side has >= 32 entries use
-    // RF = 4 register tiles, the skinny ones RF = 1.
-    GemmArgs g[2];
-    int64_t tiles[2] = {0, 0};
-    for (int v = 0; v < 2; ++v) {
-        GemmArgs& G = g[v];
-        G.Tlow = Tlow; G.Slow = Slow; G.Thigh = Thigh; G.Shigh = Shigh;
-        G.wlow = dp.wlow; G.whigh = dp.whigh;
-        G.tstride_low = tl_stride; G.tstride_high = th_stride;
-        G.lowbase = lowbase;
-        G.kc = dp.kc;
-        G.out_stride = dp.total;
-        G.acc = accbuf;
-        G.amp = amp;
-        G.prob = prob;
-        G.nk = 0;
-    }
+    GemmArgs g;
+    g.Tlow = Tlow; g.Slow = Slow; g.Thigh = Thigh; g.Shigh = Shigh;
+    g.wlow = dp.wlow; g.whigh = dp.whigh;
+    g.tstride_low = tl_stride; g.tstride_high = th_stride;
+    g.lowbase = lowbase;
+    g.kc = dp.kc;
+    g.out_stride = dp.total;
+    g.acc = accbuf;
+    g.amp = amp;
+    g.prob = prob;
+    g.nk = 0;
+    int64_t tiles = 0;
     for (int k = 0; k <= n; ++k) {
         const int64_t M = mset(dp.h, k), N = mset(m - dp.h, n - k);
         if (M == 0 || N == 0) continue;
         const bool qstrip = N >= M;
         const int64_t nstrip = qstrip ? N : M, nfixed = qstrip ? M : N;
-        const int v = 0;     // RF = 1 everywhere: RF = 4 measured slower (one block per SM at 254 registers)
-        const int rf = v ? 4 : 1;
-        GemmArgs& G = g[v];
-        G.lowoff[G.nk] = dp.lowoff[k];
-        G.highoff[G.nk] = dp.highoff[n - k];
-        G.M[G.nk] = M;
-        G.N[G.nk] = N;
-        G.tile0[G.nk] = tiles[v];
-        tiles[v] += ((nstrip + 32 * kStrip - 1) / (32 * kStrip)) * ((nfixed + kWarps * rf - 1) / (kWarps * rf));
-        G.nk++;
+        g.lowoff[g.nk] = dp.lowoff[k];
+        g.highoff[g.nk] = dp.highoff[n - k];
+        g.M[g.nk] = M;
+        g.N[g.nk] = N;
+        g.tile0[g.nk] = tiles;
+        tiles += ((nstrip + 32 * kStrip - 1) / (32 * kStrip)) * ((nfixed + kWarps - 1) / kWarps);
+        g.nk++;
     }
-    for (int v = 0; v < 2; ++v) {
-        g[v].tile0[g[v].nk] = tiles[v];
-        if (tiles[v] > INT32_MAX) return cudaErrorInvalidConfiguration;
-    }
+    g.tile0[g.nk] = tiles;
+    if (tiles > INT32_MAX) return cudaErrorInvalidConfiguration;
 
     for (int ch = 0; ch < nchunks; ++ch) {
         const int64_t d0 = (int64_t)ch * dp.kc;
@@ -473,15 +434,11 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
         }
         stage_end(kStageTables, s);
         stage_begin(kStageGemm, s);
-        for (int v = 0; v < 2; ++v) {
-            if (tiles[v] == 0) continue;
-            g[v].first = ch == 0;
-            g[v].last = ch == nchunks - 1;
-            if (v) gemm_kernel<4><<<dim3((unsigned)tiles[v], (unsigned)B), 256, 0, s>>>(g[v]);
-            else   gemm_kernel<1><<<dim3((unsigned)tiles[v], (unsigned)B), 256, 0, s>>>(g[v]);
-            note_launches(1);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
+        g.first = ch == 0;
+        g.last = ch == nchunks - 1;
+        gemm_kernel<<<dim3((unsigned)tiles, (unsigned)B), 256, 0, s>>>(g);
+        note_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         stage_end(kStageGemm, s);
     }
     return cudaSuccess;

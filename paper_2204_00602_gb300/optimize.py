@@ -109,7 +109,7 @@ def surrogate_loop(problem: MeshProblem, net: MLP, phases0: torch.Tensor, steps:
     net.predict_phases(warm)
     net.grad_phases(warm, dy)
     abi.pcv_exp_f32_to_f64(net.predict_phases(warm), B * problem.n_set, phat, problem.stream)
-    dist_stats(phat, phat)
+    dist_stats(phat, phat)[:, 1].cpu()
     exact_steps, checks, tvds = 0, 0, []
     use_exact_until = 0
     torch.cuda.synchronize()
@@ -120,7 +120,7 @@ def surrogate_loop(problem: MeshProblem, net: MLP, phases0: torch.Tensor, steps:
             _, p = problem.probs(phases)
             y = net.predict_phases(phases)
             abi.pcv_exp_f32_to_f64(y, y.numel(), phat, problem.stream)
-            tvd = float(dist_stats(p, phat)[:, 1].max().item())      # host read once per check
+            tvd = float(dist_stats(p, phat)[:, 1].cpu().numpy().max())   # host read once per check
             tvds.append(tvd)
             if tvd > tvd_tol:
                 use_exact_until = s + check_every
@@ -178,7 +178,7 @@ def run(samples: int, epochs: int, steps: int, B: int, seed: int = 2204006025, l
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     val_ph = torch.from_numpy(np.random.default_rng(seed + 30).uniform(0, 2 * np.pi, (B, problem.P))).to(problem.dev)
-    val_tvd = validate(net, problem, val_ph)
+    val_tvd = validate(net, problem, val_ph).cpu().numpy()
     phases0 = torch.from_numpy(np.random.default_rng(seed + 40).uniform(0, 2 * np.pi, (B, problem.P))).to(problem.dev)
     loss0 = problem.loss(phases0).clone()
     ph_e, wall_e = exact_loop(problem, phases0, steps)
@@ -188,10 +188,10 @@ def run(samples: int, epochs: int, steps: int, B: int, seed: int = 2204006025, l
     return {
         "samples": samples, "epochs": epochs, "steps": steps, "batch_phase_sets": B,
         "t_data_s": t_data, "t_train_s": t_train, "train_mse_per_epoch": losses,
-        "val_tvd_median": float(val_tvd.median().item()), "val_tvd_max": float(val_tvd.max().item()),
-        "loss_initial_mean": float(loss0.mean().item()),
-        "exact": {"wall_s": wall_e, "loss_mean": float(loss_e.mean().item())},
-        "surrogate": {"wall_s": wall_s, "loss_mean": float(loss_s.mean().item()), **info},
+        "val_tvd_median": float(np.median(val_tvd)), "val_tvd_max": float(val_tvd.max()),
+        "loss_initial_mean": float(loss0.cpu().numpy().mean()),
+        "exact": {"wall_s": wall_e, "loss_mean": float(loss_e.cpu().numpy().mean())},
+        "surrogate": {"wall_s": wall_s, "loss_mean": float(loss_s.cpu().numpy().mean()), **info},
         "speedup_wall": wall_e / wall_s,
     }
 

@@ -31,6 +31,7 @@ def test_exact_loop_descends_and_surrogate_steps_are_cheaper():
     _, wall_sur, info = opt.surrogate_loop(prob, net, ph0, 100, check_every=1000, tvd_tol=1e9)
     assert info["exact_steps"] == 0
     print(f"100 steps: exact {wall_exact:.3f} s, surrogate only {wall_sur:.3f} s")
+    assert wall_sur < wall_exact
     # with the 1e-3 tolerance the loop falls back to exact gradients when the
     # surrogate is off: the exact steps are counted and reported
     _, _, info = opt.surrogate_loop(prob, net, ph0, 100, check_every=50, tvd_tol=1e-3)
