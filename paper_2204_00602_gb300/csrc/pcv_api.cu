@@ -94,9 +94,12 @@ int auto_splits(int n, int64_t n_out)
 
 struct AmpChoice { int algo, param; };
 
-AmpChoice choose_amp(int n, int64_t n_out, int algo, int param)
+AmpChoice choose_amp(int m, int n, int64_t n_out, int algo, int param)
 {
     if (algo == PCV_ALGO_AUTO) {
+        // shared row sums when there are enough outputs to give every SM a tile
+        if (m <= pcv::tile_max_modes() && n >= 1 && n_out >= (int64_t)kSMs * (256 / pcv::tile_splits(n)))
+            return {PCV_ALGO_TILE, 0};
         if (n <= 12 || (n <= 16 && n_out >= (int64_t)kSMs * 256)) return {PCV_ALGO_GROUP, auto_group(n, n_out)};
         return {PCV_ALGO_BLOCK, auto_splits(n, n_out)};
     }
@@ -272,7 +275,7 @@ int64_t pcv_rank(int m, const uint8_t* occ)
 int64_t pcv_amplitudes_workspace(int m, int n, int64_t n_out)
 {
     if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS || n_out < 0) return fail(PCV_EINVAL, "bad sizes");
-    return amp_workspace(choose_amp(n, n_out, PCV_ALGO_AUTO, 0), n_out);
+    return amp_workspace(choose_amp(m, n, n_out, PCV_ALGO_AUTO, 0), n_out);
 }
 
 int pcv_amplitudes_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
@@ -295,7 +298,7 @@ int pcv_amplitudes_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                                                 (double2*)amp, prob, 1, s);
         return e == cudaSuccess ? PCV_OK : cuda_fail(e, "n0 kernel");
     }
-    AmpChoice c = choose_amp(p.n, n_out, algo, param);
+    AmpChoice c = choose_amp(m, p.n, n_out, algo, param);
     if ((rc = check_choice(c, p.n))) return rc;
     const int64_t need = amp_workspace(c, n_out);
     if (need > 0 && (!workspace || workspace_bytes < need))

@@ -137,6 +137,38 @@ def surrogate_loop(problem: MeshProblem, net: MLP, phases0: torch.Tensor, steps:
                           "min_tvd_seen": min(tvds), "tvd_tol": tvd_tol}
 
 
+def time_to_target(problem: MeshProblem, net: MLP, phases0: torch.Tensor, target: float, warm_steps: int,
+                   max_exact_steps: int, lr: float = 0.02, every: int = 25):
+    """Wall-clock until the mean exact loss over the batch reaches `target`:
+    `warm_steps` surrogate-only steps (0 = none), then exact steps, checking the
+    exact loss every `every` steps.  Returns (seconds, exact steps used, reached)."""
+    phases = phases0.clone()
+    B = phases.shape[0]
+    dy = torch.empty(B, problem.n_set, dtype=torch.bfloat16, device=phases.device)
+    abi.pcv_f32_to_bf16((-problem.q).to(torch.float32).repeat(B).contiguous(), B * problem.n_set, dy, problem.stream)
+    warm = phases0.clone()
+    problem.loss_and_grad(warm)
+    net.predict_phases(warm)
+    net.grad_phases(warm, dy)
+    problem.loss(warm).cpu()
+    opt = Adam64(phases, lr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(warm_steps):
+        net.predict_phases(phases)
+        opt.step(net.grad_phases(phases, dy))
+    opt = Adam64(phases, lr)                 # fresh moments for the exact phase
+    used = 0
+    while used < max_exact_steps:
+        if used % every == 0 and float(problem.loss(phases).cpu().numpy().mean()) <= target:
+            break
+        opt.step(problem.loss_and_grad(phases))
+        used += 1
+    reached = float(problem.loss(phases).cpu().numpy().mean()) <= target
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, used, reached
+
+
 def make_dataset(problem: MeshProblem, n_samples: int, seed: int):
     """Uniform phases and exact log-probabilities of the set (fp32)."""
     g = np.random.default_rng(seed)
@@ -152,7 +184,8 @@ def train(net: MLP, phases: torch.Tensor, targets: torch.Tensor, epochs: int, ba
         for s in range(0, n, batch):
             X = net.features(phases[s:s + batch])
             loss = net.train_step(X, targets[s:s + batch])
-        losses.append(float(loss.item()))
+        losses.append(float(loss.cpu().numpy()[0]))
+        net.check()
     return losses
 
 
@@ -185,7 +218,17 @@ def run(samples: int, epochs: int, steps: int, B: int, seed: int = 2204006025, l
     loss_e = problem.loss(ph_e).clone()
     ph_s, wall_s, info = surrogate_loop(problem, net, phases0, steps)
     loss_s = problem.loss(ph_s).clone()
+    # the same loop without the TVD gate: what the network alone achieves
+    ph_u, wall_u, info_u = surrogate_loop(problem, net, phases0, steps, check_every=steps + 1, tvd_tol=float("inf"))
+    loss_u = problem.loss(ph_u).clone()
+    # time to reach the exact loop's final loss: exact only vs surrogate warm start + exact
+    target = float(loss_e.cpu().numpy().mean())
+    tt = {}
+    for warm in (0, steps // 4, steps):
+        sec, used, ok = time_to_target(problem, net, phases0, target, warm, 4 * steps)
+        tt[f"warm_{warm}"] = {"seconds": sec, "exact_steps": used, "reached": ok}
     return {
+        "time_to_exact_final_loss": tt,
         "samples": samples, "epochs": epochs, "steps": steps, "batch_phase_sets": B,
         "t_data_s": t_data, "t_train_s": t_train, "train_mse_per_epoch": losses,
         "val_tvd_median": float(np.median(val_tvd)), "val_tvd_max": float(val_tvd.max()),
@@ -193,6 +236,9 @@ def run(samples: int, epochs: int, steps: int, B: int, seed: int = 2204006025, l
         "exact": {"wall_s": wall_e, "loss_mean": float(loss_e.cpu().numpy().mean())},
         "surrogate": {"wall_s": wall_s, "loss_mean": float(loss_s.cpu().numpy().mean()), **info},
         "speedup_wall": wall_e / wall_s,
+        "surrogate_ungated": {"wall_s": wall_u, "loss_mean": float(loss_u.cpu().numpy().mean()),
+                              "exact_steps": info_u["exact_steps"]},
+        "tensor_core": net.tensor_core,
     }
 
 

@@ -6,7 +6,9 @@ to 288) -> 1024 -> 1024 -> 1024 (GELU) -> 512.  Weights and activations are
 BF16, products accumulate in FP32 on the tensor cores, master weights and
 Adam state are FP32.  Every step (features, GEMMs with fused bias/GELU,
 transposes, bias gradients, MSE, Adam) runs in the library's kernels; torch
-only owns the buffers.
+only owns the buffers.  The GEMMs run on the 5th-generation tensor cores
+(tcgen05 + TMEM, TMA-staged operands) by default; `tensor_core="mma_sync"`
+selects the warp-level mma.sync kernel.
 
 Training data come from the exact kernels: U(phi) by the mesh kernel, then the
 512 amplitudes per phase set by the shared-row-sum tile kernel.
@@ -54,8 +56,12 @@ def init_weights(seed: int, dims=DIMS, n_features: int = 2 * P_MESH + 1):
 class MLP:
     """Device-resident surrogate network with Adam state."""
 
-    def __init__(self, Ws, bs, device="cuda", lr=1e-3, betas=(0.9, 0.999), eps=1e-8):
+    def __init__(self, Ws, bs, device="cuda", lr=1e-3, betas=(0.9, 0.999), eps=1e-8, tensor_core: str = "tcgen05"):
         self.dev = torch.device(device)
+        if tensor_core not in ("tcgen05", "mma_sync"):
+            raise ValueError("tensor_core must be 'tcgen05' or 'mma_sync'")
+        self.tensor_core = tensor_core
+        self.error = torch.zeros(1, dtype=torch.int32, device=self.dev)
         self.L = len(Ws)
         self.dims = [Ws[0].shape[1]] + [W.shape[0] for W in Ws]
         self.W = [torch.from_numpy(np.ascontiguousarray(W, np.float32)).to(self.dev) for W in Ws]
@@ -90,6 +96,21 @@ class MLP:
             self._bufs[name] = t
         return t
 
+    def gemm(self, A, lda, B, ldb, M, N, K, mode, bias, outf, ldo, outb, ldob, pre, ldp):
+        """C = A B^T with a fused epilogue on the BF16 tensor cores (tcgen05 by default)."""
+        if self.tensor_core == "tcgen05":
+            abi.pcv_gemm_bf16_tc(A, lda, B, ldb, M, N, K, mode, bias, outf, ldo, outb, ldob, pre, ldp, self.error,
+                                 self.stream)
+        else:
+            abi.pcv_gemm_bf16(A, lda, B, ldb, M, N, K, mode, bias, outf, ldo, outb, ldob, pre, ldp, self.stream)
+
+    def check(self):
+        """Raise if a tcgen05 pipeline wait gave up since the last check (host sync)."""
+        code = int(self.error.cpu().numpy()[0])
+        if code:
+            self.error.zero_()
+            raise RuntimeError(f"tcgen05 GEMM pipeline wait gave up (code {code})")
+
     def features(self, phases: torch.Tensor) -> torch.Tensor:
         B = phases.shape[0]
         X = self._buf("X", (B, self.dims[0]), torch.bfloat16)
@@ -107,13 +128,13 @@ class MLP:
             if l + 1 < self.L:
                 pre = self._buf(f"pre{l}", (B, o), torch.float32)
                 out = self._buf(f"act{l}", (B, o), torch.bfloat16)
-                abi.pcv_gemm_bf16(h, i, self.Wb[l], i, B, o, i, 1, self.b[l], pre, o, out, o, None, 0, self.stream)
+                self.gemm(h, i, self.Wb[l], i, B, o, i, 1, self.b[l], pre, o, out, o, None, 0)
                 self.pres.append(pre)
                 self.acts.append(out)
                 h = out
             else:
                 y = self._buf("y", (B, o), torch.float32)
-                abi.pcv_gemm_bf16(h, i, self.Wb[l], i, B, o, i, 2, self.b[l], y, o, None, 0, None, 0, self.stream)
+                self.gemm(h, i, self.Wb[l], i, B, o, i, 2, self.b[l], y, o, None, 0, None, 0)
                 return y
         raise RuntimeError("no layers")
 
@@ -134,18 +155,17 @@ class MLP:
                 abi.pcv_transpose_bf16(dY, B, o, o, dYT, B, self.stream)
                 abi.pcv_transpose_bf16(self.acts[l], B, i, i, XT, B, self.stream)
                 gW = self._buf(f"gW{l}", (o, i), torch.float32)
-                abi.pcv_gemm_bf16(dYT, B, XT, B, o, i, B, 0, None, gW, i, None, 0, None, 0, self.stream)
+                self.gemm(dYT, B, XT, B, o, i, B, 0, None, gW, i, None, 0, None, 0)
                 gb = self._buf(f"gb{l}", (o,), torch.float32)
                 abi.pcv_colsum_bf16(dY, B, o, o, gb, self.stream)
                 self.gW[l], self.gb[l] = gW, gb
             if l > 0:
                 dprev = self._buf(f"dY{l - 1}", (B, i), torch.bfloat16)
-                abi.pcv_gemm_bf16(dY, o, self.WTb[l], o, B, i, o, 3, None, None, 0, dprev, i, self.pres[l - 1], i,
-                                  self.stream)
+                self.gemm(dY, o, self.WTb[l], o, B, i, o, 3, None, None, 0, dprev, i, self.pres[l - 1], i)
                 dY = dprev
             elif want_input_grad:
                 dX0 = self._buf("dX0", (B, i), torch.float32)
-                abi.pcv_gemm_bf16(dY, o, self.WTb[0], o, B, i, o, 0, None, dX0, i, None, 0, None, 0, self.stream)
+                self.gemm(dY, o, self.WTb[0], o, B, i, o, 0, None, dX0, i, None, 0, None, 0)
         return dX0
 
     def adam_step(self):
@@ -194,10 +214,10 @@ class MLP:
         torch.save(self.state_dict(), f)
 
     @classmethod
-    def load(cls, f, device="cuda"):
+    def load(cls, f, device="cuda", tensor_core: str = "tcgen05"):
         sd = torch.load(f, map_location="cpu")
         net = cls([w.numpy() for w in sd["W"]], [b.numpy() for b in sd["b"]], device, sd["lr"], tuple(sd["betas"]),
-                  sd["eps"])
+                  sd["eps"], tensor_core)
         for dst, src in ((net.mW, sd["mW"]), (net.vW, sd["vW"]), (net.mb, sd["mb"]), (net.vb, sd["vb"])):
             for d, s in zip(dst, src):
                 d.copy_(s.to(net.dev))

@@ -104,14 +104,18 @@ def test_small_kernels(pcv):
     assert np.array_equal(to64(wb), ref.bf16(w.cpu().numpy()))
 
 
-def _net(pcv, seed=21, lr=1e-3):
+def _net(pcv, seed=21, lr=1e-3, tc="tcgen05"):
     from paper_2204_00602_gb300 import surrogate
     Ws, bs = surrogate.init_weights(seed)
-    return surrogate, surrogate.MLP(Ws, bs, lr=lr), Ws, bs
+    return surrogate, surrogate.MLP(Ws, bs, lr=lr, tensor_core=tc), Ws, bs
 
 
-def test_mlp_forward_backward_layer_by_layer(pcv):
-    surrogate, net, Ws, bs = _net(pcv)
+TC = pytest.mark.parametrize("tc", ["tcgen05", "mma_sync"])
+
+
+@TC
+def test_mlp_forward_backward_layer_by_layer(pcv, tc):
+    surrogate, net, Ws, bs = _net(pcv, tc=tc)
     B = 256
     ph = torch.from_numpy(pin.mesh_phases(B, 132, 22)).cuda()
     X = net.features(ph)
@@ -147,8 +151,9 @@ def test_mlp_forward_backward_layer_by_layer(pcv):
             assert np.all(np.abs(net._bufs["dX0"].cpu().numpy() - dX) <= ref.gemm_error_bound(dY, Wr[0].T, 512) + 1e-9)
 
 
-def test_mlp_training_reduces_loss_and_resumes_bitwise(pcv):
-    surrogate, net, Ws, bs = _net(pcv, lr=1e-3)
+@TC
+def test_mlp_training_reduces_loss_and_resumes_bitwise(pcv, tc):
+    surrogate, net, Ws, bs = _net(pcv, lr=1e-3, tc=tc)
     B = 512
     g = np.random.default_rng(30)
     ph = torch.from_numpy(pin.mesh_phases(B, 132, 31)).cuda()
@@ -157,27 +162,30 @@ def test_mlp_training_reduces_loss_and_resumes_bitwise(pcv):
     losses = [net.train_step(X, tgt).item() for _ in range(40)]
     assert losses[-1] < 0.2 * losses[0]
     # checkpoint / resume: k steps + save/load + j steps == k + j steps
-    _, a, _, _ = _net(pcv, seed=40)
-    _, b, _, _ = _net(pcv, seed=40)
+    _, a, _, _ = _net(pcv, seed=40, tc=tc)
+    _, b, _, _ = _net(pcv, seed=40, tc=tc)
     for _ in range(5):
         a.train_step(X, tgt)
         b.train_step(X, tgt)
     f = io.BytesIO()
     b.save(f)
     f.seek(0)
-    c = surrogate.MLP.load(f)
+    c = surrogate.MLP.load(f, tensor_core=tc)
     for _ in range(4):
         a.train_step(X, tgt)
         c.train_step(X, tgt)
     torch.cuda.synchronize()
     for wa, wc in zip(a.W, c.W):
         assert torch.equal(wa, wc)
+    for n_ in (net, a, c):
+        n_.check()
 
 
-def test_phase_gradient_of_the_surrogate(pcv):
-    # d(sum y)/dphi through the network against central differences of the
-    # GPU forward (bf16 rounding makes the function piecewise; use a coarse step)
-    surrogate, net, Ws, bs = _net(pcv, seed=50)
+@TC
+def test_phase_gradient_of_the_surrogate(pcv, tc):
+    # d(sum y)/dphi through the network against central differences of an FP64
+    # evaluation of the same BF16 weights (no activation rounding)
+    surrogate, net, Ws, bs = _net(pcv, seed=50, tc=tc)
     ph = pin.mesh_phases(2, 132, 51)
     phd = torch.from_numpy(ph).cuda()
     net.predict_phases(phd)
