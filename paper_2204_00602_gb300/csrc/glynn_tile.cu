@@ -22,7 +22,7 @@ namespace pcv {
 
 // Splits per block as a function of n: more sign-vector parallelism for
 // larger permanents, whole tiles of 256 outputs for small ones.
-__host__ __device__ inline int tile_splits(int n)
+__host__ __device__ int tile_splits(int n)
 {
     if (n <= 10) return 1;
     if (n <= 13) return 2;
