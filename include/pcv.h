@@ -274,7 +274,7 @@ int pcv_gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, 
                   const float* bias, float* outf, int ldo, void* outb, int ldob, const float* pre, int ldp,
                   void* stream);
 /* The same product on the 5th-generation tensor cores: TMA loads of 128 x 64
- * bf16 tiles (128-byte swizzle) into a 4-stage shared-memory ring,
+ * bf16 tiles (128-byte swizzle) into a 3-stage shared-memory ring,
  * tcgen05.mma (M = N = 128, K = 16) accumulating FP32 in tensor memory,
  * tcgen05.ld epilogue with the same `mode`s.  K must be a multiple of 8 (no
  * multiple of 32 needed: TMA zero-fills beyond K).  `error` (device int, may

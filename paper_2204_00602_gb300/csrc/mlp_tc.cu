@@ -6,13 +6,16 @@
 //
 // One CTA computes a 128 x 128 tile with 128 threads:
 //   thread 0    TMA producer: 64-wide K blocks of A and B (128B swizzle) into a
-//               4-stage shared-memory ring, completion tracked by mbarriers;
+//               3-stage shared-memory ring, completion tracked by mbarriers;
 //   thread 32   MMA issuer: tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128,
 //               K=16) from shared-memory descriptors into a 128-column TMEM
 //               accumulator; tcgen05.commit frees each stage and finally
 //               signals the epilogue;
 //   all warps   epilogue: warp w reads TMEM lanes 32w..32w+31 (rows) with
-//               tcgen05.ld.32x32b and writes its rows.
+//               tcgen05.ld.32x32b, turns each 32 x 32 block around in shared
+//               memory and stores it row-contiguously.
+// Three stages (97 KB of shared memory) let two CTAs share an SM, so one
+// CTA's epilogue overlaps the other's main loop.
 // Out-of-range rows, columns and K are zero-filled by TMA and skipped on
 // store.  Every mbarrier wait gives up after a bounded number of polls and
 // raises an error flag the host reads; TMEM is always released.
@@ -30,7 +33,7 @@ namespace pcv {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;   // 97 KB: two CTAs per SM
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_STAGE_BYTES = (TC_BM + TC_BN) * TC_BK * 2;     // 32 KB per stage
 constexpr uint32_t TC_TMEM_COLS = 128;
@@ -117,7 +120,7 @@ __device__ __forceinline__ float gelu_grad_tc(float x)
     return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
 gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const TcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -199,7 +202,9 @@ gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     __syncwarp();
     if (ok) {
-        const int row = m0 + warp * 32 + lane;
+        // Each warp moves its 32 rows x 32 columns through a padded shared tile
+        // (the drained stage ring) so that global stores are row-contiguous.
+        float* stage = reinterpret_cast<float*>(ring) + warp * (32 * 33);
 #pragma unroll 1
         for (int c0 = 0; c0 < TC_BN; c0 += 32) {
             uint32_t r[32];
@@ -214,12 +219,16 @@ gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            if (row < a.M) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col >= a.N) continue;
-                    float x = __uint_as_float(r[j]);
+            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);   // row = lane
+            __syncwarp();
+            const int col = n0 + c0 + lane;
+            if (col < a.N) {
+#pragma unroll 4
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int row = m0 + warp * 32 + rr;
+                    if (row >= a.M) break;
+                    float x = stage[rr * 33 + lane];
                     switch (a.mode) {
                     case 0: a.outf[(size_t)row * a.ldo + col] = x; break;
                     case 2: a.outf[(size_t)row * a.ldo + col] = x + a.bias[col]; break;
@@ -235,6 +244,7 @@ gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                     }
                 }
             }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
