@@ -36,9 +36,10 @@ def workload_text(m, n, count):
             "outputs, complex FP64 amplitudes and probabilities")
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2, written between timed steps
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture, or None
-# when no capture of the current kernel exists.
-NCU_TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) of one launch of the dominant kernel, m=20 n=10,
+# from one ncu capture of the current kernel (dram__bytes_read.sum 15.49 GB +
+# dram__bytes_write.sum 0.51 GB); None when no capture of the current kernel exists.
+NCU_TRAFFIC_PER_LAUNCH = 16.00e9
 
 
 def parse():
@@ -57,6 +58,28 @@ def parse():
     global M, N_PH
     M, N_PH = args.m, args.n
     return args
+
+
+def rank_unitary_seed(rank: int) -> int:
+    """Each rank simulates its own Haar unitary (independent problems, weak scaling)."""
+    import pcv_inputs as pin
+    return pin.BASE_SEED + 2 + 1000 * rank
+
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    """Slowest rank's time: the only collective of the multi-GPU bench."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.cpu().numpy()[0])
+
+
+def whole_job_rate(units_per_rank_step: int, steps: int, world: int, seconds: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return units_per_rank_step * steps * world / seconds
 
 
 def dist_env():
@@ -153,7 +176,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
 
-    U_h = pin.haar_unitary(M, pin.BASE_SEED + 2 + 1000 * rank)
+    U_h = pin.haar_unitary(M, rank_unitary_seed(rank))
     t = pin.single_photon_input(M, N_PH)
     Ntot = pcv.num_outputs(M, N_PH)
     algo = pcv.PCV_ALGO_FACTOR if args.algo == "factor" else pcv.PCV_ALGO_GROUP
@@ -208,13 +231,10 @@ def run_ours(args):
     abi.pcv_profile_enable(False)
     stages = abi.pcv_profile_read()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_dev = sum(step_ms) / 1e3
+    t_dev = max_over_ranks(sum(step_ms) / 1e3, world, dev)
     if world > 1:
-        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(tt.item())
         torch.distributed.barrier()
-    value = Ntot * args.steps * world / t_dev
+    value = whole_job_rate(Ntot, args.steps, world, t_dev)
 
     # ---------------- end to end through the public API with host buffers
     e2e = None
@@ -241,12 +261,8 @@ def run_ours(args):
             e2e_step()
         ee.record(stream)
         torch.cuda.synchronize()
-        te = es.elapsed_time(ee) / 1e3
-        if world > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": Ntot * args.steps * world / te, "unit": "amplitudes/s",
+        te = max_over_ranks(es.elapsed_time(ee) / 1e3, world, dev)
+        e2e = {"value": whole_job_rate(Ntot, args.steps, world, te), "unit": "amplitudes/s",
                "h2d_bytes_per_step": U_pin.numel() * 16,
                "d2h_bytes_per_step": prob_h.numel() * 8 + amp_h.numel() * 16}
 
@@ -273,7 +289,7 @@ def run_ours(args):
             "frac": achieved / peak_tflops if achieved else None,
             "peak_source": f"derived: {sms} SMs x 2 DFMA/clk x 2 flop x {sm_max:.0f} MHz (FP64 ALU)",
             "fp64_probe_tflops": probe_tflops,
-            "traffic": NCU_TRAFFIC_PER_LAUNCH,
+            "traffic": NCU_TRAFFIC_PER_LAUNCH if (M, N_PH, args.algo) == (20, 10, "factor") else None,
             "launches_per_step": launches_per_call,
             "stage_ms_per_step": {k: (v[0] / v[1] if v[1] else None) for k, v in stages.items()}}
 
