@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="factor", choices=["factor", "group"])
+    ap.add_argument("--algo", default="factor", choices=["factor", "group", "slos"],
+                    help="factor: factorised Glynn (default); group: plain Glynn; slos: state expansion")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -179,8 +180,8 @@ def run_ours(args):
     U_h = pin.haar_unitary(M, rank_unitary_seed(rank))
     t = pin.single_photon_input(M, N_PH)
     Ntot = pcv.num_outputs(M, N_PH)
-    algo = pcv.PCV_ALGO_FACTOR if args.algo == "factor" else pcv.PCV_ALGO_GROUP
-    param = 0 if args.algo == "factor" else 32
+    algo = {"factor": pcv.PCV_ALGO_FACTOR, "group": pcv.PCV_ALGO_GROUP, "slos": pcv.PCV_ALGO_SLOS}[args.algo]
+    param = 32 if args.algo == "group" else 0
     U = torch.from_numpy(U_h).to(dev)
     prob = torch.empty(Ntot, dtype=torch.float64, device=dev)
     amp = torch.empty(Ntot, dtype=torch.complex128, device=dev)
@@ -279,12 +280,21 @@ def run_ours(args):
         flops_per_call = Ntot * (2 ** (N_PH - 1)) * 6     # 3 DFMA per output and sign vector
         kname = "gemm_kernel (factorised Glynn products, 3 DFMA per output and sign vector)"
         launches_per_call = 1
-    else:
+    elif args.algo == "group":
         ms, calls = stages["glynn_plain"]
         flops_per_call = Ntot * (2 ** (N_PH - 1)) * (8 * N_PH - 4)
         kname = "glynn_group_kernel<10,32> (plain Glynn)"
         launches_per_call = 1
-    achieved = flops_per_call * calls / (ms * 1e-3) / 1e12 if ms > 0 else None
+    else:
+        # state expansion: one complex multiply-add (8 flops) per state and distinct occupied mode;
+        # counted exactly over every level
+        ms, calls = stages["glynn_plain"]
+        # multisets of size k over M modes with d distinct modes: C(M, d) C(k-1, d-1)
+        flops_per_call = sum(8 * d * math.comb(M, d) * math.comb(k - 1, d - 1)
+                             for k in range(1, N_PH + 1) for d in range(1, min(k, M) + 1))
+        kname = "slos_level_kernel (state expansion)"
+        launches_per_call = N_PH
+    achieved = flops_per_call * calls / (ms * 1e-3) / 1e12 if ms > 0 and flops_per_call else None
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops if achieved else None,
             "peak_source": f"derived: {sms} SMs x 2 DFMA/clk x 2 flop x {sm_max:.0f} MHz (FP64 ALU)",
@@ -292,6 +302,24 @@ def run_ours(args):
             "traffic": NCU_TRAFFIC_PER_LAUNCH if (M, N_PH, args.algo) == (20, 10, "factor") else None,
             "launches_per_step": launches_per_call,
             "stage_ms_per_step": {k: (v[0] / v[1] if v[1] else None) for k, v in stages.items()}}
+
+    # context: the same workload by photon-by-photon state expansion (not the Glynn path)
+    alt = None
+    if args.algo == "factor" and not args.no_e2e:
+        ws_s = pcv.workspace(pcv.distribution_workspace_bytes(M, N_PH, pcv.PCV_ALGO_SLOS), dev)
+        for _ in range(2):
+            pcv.distribution(U, t, algo=pcv.PCV_ALGO_SLOS, ws=ws_s, out=(prob, amp))
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            pcv.distribution(U, t, algo=pcv.PCV_ALGO_SLOS, ws=ws_s, out=(prob, amp))
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = a0.elapsed_time(a1) / args.steps
+        alt = {"algo": "state expansion (pcv_distribution_slos)", "ms_per_step": ms_s,
+               "value": Ntot / (ms_s * 1e-3), "unit": "amplitudes/s", "note": "context only; not the Glynn path"}
+        del ws_s
 
     cpu = None
     if not args.no_cpu and (world == 1 or rank == 0):
@@ -305,6 +333,7 @@ def run_ours(args):
         "config": {"workload": workload_text(M, N_PH, Ntot), "m": M, "n": N_PH, "outputs": Ntot, "algo": args.algo,
                    "l2": "flushed between steps (256 MiB write, untimed)", "parallelism": f"replicas{world}"},
         "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        "state_expansion": alt,
         "wall_s_timed_region": wall,
     }
     print(json.dumps(line), flush=True)

@@ -92,6 +92,7 @@ enum {
     PCV_ALGO_BLOCK = 2,   /* plain Glynn, one block (x splits) per permanent, n <= 30   */
     PCV_ALGO_FACTOR = 3,  /* factorised Glynn sum over the whole output space           */
     PCV_ALGO_TILE = 4,    /* shared row sums, one block per tile of outputs, m <= 128   */
+    PCV_ALGO_SLOS = 5,    /* full distribution by photon-by-photon state expansion      */
 };
 
 /* Workspace bytes pcv_amplitudes needs for these sizes (0 if none). */
@@ -184,9 +185,22 @@ int pcv_distribution_batched(const pcv_c64* U, int B, int m, const uint8_t* inpu
                              double* prob, pcv_c64* amp,
                              void* workspace, int64_t workspace_bytes, void* stream);
 
+/* Full distributions by photon-by-photon state expansion, the computation the
+ * paper's SLOS back-end unfolds (Sec. 3.2.3: O(n C(m+n-1, n)) time and
+ * memory).  Photons are created one at a time:
+ *     B_k(s) = sum_{r: s_r >= 1} U[r][c_k] sqrt(s_r) B_{k-1}(s - e_r),  B_0 = 1,
+ * and a(S) = B_n(S) / sqrt(prod t!) gives Eq. eqperm's amplitudes in canonical
+ * order; level k keeps C(m+k-1, k) complex values.  Layouts as
+ * pcv_distribution_batched (U [B][m][m], outputs [B][C(m+n-1,n)]). */
+int64_t pcv_distribution_slos_workspace(int B, int m, int n);
+int pcv_distribution_slos(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
+                          double* prob, pcv_c64* amp,
+                          void* workspace, int64_t workspace_bytes, void* stream);
+
 /* pcv_distribution with an explicit algorithm: PCV_ALGO_FACTOR (param
  * ignored), PCV_ALGO_GROUP (param = threads per permanent; unranks each
- * output), PCV_ALGO_BLOCK (param = blocks per permanent). */
+ * output), PCV_ALGO_BLOCK (param = blocks per permanent), PCV_ALGO_SLOS
+ * (state expansion; workspace of pcv_distribution_slos_workspace(1, m, n)). */
 int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                         double* prob, pcv_c64* amp, int algo, int param,
                         void* workspace, int64_t workspace_bytes, void* stream);

@@ -30,6 +30,7 @@ PCV_ALGO_GROUP = 1
 PCV_ALGO_BLOCK = 2
 PCV_ALGO_FACTOR = 3
 PCV_ALGO_TILE = 4
+PCV_ALGO_SLOS = 5
 PCV_MAX_PHOTONS = 30
 PCV_MAX_MODES = 1024
 
@@ -53,6 +54,8 @@ SIGNATURES = {
     "pcv_distribution_ex": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _vp, _i64, _vp]),
     "pcv_distribution_batched_workspace": (_i64, [_i, _i, _i]),
     "pcv_distribution_batched": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "pcv_distribution_slos_workspace": (_i64, [_i, _i, _i]),
+    "pcv_distribution_slos": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
     "pcv_amplitudes_backward": (_i, [_vp, _i, _vp, _vp, _i64, _vp, _vp, _vp]),
     "pcv_distribution_backward_workspace": (_i64, [_i, _i]),
     "pcv_distribution_backward": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
@@ -310,6 +313,15 @@ def pcv_adam_f64(w, m, v, g, count, lr, beta1, beta2, eps, step, stream):
 def pcv_amplitudes_backward_multi(U, B, m, input_occ, output_occ, n_out, grad_amp, grad_U, stream):
     return _call("pcv_amplitudes_backward_multi", ptr(U), B, m, ptr(input_occ), ptr(output_occ), n_out,
                  ptr(grad_amp), ptr(grad_U), stream)
+
+
+def pcv_distribution_slos_workspace(B, m, n) -> int:
+    return _call("pcv_distribution_slos_workspace", B, m, n)
+
+
+def pcv_distribution_slos(U, B, m, input_occ, prob, amp, workspace, workspace_bytes, stream):
+    return _call("pcv_distribution_slos", ptr(U), B, m, ptr(input_occ), ptr(prob), ptr(amp), ptr(workspace),
+                 workspace_bytes, stream)
 
 
 def pcv_fp64_probe(out, blocks, threads, iters, stream):

@@ -466,10 +466,53 @@ int pcv_distribution_batched(const pcv_c64* U, int B, int m, const uint8_t* inpu
     return e == cudaSuccess ? PCV_OK : cuda_fail(e, "factorised distribution");
 }
 
+int64_t pcv_distribution_slos_workspace(int B, int m, int n)
+{
+    if (B < 1 || m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "bad sizes");
+    if (msets(m, n) < 0) return fail(PCV_ERANGE, "output space too large");
+    const int64_t r = pcv::slos_workspace(B, m, n);
+    return r < 0 ? fail(PCV_ERANGE, "workspace size overflows") : r;
+}
+
+int pcv_distribution_slos(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
+                          double* prob, pcv_c64* amp,
+                          void* workspace, int64_t workspace_bytes, void* stream)
+{
+    pcv::Plan p;
+    int rc = make_plan(U, m, input_occ, &p);
+    if (rc) return rc;
+    if (B < 1 || B > 65535) return fail(PCV_EINVAL, "batch %d outside [1, 65535]", B);
+    if (!amp && !prob) return fail(PCV_EINVAL, "amp and prob are both NULL");
+    if (amp && !aligned(amp, 16)) return fail(PCV_EINVAL, "amp is not 16-byte aligned");
+    if (prob && !aligned(prob, 8)) return fail(PCV_EINVAL, "prob is not 8-byte aligned");
+    const int64_t N = msets(m, p.n);
+    if (N < 0 || (N + 255) / 256 > INT32_MAX) return fail(PCV_ERANGE, "output space C(%d,%d) too large", m + p.n - 1, p.n);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p.n == 0) {
+        for (int b = 0; b < B; ++b) {
+            cudaError_t e = pcv::launch_glynn_group(p, (const double2*)U, nullptr, nullptr, 0, 1,
+                                                    amp ? (double2*)amp + b : nullptr, prob ? prob + b : nullptr, 1, s);
+            if (e != cudaSuccess) return cuda_fail(e, "n0 kernel");
+        }
+        return PCV_OK;
+    }
+    const int64_t need = pcv::slos_workspace(B, m, p.n);
+    if (need < 0) return fail(PCV_ERANGE, "workspace size overflows");
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(PCV_ENOMEM, "workspace of %lld bytes (256-byte aligned) needed, %lld given", (long long)need,
+                    (long long)workspace_bytes);
+    pcv::stage_begin(pcv::kStagePlain, s);
+    cudaError_t e = pcv::launch_slos(p, B, (const double2*)U, prob, (double2*)amp, workspace, s);
+    pcv::stage_end(pcv::kStagePlain, s);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "state expansion");
+}
+
 int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                         double* prob, pcv_c64* amp, int algo, int param,
                         void* workspace, int64_t workspace_bytes, void* stream)
 {
+    if (algo == PCV_ALGO_SLOS)
+        return pcv_distribution_slos(U, 1, m, input_occ, prob, amp, workspace, workspace_bytes, stream);
     if (algo == PCV_ALGO_AUTO || algo == PCV_ALGO_FACTOR)
         return pcv_distribution_batched(U, 1, m, input_occ, prob, amp, workspace, workspace_bytes, stream);
     pcv::Plan p;

@@ -139,6 +139,10 @@ cudaError_t launch_kl_grad(const double* p, const double* q, const double2* amp,
                            const double* bscale, double scale, double2* grad, cudaStream_t s);
 cudaError_t launch_prob_grad(const double* gp, const double2* amp, int64_t count, double2* gamp, cudaStream_t s);
 
+// Photon-by-photon state expansion (slos.cu)
+int64_t slos_workspace(int B, int m, int n);
+cudaError_t launch_slos(const Plan& p, int B, const double2* U, double* prob, double2* amp, void* ws, cudaStream_t s);
+
 // Factorised full distribution (glynn_dist.cu)
 struct DistPlan {
     int h;                    // modes [0,h) are the low side, [h,m) the high side

@@ -359,3 +359,46 @@ def test_batched_distribution(pcv):
     prob2, _ = pcv.distribution_batched(dev(Us), t, want_amp=False, ws=ws)
     torch.cuda.synchronize()
     assert torch.allclose(prob2, prob, rtol=1e-12, atol=1e-18)
+
+
+# ------------------------------------- state expansion (SLOS-style) path
+
+
+@pytest.mark.parametrize("m,n,t", [(6, 3, None), (12, 6, None), (9, 5, [2, 0, 1, 0, 0, 1, 0, 1, 0]),
+                                   (5, 7, [3, 1, 0, 2, 1]), (1, 4, [4]), (7, 1, None), (11, 2, None)])
+def test_state_expansion_matches_oracle(pcv, m, n, t):
+    U = pin.haar_unitary(m, 1800 + m + n)
+    t = pin.single_photon_input(m, n) if t is None else np.array(t, np.uint8)
+    p_ref, a_ref = oracle.distribution(U, t)
+    prob, amp = pcv.distribution(dev(U), t, algo=pcv.PCV_ALGO_SLOS)
+    torch.cuda.synchronize()
+    assert amp_err(amp.cpu().numpy(), a_ref, m, n) <= tol(n)
+    assert oracle.tvd(prob.cpu().numpy(), p_ref) <= 1e-12
+
+
+def test_state_expansion_m20_n10_and_batch(pcv):
+    m, n = 20, 10
+    U = pin.haar_unitary(m, pin.BASE_SEED + 2)
+    t = pin.single_photon_input(m, n)
+    prob, amp = pcv.distribution(dev(U), t, algo=pcv.PCV_ALGO_SLOS)
+    torch.cuda.synchronize()
+    assert abs(prob.sum().item() - 1.0) < 1e-12
+    rng = np.random.default_rng(6)
+    idx = np.unique(np.concatenate([[0, prob.numel() - 1], rng.integers(0, prob.numel(), 800)]))
+    occ = np.stack([pcv.unrank(m, n, int(i)) for i in idx])
+    a_ref = oracle.amplitudes(U, t, occ)
+    assert amp_err(amp[torch.from_numpy(idx).cuda()].cpu().numpy(), a_ref, m, n) <= tol(n)
+    # batch of three unitaries through the C ABI
+    B, m2, n2 = 3, 10, 5
+    Us = np.stack([pin.haar_unitary(m2, 1900 + b) for b in range(B)])
+    t2 = pin.single_photon_input(m2, n2)
+    N = math.comb(m2 + n2 - 1, n2)
+    p2 = torch.empty(B * N, dtype=torch.float64, device="cuda")
+    a2 = torch.empty(B * N, dtype=torch.complex128, device="cuda")
+    wsb = pcv.abi.pcv_distribution_slos_workspace(B, m2, n2)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    pcv.abi.pcv_distribution_slos(dev(Us), B, m2, t2, p2, a2, ws, wsb, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for b in range(B):
+        p_ref, a_ref = oracle.distribution(Us[b], t2)
+        assert amp_err(a2[b * N:(b + 1) * N].cpu().numpy(), a_ref, m2, n2) <= tol(n2)
