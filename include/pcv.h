@@ -212,6 +212,24 @@ int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
 int pcv_amplitudes_multi(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
                          const uint8_t* output_occ, int64_t n_out, pcv_c64* amp, double* prob, void* stream);
 
+/* ------------------------------------------------------------- sampling */
+
+/* Exact boson sampling: `count` independent output states drawn from P(S)
+ * (Eq. eqperm), by the algorithm of the paper's CliffordClifford2017 back-end
+ * (Sec. 3.2.3): with the input photons' columns of U in a random order,
+ * photon k lands in mode i with weight
+ *     | sum_{l<k} U[i][c_l] Perm(U[r_1..r_{k-1}; c_0..c_{k-1} without c_l]) |^2,
+ * the k leave-one-out permanents computed together by one Glynn sum.
+ *   U         device, m*m pcv_c64; m <= 128
+ *   input_occ host, m uint8; 1 <= n <= 16 photons
+ *   perm      device, count*n uint8: a permutation of 0..n-1 per sample
+ *   uniforms  device, count*n doubles in [0, 1): one per photon and sample
+ *   samples   device, count*m uint8 occupations (written)
+ * The random numbers are inputs: a sample is a deterministic function of
+ * (U, input, perm, uniforms). */
+int pcv_sample(const pcv_c64* U, int m, const uint8_t* input_occ, const uint8_t* perm, const double* uniforms,
+               int64_t count, uint8_t* samples, void* stream);
+
 /* ------------------------------------------------------------ gradients */
 
 /* dL/dU from dL/da for explicit outputs of one U (n <= 8).

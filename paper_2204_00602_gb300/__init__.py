@@ -17,7 +17,7 @@ from . import _abi as abi
 from ._abi import (PCV_ALGO_AUTO, PCV_ALGO_BLOCK, PCV_ALGO_FACTOR, PCV_ALGO_GROUP,  # noqa: F401
                    PCV_ALGO_SLOS, PCV_ALGO_TILE, PCV_MAX_MODES, PCV_MAX_PHOTONS, PcvError)
 
-__all__ = ["amplitudes", "amplitudes_batched", "BatchPlan", "distribution", "distribution_batched", "num_outputs", "unrank", "rank",
+__all__ = ["amplitudes", "amplitudes_batched", "BatchPlan", "distribution", "distribution_batched", "sample", "num_outputs", "unrank", "rank",
            "fp64_probe", "PcvError", "PCV_ALGO_AUTO", "PCV_ALGO_GROUP", "PCV_ALGO_BLOCK", "PCV_ALGO_FACTOR",
            "PCV_ALGO_TILE", "PCV_ALGO_SLOS", "abi"]
 
@@ -201,6 +201,17 @@ def distribution_batched(U: torch.Tensor, input_occ, *, want_amp: bool = True, w
         ws = workspace(abi.pcv_distribution_batched_workspace(B, m, n), U.device)
     abi.pcv_distribution_batched(U, B, m, t, prob, amp, ws, 0 if ws is None else ws.numel(), _stream(U.device))
     return prob, amp
+
+
+def sample(U: torch.Tensor, input_occ, perm: torch.Tensor, uniforms: torch.Tensor) -> torch.Tensor:
+    """Exact boson samples (uint8 occupations [count, m]); perm uint8 [count, n]
+    and uniforms float64 [count, n] on the device carry the randomness."""
+    m = _check_U(U)
+    t = _host_occ(input_occ, m)
+    count = perm.shape[0]
+    out = torch.empty(count, m, dtype=torch.uint8, device=U.device)
+    abi.pcv_sample(U.contiguous(), m, t, perm.contiguous(), uniforms.contiguous(), count, out, _stream(U.device))
+    return out
 
 
 def fp64_probe(blocks: int, threads: int, iters: int, device="cuda") -> torch.Tensor:

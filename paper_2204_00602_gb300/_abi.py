@@ -84,6 +84,7 @@ SIGNATURES = {
     "pcv_adam_f64": (_i, [_vp, _vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                           ctypes.c_double, _i, _vp]),
     "pcv_amplitudes_backward_multi": (_i, [_vp, _i, _i, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "pcv_sample": (_i, [_vp, _i, _vp, _vp, _vp, _i64, _vp, _vp]),
     "pcv_fp64_probe": (_i, [_vp, _i, _i, _i, _vp]),
     "pcv_amplitudes_batched_workspace": (_i64, [_i, _i64]),
     "pcv_amplitudes_batched": (_i, [_vp, _i, _i64, _vp, _i64, _vp]),
@@ -322,6 +323,10 @@ def pcv_distribution_slos_workspace(B, m, n) -> int:
 def pcv_distribution_slos(U, B, m, input_occ, prob, amp, workspace, workspace_bytes, stream):
     return _call("pcv_distribution_slos", ptr(U), B, m, ptr(input_occ), ptr(prob), ptr(amp), ptr(workspace),
                  workspace_bytes, stream)
+
+
+def pcv_sample(U, m, input_occ, perm, uniforms, count, samples, stream):
+    return _call("pcv_sample", ptr(U), m, ptr(input_occ), ptr(perm), ptr(uniforms), count, ptr(samples), stream)
 
 
 def pcv_fp64_probe(out, blocks, threads, iters, stream):

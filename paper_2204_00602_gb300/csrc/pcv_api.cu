@@ -622,6 +622,27 @@ int pcv_distribution_backward(const pcv_c64* U, int B, int m, const uint8_t* inp
     return e == cudaSuccess ? PCV_OK : cuda_fail(e, "distribution adjoint");
 }
 
+// ----------------------------------------------------------- sampling
+
+int pcv_sample(const pcv_c64* U, int m, const uint8_t* input_occ, const uint8_t* perm, const double* uniforms,
+               int64_t count, uint8_t* samples, void* stream)
+{
+    pcv::Plan p;
+    int rc = make_plan(U, m, input_occ, &p);
+    if (rc) return rc;
+    if (m > 128) return fail(PCV_EINVAL, "sampler supports m <= 128 (m=%d)", m);
+    if (p.n < 1 || p.n > 16) return fail(PCV_EINVAL, "sampler supports 1 <= n <= 16 (n=%d)", p.n);
+    if (count < 0) return fail(PCV_EINVAL, "count < 0");
+    if (count == 0) return PCV_OK;
+    if (!perm || !uniforms || !samples) return fail(PCV_EINVAL, "NULL sample buffer");
+    if ((count + 3) / 4 > INT32_MAX) return fail(PCV_ERANGE, "too many samples for one launch");
+    cudaStream_t s = (cudaStream_t)stream;
+    pcv::stage_begin(pcv::kStagePlain, s);
+    cudaError_t e = pcv::launch_sampler(p, (const double2*)U, perm, uniforms, count, samples, s);
+    pcv::stage_end(pcv::kStagePlain, s);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "sampler");
+}
+
 // --------------------------------------------------------------- mesh
 
 int pcv_mesh_unitary(const double* phases, int B, int m, pcv_c64* U, void* stream)

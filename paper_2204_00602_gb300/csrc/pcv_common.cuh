@@ -139,6 +139,10 @@ cudaError_t launch_kl_grad(const double* p, const double* q, const double2* amp,
                            const double* bscale, double scale, double2* grad, cudaStream_t s);
 cudaError_t launch_prob_grad(const double* gp, const double2* amp, int64_t count, double2* gamp, cudaStream_t s);
 
+// Exact boson sampling (sampler.cu)
+cudaError_t launch_sampler(const Plan& p, const double2* U, const uint8_t* perm, const double* uni, int64_t count,
+                           uint8_t* out, cudaStream_t s);
+
 // Photon-by-photon state expansion (slos.cu)
 int64_t slos_workspace(int B, int m, int n);
 cudaError_t launch_slos(const Plan& p, int B, const double2* U, double* prob, double2* amp, void* ws, cudaStream_t s);

@@ -3,6 +3,8 @@
     python -m paper_2204_00602_gb300.workloads batched [--circuits 512] [--outputs 4096]
     python -m paper_2204_00602_gb300.workloads sweep [--nmin 16] [--nmax 30] [--outputs 256]
     python -m paper_2204_00602_gb300.workloads mesh   [--batch 64]
+    python -m paper_2204_00602_gb300.workloads sample [--m 60] [--n 14] [--samples 200000]
+    python -m paper_2204_00602_gb300.workloads pk [--unitaries 300] [--samples 20000]
 
 batched: uneven circuits (m ~ U{8..64}, n ~ U{4..min(24, m)}, Haar U, photons in
 modes 0..n-1, 4096 seeded random outputs each, collision-free for n <= 16) in
@@ -116,9 +118,66 @@ def mesh(batch: int, steps: int = 20):
             "ms_per_step": sec * 1e3, "amplitudes_per_s_forward": batch * N / sec}
 
 
+def sampling(m: int, n: int, count: int):
+    """Exact boson samples per second (the paper's Boson-sampling benchmark shape
+    is n=14 photons in m=60 modes)."""
+    from . import sample
+    U = torch.from_numpy(pin.haar_unitary(m, SEED + 60)).cuda()
+    t = pin.single_photon_input(m, n)
+    perm, uni = pin.sampler_randomness(count, n, SEED + 61)
+    perm_d, uni_d = torch.from_numpy(perm).cuda(), torch.from_numpy(uni).cuda()
+    sample(U, t, perm_d[:256], uni_d[:256])
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    sample(U, t, perm_d, uni_d)
+    b.record()
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    return {"workload": f"exact boson sampling n={n} m={m} (Haar U, photons in modes 0..{n - 1})",
+            "samples": count, "seconds": sec, "samples_per_s": count / sec}
+
+
+def pk_table(m: int, n: int, n_unitaries: int, samples_per_u: int):
+    """The paper's partial-certificate experiment (Sec. 4.2, Table figtablebs) on
+    synthetic Haar unitaries: estimate P(K), the probability that all n photons
+    leave in the first K modes, from exact samples of each unitary, average over
+    the unitaries, and set it beside Eq. eqhaarpk's Haar average."""
+    from . import sample
+    Ks = (30, 40, 50, 55, 57)
+    est = {K: [] for K in Ks}
+    t = pin.single_photon_input(m, n)
+    t0 = time.perf_counter()
+    gpu_s = 0.0
+    for u in range(n_unitaries):
+        U = torch.from_numpy(pin.haar_unitary(m, SEED + 10_000 + u)).cuda()
+        perm, uni = pin.sampler_randomness(samples_per_u, n, SEED + 20_000 + u)
+        a, b = _events()
+        a.record()
+        s = sample(U, t, torch.from_numpy(perm).cuda(), torch.from_numpy(uni).cuda())
+        b.record()
+        occ = s.cpu().numpy()
+        gpu_s += a.elapsed_time(b) / 1e3
+        for K in Ks:
+            est[K].append(np.mean(occ[:, K:].sum(axis=1) == 0))
+    wall = time.perf_counter() - t0
+    rows = []
+    for K in Ks:
+        e = np.array(est[K])
+        haar = float(np.prod([(K + i) / (m + i) for i in range(n)]))
+        rows.append({"K": K, "estimate_pct": 100 * e.mean(), "std_over_unitaries_pct": 100 * e.std(),
+                     "stderr_of_mean_pct": 100 * e.std() / math.sqrt(len(e)), "haar_average_pct": 100 * haar})
+    return {"workload": f"P(K) for n={n} m={m}: {n_unitaries} Haar unitaries x {samples_per_u} exact samples",
+            "gpu_sampling_s": gpu_s, "wall_s": wall, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["batched", "sweep", "mesh"])
+    ap.add_argument("which", choices=["batched", "sweep", "mesh", "sample", "pk"])
+    ap.add_argument("--unitaries", type=int, default=300)
+    ap.add_argument("--m", type=int, default=60)
+    ap.add_argument("--n", type=int, default=14)
+    ap.add_argument("--samples", type=int, default=200_000)
     ap.add_argument("--circuits", type=int, default=512)
     ap.add_argument("--outputs", type=int, default=None)
     ap.add_argument("--nmin", type=int, default=16)
@@ -129,8 +188,12 @@ def main():
         r = batched(a.circuits, a.outputs or 4096)
     elif a.which == "sweep":
         r = sweep(a.nmin, a.nmax, a.outputs or 256)
-    else:
+    elif a.which == "mesh":
         r = mesh(a.batch)
+    elif a.which == "sample":
+        r = sampling(a.m, a.n, a.samples)
+    else:
+        r = pk_table(a.m, a.n, a.unitaries, a.samples)
     print(json.dumps(r), flush=True)
 
 

@@ -118,3 +118,11 @@ def batched_circuits(n_circ: int, m_lo: int, m_hi: int, n_lo: int, n_hi: int,
             outputs=random_outputs(m, n, outputs_per_circ, seed + 5000 + c),
         ))
     return circs
+
+
+def sampler_randomness(count: int, n: int, seed: int):
+    """(perm uint8[count, n], uniforms float64[count, n]): a uniform random
+    permutation of the n photons and one uniform number per photon per sample."""
+    g = rng(seed)
+    perm = np.argsort(g.random((count, n)), axis=1).astype(np.uint8)
+    return perm, g.random((count, n))
