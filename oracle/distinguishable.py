@@ -4,9 +4,10 @@ TEST INFRASTRUCTURE ONLY (same rule as the rest of ``oracle/``): the tests,
 ``__graft_entry__.smoke()`` and the bench's CPU legs are the only callers; the
 CUDA library shares nothing with this file.
 
-The paper lets its source emit photons of imperfect indistinguishability
-(Sec. 2.3 and the HOM experiment of Sec. 4.1) but prints no formula for it.
-Two models are written here from the physics.
+The paper's Processor takes a source with a transmittance and an
+indistinguishability (Sec. processors, "Processors"), and its Hong-Ou-Mandel
+experiment (Sec. hom) simulates such a source, but the paper prints no
+formula for either. The models below are written from the physics.
 
 Photon classes.  The input photons are split into classes. Photons of one
 class are identical. Photons of different classes are perfectly
@@ -127,3 +128,36 @@ def source_distribution(U, input_occ, q: float) -> np.ndarray:
             p = w * class_distribution(U, classes_for_noisy(input_occ, set(noisy)))
             total = p if total is None else total + p
     return total
+
+
+def lossy_source_distribution(U, input_occ, eta: float, q: float) -> np.ndarray:
+    """Photon-number-resolved distribution of a lossy, partially
+    distinguishable source: each photon independently is absent (probability
+    1 - eta), pure (eta q) or noisy (eta (1 - q)).  The pure photons form one
+    class, every noisy photon a class of its own (module docstring).
+
+    Returns P over S_{m,0}, S_{m,1}, ..., S_{m,n} concatenated in that order,
+    each block in canonical order; the blocks sum to 1 together."""
+    U = np.asarray(U, dtype=np.complex128)
+    m = U.shape[0]
+    modes = photon_modes(input_occ)
+    n = len(modes)
+    blocks = [np.zeros(math.comb(m + k - 1, k)) for k in range(n + 1)]
+    for state in itertools.product(range(3), repeat=n):       # 0 absent, 1 pure, 2 noisy
+        w = 1.0
+        for st in state:
+            w *= (1.0 - eta) if st == 0 else (eta * q if st == 1 else eta * (1.0 - q))
+        if w == 0.0:
+            continue
+        pure = np.zeros(m, dtype=np.uint8)
+        classes = []
+        for k, st in enumerate(state):
+            if st == 1:
+                pure[modes[k]] += 1
+            elif st == 2:
+                e = np.zeros(m, dtype=np.uint8)
+                e[modes[k]] = 1
+                classes.append(e)
+        kept = sum(1 for st in state if st != 0)
+        blocks[kept] += w * class_distribution(U, [pure] + classes)
+    return np.concatenate(blocks)

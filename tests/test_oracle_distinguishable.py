@@ -88,3 +88,42 @@ def test_mixed_classes_sum_to_one_and_are_symmetric_in_class_order():
     q = od.class_distribution(U, [c3, c1, c2])
     assert abs(p.sum() - 1.0) <= 1e-14
     assert np.max(np.abs(p - q)) <= 1e-15
+
+
+def test_lossy_source_photon_number_is_binomial():
+    # the photon number of the kept light is Binomial(n, eta) whatever the
+    # interferometer and the distinguishability
+    m = 4
+    U = pin.haar_unitary(m, 5006)
+    t = np.array([1, 1, 1, 0], np.uint8)
+    for eta, q in ((0.8, 1.0), (0.5, 0.6), (1.0, 0.3)):
+        p = od.lossy_source_distribution(U, t, eta, q)
+        off = 0
+        for k in range(4):
+            N = math.comb(m + k - 1, k)
+            want = math.comb(3, k) * eta ** k * (1 - eta) ** (3 - k)
+            assert abs(p[off:off + N].sum() - want) <= 1e-14, (eta, q, k)
+            off += N
+        assert off == p.shape[0]
+
+
+def test_lossless_source_block_is_the_lossless_mixture():
+    m = 4
+    U = pin.haar_unitary(m, 5007)
+    t = np.array([1, 0, 1, 1], np.uint8)
+    p = od.lossy_source_distribution(U, t, 1.0, 0.55)
+    N3 = math.comb(m + 2, 3)
+    assert np.max(np.abs(p[-N3:] - od.source_distribution(U, t, 0.55))) <= 1e-15
+    assert np.all(p[:-N3] == 0)
+
+
+def test_lossy_hom():
+    # two photons, each kept with probability eta, on a 50:50 beam splitter:
+    # coincidence eta^2 (1 - V)/2 with V = q^2; one photon left: eta (1 - eta)
+    # in total, split evenly between the two modes
+    eta, q = 0.7, 0.8
+    p = od.lossy_source_distribution(BS, np.array([1, 1], np.uint8), eta, q)
+    # blocks: S_{2,0} (1), S_{2,1} (2), S_{2,2} (3)
+    assert abs(p[0] - (1 - eta) ** 2) <= 1e-15
+    assert np.allclose(p[1:3], [eta * (1 - eta)] * 2, atol=1e-15)
+    assert abs(p[4] - eta ** 2 * (1 - q * q) / 2) <= 1e-15
