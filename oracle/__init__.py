@@ -7,8 +7,9 @@ seeded input generator ``pcv_inputs``.
 
 Contents
 --------
-* ``perm_leibniz``, ``perm_ryser``: the permanent by its definition and by
-  Ryser's formula (plain C, ``pcv_oracle.c``).
+* ``perm_leibniz``, ``perm_ryser``, ``perm_ryser_dd``: the permanent by its
+  definition, by Ryser's formula, and by Ryser's formula in double-double
+  arithmetic (plain C, ``pcv_oracle.c``).
 * ``amplitude``, ``amplitudes``, ``distribution``: Eq. eqperm over explicit
   outputs or the whole output space S_{m,n} in canonical order.
 * ``enumerate_outputs``, ``num_outputs``: canonical order = lexicographic
@@ -56,6 +57,7 @@ def _L():
             u8 = ctypes.POINTER(ctypes.c_uint8)
             lib.oracle_perm_leibniz.argtypes = [ctypes.c_int, dp, dp]
             lib.oracle_perm_ryser.argtypes = [ctypes.c_int, dp, dp]
+            lib.oracle_perm_ryser_dd.argtypes = [ctypes.c_int, dp, dp]
             lib.oracle_amplitude.argtypes = [ctypes.c_int, dp, u8, u8, ctypes.c_int, dp]
             lib.oracle_amplitudes.argtypes = [ctypes.c_int, dp, u8, u8, ctypes.c_int64, ctypes.c_int, dp]
             lib.oracle_num_outputs.argtypes = [ctypes.c_int, ctypes.c_int]
@@ -106,6 +108,20 @@ def perm_ryser(A) -> complex:
     return complex(out[0], out[1])
 
 
+def perm_ryser_dd(A) -> complex:
+    """Ryser's formula evaluated in double-double arithmetic (about 106 bits),
+    for sizes where the plain double sum loses digits to cancellation."""
+    A = _cmat(A)
+    n = A.shape[0]
+    assert A.shape == (n, n) and n <= 40
+    out = np.zeros(2)
+    _L().oracle_perm_ryser_dd(n, _dp(A), _dp(out))
+    return complex(out[0], out[1])
+
+
+_METHODS = {"ryser": 0, "leibniz": 1, "ryser_dd": 2}
+
+
 def amplitude(U, input_occ, output_occ, method: str = "ryser") -> complex:
     """a(S) = Perm(U_{T,S}) / sqrt(prod s! prod t!) (Eq. eqperm)."""
     U = _cmat(U)
@@ -113,7 +129,7 @@ def amplitude(U, input_occ, output_occ, method: str = "ryser") -> complex:
     t = np.ascontiguousarray(input_occ, dtype=np.uint8)
     s = np.ascontiguousarray(output_occ, dtype=np.uint8)
     out = np.zeros(2)
-    _L().oracle_amplitude(m, _dp(U), _u8(t), _u8(s), 1 if method == "leibniz" else 0, _dp(out))
+    _L().oracle_amplitude(m, _dp(U), _u8(t), _u8(s), _METHODS[method], _dp(out))
     return complex(out[0], out[1])
 
 
@@ -125,7 +141,7 @@ def amplitudes(U, input_occ, outputs, method: str = "ryser") -> np.ndarray:
     s = np.ascontiguousarray(outputs, dtype=np.uint8).reshape(-1, m)
     amp = np.zeros(s.shape[0], dtype=np.complex128)
     _L().oracle_amplitudes(m, _dp(U), _u8(t), _u8(s), s.shape[0],
-                           1 if method == "leibniz" else 0, _dp(amp.view(np.float64)))
+                           _METHODS[method], _dp(amp.view(np.float64)))
     return amp
 
 

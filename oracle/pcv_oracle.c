@@ -13,7 +13,7 @@
  *     a(S) = Perm(U_{T,S}) / sqrt(s_1! ... s_m! t_1! ... t_m!)
  * and P(S) = |a(S)|^2.
  *
- * The permanent is computed two independent ways:
+ * The permanent is computed three ways:
  *   - Leibniz: the definition, sum over all n! permutations (small n only);
  *   - Ryser's formula (Sec. 3.2.3 names Ryser's and Glynn's algorithms):
  *       Perm(A) = (-1)^n sum_{S subset of columns} (-1)^{|S|} prod_i sum_{j in S} a_ij.
@@ -21,9 +21,11 @@
  *     differ by one column (the usual way Ryser's formula is evaluated); the
  *     row sums are recomputed from scratch at the start of every block of
  *     2^RYSER_BLOCK_BITS subsets so rounding does not drift, and the terms are
- *     added with Neumaier compensated summation.
+ *     added with Neumaier compensated summation;
+ *   - the same Ryser sum in double-double arithmetic, for n >= 20 where the
+ *     plain double sum loses digits to cancellation.
  *
- * Everything is plain IEEE double; compile without -ffast-math and with
+ * Everything is plain IEEE double (double-double is built from doubles); compile without -ffast-math and with
  * -ffp-contract=off.
  */
 #include <complex.h>
@@ -125,6 +127,120 @@ void oracle_perm_ryser(int n, const double* A_ri, double* out_ri)
     out_ri[1] = im.s + im.c;
 }
 
+/* -------------------------------------------------- Ryser, double-double */
+
+/*
+ * The same Ryser sum with every quantity held as an unevaluated sum of two
+ * doubles, hi + lo (about 106 bits).  Ryser's terms can exceed the
+ * permanent by many orders of magnitude, so in plain double the sum loses
+ * digits (at n = 24, Ryser on A and on A^T can disagree in the 7th digit);
+ * here the rounding error is ~1e-32 of the largest term.  The operations are
+ * the published error-free transformations: Knuth's TwoSum (TAOCP Vol. 2,
+ * Sec. 4.2.2) and Dekker's product with the exact remainder from a correctly
+ * rounded fma, combined as in Dekker (1971) / Bailey's double-double
+ * arithmetic.  Only IEEE double operations and fma() are used.
+ */
+typedef struct { double hi, lo; } dd;
+typedef struct { dd re, im; } ddc;
+
+static dd dd_two_sum(double a, double b)
+{
+    double s = a + b;
+    double bb = s - a;
+    double e = (a - (s - bb)) + (b - bb);
+    dd r = {s, e};
+    return r;
+}
+
+static dd dd_fast_two_sum(double a, double b)   /* needs |a| >= |b| or a == 0 */
+{
+    double s = a + b;
+    dd r = {s, b - (s - a)};
+    return r;
+}
+
+static dd dd_add(dd a, dd b)
+{
+    dd s = dd_two_sum(a.hi, b.hi);
+    dd t = dd_two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = dd_fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return dd_fast_two_sum(s.hi, s.lo);
+}
+
+static dd dd_neg(dd a) { dd r = {-a.hi, -a.lo}; return r; }
+
+static dd dd_mul(dd a, dd b)
+{
+    double p = a.hi * b.hi;
+    double e = fma(a.hi, b.hi, -p);          /* exact remainder of the product */
+    e += a.hi * b.lo + a.lo * b.hi;
+    return dd_fast_two_sum(p, e);
+}
+
+static ddc ddc_add(ddc a, ddc b) { ddc r = {dd_add(a.re, b.re), dd_add(a.im, b.im)}; return r; }
+
+static ddc ddc_mul(ddc a, ddc b)
+{
+    ddc r = {dd_add(dd_mul(a.re, b.re), dd_neg(dd_mul(a.im, b.im))),
+             dd_add(dd_mul(a.re, b.im), dd_mul(a.im, b.re))};
+    return r;
+}
+
+static ddc ddc_from(cplx z) { ddc r = {{creal(z), 0.0}, {cimag(z), 0.0}}; return r; }
+
+static ddc ryser_block_dd(int n, const cplx* A, uint64_t k0, uint64_t k1)
+{
+    ddc rs[64];
+    const ddc zero = {{0.0, 0.0}, {0.0, 0.0}};
+    uint64_t g = k0 ^ (k0 >> 1);
+    for (int i = 0; i < n; ++i) {
+        rs[i] = zero;
+        for (int j = 0; j < n; ++j)
+            if (g & (1ull << j)) rs[i] = ddc_add(rs[i], ddc_from(A[i * n + j]));
+    }
+    ddc acc = zero;
+    for (uint64_t k = k0; k < k1; ++k) {
+        if (k != k0) {
+            uint64_t gk = k ^ (k >> 1);
+            int j = __builtin_ctzll(k);
+            int add = (gk & (1ull << j)) != 0;
+            for (int i = 0; i < n; ++i) rs[i] = ddc_add(rs[i], ddc_from(add ? A[i * n + j] : -A[i * n + j]));
+            g = gk;
+        }
+        if (g == 0) continue;
+        ddc prod = rs[0];
+        for (int i = 1; i < n; ++i) prod = ddc_mul(prod, rs[i]);
+        int size = __builtin_popcountll(g);
+        if (((n - size) & 1) != 0) { prod.re = dd_neg(prod.re); prod.im = dd_neg(prod.im); }
+        acc = ddc_add(acc, prod);
+    }
+    return acc;
+}
+
+/* Ryser's formula in double-double; the result rounded to double. */
+void oracle_perm_ryser_dd(int n, const double* A_ri, double* out_ri)
+{
+    const cplx* A = (const cplx*)A_ri;
+    if (n == 0) { out_ri[0] = 1.0; out_ri[1] = 0.0; return; }
+    uint64_t total = 1ull << n;
+    uint64_t bs = (n > RYSER_BLOCK_BITS) ? (1ull << RYSER_BLOCK_BITS) : total;
+    int64_t nblocks = (int64_t)(total / bs);
+    ddc* part = (ddc*)malloc(sizeof(ddc) * (size_t)nblocks);
+#ifdef _OPENMP
+    int par = !omp_in_parallel() && nblocks >= 4;
+#pragma omp parallel for schedule(dynamic, 1) if (par)
+#endif
+    for (int64_t b = 0; b < nblocks; ++b)
+        part[b] = ryser_block_dd(n, A, (uint64_t)b * bs, (uint64_t)(b + 1) * bs);
+    ddc acc = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int64_t b = 0; b < nblocks; ++b) acc = ddc_add(acc, part[b]);
+    free(part);
+    out_ri[0] = acc.re.hi + acc.re.lo;
+    out_ri[1] = acc.im.hi + acc.im.lo;
+}
+
 /* --------------------------------------------------------- Eq. eqperm */
 
 static double factorial(int k)
@@ -160,7 +276,8 @@ static double occ_norm(int m, const uint8_t* in_occ, const uint8_t* out_occ)
     return 1.0 / sqrt(d);
 }
 
-/* a(S) for one output.  method: 0 = Ryser, 1 = Leibniz.  Different photon
+/* a(S) for one output.  method: 0 = Ryser, 1 = Leibniz, 2 = Ryser in
+ * double-double.  Different photon
  * numbers give 0 (linear optics conserves photon number). */
 void oracle_amplitude(int m, const double* U_ri, const uint8_t* in_occ, const uint8_t* out_occ,
                       int method, double* out_ri)
@@ -170,8 +287,9 @@ void oracle_amplitude(int m, const double* U_ri, const uint8_t* in_occ, const ui
     int n = build_submatrix(m, U, in_occ, out_occ, A);
     if (n < 0) { out_ri[0] = out_ri[1] = 0.0; return; }
     double p[2];
-    if (method == 1) oracle_perm_leibniz(n, (const double*)A, p);
-    else             oracle_perm_ryser(n, (const double*)A, p);
+    if (method == 1)      oracle_perm_leibniz(n, (const double*)A, p);
+    else if (method == 2) oracle_perm_ryser_dd(n, (const double*)A, p);
+    else                  oracle_perm_ryser(n, (const double*)A, p);
     double nrm = occ_norm(m, in_occ, out_occ);
     out_ri[0] = p[0] * nrm;
     out_ri[1] = p[1] * nrm;

@@ -121,6 +121,39 @@ def test_ryser_laplace_expansion_across_block_boundary():
     assert rel(oracle.perm_ryser(A), want) < 1e-10
 
 
+@pytest.mark.parametrize("n", range(1, 10))
+def test_ryser_double_double_matches_leibniz(n):
+    for seed in range(3):
+        A = pin.random_complex_matrix(n, n, 700 + 10 * n + seed)
+        assert rel(oracle.perm_ryser_dd(A), oracle.perm_leibniz(A)) < 1e-14
+
+
+def test_ryser_double_double_closed_forms():
+    n = 20
+    assert oracle.perm_ryser_dd(np.eye(n)) == 1.0
+    g = np.random.default_rng(711)
+    d = np.exp(1j * g.uniform(0, 2 * np.pi, n)) * g.uniform(0.5, 1.5, n)
+    assert rel(oracle.perm_ryser_dd(np.diag(d)), np.prod(d)) < 1e-15
+    u = np.exp(1j * g.uniform(0, 2 * np.pi, n)) * g.uniform(0.9, 1.1, n)
+    v = np.exp(1j * g.uniform(0, 2 * np.pi, n)) * g.uniform(0.9, 1.1, n)
+    assert rel(oracle.perm_ryser_dd(np.outer(u, v)), math.factorial(n) * np.prod(u) * np.prod(v)) < 1e-14
+
+
+def test_ryser_double_double_is_self_consistent_under_cancellation():
+    # a bunched n = 22 submatrix of a Haar unitary: the amplitude is ~1e4
+    # below Ryser's largest terms.  Transpose and Laplace expansion along a
+    # row must agree to double precision (the plain double sum does not).
+    m, n = 40, 22
+    U = pin.haar_unitary(m, 721)
+    s = pin.random_bunched_outputs(m, n, 1, 722)[0]
+    rows = np.repeat(np.arange(m), s.astype(int))
+    A = U[np.ix_(rows, np.arange(n))]
+    p = oracle.perm_ryser_dd(A)
+    assert rel(oracle.perm_ryser_dd(A.T.copy()), p) < 1e-14
+    lap = sum(A[0, j] * oracle.perm_ryser_dd(np.delete(np.delete(A, 0, 0), j, 1)) for j in range(n))
+    assert rel(lap, p) < 1e-14
+
+
 # -------------------------------------------------------- amplitudes
 
 
