@@ -93,6 +93,7 @@ enum {
     PCV_ALGO_FACTOR = 3,  /* factorised Glynn sum over the whole output space           */
     PCV_ALGO_TILE = 4,    /* shared row sums, one block per tile of outputs, m <= 128   */
     PCV_ALGO_SLOS = 5,    /* full distribution by photon-by-photon state expansion      */
+    PCV_ALGO_MULT = 6,    /* Glynn's sum with multiplicities, a warp (or more) per permanent */
 };
 
 /* Workspace bytes pcv_amplitudes needs for these sizes (0 if none). */
@@ -110,7 +111,12 @@ int64_t pcv_amplitudes_workspace(int m, int n, int64_t n_out);
  * The permanent is Glynn's formula, Perm(A) = 2^{-(n-1)} sum over sign
  * vectors d with d_1 = +1 of (prod_k d_k) prod_i sum_j d_j a_ij, with the
  * sign vectors visited in reflected Gray-code order so each step updates the
- * row sums by one column (Sec. 3.2.3 names Glynn's algorithm). */
+ * row sums by one column (Sec. 3.2.3 names Glynn's algorithm).  The kernel
+ * is chosen from m, n and n_out: with m <= 128 and enough outputs to fill
+ * the GPU, the shared-row-sum tile kernel (n <= 12), or for n >= 13 a
+ * per-output choice between the tile kernel and Glynn's sum with
+ * multiplicities (PCV_ALGO_MULT below), whichever issues fewer FP64
+ * instructions for that output; otherwise the plain Glynn kernels. */
 int pcv_amplitudes(const pcv_c64* U, int m, const uint8_t* input_occ,
                    const uint8_t* output_occ, int64_t n_out,
                    pcv_c64* amp, double* prob,
@@ -118,13 +124,28 @@ int pcv_amplitudes(const pcv_c64* U, int m, const uint8_t* input_occ,
 
 /* pcv_amplitudes with an explicit algorithm: algo = PCV_ALGO_GROUP with
  * `param` threads per permanent (1, 2, 4, 8, 16 or 32), PCV_ALGO_BLOCK with
- * `param` blocks per permanent (>= 1), or PCV_ALGO_TILE (m <= 128; the row
+ * `param` blocks per permanent (>= 1), PCV_ALGO_TILE (m <= 128; the row
  * sums y_r(d) = sum_j d_j U[r][c_j] of each sign vector are formed once per
- * block and shared by its 32..256 outputs); PCV_ALGO_AUTO ignores param. */
+ * block and shared by its 32..256 outputs), or PCV_ALGO_MULT with `param`
+ * warps per permanent (1..1024; 0 = chosen from n_out).
+ * PCV_ALGO_MULT is Glynn's sum written over the multiplicities of a bunched
+ * state (the same identity as above, with the sign vectors of the mu copies
+ * of a repeated line grouped by their number k of minus signs):
+ *   Perm = 2^{-n} sum_{k_j=0..mu_j} prod_j (-1)^{k_j} C(mu_j,k_j)
+ *          prod_i (sum_j (mu_j - 2 k_j) M[j][i])^{e_i},
+ * with j over the distinct modes of one side (the output or the input,
+ * whichever gives fewer terms) and i over those of the other; prod (mu_j+1)
+ * terms, halved by the symmetry k -> mu - k, instead of 2^{n-1}.  The paper
+ * states no such variant; it serves outputs with several photons per mode.
+ * PCV_ALGO_AUTO ignores param.  Workspace: pcv_amplitudes_ex_workspace. */
 int pcv_amplitudes_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                       const uint8_t* output_occ, int64_t n_out,
                       pcv_c64* amp, double* prob, int algo, int param,
                       void* workspace, int64_t workspace_bytes, void* stream);
+
+/* Workspace bytes pcv_amplitudes_ex needs for this algorithm and param
+ * (0 if none; negative error code for an invalid choice). */
+int64_t pcv_amplitudes_ex_workspace(int m, int n, int64_t n_out, int algo, int param);
 
 /* One circuit of a batched call.  All pointers are device pointers; the
  * descriptor array itself lives in device memory and is only read. */
@@ -143,17 +164,30 @@ typedef struct {
  * total_outputs outputs in all. */
 int64_t pcv_amplitudes_batched_workspace(int n_circ, int64_t total_outputs);
 
-/* Amplitudes of many circuits of uneven size in one persistent launch
- * (Eq. eqperm per circuit).  A planning kernel sorts the circuits by photon
- * number (largest first) and expands them into work items (circuit, tile of
- * 32..256 outputs); one block per SM slot then pulls items from a device
- * counter until the queue is empty.  No block waits on another.
+/* Amplitudes of many circuits of uneven size (Eq. eqperm per circuit).
+ * A routing kernel sends each output either to the shared-row-sum tile
+ * kernel or to Glynn's sum with multiplicities (PCV_ALGO_MULT), whichever
+ * issues fewer FP64 instructions for it; a planning kernel sorts the circuits
+ * by photon number (largest first) and expands them into tile items
+ * (circuit, tile of 32..256 outputs) and single-output entries.  Two
+ * persistent launches then pull from device counters until their queues are
+ * empty: blocks take tile items, warps take entries.  No block waits on
+ * another.
  *   descs          device, n_circ descriptors (see pcv_batch_desc)
- *   total_outputs  sum of n_out over the circuits (sizes the work queue)
- * A descriptor with n or m out of range, or input modes outside [0, m) or
- * out of order, is skipped (its outputs are not written). */
+ *   total_outputs  sum of n_out over the circuits (<= INT32_MAX; sizes the
+ *                  work lists)
+ * A descriptor with n or m out of range, input modes outside [0, m) or out
+ * of order, or outputs beyond total_outputs, is skipped (its outputs are not
+ * written). */
 int pcv_amplitudes_batched(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs,
                            void* workspace, int64_t workspace_bytes, void* stream);
+
+/* pcv_amplitudes_batched with the routing fixed: algo = PCV_ALGO_AUTO (per
+ * output, as above), PCV_ALGO_TILE (every output to the tile kernel) or
+ * PCV_ALGO_MULT (every output to Glynn's sum with multiplicities).  Same
+ * workspace. */
+int pcv_amplitudes_batched_ex(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs, int algo,
+                              void* workspace, int64_t workspace_bytes, void* stream);
 
 /* Workspace bytes pcv_distribution needs for m modes and n photons with the
  * default plan.  A smaller workspace (>= pcv_distribution_workspace_min) is
@@ -229,6 +263,55 @@ int pcv_amplitudes_multi(const pcv_c64* U, int B, int m, const uint8_t* input_oc
  * (U, input, perm, uniforms). */
 int pcv_sample(const pcv_c64* U, int m, const uint8_t* input_occ, const uint8_t* perm, const double* uniforms,
                int64_t count, uint8_t* samples, void* stream);
+
+/* ------------------------------------------ partially distinguishable photons */
+
+/* The paper's Processor takes a source with a transmittance and an
+ * indistinguishability (Sec. processors), and its Hong-Ou-Mandel experiment
+ * (Sec. hom) simulates such a source; it states no formula. The readings
+ * here: photons of one class are identical, photons of different classes are
+ * perfectly distinguishable (orthogonal internal states), and detectors
+ * count photons per mode. Then
+ *   P(S) = sum over S_1 + ... + S_G = S of prod_g P_g(S_g),
+ * each P_g being Eq. eqperm for class g alone (a multiset convolution). */
+
+/* Workspace bytes of pcv_distribution_classes. */
+int64_t pcv_distribution_classes_workspace(int m, int G, const uint8_t* class_occ);
+
+/* Distribution over S_{m,n} (canonical order) of G photon classes.
+ *   U          device, m*m pcv_c64
+ *   class_occ  host, G*m uint8: class g's input occupation at class_occ + g*m;
+ *              n = total photons <= PCV_MAX_PHOTONS; empty classes allowed
+ *   prob       device, C(m+n-1, n) doubles (written)
+ * Each class's distribution is the factorised Glynn path's; one-photon
+ * classes are folded in by a gather over the occupied modes,
+ * C(S) = sum_{r: s_r >= 1} A(S - e_r) |U[r][c]|^2, larger ones by a
+ * sub-multiset convolution. Errors: PCV_EINVAL, PCV_ERANGE, PCV_ENOMEM. */
+int pcv_distribution_classes(const pcv_c64* U, int m, int G, const uint8_t* class_occ, double* prob,
+                             void* workspace, int64_t workspace_bytes, void* stream);
+
+/* Entries of the photon-number-resolved output space: sum_{k=0..n} C(m+k-1, k). */
+int64_t pcv_distribution_source_size(int m, int n);
+
+/* Workspace bytes of pcv_distribution_source. */
+int64_t pcv_distribution_source_workspace(int m, const uint8_t* input_occ);
+
+/* Output distribution of an imperfect source (n <= 16 photons): each photon
+ * independently is absent (probability 1 - transmittance), pure
+ * (transmittance * q) or noisy (transmittance * (1 - q)), with
+ * q = sqrt(indistinguishability), so that two photons on a 50:50 beam
+ * splitter show HOM visibility = indistinguishability. Pure photons form one
+ * class, each noisy photon a class of its own; the result is the mixture
+ * over all 2^n choices of the pure set, each folded with the other photons'
+ * (absent or noisy) one-photon terms.
+ *   prob  device, pcv_distribution_source_size(m, n) doubles (written): the
+ *         blocks S_{m,0}, S_{m,1}, ..., S_{m,n} concatenated, each in
+ *         canonical order; they sum to 1 together.
+ * Errors: PCV_EINVAL (n > 16, parameters outside [0, 1]), PCV_ERANGE,
+ * PCV_ENOMEM. */
+int pcv_distribution_source(const pcv_c64* U, int m, const uint8_t* input_occ, double transmittance,
+                            double indistinguishability, double* prob, void* workspace, int64_t workspace_bytes,
+                            void* stream);
 
 /* ------------------------------------------------------------ gradients */
 

@@ -15,11 +15,12 @@ import torch
 
 from . import _abi as abi
 from ._abi import (PCV_ALGO_AUTO, PCV_ALGO_BLOCK, PCV_ALGO_FACTOR, PCV_ALGO_GROUP,  # noqa: F401
-                   PCV_ALGO_SLOS, PCV_ALGO_TILE, PCV_MAX_MODES, PCV_MAX_PHOTONS, PcvError)
+                   PCV_ALGO_MULT, PCV_ALGO_SLOS, PCV_ALGO_TILE, PCV_MAX_MODES, PCV_MAX_PHOTONS, PcvError)
 
-__all__ = ["amplitudes", "amplitudes_batched", "BatchPlan", "distribution", "distribution_batched", "sample", "num_outputs", "unrank", "rank",
+__all__ = ["amplitudes", "amplitudes_batched", "BatchPlan", "distribution", "distribution_batched",
+           "distribution_classes", "source_distribution", "sample", "num_outputs", "unrank", "rank",
            "fp64_probe", "PcvError", "PCV_ALGO_AUTO", "PCV_ALGO_GROUP", "PCV_ALGO_BLOCK", "PCV_ALGO_FACTOR",
-           "PCV_ALGO_TILE", "PCV_ALGO_SLOS", "abi"]
+           "PCV_ALGO_TILE", "PCV_ALGO_SLOS", "PCV_ALGO_MULT", "abi"]
 
 
 def _stream(device) -> int:
@@ -82,8 +83,7 @@ def amplitudes(U: torch.Tensor, input_occ, outputs: torch.Tensor, *, algo: int =
     prob = torch.empty(n_out, dtype=torch.float64, device=U.device) if want_prob else None
     n = int(t.sum())
     if ws is None:
-        need = abi.pcv_amplitudes_workspace(m, n, n_out) if algo == PCV_ALGO_AUTO else \
-            (n_out * param * 16 + 256 if algo == PCV_ALGO_BLOCK and param > 1 else 0)
+        need = abi.pcv_amplitudes_ex_workspace(m, n, n_out, algo, param)
         ws = workspace(need, U.device)
     abi.pcv_amplitudes_ex(U, m, t, outputs, n_out, amp, prob, algo, param, ws,
                           0 if ws is None else ws.numel(), _stream(U.device))
@@ -97,7 +97,7 @@ class BatchPlan:
     Keeps references to every tensor the descriptors point at.
     """
 
-    def __init__(self, circuits, want_prob: bool = True):
+    def __init__(self, circuits, want_prob: bool = True, algo: int = PCV_ALGO_AUTO):
         if not circuits:
             raise ValueError("empty batch")
         dev = circuits[0][0].device
@@ -133,17 +133,20 @@ class BatchPlan:
         self.n_circ, self.total = len(circuits), total
         self.ws = workspace(abi.pcv_amplitudes_batched_workspace(self.n_circ, total), dev)
         self.device = dev
+        self.algo = algo
 
     def run(self):
-        abi.pcv_amplitudes_batched(self.descs, self.n_circ, self.total, self.ws,
-                                   0 if self.ws is None else self.ws.numel(), _stream(self.device))
+        abi.pcv_amplitudes_batched_ex(self.descs, self.n_circ, self.total, self.algo, self.ws,
+                                      0 if self.ws is None else self.ws.numel(), _stream(self.device))
         return self.amps, self.probs
 
 
-def amplitudes_batched(circuits, want_prob: bool = True):
-    """Amplitudes of many circuits of uneven size in one persistent launch.
+def amplitudes_batched(circuits, want_prob: bool = True, algo: int = PCV_ALGO_AUTO):
+    """Amplitudes of many circuits of uneven size: per output the shared-row-sum
+    tile kernel or Glynn's sum with multiplicities (algo AUTO), or all outputs
+    through one of them (PCV_ALGO_TILE, PCV_ALGO_MULT).
     Returns (list of amp tensors, list of prob tensors or None)."""
-    return BatchPlan(circuits, want_prob).run()
+    return BatchPlan(circuits, want_prob, algo).run()
 
 
 def distribution_workspace_bytes(m: int, n: int, algo: int = PCV_ALGO_AUTO, param: int = 0) -> int:
@@ -179,6 +182,45 @@ def distribution(U: torch.Tensor, input_occ, *, want_amp: bool = True, algo: int
     abi.pcv_distribution_ex(U, m, t, prob, amp, algo, param, ws, 0 if ws is None else ws.numel(),
                             _stream(U.device))
     return prob, amp
+
+
+def distribution_classes(U: torch.Tensor, classes, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """Distribution over S_{m,n} of photon classes: `classes` is a list of
+    input occupations (host, m photon counts each); photons of one class are
+    identical, photons of different classes perfectly distinguishable.
+    Returns prob float64 [C(m+n-1, n)] in canonical order."""
+    m = _check_U(U)
+    occ = np.ascontiguousarray(np.stack([_host_occ(t, m) for t in classes]) if len(classes) else
+                               np.zeros((0, m), np.uint8), dtype=np.uint8)
+    G = occ.shape[0]
+    n = int(occ.sum())
+    U = U.contiguous()
+    prob = torch.empty(num_outputs(m, n), dtype=torch.float64, device=U.device)
+    if ws is None:
+        ws = workspace(abi.pcv_distribution_classes_workspace(m, G, occ), U.device)
+    abi.pcv_distribution_classes(U, m, G, occ, prob, ws, 0 if ws is None else ws.numel(), _stream(U.device))
+    return prob
+
+
+def source_distribution(U: torch.Tensor, input_occ, transmittance: float = 1.0, indistinguishability: float = 1.0,
+                        ws: torch.Tensor | None = None):
+    """Output distribution of an imperfect source (see pcv_distribution_source):
+    returns (prob float64 over S_{m,0}, ..., S_{m,n} concatenated, offsets
+    list with block k at prob[offsets[k]:offsets[k+1]])."""
+    m = _check_U(U)
+    t = _host_occ(input_occ, m)
+    n = int(t.sum())
+    U = U.contiguous()
+    T = abi.pcv_distribution_source_size(m, n)
+    prob = torch.empty(T, dtype=torch.float64, device=U.device)
+    if ws is None:
+        ws = workspace(abi.pcv_distribution_source_workspace(m, t), U.device)
+    abi.pcv_distribution_source(U, m, t, transmittance, indistinguishability, prob, ws,
+                                0 if ws is None else ws.numel(), _stream(U.device))
+    offsets = [0]
+    for k in range(n + 1):
+        offsets.append(offsets[-1] + num_outputs(m, k))
+    return prob, offsets
 
 
 def distribution_batched(U: torch.Tensor, input_occ, *, want_amp: bool = True, ws: torch.Tensor | None = None,

@@ -31,6 +31,7 @@ PCV_ALGO_BLOCK = 2
 PCV_ALGO_FACTOR = 3
 PCV_ALGO_TILE = 4
 PCV_ALGO_SLOS = 5
+PCV_ALGO_MULT = 6
 PCV_MAX_PHOTONS = 30
 PCV_MAX_MODES = 1024
 
@@ -48,6 +49,7 @@ SIGNATURES = {
     "pcv_amplitudes_workspace": (_i64, [_i, _i, _i64]),
     "pcv_amplitudes": (_i, [_vp, _i, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp]),
     "pcv_amplitudes_ex": (_i, [_vp, _i, _vp, _vp, _i64, _vp, _vp, _i, _i, _vp, _i64, _vp]),
+    "pcv_amplitudes_ex_workspace": (_i64, [_i, _i, _i64, _i, _i]),
     "pcv_distribution_workspace": (_i64, [_i, _i]),
     "pcv_distribution_workspace_min": (_i64, [_i, _i]),
     "pcv_distribution": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
@@ -88,6 +90,12 @@ SIGNATURES = {
     "pcv_fp64_probe": (_i, [_vp, _i, _i, _i, _vp]),
     "pcv_amplitudes_batched_workspace": (_i64, [_i, _i64]),
     "pcv_amplitudes_batched": (_i, [_vp, _i, _i64, _vp, _i64, _vp]),
+    "pcv_amplitudes_batched_ex": (_i, [_vp, _i, _i64, _i, _vp, _i64, _vp]),
+    "pcv_distribution_classes_workspace": (_i64, [_i, _i, _vp]),
+    "pcv_distribution_classes": (_i, [_vp, _i, _i, _vp, _vp, _vp, _i64, _vp]),
+    "pcv_distribution_source_size": (_i64, [_i, _i]),
+    "pcv_distribution_source_workspace": (_i64, [_i, _vp]),
+    "pcv_distribution_source": (_i, [_vp, _i, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _i64, _vp]),
     "pcv_profile_enable": (_i, [_i]),
     "pcv_profile_read": (_i, [_vp, _vp, _i]),
     "pcv_launch_count": (_i64, []),
@@ -163,6 +171,10 @@ def pcv_amplitudes_ex(U, m, input_occ, output_occ, n_out, amp, prob, algo, param
                  algo, param, ptr(workspace), workspace_bytes, stream)
 
 
+def pcv_amplitudes_ex_workspace(m, n, n_out, algo, param) -> int:
+    return _call("pcv_amplitudes_ex_workspace", m, n, n_out, algo, param)
+
+
 def pcv_distribution_workspace(m, n) -> int:
     return _call("pcv_distribution_workspace", m, n)
 
@@ -193,6 +205,34 @@ def pcv_amplitudes_batched_workspace(n_circ, total_outputs) -> int:
 
 def pcv_amplitudes_batched(descs, n_circ, total_outputs, workspace, workspace_bytes, stream):
     return _call("pcv_amplitudes_batched", ptr(descs), n_circ, total_outputs, ptr(workspace), workspace_bytes, stream)
+
+
+def pcv_amplitudes_batched_ex(descs, n_circ, total_outputs, algo, workspace, workspace_bytes, stream):
+    return _call("pcv_amplitudes_batched_ex", ptr(descs), n_circ, total_outputs, algo, ptr(workspace),
+                 workspace_bytes, stream)
+
+
+def pcv_distribution_classes_workspace(m, G, class_occ) -> int:
+    return _call("pcv_distribution_classes_workspace", m, G, ptr(class_occ))
+
+
+def pcv_distribution_classes(U, m, G, class_occ, prob, workspace, workspace_bytes, stream):
+    return _call("pcv_distribution_classes", ptr(U), m, G, ptr(class_occ), ptr(prob), ptr(workspace),
+                 workspace_bytes, stream)
+
+
+def pcv_distribution_source_size(m, n) -> int:
+    return _call("pcv_distribution_source_size", m, n)
+
+
+def pcv_distribution_source_workspace(m, input_occ) -> int:
+    return _call("pcv_distribution_source_workspace", m, ptr(input_occ))
+
+
+def pcv_distribution_source(U, m, input_occ, transmittance, indistinguishability, prob, workspace,
+                            workspace_bytes, stream):
+    return _call("pcv_distribution_source", ptr(U), m, ptr(input_occ), float(transmittance),
+                 float(indistinguishability), ptr(prob), ptr(workspace), workspace_bytes, stream)
 
 
 def pcv_distribution_batched_workspace(B, m, n) -> int:

@@ -44,16 +44,19 @@ struct TileShared {
     int cols[PCV_MAX_PHOTONS];
 };
 
-// One tile (outputs [out0, out0 + TILE)) of circuit c.
-__device__ void tile_item(const pcv_batch_desc& c, int64_t tile, TileShared& sh)
+// One tile of circuit c: positions [tile TILE, (tile + 1) TILE) of its
+// output list, which is idx[0..count) (or the outputs 0..count-1 themselves
+// when idx is null).
+__device__ void tile_item(const pcv_batch_desc& c, int64_t tile, TileShared& sh, const int* idx, int64_t count)
 {
     const int n = c.n, m = c.m;
     const int S = tile_splits(n);
     const int TILE = kThreads / S;
     const int tid = threadIdx.x;
     const int ol = tid % TILE, s = tid / TILE;
-    const int64_t o = tile * TILE + ol;
-    const bool live = o < c.n_out;
+    const int64_t pos = tile * TILE + ol;
+    const bool live = pos < count;
+    const int64_t o = live ? (idx ? (int64_t)idx[pos] : pos) : 0;
 
     if (tid < n) sh.cols[tid] = c.cols[tid];
     double norm_t = 1.0;                  // 1/sqrt(prod t!) from the sorted photon -> input-mode list
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) glynn_tile_kernel(const pcv_batch_de
 {
     extern __shared__ __align__(16) unsigned char smem[];
     TileShared& sh = *reinterpret_cast<TileShared*>(smem);
-    tile_item(c, blockIdx.x, sh);
+    tile_item(c, blockIdx.x, sh, nullptr, c.n_out);
 }
 
 // Same outputs for B unitaries: blockIdx.y selects U + b*ustride and the
@@ -172,17 +175,20 @@ __global__ void __launch_bounds__(kThreads) glynn_tile_multi_kernel(const pcv_ba
     c.U = c0.U + b * ustride;
     if (c0.amp) c.amp = c0.amp + b * ostride;
     if (c0.prob) c.prob = c0.prob + b * ostride;
-    tile_item(c, blockIdx.x, sh);
+    tile_item(c, blockIdx.x, sh, nullptr, c.n_out);
 }
 
-// Work queue of the batched launch: items (circuit, tile) in order of
-// decreasing photon number; blocks pull the next item with one atomicAdd and
-// never wait for another block.
+// Work queue of the batched launch: tile items (circuit, tile of the
+// circuit's tile-routed outputs) in order of decreasing photon number; blocks
+// pull the next item with one atomicAdd and never wait for another block.
 struct Queue {
     int* counter;
     int* total;
     int* item_circ;
     int* item_tile;
+    const int64_t* out_off;   // first entry of circuit c in idx
+    const int* n_tile;        // tile-routed outputs of circuit c (idx[out_off[c] ...])
+    const int* idx;
 };
 
 __global__ void __launch_bounds__(kThreads) glynn_persistent_kernel(const pcv_batch_desc* descs, Queue q)
@@ -197,14 +203,13 @@ __global__ void __launch_bounds__(kThreads) glynn_persistent_kernel(const pcv_ba
         const int it = s_item;
         __syncthreads();
         if (it >= total) break;
-        tile_item(descs[q.item_circ[it]], q.item_tile[it], sh);
+        const int c = q.item_circ[it];
+        tile_item(descs[c], q.item_tile[it], sh, q.idx + q.out_off[c], q.n_tile[c]);
     }
 }
 
-// Builds the work queue on the device (one block): per-circuit photon number
-// and norm, a counting sort by n (descending), and the expanded item list.
 // A descriptor the kernels cannot run (n or m out of range, an input mode
-// outside [0, m) or out of order) gets no work items; the binding checks
+// outside [0, m) or out of order) gets no work; the binding checks
 // descriptors before they reach the device.
 __device__ bool desc_ok(const pcv_batch_desc& d)
 {
@@ -214,19 +219,162 @@ __device__ bool desc_ok(const pcv_batch_desc& d)
     return true;
 }
 
-__device__ int desc_items(const pcv_batch_desc& d)
+// Block-wide exclusive scan of one value per thread (1024 threads at most);
+// returns the thread's offset, *total the sum.  buf holds 64 values.
+template <typename T>
+__device__ T block_scan(T v, T* buf, T* total)
 {
-    if (!desc_ok(d) || d.n_out == 0) return 0;
-    const int tilesz = kThreads / tile_splits(d.n);
-    return (int)((d.n_out + tilesz - 1) / tilesz);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+    T incl = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        const T t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) buf[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        T w = lane < nw ? buf[lane] : T(0);
+        for (int off = 1; off < 32; off <<= 1) {
+            const T t = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += t;
+        }
+        if (lane < nw) buf[32 + lane] = w;       // inclusive prefix over warps
+    }
+    __syncthreads();
+    const T res = (wid ? buf[32 + wid - 1] : T(0)) + incl - v;
+    *total = buf[32 + nw - 1];
+    __syncthreads();
+    return res;
 }
 
-__global__ void __launch_bounds__(1024) plan_kernel(const pcv_batch_desc* descs, int n_circ, Queue q, int* order,
-                                                    int* item_off, int max_items)
+// out_off[c]: exclusive prefix of the output counts of valid circuits, in
+// circuit order (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) offsets_kernel(const pcv_batch_desc* descs, int n_circ, int64_t* out_off)
+{
+    __shared__ int64_t buf[64];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < n_circ; b0 += 1024) {
+        const int c = b0 + threadIdx.x;
+        const int64_t cnt = c < n_circ && desc_ok(descs[c]) ? descs[c].n_out : 0;
+        int64_t tot = 0;
+        const int64_t ex = block_scan<int64_t>(cnt, buf, &tot);
+        if (c < n_circ) out_off[c] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+}
+
+// FP64 pipe instructions of one output: the tile kernel spends 4n - 2 per
+// sign vector (n - 1 complex products and the accumulation) plus its share
+// 2m / TILE of the row-sum updates; Glynn's sum with multiplicities spends
+// 2q + 4n - 1 per term (q line-sum updates, n - 1 complex products, the
+// weight and the accumulation).
+__device__ double tile_cost(int m, int n)
+{
+    return ldexp(1.0, n - 1) * (4.0 * n - 2.0 + 2.0 * m / (double)(kThreads / tile_splits(n)));
+}
+
+__device__ double mult_side_cost(const int* mu, int d, int q, int n)
+{
+    double t = 1.0;
+    int odd = -1, big = 0;
+    for (int j = 0; j < d; ++j) {
+        t *= mu[j] + 1;
+        if (odd < 0 && (mu[j] & 1)) odd = j;
+        if (mu[j] > mu[big]) big = j;
+    }
+    const int p = odd >= 0 ? odd : big;
+    t = t / (mu[p] + 1) * (mu[p] / 2 + 1);
+    return t * (2.0 * q + 4.0 * n - 1.0);
+}
+
+// One block per circuit: route each output to the tile kernel or to Glynn's
+// sum with multiplicities; idx[out_off[c] ..] lists the tile outputs first
+// (in order) and the others after them (in reverse order).
+__global__ void __launch_bounds__(256) classify_kernel(const pcv_batch_desc* descs, const int64_t* out_off, int route,
+                                                       int64_t cap, int* idx, int* n_tile, int* n_mult)
+{
+    __shared__ int buf[64];
+    __shared__ int s_tile, s_mult;
+    const int ci = blockIdx.x;
+    const pcv_batch_desc& c = descs[ci];
+    const bool valid = desc_ok(c) && out_off[ci] + c.n_out <= cap;
+    if (!valid) {
+        if (threadIdx.x == 0) n_tile[ci] = n_mult[ci] = 0;
+        return;
+    }
+    const int m = c.m, n = c.n;
+    const int64_t no = c.n_out;
+    int* list = idx + out_off[ci];
+    // input side: distinct modes and multiplicities
+    int imu[PCV_MAX_PHOTONS];
+    int d_in = 0;
+    for (int j = 0; j < n; ++j) {
+        if (j == 0 || c.cols[j] != c.cols[j - 1]) imu[d_in++] = 0;
+        imu[d_in - 1] += 1;
+    }
+    const double ct = tile_cost(m, n);
+    if (threadIdx.x == 0) s_tile = s_mult = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < no; b0 += blockDim.x) {
+        const int64_t o = b0 + threadIdx.x;
+        int to_mult = 0;
+        if (o < no) {
+            if (route == PCV_ALGO_MULT) {
+                to_mult = 1;
+            } else if (route == PCV_ALGO_AUTO) {
+                const uint8_t* occ = c.outputs + o * m;
+                int omu[PCV_MAX_PHOTONS];
+                int d_out = 0, tot = 0;
+                for (int r = 0; r < m; ++r) {
+                    const int v = occ[r];
+                    if (v > 0 && d_out < PCV_MAX_PHOTONS) omu[d_out++] = v;
+                    tot += v;
+                }
+                if (tot != n) {
+                    to_mult = 1;                      // not in S_{m,n}: amplitude 0, cheapest there
+                } else {
+                    const double cm = fmin(mult_side_cost(omu, d_out, d_in, n), mult_side_cost(imu, d_in, d_out, n));
+                    to_mult = cm < ct;
+                }
+            }
+        }
+        int tot_m = 0;
+        const int pm = block_scan<int>(to_mult, buf, &tot_m);
+        const int live = o < no ? 1 : 0;
+        int tot_t = 0;
+        const int pt = block_scan<int>(live - to_mult, buf, &tot_t);
+        if (o < no) {
+            if (to_mult) list[no - 1 - (s_mult + pm)] = (int)o;
+            else list[s_tile + pt] = (int)o;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_tile += tot_t;
+            s_mult += tot_m;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        n_tile[ci] = s_tile;
+        n_mult[ci] = s_mult;
+    }
+}
+
+// Builds both work lists on the device (one block): a counting sort of the
+// circuits by n (descending), then tile items and multiplicity entries in
+// that order.
+__global__ void __launch_bounds__(1024) plan_kernel(const pcv_batch_desc* descs, int n_circ, Queue q, MultQueue mq,
+                                                    int* order, int* item_off, int* mult_off, const int* n_mult,
+                                                    int* mult_circ, int* mult_out, int max_items)
 {
     __shared__ int bucket[PCV_MAX_PHOTONS + 2];
     __shared__ int cursor[PCV_MAX_PHOTONS + 2];
-    __shared__ int carry;
+    __shared__ int buf[64];
+    __shared__ int carry_t, carry_m;
     const int tid = threadIdx.x;
     if (tid < PCV_MAX_PHOTONS + 2) bucket[tid] = 0;
     __syncthreads();
@@ -236,44 +384,59 @@ __global__ void __launch_bounds__(1024) plan_kernel(const pcv_batch_desc* descs,
     if (tid == 0) {
         int acc = 0;
         for (int n = PCV_MAX_PHOTONS; n >= 0; --n) { cursor[n] = acc; acc += bucket[n]; }
-        carry = 0;
+        carry_t = carry_m = 0;
     }
     __syncthreads();
     for (int c = tid; c < n_circ; c += blockDim.x)
         order[atomicAdd(&cursor[desc_ok(descs[c]) ? descs[c].n : 0], 1)] = c;
     __syncthreads();
-    // exclusive scan of item counts over the sorted order, 1024 circuits at a time
-    __shared__ int scan[1024];
+    // exclusive scans of tile-item and entry counts over the sorted order
     for (int b0 = 0; b0 < n_circ; b0 += 1024) {
         const int p = b0 + tid;
-        const int cnt = p < n_circ ? desc_items(descs[order[p]]) : 0;
-        scan[tid] = cnt;
-        __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            const int v = tid >= off ? scan[tid - off] : 0;
-            __syncthreads();
-            scan[tid] += v;
-            __syncthreads();
+        int ct = 0, cm = 0;
+        if (p < n_circ) {
+            const int c = order[p];
+            const int tilesz = kThreads / tile_splits(descs[c].n);
+            ct = (q.n_tile[c] + tilesz - 1) / tilesz;
+            cm = n_mult[c];
         }
-        if (p < n_circ) item_off[p] = carry + scan[tid] - cnt;
+        int tt = 0, tm = 0;
+        const int et = block_scan<int>(ct, buf, &tt);
+        const int em = block_scan<int>(cm, buf, &tm);
+        if (p < n_circ) {
+            item_off[p] = carry_t + et;
+            mult_off[p] = carry_m + em;
+        }
         __syncthreads();
-        if (tid == 1023) carry += scan[1023];
+        if (tid == 0) {
+            carry_t += tt;
+            carry_m += tm;
+        }
         __syncthreads();
     }
     if (tid == 0) {
-        *q.total = carry < max_items ? carry : max_items;
+        *q.total = carry_t < max_items ? carry_t : max_items;
         *q.counter = 0;
+        *mq.total = carry_m;
+        *mq.counter = 0;
     }
     __syncthreads();
     for (int p = 0; p < n_circ; ++p) {
         const int c = order[p];
-        const int cnt = desc_items(descs[c]);
+        const int tilesz = kThreads / tile_splits(descs[c].n);
+        const int cnt = (q.n_tile[c] + tilesz - 1) / tilesz;
         for (int t = tid; t < cnt; t += blockDim.x) {
             const int it = item_off[p] + t;
             if (it < max_items) {
                 q.item_circ[it] = c;
                 q.item_tile[it] = t;
             }
+        }
+        const int cm = n_mult[c];
+        const int* src = q.idx + q.out_off[c] + q.n_tile[c];
+        for (int t = tid; t < cm; t += blockDim.x) {
+            mult_circ[mult_off[p] + t] = c;
+            mult_out[mult_off[p] + t] = src[t];
         }
     }
 }
@@ -299,9 +462,18 @@ cudaError_t ensure_smem_attr()
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+__global__ void store_desc_kernel(const pcv_batch_desc d, pcv_batch_desc* out) { *out = d; }
+
 }  // namespace
 
 int tile_max_modes() { return kMaxModes; }
+
+cudaError_t launch_store_desc(const pcv_batch_desc& d, pcv_batch_desc* out, cudaStream_t s)
+{
+    store_desc_kernel<<<1, 1, 0, s>>>(d, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_glynn_tile(const pcv_batch_desc& d, cudaStream_t s)
 {
@@ -328,30 +500,55 @@ cudaError_t launch_glynn_tile_multi(const pcv_batch_desc& d, int B, cudaStream_t
     return cudaGetLastError();
 }
 
+// Workspace of the batched launch: counters, per-circuit arrays, the routed
+// output lists and the tile items.
 int64_t batched_workspace(int n_circ, int64_t total_outputs)
 {
     const int64_t max_items = total_outputs / 32 + n_circ + 1;
-    return (int64_t)(al256(2 * sizeof(int)) + 3 * al256((size_t)n_circ * sizeof(int)) +
+    return (int64_t)(al256(4 * sizeof(int)) + 6 * al256((size_t)n_circ * sizeof(int)) +
+                     al256((size_t)n_circ * sizeof(int64_t)) + 3 * al256((size_t)total_outputs * sizeof(int)) +
                      2 * al256((size_t)max_items * sizeof(int)));
 }
 
 cudaError_t launch_glynn_batched(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs, void* ws,
-                                 int sms, cudaStream_t s)
+                                 int sms, int route, cudaStream_t s)
 {
     cudaError_t e = ensure_smem_attr();
     if (e != cudaSuccess) return e;
     const int64_t max_items = total_outputs / 32 + n_circ + 1;
     char* w = (char*)ws;
-    Queue q;
-    q.counter = (int*)w;
-    q.total = q.counter + 1;                          w += al256(2 * sizeof(int));
+    int* counters = (int*)w;                          w += al256(4 * sizeof(int));
     int* order = (int*)w;                             w += al256((size_t)n_circ * sizeof(int));
     int* item_off = (int*)w;                          w += al256((size_t)n_circ * sizeof(int));
+    int* mult_off = (int*)w;                          w += al256((size_t)n_circ * sizeof(int));
+    int* n_tile = (int*)w;                            w += al256((size_t)n_circ * sizeof(int));
+    int* n_mult = (int*)w;                            w += al256((size_t)n_circ * sizeof(int));
     w += al256((size_t)n_circ * sizeof(int));
-    q.item_circ = (int*)w;                            w += al256((size_t)max_items * sizeof(int));
-    q.item_tile = (int*)w;
-    plan_kernel<<<1, 1024, 0, s>>>(descs, n_circ, q, order, item_off, (int)max_items);
-    note_launches(1);
+    int64_t* out_off = (int64_t*)w;                   w += al256((size_t)n_circ * sizeof(int64_t));
+    int* idx = (int*)w;                               w += al256((size_t)total_outputs * sizeof(int));
+    int* mult_circ = (int*)w;                         w += al256((size_t)total_outputs * sizeof(int));
+    int* mult_out = (int*)w;                          w += al256((size_t)total_outputs * sizeof(int));
+    int* item_circ = (int*)w;                         w += al256((size_t)max_items * sizeof(int));
+    int* item_tile = (int*)w;
+    Queue q;
+    q.counter = counters;
+    q.total = counters + 1;
+    q.item_circ = item_circ;
+    q.item_tile = item_tile;
+    q.out_off = out_off;
+    q.n_tile = n_tile;
+    q.idx = idx;
+    MultQueue mq;
+    mq.counter = counters + 2;
+    mq.total = counters + 3;
+    mq.circ = mult_circ;
+    mq.out = mult_out;
+
+    offsets_kernel<<<1, 1024, 0, s>>>(descs, n_circ, out_off);
+    classify_kernel<<<n_circ, 256, 0, s>>>(descs, out_off, route, total_outputs, idx, n_tile, n_mult);
+    plan_kernel<<<1, 1024, 0, s>>>(descs, n_circ, q, mq, order, item_off, mult_off, n_mult, mult_circ, mult_out,
+                                   (int)max_items);
+    note_launches(3);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, glynn_persistent_kernel, kThreads, sizeof(TileShared));
@@ -359,7 +556,8 @@ cudaError_t launch_glynn_batched(const pcv_batch_desc* descs, int n_circ, int64_
     if (per_sm < 1) per_sm = 1;
     glynn_persistent_kernel<<<sms * per_sm, kThreads, sizeof(TileShared), s>>>(descs, q);
     note_launches(1);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_glynn_mult_persistent(descs, mq, sms, s);
 }
 
 }  // namespace pcv

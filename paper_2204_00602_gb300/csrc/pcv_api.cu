@@ -72,6 +72,11 @@ int make_plan(const pcv_c64* U, int m, const uint8_t* input_occ, pcv::Plan* p)
 }
 
 constexpr int kSMs = 152;
+// Internal choice of PCV_ALGO_AUTO for explicit outputs: the batched
+// launch's per-output routing (tile kernel or Glynn's sum with
+// multiplicities) applied to one circuit.
+constexpr int kAlgoRouted = 100;
+constexpr int kRouteMinPhotons = 13;
 
 // Threads per permanent for the group kernel: enough threads in flight to
 // cover the GPU, never more lanes than Gray steps.
@@ -99,9 +104,15 @@ AmpChoice choose_amp(int m, int n, int64_t n_out, int algo, int param)
     if (algo == PCV_ALGO_AUTO) {
         // shared row sums when there are enough outputs to give every SM a tile
         if (m <= pcv::tile_max_modes() && n >= 1 && n_out >= (int64_t)kSMs * (256 / pcv::tile_splits(n)))
-            return {PCV_ALGO_TILE, 0};
+            return {n >= kRouteMinPhotons && n_out <= INT32_MAX ? kAlgoRouted : PCV_ALGO_TILE, 0};
         if (n <= 12 || (n <= 16 && n_out >= (int64_t)kSMs * 256)) return {PCV_ALGO_GROUP, auto_group(n, n_out)};
         return {PCV_ALGO_BLOCK, auto_splits(n, n_out)};
+    }
+    if (algo == PCV_ALGO_MULT && param == 0) {
+        // enough warps in flight for every SM slot
+        const int64_t want = (int64_t)kSMs * 16;
+        const int64_t parts = n_out >= want ? 1 : (want + n_out - 1) / std::max<int64_t>(n_out, 1);
+        return {algo, (int)std::min<int64_t>(parts, 1024)};
     }
     return {algo, param};
 }
@@ -120,6 +131,12 @@ int check_choice(const AmpChoice& c, int n)
         if (n > 0 && (1ll << (n - 1)) < G) return fail(PCV_EINVAL, "threads per permanent %d exceed 2^(n-1)=%lld", G, 1ll << (n - 1));
         return PCV_OK;
     }
+    if (c.algo == kAlgoRouted) return PCV_OK;
+    if (c.algo == PCV_ALGO_MULT) {
+        if (n < 1) return fail(PCV_EINVAL, "multiplicity kernel needs n >= 1");
+        if (c.param < 1 || c.param > 1024) return fail(PCV_EINVAL, "warps per permanent %d outside [1, 1024]", c.param);
+        return PCV_OK;
+    }
     if (c.algo == PCV_ALGO_BLOCK) {
         if (n < 9 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "block kernel supports 9 <= n <= 30 (n=%d)", n);
         if (c.param < 1 || (int64_t)c.param * pcv::glynn_block_threads() > (1ll << (n - 1)))
@@ -133,7 +150,10 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int64_t amp_workspace(const AmpChoice& c, int64_t n_out)
 {
-    if (c.algo == PCV_ALGO_BLOCK && c.param > 1) return (int64_t)align256((size_t)n_out * c.param * sizeof(double2));
+    if (c.algo == kAlgoRouted)
+        return (int64_t)align256(sizeof(pcv_batch_desc)) + pcv::batched_workspace(1, n_out);
+    if ((c.algo == PCV_ALGO_BLOCK || c.algo == PCV_ALGO_MULT) && c.param > 1)
+        return (int64_t)align256((size_t)n_out * c.param * sizeof(double2));
     return 0;
 }
 
@@ -278,6 +298,16 @@ int64_t pcv_amplitudes_workspace(int m, int n, int64_t n_out)
     return amp_workspace(choose_amp(m, n, n_out, PCV_ALGO_AUTO, 0), n_out);
 }
 
+int64_t pcv_amplitudes_ex_workspace(int m, int n, int64_t n_out, int algo, int param)
+{
+    if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS || n_out < 0) return fail(PCV_EINVAL, "bad sizes");
+    if (n == 0) return 0;
+    const AmpChoice c = choose_amp(m, n, n_out, algo, param);
+    const int rc = check_choice(c, n);
+    if (rc) return rc;
+    return amp_workspace(c, n_out);
+}
+
 int pcv_amplitudes_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                       const uint8_t* output_occ, int64_t n_out,
                       pcv_c64* amp, double* prob, int algo, int param,
@@ -304,8 +334,45 @@ int pcv_amplitudes_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
     if (need > 0 && (!workspace || workspace_bytes < need))
         return fail(PCV_ENOMEM, "workspace of %lld bytes needed, %lld given", (long long)need, (long long)workspace_bytes);
     if (need > 0 && !aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
-    if ((int64_t)n_out * (c.algo == PCV_ALGO_BLOCK ? c.param : 1) > INT32_MAX)
+    if ((int64_t)n_out * ((c.algo == PCV_ALGO_BLOCK || c.algo == PCV_ALGO_MULT) ? c.param : 1) > INT32_MAX)
         return fail(PCV_ERANGE, "too many permanents for one launch");
+    if (c.algo == kAlgoRouted) {
+        pcv_batch_desc d;
+        d.U = U;
+        d.outputs = output_occ;
+        d.amp = amp;
+        d.prob = prob;
+        d.n_out = n_out;
+        d.m = m;
+        d.n = p.n;
+        for (int j = 0; j < PCV_MAX_PHOTONS; ++j) d.cols[j] = p.cols[j];
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "device query");
+        pcv_batch_desc* dd = (pcv_batch_desc*)workspace;
+        void* bws = (char*)workspace + align256(sizeof(pcv_batch_desc));
+        pcv::stage_begin(pcv::kStagePlain, s);
+        e = pcv::launch_store_desc(d, dd, s);
+        if (e == cudaSuccess) e = pcv::launch_glynn_batched(dd, 1, n_out, bws, sms, PCV_ALGO_AUTO, s);
+        pcv::stage_end(pcv::kStagePlain, s);
+        return e == cudaSuccess ? PCV_OK : cuda_fail(e, "routed launch");
+    }
+    if (c.algo == PCV_ALGO_MULT) {
+        pcv_batch_desc d;
+        d.U = U;
+        d.outputs = output_occ;
+        d.amp = amp;
+        d.prob = prob;
+        d.n_out = n_out;
+        d.m = m;
+        d.n = p.n;
+        for (int j = 0; j < PCV_MAX_PHOTONS; ++j) d.cols[j] = p.cols[j];
+        pcv::stage_begin(pcv::kStagePlain, s);
+        cudaError_t e = pcv::launch_glynn_mult(d, c.param, 0, (double2*)workspace, s);
+        pcv::stage_end(pcv::kStagePlain, s);
+        return e == cudaSuccess ? PCV_OK : cuda_fail(e, "multiplicity launch");
+    }
     if (c.algo == PCV_ALGO_TILE) {
         if (m > pcv::tile_max_modes()) return fail(PCV_EINVAL, "tile kernel supports m <= %d (m=%d)", pcv::tile_max_modes(), m);
         pcv_batch_desc d;
@@ -377,13 +444,16 @@ int64_t pcv_amplitudes_batched_workspace(int n_circ, int64_t total_outputs)
     return pcv::batched_workspace(n_circ, total_outputs);
 }
 
-int pcv_amplitudes_batched(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs,
-                           void* workspace, int64_t workspace_bytes, void* stream)
+int pcv_amplitudes_batched_ex(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs, int algo,
+                              void* workspace, int64_t workspace_bytes, void* stream)
 {
     if (n_circ < 0 || total_outputs < 0) return fail(PCV_EINVAL, "n_circ=%d total_outputs=%lld", n_circ, (long long)total_outputs);
+    if (algo != PCV_ALGO_AUTO && algo != PCV_ALGO_TILE && algo != PCV_ALGO_MULT)
+        return fail(PCV_EINVAL, "batched routing %d is not AUTO, TILE or MULT", algo);
     if (n_circ == 0) return PCV_OK;
     if (!descs) return fail(PCV_EINVAL, "descs is NULL");
-    if ((total_outputs / 32 + n_circ + 1) > INT32_MAX) return fail(PCV_ERANGE, "too many outputs for one launch");
+    if (total_outputs > INT32_MAX || (total_outputs / 32 + n_circ + 1) > INT32_MAX)
+        return fail(PCV_ERANGE, "too many outputs for one launch");
     const int64_t need = pcv::batched_workspace(n_circ, total_outputs);
     if (!workspace || workspace_bytes < need)
         return fail(PCV_ENOMEM, "workspace of %lld bytes needed, %lld given", (long long)need, (long long)workspace_bytes);
@@ -394,9 +464,15 @@ int pcv_amplitudes_batched(const pcv_batch_desc* descs, int n_circ, int64_t tota
     if (e != cudaSuccess) return cuda_fail(e, "device query");
     cudaStream_t s = (cudaStream_t)stream;
     pcv::stage_begin(pcv::kStagePlain, s);
-    e = pcv::launch_glynn_batched(descs, n_circ, total_outputs, workspace, sms, s);
+    e = pcv::launch_glynn_batched(descs, n_circ, total_outputs, workspace, sms, algo, s);
     pcv::stage_end(pcv::kStagePlain, s);
     return e == cudaSuccess ? PCV_OK : cuda_fail(e, "batched launch");
+}
+
+int pcv_amplitudes_batched(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs,
+                           void* workspace, int64_t workspace_bytes, void* stream)
+{
+    return pcv_amplitudes_batched_ex(descs, n_circ, total_outputs, PCV_ALGO_AUTO, workspace, workspace_bytes, stream);
 }
 
 static int64_t dist_ws(int B, int m, int n, int algo, int param, bool need_acc, int64_t ws_bytes, pcv::DistPlan* dp)
@@ -723,4 +799,271 @@ extern "C" int pcv_fp64_probe(double* out, int blocks, int threads, int iters, v
     pcv::note_launches(1);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PCV_OK : cuda_fail(e, "fp64 probe");
+}
+
+// ------------------------------------------- partially distinguishable photons
+
+namespace {
+
+// Workspace of one class distribution of k photons: the default plan when it
+// is at most 1 GiB, else the smallest plan.
+int64_t class_dist_ws(int m, int k)
+{
+    if (k == 0) return 0;
+    const int64_t full = pcv_distribution_workspace(m, k);
+    if (full >= 0 && full <= (1ll << 30)) return full;
+    return pcv_distribution_workspace_min(m, k);
+}
+
+int64_t tables_bytes(int m, int n) { return 2 * (int64_t)align256((size_t)(m + 1) * (n + 1) * sizeof(int64_t)); }
+
+struct Classes {
+    int m, n, G;                                  // G non-empty classes, largest first
+    int size[PCV_MAX_PHOTONS];
+    std::vector<uint8_t> occ;                     // G * m
+};
+
+int make_classes(int m, int G, const uint8_t* class_occ, Classes* c)
+{
+    if (m < 1 || m > PCV_MAX_MODES) return fail(PCV_EINVAL, "m=%d outside [1, %d]", m, PCV_MAX_MODES);
+    if (G < 0 || G > 4096) return fail(PCV_EINVAL, "G=%d outside [0, 4096]", G);
+    if (G > 0 && !class_occ) return fail(PCV_EINVAL, "class_occ is NULL");
+    std::vector<std::pair<int, int>> order;      // (size, class)
+    int n = 0;
+    for (int g = 0; g < G; ++g) {
+        int k = 0;
+        for (int j = 0; j < m; ++j) k += class_occ[(size_t)g * m + j];
+        if (k > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "class %d has %d photons", g, k);
+        n += k;
+        if (n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "%d photons in all, more than %d", n, PCV_MAX_PHOTONS);
+        if (k > 0) order.push_back({k, g});
+    }
+    std::stable_sort(order.begin(), order.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+        return a.first > b.first;
+    });
+    if (msets(m, n) < 0) return fail(PCV_ERANGE, "output space too large");
+    c->m = m;
+    c->n = n;
+    c->G = (int)order.size();
+    c->occ.assign((size_t)c->G * m, 0);
+    for (int g = 0; g < c->G; ++g) {
+        c->size[g] = order[g].first;
+        std::copy(class_occ + (size_t)order[g].second * m, class_occ + (size_t)(order[g].second + 1) * m,
+                  c->occ.begin() + (size_t)g * m);
+    }
+    return PCV_OK;
+}
+
+int64_t classes_ws(const Classes& c)
+{
+    const int64_t N = msets(c.m, c.n);
+    const int64_t NB = c.G > 1 ? msets(c.m, c.size[1]) : 0;
+    int64_t dws = 0;
+    for (int g = 0; g < c.G; ++g) {
+        if (g > 0 && c.size[g] == 1) continue;
+        const int64_t w = class_dist_ws(c.m, c.size[g]);
+        if (w < 0) return w;
+        dws = std::max(dws, w);
+    }
+    return tables_bytes(c.m, c.n) + 2 * (int64_t)align256((size_t)N * 8) + (int64_t)align256((size_t)NB * 8) + dws;
+}
+
+}  // namespace
+
+int64_t pcv_distribution_classes_workspace(int m, int G, const uint8_t* class_occ)
+{
+    Classes c;
+    const int rc = make_classes(m, G, class_occ, &c);
+    if (rc) return rc;
+    return classes_ws(c);
+}
+
+int pcv_distribution_classes(const pcv_c64* U, int m, int G, const uint8_t* class_occ, double* prob,
+                             void* workspace, int64_t workspace_bytes, void* stream)
+{
+    Classes c;
+    int rc = make_classes(m, G, class_occ, &c);
+    if (rc) return rc;
+    if (!U || !aligned(U, 16)) return fail(PCV_EINVAL, "U is NULL or not 16-byte aligned");
+    if (!prob || !aligned(prob, 8)) return fail(PCV_EINVAL, "prob is NULL or not 8-byte aligned");
+    const int64_t need = classes_ws(c);
+    if (need < 0) return (int)need;
+    if (!workspace || workspace_bytes < need)
+        return fail(PCV_ENOMEM, "workspace of %lld bytes needed, %lld given", (long long)need, (long long)workspace_bytes);
+    if (!aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (c.G == 0) {
+        e = pcv::launch_set_one(prob, s);
+        return e == cudaSuccess ? PCV_OK : cuda_fail(e, "empty input");
+    }
+    const int64_t N = msets(m, c.n);
+    char* w = (char*)workspace;
+    int64_t* mc = (int64_t*)w;               w += align256((size_t)(m + 1) * (c.n + 1) * sizeof(int64_t));
+    int64_t* cum = (int64_t*)w;              w += align256((size_t)(m + 1) * (c.n + 1) * sizeof(int64_t));
+    double* bufA = (double*)w;               w += align256((size_t)N * 8);
+    double* bufC = (double*)w;               w += align256((size_t)N * 8);
+    double* bufB = (double*)w;               w += align256((size_t)(c.G > 1 ? msets(m, c.size[1]) : 0) * 8);
+    void* dws = w;
+    const int64_t dws_bytes = need - (int64_t)(w - (char*)workspace);
+    if ((e = pcv::build_multiset_table(mc, m, c.n, s)) != cudaSuccess) return cuda_fail(e, "multiset table");
+    if ((e = pcv::build_cum_table(mc, m, c.n, cum, s)) != cudaSuccess) return cuda_fail(e, "rank table");
+    double* cur = c.G == 1 ? prob : bufA;
+    rc = pcv_distribution_ex(U, m, c.occ.data(), cur, nullptr, PCV_ALGO_AUTO, 0, dws, dws_bytes, stream);
+    if (rc) return rc;
+    int k = c.size[0];
+    for (int g = 1; g < c.G; ++g) {
+        double* out = g == c.G - 1 ? prob : (cur == bufA ? bufC : bufA);
+        const uint8_t* t = c.occ.data() + (size_t)g * m;
+        const int kn = k + c.size[g];
+        if (c.size[g] == 1) {
+            int mode = 0;
+            while (t[mode] == 0) ++mode;
+            e = pcv::launch_photon_step(mc, cum, m, c.n, kn, (const double2*)U, mode, nullptr, cur, 0.0, 1.0, out,
+                                        msets(m, kn), s);
+        } else {
+            rc = pcv_distribution_ex(U, m, t, bufB, nullptr, PCV_ALGO_AUTO, 0, dws, dws_bytes, stream);
+            if (rc) return rc;
+            e = pcv::launch_class_conv(mc, cum, m, c.n, k, c.size[g], cur, bufB, out, msets(m, kn), s);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "class convolution");
+        cur = out;
+        k = kn;
+    }
+    return PCV_OK;
+}
+
+namespace {
+
+constexpr int kSourceMaxPhotons = 16;
+
+// Sum of |S_{m,k}| for k = 0..n (the photon-number-resolved output space).
+int64_t graded_size(int m, int n)
+{
+    int64_t t = 0;
+    for (int k = 0; k <= n; ++k) {
+        const int64_t c = msets(m, k);
+        if (c < 0 || t > INT64_MAX / 2) return -1;
+        t += c;
+    }
+    return t;
+}
+
+int64_t source_ws(int m, int n)
+{
+    const int64_t T = graded_size(m, n);
+    if (T < 0) return fail(PCV_ERANGE, "output space too large");
+    int64_t dws = 0;
+    for (int k = 1; k <= n; ++k) {
+        const int64_t w = class_dist_ws(m, k);
+        if (w < 0) return w;
+        dws = std::max(dws, w);
+    }
+    return tables_bytes(m, n) + 2 * (int64_t)align256((size_t)T * 8) + dws;
+}
+
+int check_source_input(int m, const uint8_t* input_occ, int* n)
+{
+    if (m < 1 || m > PCV_MAX_MODES) return fail(PCV_EINVAL, "m=%d outside [1, %d]", m, PCV_MAX_MODES);
+    if (!input_occ) return fail(PCV_EINVAL, "input_occ is NULL");
+    int k = 0;
+    for (int j = 0; j < m; ++j) k += input_occ[j];
+    if (k > kSourceMaxPhotons) return fail(PCV_EINVAL, "source model supports n <= %d (n=%d)", kSourceMaxPhotons, k);
+    *n = k;
+    return PCV_OK;
+}
+
+}  // namespace
+
+int64_t pcv_distribution_source_size(int m, int n)
+{
+    if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "bad sizes");
+    const int64_t T = graded_size(m, n);
+    return T < 0 ? fail(PCV_ERANGE, "output space too large") : T;
+}
+
+int64_t pcv_distribution_source_workspace(int m, const uint8_t* input_occ)
+{
+    int n = 0;
+    const int rc = check_source_input(m, input_occ, &n);
+    if (rc) return rc;
+    return source_ws(m, n);
+}
+
+int pcv_distribution_source(const pcv_c64* U, int m, const uint8_t* input_occ, double transmittance,
+                            double indistinguishability, double* prob, void* workspace, int64_t workspace_bytes,
+                            void* stream)
+{
+    int n = 0;
+    int rc = check_source_input(m, input_occ, &n);
+    if (rc) return rc;
+    if (!(transmittance >= 0.0 && transmittance <= 1.0)) return fail(PCV_EINVAL, "transmittance outside [0, 1]");
+    if (!(indistinguishability >= 0.0 && indistinguishability <= 1.0))
+        return fail(PCV_EINVAL, "indistinguishability outside [0, 1]");
+    if (!U || !aligned(U, 16)) return fail(PCV_EINVAL, "U is NULL or not 16-byte aligned");
+    if (!prob || !aligned(prob, 8)) return fail(PCV_EINVAL, "prob is NULL or not 8-byte aligned");
+    const int64_t need = source_ws(m, n);
+    if (need < 0) return (int)need;
+    if (!workspace || workspace_bytes < need)
+        return fail(PCV_ENOMEM, "workspace of %lld bytes needed, %lld given", (long long)need, (long long)workspace_bytes);
+    if (!aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t T = graded_size(m, n);
+    int64_t off[PCV_MAX_PHOTONS + 2];
+    off[0] = 0;
+    for (int k = 0; k <= n; ++k) off[k + 1] = off[k] + msets(m, k);
+    char* w = (char*)workspace;
+    int64_t* mc = (int64_t*)w;               w += align256((size_t)(m + 1) * (n + 1) * sizeof(int64_t));
+    int64_t* cum = (int64_t*)w;              w += align256((size_t)(m + 1) * (n + 1) * sizeof(int64_t));
+    double* G0 = (double*)w;                 w += align256((size_t)T * 8);
+    double* G1 = (double*)w;                 w += align256((size_t)T * 8);
+    void* dws = w;
+    const int64_t dws_bytes = need - (int64_t)(w - (char*)workspace);
+    cudaError_t e = cudaMemsetAsync(prob, 0, (size_t)T * 8, s);
+    if (e != cudaSuccess) return cuda_fail(e, "clear output");
+    if ((e = pcv::build_multiset_table(mc, m, n, s)) != cudaSuccess) return cuda_fail(e, "multiset table");
+    if ((e = pcv::build_cum_table(mc, m, n, cum, s)) != cudaSuccess) return cuda_fail(e, "rank table");
+    // photon j enters mode modes[j]; a photon is absent (1 - eta), pure
+    // (eta q) or noisy (eta (1 - q)), q = sqrt(indistinguishability)
+    int modes[PCV_MAX_PHOTONS];
+    for (int j = 0, c = 0; j < m; ++j)
+        for (int r = 0; r < input_occ[j]; ++r) modes[c++] = j;
+    const double eta = transmittance, q = std::sqrt(indistinguishability);
+    const double alpha = 1.0 - eta, beta = eta * (1.0 - q), gamma = eta * q;
+    std::vector<uint8_t> tP(m);
+    for (uint32_t P = 0; P < (1u << n); ++P) {
+        const int kP = __builtin_popcount(P);
+        const double wP = std::pow(gamma, kP);
+        if (wP == 0.0) continue;
+        if (kP < n && alpha == 0.0 && beta == 0.0) continue;       // every other photon must be pure
+        std::fill(tP.begin(), tP.end(), 0);
+        for (int j = 0; j < n; ++j)
+            if ((P >> j) & 1u) tP[modes[j]] += 1;
+        double* cur = G0;
+        double* nxt = G1;
+        if (kP == 0) {
+            if ((e = pcv::launch_set_one(cur + off[0], s)) != cudaSuccess) return cuda_fail(e, "pure set");
+        } else {
+            rc = pcv_distribution_ex(U, m, tP.data(), cur + off[kP], nullptr, PCV_ALGO_AUTO, 0, dws, dws_bytes, stream);
+            if (rc) return rc;
+        }
+        int lo = kP, hi = kP;
+        for (int j = 0; j < n; ++j) {
+            if ((P >> j) & 1u) continue;
+            const int klo = alpha == 0.0 ? hi + 1 : lo;
+            for (int k = klo; k <= hi + 1; ++k) {
+                const double* same = k <= hi ? cur + off[k] : nullptr;
+                const double* prev = k - 1 >= lo ? cur + off[k - 1] : nullptr;
+                e = pcv::launch_photon_step(mc, cum, m, n, k, (const double2*)U, modes[j], same, prev, alpha, beta,
+                                            nxt + off[k], off[k + 1] - off[k], s);
+                if (e != cudaSuccess) return cuda_fail(e, "photon step");
+            }
+            lo = klo;
+            hi += 1;
+            std::swap(cur, nxt);
+        }
+        if ((e = pcv::launch_scale_add(prob + off[lo], cur + off[lo], wP, off[hi + 1] - off[lo], s)) != cudaSuccess)
+            return cuda_fail(e, "accumulate");
+    }
+    return PCV_OK;
 }

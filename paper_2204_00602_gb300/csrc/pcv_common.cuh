@@ -95,6 +95,10 @@ struct Plan {           // host-side description of one (U, input) problem
 };
 
 cudaError_t build_multiset_table(int64_t* t, int amax, int kmax, cudaStream_t s);
+// CUM[a*(kmax+1)+k] = sum_{v < a} MC[(m-v)*(kmax+1)+k] (a = 0..m): the rank of a
+// sorted mode list of length k is sum_p CUM[mode_p][k-p-1] - CUM[mode_{p-1}][k-p-1]
+// (slos.cu)
+cudaError_t build_cum_table(const int64_t* mc, int m, int kmax, int64_t* cum, cudaStream_t s);
 
 // Per-stage timing (pcv_api.cu): when enabled, stage_begin/stage_end record
 // CUDA events on the launching stream around a group of launches; the times
@@ -121,8 +125,23 @@ int tile_max_modes();
 cudaError_t launch_glynn_tile(const pcv_batch_desc& d, cudaStream_t s);
 cudaError_t launch_glynn_tile_multi(const pcv_batch_desc& d, int B, cudaStream_t s);
 int64_t batched_workspace(int n_circ, int64_t total_outputs);
+// copies a descriptor (passed by value) into device memory
+cudaError_t launch_store_desc(const pcv_batch_desc& d, pcv_batch_desc* out, cudaStream_t s);
+// route: PCV_ALGO_AUTO (per output, by FP64 instruction count), PCV_ALGO_TILE
+// or PCV_ALGO_MULT (every output to that kernel)
 cudaError_t launch_glynn_batched(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs, void* ws,
-                                 int sms, cudaStream_t s);
+                                 int sms, int route, cudaStream_t s);
+
+// Glynn's sum with multiplicities (glynn_mult.cu).  side: 0 = fewer terms,
+// 1 = sign vectors on the output modes, 2 = on the input modes.
+struct MultQueue {
+    int* counter;            // next entry
+    int* total;              // entries
+    const int* circ;         // circuit of entry e
+    const int* out;          // output index of entry e within its circuit
+};
+cudaError_t launch_glynn_mult(const pcv_batch_desc& d, int parts, int side, double2* partial, cudaStream_t s);
+cudaError_t launch_glynn_mult_persistent(const pcv_batch_desc* descs, const MultQueue& q, int sms, cudaStream_t s);
 
 // Adjoint (adjoint.cu), mesh (mesh.cu), reductions (reduce.cu)
 int adjoint_max_photons();
@@ -142,6 +161,16 @@ cudaError_t launch_prob_grad(const double* gp, const double2* amp, int64_t count
 // Exact boson sampling (sampler.cu)
 cudaError_t launch_sampler(const Plan& p, const double2* U, const uint8_t* perm, const double* uni, int64_t count,
                            uint8_t* out, cudaStream_t s);
+
+// Partially distinguishable photons (distinguish.cu); mc and cum are the
+// tables of S_{m,k} for k <= kmax.
+cudaError_t launch_photon_step(const int64_t* mc, const int64_t* cum, int m, int kmax, int k, const double2* U, int c,
+                               const double* in_same, const double* in_prev, double alpha, double beta, double* out,
+                               int64_t count, cudaStream_t s);
+cudaError_t launch_class_conv(const int64_t* mc, const int64_t* cum, int m, int kmax, int a, int b, const double* A,
+                              const double* B, double* C, int64_t count, cudaStream_t s);
+cudaError_t launch_scale_add(double* acc, const double* x, double w, int64_t count, cudaStream_t s);
+cudaError_t launch_set_one(double* p, cudaStream_t s);
 
 // Photon-by-photon state expansion (slos.cu)
 int64_t slos_workspace(int B, int m, int n);

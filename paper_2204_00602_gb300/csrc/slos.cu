@@ -157,6 +157,13 @@ cudaError_t slos_levels(SlosArgs a, int B, const Plan& p, double2* buf0, double2
 
 }  // namespace
 
+cudaError_t build_cum_table(const int64_t* mc, int m, int kmax, int64_t* cum, cudaStream_t s)
+{
+    cum_table_kernel<<<(kmax + 32) / 32, 32, 0, s>>>(mc, m, kmax, cum);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 // Workspace: MC and CUM tables, then two level buffers of the largest
 // intermediate level per batch entry.
 int64_t slos_workspace(int B, int m, int n)
@@ -186,9 +193,7 @@ cudaError_t launch_slos(const Plan& p, int B, const double2* U, double* prob, do
     double2* buf1 = (double2*)w;
     cudaError_t e = build_multiset_table(mc, m, n, s);
     if (e != cudaSuccess) return e;
-    cum_table_kernel<<<1, 32, 0, s>>>(mc, m, n, cum);
-    note_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = build_cum_table(mc, m, n, cum, s)) != cudaSuccess) return e;
     slos_init_kernel<<<(B + 127) / 128, 128, 0, s>>>(buf0, half, B);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -1,14 +1,17 @@
 """Secondary throughput workloads (the headline m=20 n=10 distribution is bench.py).
 
-    python -m paper_2204_00602_gb300.workloads batched [--circuits 512] [--outputs 4096]
+    python -m paper_2204_00602_gb300.workloads batched [--circuits 512] [--outputs 4096] [--route auto|tile|mult]
     python -m paper_2204_00602_gb300.workloads sweep [--nmin 16] [--nmax 30] [--outputs 256]
     python -m paper_2204_00602_gb300.workloads mesh   [--batch 64]
     python -m paper_2204_00602_gb300.workloads sample [--m 60] [--n 14] [--samples 200000]
     python -m paper_2204_00602_gb300.workloads pk [--unitaries 300] [--samples 20000]
+    python -m paper_2204_00602_gb300.workloads source [--m 12] [--n 6] [--eta 0.9] [--V 0.9]
 
 batched: uneven circuits (m ~ U{8..64}, n ~ U{4..min(24, m)}, Haar U, photons in
-modes 0..n-1, 4096 seeded random outputs each, collision-free for n <= 16) in
-one persistent launch of the shared-row-sum tile kernel.
+modes 0..n-1, 4096 seeded random outputs each, collision-free for n <= 16,
+uniform multisets above) in persistent launches: each output goes to the
+shared-row-sum tile kernel or to Glynn's sum with multiplicities, whichever
+issues fewer FP64 instructions (--route forces one of them).
 sweep: one Haar unitary per n = 16..30 at m = n^2, 256 collision-free outputs,
 plain Glynn block kernel (m is too large for the shared-row-sum tiles).
 mesh: the differentiable m=12 n=6 mesh, 64 phase sets, forward (all 12,376
@@ -44,21 +47,53 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def batched(n_circ: int, n_out: int, reps: int = 1):
+def _tile_splits(n: int) -> int:
+    return 1 if n <= 10 else 2 if n <= 13 else 4 if n <= 16 else 8
+
+
+def routed_fp64_instructions(m: int, n: int, outs: np.ndarray):
+    """FP64 pipe instructions per output under the batched launch's cost model
+    (single-photon input): the tile kernel's 2^{n-1} (4n - 2 + 2m/TILE) or, for
+    Glynn's sum with multiplicities, terms x (2q + 4n - 1) on the cheaper side.
+    Returns (tile-only instructions, routed instructions, outputs routed to the
+    multiplicity kernel)."""
+    tile = 2.0 ** (n - 1) * (4 * n - 2 + 2 * m / (256 // _tile_splits(n)))
+    s = outs.astype(np.int64)
+    d_out = (s > 0).sum(axis=1)
+    prod = np.prod(s + 1, axis=1).astype(np.float64)
+    odd = np.any(s % 2 == 1, axis=1)
+    big = s.max(axis=1)
+    t_out = np.where(odd, prod / 2, prod / (big + 1) * (big // 2 + 1))
+    cost_out = t_out * (2 * n + 4 * n - 1)              # product side: the n input photons
+    cost_in = 2.0 ** (n - 1) * (2 * d_out + 4 * n - 1)  # sign side: the n input photons
+    mult = np.minimum(cost_out, cost_in)
+    to_mult = mult < tile
+    return tile * len(s), float(np.where(to_mult, mult, tile).sum()), int(to_mult.sum())
+
+
+def batched(n_circ: int, n_out: int, reps: int = 1, route: str = "auto"):
+    from . import PCV_ALGO_AUTO, PCV_ALGO_MULT, PCV_ALGO_TILE
+    algo = {"auto": PCV_ALGO_AUTO, "tile": PCV_ALGO_TILE, "mult": PCV_ALGO_MULT}[route]
     g = np.random.default_rng(SEED)
     circs = []
-    work_fp64_instr = 0.0   # per output and sign vector: (n-1) complex products (4 each) + signed add (2)
-    fl = 0.0                # the same in flops: 6 per complex product, 2 per complex add
+    tile_instr = 0.0        # FP64 instructions if every output went to the tile kernel
+    routed_instr = 0.0      # the same under the routing model
+    n_mult = 0
+    fl = 0.0                # plain Glynn flops: 6 per complex product, 2 per complex add
     for c in range(n_circ):
         m = int(g.integers(8, 65))
         n = int(g.integers(4, min(24, m) + 1))
+        outs_np = pin.random_outputs(m, n, n_out, SEED + 5000 + c)
         U = torch.from_numpy(pin.haar_unitary(m, SEED + 1000 + c)).cuda()
-        outs = torch.from_numpy(pin.random_outputs(m, n, n_out, SEED + 5000 + c)).cuda()
-        circs.append((U, pin.single_photon_input(m, n), outs))
-        work_fp64_instr += n_out * 2 ** (n - 1) * (4 * n - 2)
+        circs.append((U, pin.single_photon_input(m, n), torch.from_numpy(outs_np).cuda()))
+        ti, ri, nm = routed_fp64_instructions(m, n, outs_np)
+        tile_instr += ti
+        routed_instr += ri if route == "auto" else ti
+        n_mult += nm if route == "auto" else 0
         fl += n_out * 2 ** (n - 1) * (6 * (n - 1) + 2)
-    plan = BatchPlan(circs, want_prob=True)
-    plan.run()
+    # warm-up on one output per circuit (module load, attribute setup)
+    BatchPlan([(U, t, o[:1]) for U, t, o in circs], want_prob=True, algo=algo).run()
+    plan = BatchPlan(circs, want_prob=True, algo=algo)
     torch.cuda.synchronize()
     a, b = _events()
     a.record()
@@ -68,10 +103,17 @@ def batched(n_circ: int, n_out: int, reps: int = 1):
     torch.cuda.synchronize()
     sec = a.elapsed_time(b) / 1e3 / reps
     amps = n_circ * n_out
-    return {"workload": f"batched {n_circ} uneven circuits x {n_out} outputs (m~U[8,64], n~U[4,24])",
-            "amplitudes_per_s": amps / sec, "seconds": sec, "amplitudes": amps,
-            "fp64_tflops": fl / sec / 1e12, "frac_of_fp64_peak": fl / sec / _peak_flops(),
-            "fp64_instr_per_s": work_fp64_instr / sec}
+    issue = _peak_flops() / 2          # DFMA-pipe instructions per second
+    r = {"workload": f"batched {n_circ} uneven circuits x {n_out} outputs (m~U[8,64], n~U[4,24])",
+         "route": route, "amplitudes_per_s": amps / sec, "seconds": sec, "amplitudes": amps,
+         "fp64_instr_per_s": routed_instr / sec, "frac_of_fp64_issue_rate": routed_instr / sec / issue,
+         "tile_only_fp64_instr": tile_instr, "routed_fp64_instr": routed_instr}
+    if route == "auto":
+        r["outputs_to_multiplicity_kernel"] = n_mult
+    if route == "tile":
+        r["fp64_tflops"] = fl / sec / 1e12
+        r["frac_of_fp64_peak"] = fl / sec / _peak_flops()
+    return r
 
 
 def sweep(nmin: int, nmax: int, n_out: int):
@@ -171,9 +213,30 @@ def pk_table(m: int, n: int, n_unitaries: int, samples_per_u: int):
             "gpu_sampling_s": gpu_s, "wall_s": wall, "rows": rows}
 
 
+def source(m: int, n: int, eta: float, V: float, reps: int = 3):
+    """Output distribution of an imperfect source (transmittance eta,
+    indistinguishability V): the mixture over the 2^n pure sets."""
+    from . import source_distribution
+    U = torch.from_numpy(pin.haar_unitary(m, SEED + 7000 + m)).cuda()
+    t = pin.single_photon_input(m, n)
+    p, off = source_distribution(U, t, eta, V)
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    for _ in range(reps):
+        p, off = source_distribution(U, t, eta, V)
+    b.record()
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3 / reps
+    return {"workload": f"imperfect source m={m} n={n} eta={eta} V={V}: all {off[-1]} photon-number-resolved outputs",
+            "seconds": sec, "outputs": off[-1], "pure_sets": 2 ** n, "sum": float(p.sum().item())}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["batched", "sweep", "mesh", "sample", "pk"])
+    ap.add_argument("which", choices=["batched", "sweep", "mesh", "sample", "pk", "source"])
+    ap.add_argument("--eta", type=float, default=0.9)
+    ap.add_argument("--V", type=float, default=0.9)
     ap.add_argument("--unitaries", type=int, default=300)
     ap.add_argument("--m", type=int, default=60)
     ap.add_argument("--n", type=int, default=14)
@@ -183,13 +246,16 @@ def main():
     ap.add_argument("--nmin", type=int, default=16)
     ap.add_argument("--nmax", type=int, default=30)
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--route", choices=["auto", "tile", "mult"], default="auto")
     a = ap.parse_args()
     if a.which == "batched":
-        r = batched(a.circuits, a.outputs or 4096)
+        r = batched(a.circuits, a.outputs or 4096, route=a.route)
     elif a.which == "sweep":
         r = sweep(a.nmin, a.nmax, a.outputs or 256)
     elif a.which == "mesh":
         r = mesh(a.batch)
+    elif a.which == "source":
+        r = source(a.m, a.n, a.eta, a.V)
     elif a.which == "sample":
         r = sampling(a.m, a.n, a.samples)
     else:

@@ -111,6 +111,9 @@ def test_argument_errors_are_reported_before_any_launch():
         (dict(U=fake, m=3, algo=_abi.PCV_ALGO_GROUP, param=3), _abi.PCV_EINVAL),
         (dict(U=fake, m=3, algo=_abi.PCV_ALGO_GROUP, param=4), _abi.PCV_EINVAL),   # 4 > 2^(n-1)
         (dict(U=fake, m=3, algo=_abi.PCV_ALGO_BLOCK, param=1), _abi.PCV_EINVAL),   # n < 9
+        (dict(U=fake, m=3, algo=_abi.PCV_ALGO_MULT, param=-1), _abi.PCV_EINVAL),
+        (dict(U=fake, m=3, algo=_abi.PCV_ALGO_MULT, param=1025), _abi.PCV_EINVAL),
+        (dict(U=fake, m=3, algo=_abi.PCV_ALGO_MULT, param=4), _abi.PCV_ENOMEM),    # partial sums need workspace
     ]
     for kw, code in cases:
         a = dict(U=fake, m=3, input=t, out=fake, n_out=4, amp=fake, prob=None, algo=0, param=0)
@@ -137,3 +140,54 @@ def test_distribution_workspace_sizes():
         fake = 1 << 40
         _abi.pcv_distribution(fake, 20, np.array([1] * 10 + [0] * 10, np.uint8), fake, None, fake, small - 1024, None)
     assert e.value.code in (_abi.PCV_ENOMEM, _abi.PCV_EINVAL)
+
+
+def test_explicit_algorithm_workspace_sizes():
+    from paper_2204_00602_gb300 import _abi
+    assert _abi.pcv_amplitudes_ex_workspace(20, 10, 100, _abi.PCV_ALGO_MULT, 1) == 0
+    assert _abi.pcv_amplitudes_ex_workspace(20, 10, 100, _abi.PCV_ALGO_MULT, 4) >= 100 * 4 * 16
+    # automatic warps per permanent: small output counts get several warps each
+    assert _abi.pcv_amplitudes_ex_workspace(20, 10, 10, _abi.PCV_ALGO_MULT, 0) >= 10 * 2 * 16
+    assert _abi.pcv_amplitudes_ex_workspace(20, 10, 1 << 20, _abi.PCV_ALGO_MULT, 0) == 0
+    assert _abi.pcv_amplitudes_ex_workspace(20, 12, 100, _abi.PCV_ALGO_BLOCK, 2) >= 100 * 2 * 16
+    assert _abi.pcv_amplitudes_ex_workspace(20, 10, 100, _abi.PCV_ALGO_AUTO, 0) == \
+        _abi.pcv_amplitudes_workspace(20, 10, 100)
+    with pytest.raises(_abi.PcvError) as e:
+        _abi.pcv_amplitudes_ex_workspace(20, 10, 100, _abi.PCV_ALGO_MULT, 5000)
+    assert e.value.code == _abi.PCV_EINVAL
+
+
+def test_batched_routing_is_checked():
+    from paper_2204_00602_gb300 import _abi
+    fake = 1 << 40
+    for algo in (_abi.PCV_ALGO_GROUP, _abi.PCV_ALGO_FACTOR, 99):
+        with pytest.raises(_abi.PcvError) as e:
+            _abi.pcv_amplitudes_batched_ex(fake, 2, 10, algo, fake, 1 << 20, None)
+        assert e.value.code == _abi.PCV_EINVAL
+    with pytest.raises(_abi.PcvError) as e:
+        _abi.pcv_amplitudes_batched_ex(fake, 2, 1 << 31, _abi.PCV_ALGO_AUTO, fake, 1 << 40, None)
+    assert e.value.code == _abi.PCV_ERANGE
+    # the work lists grow with the outputs: three ints per output at least
+    assert _abi.pcv_amplitudes_batched_workspace(4, 1000) >= 3 * 4 * 1000
+
+
+def test_distinguishability_arguments_are_checked():
+    from paper_2204_00602_gb300 import _abi
+    fake = 1 << 40
+    with pytest.raises(_abi.PcvError) as e:       # 17 photons: 2^17 pure sets is over the limit
+        _abi.pcv_distribution_source(fake, 20, np.array([1] * 17 + [0] * 3, np.uint8), 1.0, 1.0, fake, fake,
+                                     1 << 40, None)
+    assert e.value.code == _abi.PCV_EINVAL
+    for eta, V in ((1.2, 1.0), (0.5, -0.1), (float("nan"), 0.5)):
+        with pytest.raises(_abi.PcvError) as e:
+            _abi.pcv_distribution_source(fake, 4, np.array([1, 1, 0, 0], np.uint8), eta, V, fake, fake, 1 << 40, None)
+        assert e.value.code == _abi.PCV_EINVAL
+    cls = np.zeros((2, 4), np.uint8)
+    cls[0, 0] = 20
+    cls[1, 1] = 11                                 # 31 photons in all
+    with pytest.raises(_abi.PcvError) as e:
+        _abi.pcv_distribution_classes_workspace(4, 2, cls)
+    assert e.value.code == _abi.PCV_EINVAL
+    assert _abi.pcv_distribution_source_size(6, 3) == sum(math.comb(6 + k - 1, k) for k in range(4))
+    cls[0, 0], cls[1, 1] = 2, 1
+    assert _abi.pcv_distribution_classes_workspace(4, 2, cls) > 0
