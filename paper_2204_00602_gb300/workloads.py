@@ -91,10 +91,19 @@ def batched(n_circ: int, n_out: int, reps: int = 1, route: str = "auto"):
         routed_instr += ri if route == "auto" else ti
         n_mult += nm if route == "auto" else 0
         fl += n_out * 2 ** (n - 1) * (6 * (n - 1) + 2)
+    # under torchrun: each rank takes its share of the circuits by greedy
+    # longest-processing-time on the routed cost; no exchange on the data path
+    from .sharding import circuit_cost, lpt_assign, world_and_rank
+    world, rank = world_and_rank()
+    if world > 1:
+        costs = [circuit_cost(c[0].shape[0], int(c[1].sum()), c[1], c[2].cpu().numpy()) for c in circs]
+        circs = [circs[i] for i in lpt_assign(costs, world)[rank]]
     # warm-up on one output per circuit (module load, attribute setup)
     BatchPlan([(U, t, o[:1]) for U, t, o in circs], want_prob=True, algo=algo).run()
     plan = BatchPlan(circs, want_prob=True, algo=algo)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     a, b = _events()
     a.record()
     for _ in range(reps):
@@ -102,6 +111,10 @@ def batched(n_circ: int, n_out: int, reps: int = 1, route: str = "auto"):
     b.record()
     torch.cuda.synchronize()
     sec = a.elapsed_time(b) / 1e3 / reps
+    if world > 1:                      # the job takes as long as its slowest rank
+        t = torch.tensor([sec], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        sec = float(t.item())
     amps = n_circ * n_out
     issue = _peak_flops() / 2          # DFMA-pipe instructions per second
     r = {"workload": f"batched {n_circ} uneven circuits x {n_out} outputs (m~U[8,64], n~U[4,24])",
@@ -248,6 +261,10 @@ def main():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--route", choices=["auto", "tile", "mult"], default="auto")
     a = ap.parse_args()
+    import os
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:          # torchrun: one rank per GPU
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
     if a.which == "batched":
         r = batched(a.circuits, a.outputs or 4096, route=a.route)
     elif a.which == "sweep":
@@ -260,7 +277,10 @@ def main():
         r = sampling(a.m, a.n, a.samples)
     else:
         r = pk_table(a.m, a.n, a.unitaries, a.samples)
-    print(json.dumps(r), flush=True)
+    if not torch.distributed.is_initialized() or torch.distributed.get_rank() == 0:
+        print(json.dumps(r), flush=True)
+    if torch.distributed.is_initialized():
+        torch.distributed.destroy_process_group()
 
 
 if __name__ == "__main__":
