@@ -183,8 +183,14 @@ __device__ double2 mult_range(const double2* __restrict__ U, const MultWarp& w, 
     if (g0 >= g1) return acc;
     const int d = w.d, q = w.q, piv = w.piv;
     double2 x[QMAX];
+    int oo[QMAX];                               // product-side offsets, kept in registers
+    bool ones = true;                           // every product-side multiplicity is 1
 #pragma unroll
-    for (int i = 0; i < QMAX; ++i) x[i] = make_double2(0.0, 0.0);
+    for (int i = 0; i < QMAX; ++i) {
+        x[i] = make_double2(0.0, 0.0);
+        oo[i] = i < q ? w.ooff[i] : 0;
+        if (i < q && w.e[i] != 1) ones = false;
+    }
     // digits of g0: with a_j the plain mixed-radix digits and h_j the number
     // formed by the digits above j, k_j = a_j if h_j is even, R_j - 1 - a_j if
     // odd; the parity of h_j is also the direction k_j moves next.
@@ -206,15 +212,32 @@ __device__ double2 mult_range(const double2* __restrict__ U, const MultWarp& w, 
         const double2* Uj = U + w.moff[j];
 #pragma unroll
         for (int i = 0; i < QMAX; ++i)
-            if (i < q) caxpy(x[i], f, ld(Uj + w.ooff[i]));
+            if (i < q) caxpy(x[i], f, ld(Uj + oo[i]));
     }
     for (uint64_t g = g0;;) {
-        double2 p = x[0];
-        for (int t = 1; t < w.e[0]; ++t) p = cmul(p, x[0]);
+        double2 p;
+        if (ones) {
+            // two independent chains (even and odd i) joined at the end: the
+            // same n - 1 complex products with twice the instruction-level
+            // parallelism
+            double2 pa = x[0];
+            double2 pb = q > 1 ? x[1] : make_double2(1.0, 0.0);
 #pragma unroll
-        for (int i = 1; i < QMAX; ++i)
-            if (i < q)
-                for (int t = 0; t < w.e[i]; ++t) p = cmul(p, x[i]);
+            for (int i = 2; i < QMAX; ++i) {
+                if (i < q) {
+                    if (i & 1) pb = cmul(pb, x[i]);
+                    else pa = cmul(pa, x[i]);
+                }
+            }
+            p = q > 1 ? cmul(pa, pb) : pa;
+        } else {
+            p = x[0];
+            for (int t = 1; t < w.e[0]; ++t) p = cmul(p, x[0]);
+#pragma unroll
+            for (int i = 1; i < QMAX; ++i)
+                if (i < q)
+                    for (int t = 0; t < w.e[i]; ++t) p = cmul(p, x[i]);
+        }
         double cf = (double)cw;
         if (par & 1u) cf = -cf;
         acc.x = fma(cf, p.x, acc.x);
@@ -240,7 +263,7 @@ __device__ double2 mult_range(const double2* __restrict__ U, const MultWarp& w, 
         const double2* Uj = U + w.moff[j];
 #pragma unroll
         for (int i = 0; i < QMAX; ++i)
-            if (i < q) caxpy(x[i], f, ld(Uj + w.ooff[i]));
+            if (i < q) caxpy(x[i], f, ld(Uj + oo[i]));
         const bool pj = j == piv;
         cw = cw / weight(binom, w.mu[j], b, pj) * weight(binom, w.mu[j], nb, pj);
         par ^= 1u;

@@ -291,9 +291,28 @@ __device__ double mult_side_cost(const int* mu, int d, int q, int n)
     return t * (2.0 * q + 4.0 * n - 1.0);
 }
 
+// FP64 instructions of output o by Glynn's sum with multiplicities on its
+// cheaper side; a negative value for an output outside S_{m,n} (amplitude 0).
+__device__ double output_mult_cost(const pcv_batch_desc& c, int64_t o, const int* imu, int d_in)
+{
+    const uint8_t* occ = c.outputs + o * c.m;
+    int omu[PCV_MAX_PHOTONS];
+    int d_out = 0, tot = 0;
+    for (int r = 0; r < c.m; ++r) {
+        const int v = occ[r];
+        if (v > 0 && d_out < PCV_MAX_PHOTONS) omu[d_out++] = v;
+        tot += v;
+    }
+    if (tot != c.n) return -1.0;
+    return fmin(mult_side_cost(omu, d_out, d_in, c.n), mult_side_cost(imu, d_in, d_out, c.n));
+}
+
 // One block per circuit: route each output to the tile kernel or to Glynn's
 // sum with multiplicities; idx[out_off[c] ..] lists the tile outputs first
-// (in order) and the others after them (in reverse order).
+// (in order) and the others after them (in reverse order).  A tile block
+// costs as much with one live output as with TILE of them, so a last,
+// partly filled tile is re-routed when its outputs cost less on the
+// multiplicity kernel than the whole block.
 __global__ void __launch_bounds__(256) classify_kernel(const pcv_batch_desc* descs, const int64_t* out_off, int route,
                                                        int64_t cap, int* idx, int* n_tile, int* n_mult)
 {
@@ -326,20 +345,8 @@ __global__ void __launch_bounds__(256) classify_kernel(const pcv_batch_desc* des
             if (route == PCV_ALGO_MULT) {
                 to_mult = 1;
             } else if (route == PCV_ALGO_AUTO) {
-                const uint8_t* occ = c.outputs + o * m;
-                int omu[PCV_MAX_PHOTONS];
-                int d_out = 0, tot = 0;
-                for (int r = 0; r < m; ++r) {
-                    const int v = occ[r];
-                    if (v > 0 && d_out < PCV_MAX_PHOTONS) omu[d_out++] = v;
-                    tot += v;
-                }
-                if (tot != n) {
-                    to_mult = 1;                      // not in S_{m,n}: amplitude 0, cheapest there
-                } else {
-                    const double cm = fmin(mult_side_cost(omu, d_out, d_in, n), mult_side_cost(imu, d_in, d_out, n));
-                    to_mult = cm < ct;
-                }
+                const double cm = output_mult_cost(c, o, imu, d_in);
+                to_mult = cm < ct;                    // cm < 0: not in S_{m,n}, amplitude 0
             }
         }
         int tot_m = 0;
@@ -357,6 +364,30 @@ __global__ void __launch_bounds__(256) classify_kernel(const pcv_batch_desc* des
             s_mult += tot_m;
         }
         __syncthreads();
+    }
+    if (route == PCV_ALGO_AUTO) {
+        const int tilesz = kThreads / tile_splits(n);
+        const int r = s_tile % tilesz;
+        if (r > 0) {
+            // the last r tile outputs sit just below the multiplicity outputs
+            // in the list; moving the boundary re-routes them
+            double part = 0.0;
+            for (int k = threadIdx.x; k < r; k += blockDim.x)
+                part += output_mult_cost(c, list[s_tile - r + k], imu, d_in);
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            __shared__ double wsum[8];
+            if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = part;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsum[w];
+                if (tot < ct * tilesz) {
+                    s_tile -= r;
+                    s_mult += r;
+                }
+            }
+            __syncthreads();
+        }
     }
     if (threadIdx.x == 0) {
         n_tile[ci] = s_tile;

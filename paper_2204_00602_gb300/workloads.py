@@ -52,11 +52,12 @@ def _tile_splits(n: int) -> int:
 
 
 def routed_fp64_instructions(m: int, n: int, outs: np.ndarray):
-    """FP64 pipe instructions per output under the batched launch's cost model
-    (single-photon input): the tile kernel's 2^{n-1} (4n - 2 + 2m/TILE) or, for
-    Glynn's sum with multiplicities, terms x (2q + 4n - 1) on the cheaper side.
-    Returns (tile-only instructions, routed instructions, outputs routed to the
-    multiplicity kernel)."""
+    """FP64 pipe instructions under the batched launch's cost model
+    (single-photon input): the tile kernel's 2^{n-1} (4n - 2 + 2m/TILE) per
+    output, a tile block costing as much as TILE outputs however many are live,
+    or, for Glynn's sum with multiplicities, terms x (2q + 4n - 1) on the
+    cheaper side.  Returns (tile-only instructions, routed instructions,
+    outputs routed to the multiplicity kernel)."""
     tile = 2.0 ** (n - 1) * (4 * n - 2 + 2 * m / (256 // _tile_splits(n)))
     s = outs.astype(np.int64)
     d_out = (s > 0).sum(axis=1)
@@ -68,7 +69,16 @@ def routed_fp64_instructions(m: int, n: int, outs: np.ndarray):
     cost_in = 2.0 ** (n - 1) * (2 * d_out + 4 * n - 1)  # sign side: the n input photons
     mult = np.minimum(cost_out, cost_in)
     to_mult = mult < tile
-    return tile * len(s), float(np.where(to_mult, mult, tile).sum()), int(to_mult.sum())
+    # a last, partly filled tile goes to the multiplicity kernel when its
+    # outputs cost less there than the whole tile block (as the routing kernel does)
+    tile_idx = np.flatnonzero(~to_mult)
+    tsz = 256 // _tile_splits(n)
+    r = len(tile_idx) % tsz
+    if r and mult[tile_idx[-r:]].sum() < tile * tsz:
+        to_mult[tile_idx[-r:]] = True
+    n_tile_blocks = -(-int((~to_mult).sum()) // tsz)
+    routed = n_tile_blocks * tsz * tile + float(mult[to_mult].sum())
+    return tile * len(s), routed, int(to_mult.sum())
 
 
 def batched(n_circ: int, n_out: int, reps: int = 1, route: str = "auto"):
