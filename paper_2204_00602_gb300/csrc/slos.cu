@@ -7,10 +7,17 @@
 // |psi_k> = prod_{j<=k} (sum_r U[r][c_j] a_r^dagger) |0> = sum_{s in S_{m,k}} B_k(s) |s>
 // and a_r^dagger |s - e_r> = sqrt(s_r) |s>,
 //     B_k(s) = sum_{r : s_r >= 1} U[r][c_k] sqrt(s_r) B_{k-1}(s - e_r),
-// B_0 = 1, and a(S) = B_n(S) / sqrt(prod t!).  Each level k is a gather: one
-// thread per state s of S_{m,k} (canonical order) adds one complex
-// multiply-add per distinct occupied mode.  The last level is the
-// distribution in canonical order.
+// B_0 = 1, and a(S) = B_n(S) / sqrt(prod t!).  The kernels carry
+// C_k(s) = B_k(s) / sqrt(prod_r s_r!) instead: since (s - e_r)! differs from
+// s! by the factor s_r, the square roots cancel and
+//     C_k(s) = sum_{r : s_r >= 1} U[r][c_k] C_{k-1}(s - e_r),
+// a plain gather with one complex multiply-add per distinct occupied mode
+// and no square root; the last level applies
+// a(S) = C_n(S) sqrt(prod s!) / sqrt(prod t!).  One thread per state s of
+// S_{m,k} (canonical order); the last level is the distribution in
+// canonical order.
+
+#include <cmath>
 
 #include "pcv_common.cuh"
 
@@ -42,6 +49,7 @@ struct SlosArgs {
     const double2* prev;       // [B][C(m+k-2, k-1)]
     double2* cur;              // [B][count] (intermediate levels)
     double norm_t;             // last level: 1/sqrt(prod t!)
+    double sqrtfact[PCV_MAX_PHOTONS + 1];   // sqrt(j!)
     double2* amp;              // last level outputs (or null)
     double* prob;
 };
@@ -71,33 +79,39 @@ __global__ void __launch_bounds__(256) slos_level_kernel(const SlosArgs a)
     }
     const double2* U = a.U + (size_t)b * m * m;
     const double2* prev = a.prev + (size_t)b * a.prev_stride;
+    // Predecessor of position p (the list without modes[p]) in S_{m,k-1}:
+    //   rank_p = A_p + J_p + B_p, with
+    //   A_p = sum_{q<p} CUM[modes_q][k-2-q] - CUM[modes_{q-1}][k-2-q]   (positions before p keep their index)
+    //   J_p = CUM[modes_{p+1}][k-2-p] - CUM[modes_{p-1}][k-2-p]         (the position after p, shifted down)
+    //   B_p = sum_{q>=p+2} CUM[modes_q][k-1-q] - CUM[modes_{q-1}][k-1-q] (later positions, shifted down)
+    // with modes_{-1} = 0; B is a suffix sum, so all predecessors cost O(k).
+    int64_t suffix = 0;                        // B for the current p, starting from the full sum over q >= 2
+    for (int q = 2; q < k; ++q) suffix += a.cum[modes[q] * W + (k - 1 - q)] - a.cum[modes[q - 1] * W + (k - 1 - q)];
     double2 acc = make_double2(0.0, 0.0);
-    // for each distinct mode r (its last occurrence at position p): predecessor
-    // = the list without position p (still sorted), ranked in S_{m,k-1}
+    int64_t pre = 0;                           // A_p
+    int mult = 0;
+    double sfac = 1.0;                         // sqrt(prod s!) (used by the last level)
     for (int p = 0; p < k; ++p) {
-        if (p + 1 < k && modes[p + 1] == modes[p]) continue;
         const int r = modes[p];
-        int mult = 1;
-        for (int q = p - 1; q >= 0 && modes[q] == r; --q) ++mult;
-        int64_t rk = 0;
-        int prevm = 0, pos = 0;
-        for (int q = 0; q < k; ++q) {
-            if (q == p) continue;
-            const int rest = (k - 1) - pos - 1;
-            rk += a.cum[modes[q] * W + rest] - a.cum[prevm * W + rest];
-            prevm = modes[q];
-            ++pos;
+        mult = (p > 0 && modes[p - 1] == r) ? mult + 1 : 1;
+        const bool last = !(p + 1 < k && modes[p + 1] == r);   // one term per distinct mode, at its last copy
+        if (last) {
+            const int before = p > 0 ? modes[p - 1] : 0;
+            const int64_t junction = p + 1 < k ? a.cum[modes[p + 1] * W + (k - 2 - p)] - a.cum[before * W + (k - 2 - p)] : 0;
+            const int64_t rk = pre + junction + suffix;
+            cmac(acc, U[(size_t)r * m + a.col], prev[rk]);
+            if (mult > 1) sfac *= a.sqrtfact[mult];
         }
-        double2 u = U[(size_t)r * m + a.col];
-        if (mult > 1) {
-            const double sq = sqrt((double)mult);
-            u.x *= sq;
-            u.y *= sq;
+        // advance to p + 1: A gains position p at rest k-2-p; B loses position p+2
+        if (p + 1 < k) {
+            const int pm = p > 0 ? modes[p - 1] : 0;
+            pre += a.cum[r * W + (k - 2 - p)] - a.cum[pm * W + (k - 2 - p)];
+            if (p + 2 < k) suffix -= a.cum[modes[p + 2] * W + (k - 3 - p)] - a.cum[modes[p + 1] * W + (k - 3 - p)];
         }
-        cmac(acc, u, prev[rk]);
     }
     if (a.amp || a.prob) {
-        const double2 v = make_double2(acc.x * a.norm_t, acc.y * a.norm_t);
+        const double sc = sfac * a.norm_t;
+        const double2 v = make_double2(acc.x * sc, acc.y * sc);
         if (a.amp) a.amp[(size_t)b * a.cur_stride + i] = v;
         if (a.prob) a.prob[(size_t)b * a.cur_stride + i] = fma(v.x, v.x, v.y * v.y);
     } else {
@@ -205,6 +219,14 @@ cudaError_t launch_slos(const Plan& p, int B, const double2* U, double* prob, do
     a.mc = mc;
     a.cum = cum;
     a.norm_t = p.norm_t;
+    {
+        double f = 1.0;
+        a.sqrtfact[0] = 1.0;
+        for (int j = 1; j <= PCV_MAX_PHOTONS; ++j) {
+            f *= j;
+            a.sqrtfact[j] = std::sqrt(f);
+        }
+    }
     if (n <= 8) return slos_levels<8>(a, B, p, buf0, buf1, half, prob, amp, s);
     if (n <= 16) return slos_levels<16>(a, B, p, buf0, buf1, half, prob, amp, s);
     return slos_levels<PCV_MAX_PHOTONS>(a, B, p, buf0, buf1, half, prob, amp, s);

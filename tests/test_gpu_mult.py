@@ -222,3 +222,34 @@ def test_auto_routes_single_circuit_explicit_outputs(pcv):
     assert amp_err(auto, tile, m, n) <= tol(n)
     pick = np.r_[0:40, 5980:6040, 9960:10000]
     assert amp_err(auto[pick], oracle.amplitudes(U, t, outs[pick]), m, n) <= tol(n)
+
+
+def test_batched_workload_full_size_sampled():
+    """The 512-circuit x 4096-output uneven workload in the launch configuration
+    the workload runner times (AUTO routing): every amplitude finite with
+    prob = |amp|^2 <= 1; two outputs of every circuit with n <= 16 and one
+    output of 16 seeded circuits with n >= 17 against the oracle."""
+    import paper_2204_00602_gb300 as pcv
+    g = np.random.default_rng(pin.BASE_SEED + 3)
+    circs = []
+    for c in range(512):                       # the workload runner's recipe
+        m = int(g.integers(8, 65))
+        n = int(g.integers(4, min(24, m) + 1))
+        circs.append(dict(m=m, n=n, U=pin.haar_unitary(m, pin.BASE_SEED + 3 + 1000 + c),
+                          input_occ=pin.single_photon_input(m, n),
+                          outputs=pin.random_outputs(m, n, 4096, pin.BASE_SEED + 3 + 5000 + c)))
+    amps, probs = _batch(pcv, circs, pcv.PCV_ALGO_AUTO)
+    pick = np.random.default_rng(4301)
+    big = [i for i, c in enumerate(circs) if c["n"] >= 17]
+    checked_big = set(pick.choice(big, size=16, replace=False).tolist())
+    for i, (c, a, p) in enumerate(zip(circs, amps, probs)):
+        assert np.all(np.isfinite(a)) and np.all(p <= 1.0)
+        assert np.allclose(p, np.abs(a) ** 2, rtol=1e-12, atol=0)
+        if c["n"] <= 16:
+            k = pick.choice(4096, size=2, replace=False)
+        elif i in checked_big:
+            k = pick.choice(4096, size=1)
+        else:
+            continue
+        ref = ref_amplitudes(c["U"], c["input_occ"], c["outputs"][k], c["n"])
+        assert amp_err(a[k], ref, c["m"], c["n"]) <= tol(c["n"]), (i, c["m"], c["n"])
