@@ -12,7 +12,9 @@ L(phi) = KL(q || p(phi)) restricted to the set (= -sum q log p + const).
   MLP backward to its inputs and the sin/cos chain give dL/dphi.  Every
   `check_every` steps the exact probabilities of the set are computed and the
   surrogate's TVD on the set, 1/2 sum |p_hat - p|, is checked; above `tvd_tol`
-  the loop uses exact gradients for the next `check_every` steps.
+  the loop uses exact gradients for the next `check_every` steps.  Optionally
+  the network is refined online on the exact probabilities the loop computes
+  anyway (``refine_steps``).
 """
 from __future__ import annotations
 
@@ -95,9 +97,46 @@ def exact_loop(problem: MeshProblem, phases0: torch.Tensor, steps: int, lr: floa
     return phases, wall
 
 
+class TrajectoryBuffer:
+    """Ring buffer of (phases, log p of the set) met along the optimisation, for
+    refining the surrogate online (exact probabilities are computed anyway at
+    every check and every exact step)."""
+
+    def __init__(self, size: int, n_phases: int, n_set: int, device, seed: int = 1):
+        self.ph = torch.zeros(size, n_phases, dtype=torch.float64, device=device)
+        self.y = torch.zeros(size, n_set, dtype=torch.float32, device=device)
+        self.size, self.filled, self.head = size, 0, 0
+        self.gen = torch.Generator(device=device)
+        self.gen.manual_seed(seed)
+
+    def push(self, phases: torch.Tensor, p: torch.Tensor):
+        k = phases.shape[0]
+        idx = (torch.arange(k, device=phases.device) + self.head) % self.size
+        self.ph[idx] = phases
+        self.y[idx] = torch.log(torch.clamp(p, min=1e-300)).to(torch.float32)
+        self.head = (self.head + k) % self.size
+        self.filled = min(self.size, self.filled + k)
+
+    def refine(self, net: MLP, steps: int, batch: int = 512):
+        bs = min(batch, self.filled) // 32 * 32          # the training kernels take multiples of 32 rows
+        if bs == 0:
+            return
+        for _ in range(steps):
+            sel = torch.randint(0, self.filled, (bs,), device=self.ph.device, generator=self.gen)
+            net.train_step(net.features(self.ph[sel]), self.y[sel])
+
+
 def surrogate_loop(problem: MeshProblem, net: MLP, phases0: torch.Tensor, steps: int, lr: float = 0.02,
-                   check_every: int = 50, tvd_tol: float = 1e-3):
+                   check_every: int = 50, tvd_tol: float = 1e-3, refine_steps: int = 0,
+                   refine_lr: float = 1e-3, buffer_size: int = 4096):
+    """The gated loop.  With refine_steps > 0 the network is also trained
+    online: the exact probabilities met at every check and every exact step go
+    to a ring buffer, and after each check `refine_steps` Adam steps (learning
+    rate refine_lr) are taken on random batches of it."""
     phases = phases0.clone()
+    buf = TrajectoryBuffer(buffer_size, problem.P, problem.n_set, phases.device) if refine_steps > 0 else None
+    if buf is not None:
+        net.lr = refine_lr
     opt = Adam64(phases, lr)
     B = phases.shape[0]
     dy = torch.empty(B, problem.n_set, dtype=torch.bfloat16, device=phases.device)
@@ -124,9 +163,14 @@ def surrogate_loop(problem: MeshProblem, net: MLP, phases0: torch.Tensor, steps:
             tvds.append(tvd)
             if tvd > tvd_tol:
                 use_exact_until = s + check_every
+            if buf is not None:
+                buf.push(phases, p)
+                buf.refine(net, refine_steps)
         if s < use_exact_until:
             g = problem.loss_and_grad(phases)
             exact_steps += 1
+            if buf is not None:
+                buf.push(phases, problem.prob)
         else:
             net.predict_phases(phases)
             g = net.grad_phases(phases, dy)
@@ -134,7 +178,8 @@ def surrogate_loop(problem: MeshProblem, net: MLP, phases0: torch.Tensor, steps:
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     return phases, wall, {"exact_steps": exact_steps, "checks": checks, "max_tvd_seen": max(tvds),
-                          "min_tvd_seen": min(tvds), "tvd_tol": tvd_tol}
+                          "min_tvd_seen": min(tvds), "median_tvd_seen": float(np.median(tvds)), "tvd_tol": tvd_tol,
+                          "refine_steps": refine_steps}
 
 
 def time_to_target(problem: MeshProblem, net: MLP, phases0: torch.Tensor, target: float, warm_steps: int,
@@ -198,7 +243,8 @@ def validate(net: MLP, problem: MeshProblem, phases: torch.Tensor):
     return dist_stats(p, phat)[:, 1]
 
 
-def run(samples: int, epochs: int, steps: int, B: int, seed: int = 2204006025, lr_net: float = 1e-3):
+def run(samples: int, epochs: int, steps: int, B: int, seed: int = 2204006025, lr_net: float = 1e-3,
+        refine: bool = True):
     problem = MeshProblem(B=B, seed=seed)
     t0 = time.perf_counter()
     ph_train, y_train = make_dataset(problem, samples, seed + 10)
@@ -218,6 +264,14 @@ def run(samples: int, epochs: int, steps: int, B: int, seed: int = 2204006025, l
     loss_e = problem.loss(ph_e).clone()
     ph_s, wall_s, info = surrogate_loop(problem, net, phases0, steps)
     loss_s = problem.loss(ph_s).clone()
+    refined = None
+    if refine:
+        # online refinement on the trajectory, from a copy of the trained network
+        net_r = MLP([w.cpu().numpy() for w in net.W], [b.cpu().numpy() for b in net.b], lr=lr_net,
+                    tensor_core=net.tensor_core)
+        ph_r, wall_r, info_r = surrogate_loop(problem, net_r, phases0, steps, check_every=10, refine_steps=20)
+        refined = {"wall_s": wall_r, "loss_mean": float(problem.loss(ph_r).cpu().numpy().mean()), **info_r,
+                   "check_every": 10}
     # the same loop without the TVD gate: what the network alone achieves
     ph_u, wall_u, info_u = surrogate_loop(problem, net, phases0, steps, check_every=steps + 1, tvd_tol=float("inf"))
     loss_u = problem.loss(ph_u).clone()
@@ -236,6 +290,7 @@ def run(samples: int, epochs: int, steps: int, B: int, seed: int = 2204006025, l
         "exact": {"wall_s": wall_e, "loss_mean": float(loss_e.cpu().numpy().mean())},
         "surrogate": {"wall_s": wall_s, "loss_mean": float(loss_s.cpu().numpy().mean()), **info},
         "speedup_wall": wall_e / wall_s,
+        "surrogate_refined_online": refined,
         "surrogate_ungated": {"wall_s": wall_u, "loss_mean": float(loss_u.cpu().numpy().mean()),
                               "exact_steps": info_u["exact_steps"]},
         "tensor_core": net.tensor_core,
@@ -248,8 +303,9 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--no-refine", action="store_true", help="skip the online-refinement variant")
     a = ap.parse_args(argv)
-    print(json.dumps(run(a.samples, a.epochs, a.steps, a.batch)), flush=True)
+    print(json.dumps(run(a.samples, a.epochs, a.steps, a.batch, refine=not a.no_refine)), flush=True)
 
 
 if __name__ == "__main__":

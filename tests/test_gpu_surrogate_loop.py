@@ -36,3 +36,22 @@ def test_exact_loop_descends_and_surrogate_steps_are_cheaper():
     # surrogate is off: the exact steps are counted and reported
     _, _, info = opt.surrogate_loop(prob, net, ph0, 100, check_every=50, tvd_tol=1e-3)
     assert info["checks"] == 2 and 0 <= info["exact_steps"] <= 100
+
+
+def test_online_refinement_lowers_the_surrogate_tvd():
+    # refinement on the trajectory's exact probabilities (computed anyway at
+    # checks and exact steps) must bring the surrogate closer to the exact
+    # kernel along the path than the same network without it
+    from paper_2204_00602_gb300 import optimize as opt
+    from paper_2204_00602_gb300.surrogate import MLP, init_weights
+    prob = opt.MeshProblem(B=16)
+    ph0 = torch.from_numpy(np.random.default_rng(2).uniform(0, 2 * np.pi, (16, prob.P))).cuda()
+    ph_tr, y_tr = opt.make_dataset(prob, 32768, 7)
+    Ws, bs = init_weights(8)
+    base = MLP(Ws, bs, lr=1e-3)
+    opt.train(base, ph_tr, y_tr, epochs=2)
+    copy = lambda: MLP([w.cpu().numpy() for w in base.W], [b.cpu().numpy() for b in base.b], lr=1e-3)  # noqa: E731
+    _, _, plain = opt.surrogate_loop(prob, copy(), ph0, 200, check_every=10, tvd_tol=1e-3)
+    _, _, refined = opt.surrogate_loop(prob, copy(), ph0, 200, check_every=10, tvd_tol=1e-3, refine_steps=20)
+    assert refined["refine_steps"] == 20 and refined["checks"] == 20
+    assert refined["median_tvd_seen"] < plain["median_tvd_seen"], (plain, refined)
