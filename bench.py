@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="factor", choices=["factor", "group", "slos"],
+    ap.add_argument("--algo", default="factor", choices=["factor", "factor_tc", "group", "slos"],
                     help="factor: factorised Glynn (default); group: plain Glynn; slos: state expansion")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
@@ -59,6 +59,16 @@ def parse():
     global M, N_PH
     M, N_PH = args.m, args.n
     return args
+
+
+def measured_bf16_peak() -> float:
+    """Dense BF16 TFLOP/s measured on the GB300s (burst), else the
+    recipe's fallback figure."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
 
 
 def rank_unitary_seed(rank: int) -> int:
@@ -180,7 +190,8 @@ def run_ours(args):
     U_h = pin.haar_unitary(M, rank_unitary_seed(rank))
     t = pin.single_photon_input(M, N_PH)
     Ntot = pcv.num_outputs(M, N_PH)
-    algo = {"factor": pcv.PCV_ALGO_FACTOR, "group": pcv.PCV_ALGO_GROUP, "slos": pcv.PCV_ALGO_SLOS}[args.algo]
+    algo = {"factor": pcv.PCV_ALGO_FACTOR, "factor_tc": pcv.PCV_ALGO_FACTOR_TC, "group": pcv.PCV_ALGO_GROUP,
+            "slos": pcv.PCV_ALGO_SLOS}[args.algo]
     param = 32 if args.algo == "group" else 0
     U = torch.from_numpy(U_h).to(dev)
     prob = torch.empty(Ntot, dtype=torch.float64, device=dev)
@@ -298,6 +309,13 @@ def run_ours(args):
         flops_per_call = Ntot * (2 ** (N_PH - 1)) * 6     # 3 DFMA per output and sign vector
         kname = "gemm_kernel (factorised Glynn products, 3 DFMA per output and sign vector)"
         launches_per_call = 1
+    elif args.algo == "factor_tc":
+        # BF16 tensor-core work: 3 real products x 36 digit pairs x 2 flops per
+        # output and sign vector (useful outputs only)
+        ms, calls = stages["dist_products"]
+        flops_per_call = Ntot * (2 ** (N_PH - 1)) * 3 * 36 * 2
+        kname = "tc_product_kernel (exact-digit BF16 tcgen05 products, 36 digit pairs x 3 real products)"
+        launches_per_call = 1
     elif args.algo == "group":
         ms, calls = stages["glynn_plain"]
         flops_per_call = Ntot * (2 ** (N_PH - 1)) * (8 * N_PH - 4)
@@ -313,9 +331,14 @@ def run_ours(args):
         kname = "slos_level_kernel (state expansion)"
         launches_per_call = N_PH
     achieved = flops_per_call * calls / (ms * 1e-3) / 1e12 if ms > 0 and flops_per_call else None
-    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+    peak_src = f"derived: {sms} SMs x 2 DFMA/clk x 2 flop x {sm_max:.0f} MHz (FP64 ALU)"
+    bound = "alu"
+    if args.algo == "factor_tc":
+        peak_tflops, bound = measured_bf16_peak(), "tensor"
+        peak_src = "MEASURED_PEAKS.json bf16_tflops (burst cuBLAS bf16 GEMM, measured)"
+    roof = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops if achieved else None,
-            "peak_source": f"derived: {sms} SMs x 2 DFMA/clk x 2 flop x {sm_max:.0f} MHz (FP64 ALU)",
+            "peak_source": peak_src,
             "fp64_probe_tflops": probe_tflops,
             "traffic": NCU_TRAFFIC_PER_LAUNCH if (M, N_PH, args.algo) == (20, 10, "factor") else None,
             "launches_per_step": launches_per_call,
@@ -347,7 +370,9 @@ def run_ours(args):
         "metric": f"amplitudes/s (m={M} n={N_PH} full distribution, complex FP64)",
         "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": "f64" if args.algo != "factor_tc" else "f64 (tables, scaling, results; products as exact bf16 digit MMAs)",
+        "data": "synthetic",
         "config": {"workload": workload_text(M, N_PH, Ntot), "m": M, "n": N_PH, "outputs": Ntot, "algo": args.algo,
                    "l2": "flushed between steps (256 MiB write, untimed)", "parallelism": f"replicas{world}"},
         "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,

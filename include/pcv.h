@@ -94,6 +94,7 @@ enum {
     PCV_ALGO_TILE = 4,    /* shared row sums, one block per tile of outputs, m <= 128   */
     PCV_ALGO_SLOS = 5,    /* full distribution by photon-by-photon state expansion      */
     PCV_ALGO_MULT = 6,    /* Glynn's sum with multiplicities, a warp (or more) per permanent */
+    PCV_ALGO_FACTOR_TC = 7, /* factorised Glynn sum, products on the tensor cores (exact digits) */
 };
 
 /* Workspace bytes pcv_amplitudes needs for these sizes (0 if none). */
@@ -189,6 +190,12 @@ int pcv_amplitudes_batched(const pcv_batch_desc* descs, int n_circ, int64_t tota
 int pcv_amplitudes_batched_ex(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs, int algo,
                               void* workspace, int64_t workspace_bytes, void* stream);
 
+/* Workspace bytes of pcv_distribution_ex with PCV_ALGO_FACTOR_TC (1 <= n <= 10):
+ * the FP64 factor tables of all sign vectors, an amplitude buffer (used when
+ * amp is NULL) and the digit tensors (48 bytes per table entry and sign
+ * vector). */
+int64_t pcv_distribution_tc_workspace(int m, int n);
+
 /* Workspace bytes pcv_distribution needs for m modes and n photons with the
  * default plan.  A smaller workspace (>= pcv_distribution_workspace_min) is
  * accepted and processed in more passes. */
@@ -234,7 +241,19 @@ int pcv_distribution_slos(const pcv_c64* U, int B, int m, const uint8_t* input_o
 /* pcv_distribution with an explicit algorithm: PCV_ALGO_FACTOR (param
  * ignored), PCV_ALGO_GROUP (param = threads per permanent; unranks each
  * output), PCV_ALGO_BLOCK (param = blocks per permanent), PCV_ALGO_SLOS
- * (state expansion; workspace of pcv_distribution_slos_workspace(1, m, n)). */
+ * (state expansion; workspace of pcv_distribution_slos_workspace(1, m, n)),
+ * or PCV_ALGO_FACTOR_TC (workspace of pcv_distribution_tc_workspace).
+ *
+ * PCV_ALGO_FACTOR_TC computes the factorised sum's complex products over the
+ * 2^{n-1} sign vectors on the BF16 tensor cores with exact integer
+ * arithmetic.  Every FP64 table value is split into 8 balanced base-128
+ * digits under a per-row power-of-two scale (the error-free splitting of
+ * Ozaki, Ogita, Oishi and Rump, 2012); digit products are exact in BF16 and
+ * each diagonal of digit pairs sums to at most 2^24, so its FP32 tensor-core
+ * accumulation is exact; the diagonals are recombined in 64-bit integers and
+ * scaled in FP64.  Results agree with the FP64 path to double precision.
+ * The paper has no such variant (its back-ends run on CPUs).  n <= 10
+ * (2^{n-1} <= 512 keeps each diagonal sum below 2^24). */
 int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                         double* prob, pcv_c64* amp, int algo, int param,
                         void* workspace, int64_t workspace_bytes, void* stream);
@@ -468,7 +487,8 @@ int pcv_fp64_probe(double* out, int blocks, int threads, int iters, void* stream
 /* Stage timing for measurement.  pcv_profile_enable(1) makes the library
  * record CUDA events on the launching stream around each stage of a call
  * (stage 0: factorised-distribution tables, 1: factorised-distribution
- * products, 2: plain Glynn kernels).  pcv_profile_read waits for the recorded
+ * products, 2: plain Glynn kernels, 3: digit splitting of the tensor-core
+ * products).  pcv_profile_read waits for the recorded
  * events, writes the accumulated milliseconds and call counts of the first
  * `nstages` stages to ms[] and calls[] (host) and resets them.
  * pcv_launch_count returns the number of kernels the library has launched

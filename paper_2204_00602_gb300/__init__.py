@@ -15,12 +15,13 @@ import torch
 
 from . import _abi as abi
 from ._abi import (PCV_ALGO_AUTO, PCV_ALGO_BLOCK, PCV_ALGO_FACTOR, PCV_ALGO_GROUP,  # noqa: F401
-                   PCV_ALGO_MULT, PCV_ALGO_SLOS, PCV_ALGO_TILE, PCV_MAX_MODES, PCV_MAX_PHOTONS, PcvError)
+                   PCV_ALGO_FACTOR_TC, PCV_ALGO_MULT, PCV_ALGO_SLOS, PCV_ALGO_TILE, PCV_MAX_MODES,
+                   PCV_MAX_PHOTONS, PcvError)
 
 __all__ = ["amplitudes", "amplitudes_batched", "BatchPlan", "distribution", "distribution_batched",
            "distribution_classes", "source_distribution", "sample", "num_outputs", "unrank", "rank",
            "fp64_probe", "PcvError", "PCV_ALGO_AUTO", "PCV_ALGO_GROUP", "PCV_ALGO_BLOCK", "PCV_ALGO_FACTOR",
-           "PCV_ALGO_TILE", "PCV_ALGO_SLOS", "PCV_ALGO_MULT", "abi"]
+           "PCV_ALGO_TILE", "PCV_ALGO_SLOS", "PCV_ALGO_MULT", "PCV_ALGO_FACTOR_TC", "abi"]
 
 
 def _stream(device) -> int:
@@ -154,6 +155,8 @@ def distribution_workspace_bytes(m: int, n: int, algo: int = PCV_ALGO_AUTO, para
         return abi.pcv_distribution_workspace(m, n)
     if algo == PCV_ALGO_SLOS:
         return abi.pcv_distribution_slos_workspace(1, m, n)
+    if algo == PCV_ALGO_FACTOR_TC:
+        return abi.pcv_distribution_tc_workspace(m, n)
     nb = ((m + 1) * (n + 1) * 8 + 255) // 256 * 256
     if algo == PCV_ALGO_BLOCK and param > 1:
         nb += num_outputs(m, n) * param * 16 + 256

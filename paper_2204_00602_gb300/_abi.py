@@ -32,6 +32,7 @@ PCV_ALGO_FACTOR = 3
 PCV_ALGO_TILE = 4
 PCV_ALGO_SLOS = 5
 PCV_ALGO_MULT = 6
+PCV_ALGO_FACTOR_TC = 7
 PCV_MAX_PHOTONS = 30
 PCV_MAX_MODES = 1024
 
@@ -51,6 +52,7 @@ SIGNATURES = {
     "pcv_amplitudes_ex": (_i, [_vp, _i, _vp, _vp, _i64, _vp, _vp, _i, _i, _vp, _i64, _vp]),
     "pcv_amplitudes_ex_workspace": (_i64, [_i, _i, _i64, _i, _i]),
     "pcv_distribution_workspace": (_i64, [_i, _i]),
+    "pcv_distribution_tc_workspace": (_i64, [_i, _i]),
     "pcv_distribution_workspace_min": (_i64, [_i, _i]),
     "pcv_distribution": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
     "pcv_distribution_ex": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _vp, _i64, _vp]),
@@ -177,6 +179,10 @@ def pcv_amplitudes_ex_workspace(m, n, n_out, algo, param) -> int:
 
 def pcv_distribution_workspace(m, n) -> int:
     return _call("pcv_distribution_workspace", m, n)
+
+
+def pcv_distribution_tc_workspace(m, n) -> int:
+    return _call("pcv_distribution_tc_workspace", m, n)
 
 
 def pcv_distribution_workspace_min(m, n) -> int:
@@ -373,7 +379,7 @@ def pcv_fp64_probe(out, blocks, threads, iters, stream):
     return _call("pcv_fp64_probe", ptr(out), blocks, threads, iters, stream)
 
 
-STAGES = ("dist_tables", "dist_products", "glynn_plain")
+STAGES = ("dist_tables", "dist_products", "glynn_plain", "tc_split")
 
 
 def pcv_profile_enable(on: bool):

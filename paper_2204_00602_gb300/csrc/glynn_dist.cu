@@ -338,6 +338,19 @@ int64_t dist_plan(const Plan& p, int B, int64_t ws_bytes, bool need_acc, DistPla
     return (int64_t)L.total;
 }
 
+int64_t dist_plan_tc(const Plan& p, bool need_amp_buffer, DistPlan* dp)
+{
+    if (dist_plan(p, 1, INT64_MAX / 4, false, dp) < 0) return -1;
+    const int64_t dmax = p.n > 0 ? (1ll << (p.n - 1)) : 1;
+    if (dp->kc != dmax) return -1;
+    dp->ws_acc = need_amp_buffer ? align256((size_t)dp->total * sizeof(double2)) : 0;
+    dp->tc = true;
+    dp->ws_tc = (size_t)tc_workspace(dp->wlow, dp->whigh, (int)dmax);
+    dp->ws_total = dp->ws_table + dp->ws_base + dp->ws_acc + dp->ws_y + dp->ws_tl + dp->ws_sl + dp->ws_th + dp->ws_sh +
+                   dp->ws_tc;
+    return (int64_t)dp->ws_total;
+}
+
 cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* U,
                               double* prob, double2* amp, void* ws, cudaStream_t s)
 {
@@ -350,7 +363,9 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
     double2* Tlow = (double2*)w;             w += dp.ws_tl;
     double* Slow = (double*)w;               w += dp.ws_sl;
     double2* Thigh = (double2*)w;            w += dp.ws_th;
-    double* Shigh = (double*)w;
+    double* Shigh = (double*)w;              w += dp.ws_sh;
+    void* tcws = w;
+    if (dp.tc && (B != 1 || dp.kc != (1ll << (n - 1)))) return cudaErrorInvalidValue;
 
     cudaError_t e = build_multiset_table(table, m, n, s);
     if (e != cudaSuccess) return e;
@@ -434,6 +449,24 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
         }
         stage_end(kStageTables, s);
         stage_begin(kStageGemm, s);
+        if (dp.tc) {
+            TcInputs ti;
+            ti.Tlow = Tlow; ti.Slow = Slow; ti.Thigh = Thigh; ti.Shigh = Shigh;
+            ti.wlow = dp.wlow; ti.whigh = dp.whigh;
+            ti.K = (int)dp.kc; ti.n = n; ti.m = m; ti.h = dp.h;
+            for (int k = 0; k <= PCV_MAX_PHOTONS + 1; ++k) {
+                ti.lowoff[k] = dp.lowoff[k];
+                ti.highoff[k] = dp.highoff[k];
+            }
+            ti.lowbase = lowbase;
+            ti.acc = accbuf;
+            ti.prob = prob;
+            ti.ws = tcws;
+            ti.error = nullptr;
+            if ((e = launch_tc_products(ti, s)) != cudaSuccess) return e;
+            stage_end(kStageGemm, s);
+            continue;
+        }
         g.first = ch == 0;
         g.last = ch == nchunks - 1;
         gemm_kernel<<<dim3((unsigned)tiles, (unsigned)B), 256, 0, s>>>(g);

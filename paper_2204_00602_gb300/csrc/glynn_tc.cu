@@ -1,0 +1,580 @@
+// Product stage of the factorised full distribution on the BF16 tensor cores,
+// with exact integer arithmetic.
+//
+// After the factor tables are built (glynn_dist.cu), every output is
+//     a(S) = sum_d alpha_P(d) beta_Q(d),
+// for each k a complex matrix product over the K = 2^{n-1} sign vectors, done
+// as three real products (Gauss): t1 = Ar Br, t2 = Ai Bi, t3 = (Ar+Ai)(Br+Bi),
+// Re a = t1 - t2, Im a = t3 - t1 - t2.  Here each real product runs on the
+// tensor cores without losing FP64 accuracy, by splitting every table value
+// into integer digits (the error-free splitting idea of Ozaki, Ogita, Oishi
+// and Rump, 2012):
+//
+//   * each row (table entry, per product t) gets an exponent E with
+//     max_d |x(d)| <= 2^{E-1}; X = round(x 2^{56-E}) is an integer with
+//     |X| <= 2^55, written as 8 balanced base-128 digits,
+//         X = sum_{i=0..7} D_i 128^{7-i},   |D_i| <= 64,
+//     so x = 2^E sum_i D_i 2^{-7(i+1)} up to 2^{E-56} (FP64 accuracy);
+//   * a digit is an integer of at most 7 bits, exact in BF16, and a product of
+//     two is at most 2^12; over K <= 512 sign vectors a digit-pair product
+//     sums to at most 2^21, and the 8 pairs (i, j) of one diagonal i + j = d
+//     to at most 2^24, so an FP32 accumulator holds every partial sum of a
+//     diagonal exactly, in any order the tensor core adds them;
+//   * diagonals d = 0..7 are kept (36 digit pairs); the dropped ones weigh
+//     2^{-56} and less relative to the row and column scales;
+//   * the 8 diagonal sums (exact integers) are combined on the integer pipe,
+//     hi = sum_{d<4} acc_d 128^{3-d}, lo = sum_{d>=4} acc_d 128^{7-d}, and
+//     x_t = 2^{E_row + E_col - 14} (hi 2^{-21} + lo 2^{-49}) in FP64.
+//
+// Kernels: split_exp_kernel (the row exponents, integer max of the exponent
+// fields), split_digits_kernel (digits as BF16, laid out [t][digit][entry][K]
+// for TMA), and tc_product_kernel: one CTA per 128 x N output tile of one k
+// (N = 16..64), six warps:
+//   warp 0  TMA producer: per 64-wide K block, the 8 digit slices of the
+//           column operand (64 rows each, one 64 KB set, double-buffered),
+//           then the 8 digit slices of the row operand one at a time
+//           (16 KB slots, triple-buffered), 128B swizzle;
+//   warp 1  MMA issuer: for row digit i, tcgen05.mma kind::f16 (M=128, N,
+//           K=16) with every column digit j <= 7 - i into the TMEM
+//           accumulator of diagonal i + j (8 accumulators x 64 columns =
+//           all 512 TMEM columns); commits free the slots;
+//   warps 2-5  drain: after each of the three products, tcgen05.ld of the 8
+//           diagonals (warp w owns TMEM lanes 32 (w mod 4) ..), integer
+//           combination, FP64 scaling, and the running Re/Im of the outputs
+//           in global memory (written at t1, updated at t2 and t3, with the
+//           probability at the end), at canonical index lowbase(P) + rank(Q).
+// Every mbarrier wait is bounded; on a time-out the kernel records an error
+// code and returns after releasing its tensor memory.
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "pcv_common.cuh"
+
+namespace pcv {
+namespace {
+
+constexpr int kDigits = 8;
+constexpr int TBM = 128, TBN = 64, TBK = 64;
+constexpr int kASlots = 3, kBSets = 2;
+constexpr uint32_t kABytes = TBM * TBK * 2;             // 16 KB: one digit slice of the row operand
+constexpr uint32_t kBSliceBytes = TBN * TBK * 2;        // 8 KB: one digit slice of the column operand
+constexpr uint32_t kBBytes = kDigits * kBSliceBytes;    // 64 KB: all digit slices of the column operand
+constexpr uint32_t kSmemBytes = kBSets * kBBytes + kASlots * kABytes + 1024;
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 512;
+constexpr long long kMaxPolls = 1ll << 26;
+constexpr int kNoExp = -100000;                          // an all-zero row
+
+// ------------------------------------------------------------ splitting
+
+__device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// E_t(entry) for t = re, im, re+im: the smallest E with max |x| <= 2^{E-1}
+// (from the largest exponent field; a power of two costs one spare bit).
+__global__ void split_exp_kernel(const double2* __restrict__ T, const double* __restrict__ Sm, int64_t w, int K,
+                                 int* __restrict__ ex)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= w) return;
+    int f0 = 0, f1 = 0, f2 = 0;
+    for (int d = 0; d < K; ++d) {
+        const double2 v = T[(int64_t)d * w + e];
+        f0 = max(f0, exp_field(v.x));
+        f1 = max(f1, exp_field(v.y));
+        f2 = max(f2, exp_field(Sm[(int64_t)d * w + e]));
+    }
+    ex[e] = f0 ? f0 - 1021 : kNoExp;
+    ex[w + e] = f1 ? f1 - 1021 : kNoExp;
+    ex[2 * w + e] = f2 ? f2 - 1021 : kNoExp;
+}
+
+// Balanced base-128 digits of round(x 2^{56-E}), most significant first.
+__device__ __forceinline__ void digits_of(double x, int E, int* D)
+{
+    const long long bits = __double_as_longlong(x);
+    const int ef = (int)((bits >> 52) & 0x7FF);
+    long long X = 0;
+    if (ef != 0 && E != kNoExp) {
+        const long long mant = (bits & ((1ll << 52) - 1)) | (1ll << 52);
+        const int sh = ef - 1019 - E;                      // X = mant 2^{sh}, sh <= 3
+        if (sh >= 0) X = mant << sh;
+        else if (sh > -60) X = (mant + (1ll << (-sh - 1))) >> (-sh);
+        if (bits < 0) X = -X;
+    }
+#pragma unroll
+    for (int i = kDigits - 1; i >= 1; --i) {
+        const long long d = ((X + 64) & 127) - 64;
+        D[i] = (int)d;
+        X = (X - d) >> 7;
+    }
+    D[0] = (int)X;
+}
+
+// One block: 32 entries x 64 sign vectors of one side.  Loads are coalesced
+// along entries, stores along sign vectors (the digit tensors are K-major).
+__global__ void __launch_bounds__(256) split_digits_kernel(const double2* __restrict__ T, const double* __restrict__ Sm,
+                                                           int64_t w, int K, int Kpad, const int* __restrict__ ex,
+                                                           __nv_bfloat16* __restrict__ out)
+{
+    __shared__ double2 sT[64][33];
+    __shared__ double sS[64][33];
+    const int64_t e0 = (int64_t)blockIdx.x * 32;
+    const int d0 = blockIdx.y * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;     // 32 x 8
+    for (int r = ty; r < 64; r += 8) {
+        const int d = d0 + r;
+        const int64_t e = e0 + tx;
+        double2 v = make_double2(0.0, 0.0);
+        double s = 0.0;
+        if (d < K && e < w) {
+            v = T[(int64_t)d * w + e];
+            s = Sm[(int64_t)d * w + e];
+        }
+        sT[r][tx] = v;
+        sS[r][tx] = s;
+    }
+    __syncthreads();
+    // thread -> (entry ee, sign vectors dd and dd + 32)
+    for (int q = threadIdx.x; q < 32 * 64; q += 256) {
+        const int dd = q & 63, ee = q >> 6;
+        const int64_t e = e0 + ee;
+        const int d = d0 + dd;
+        if (e >= w || d >= Kpad) continue;
+        const double2 v = sT[dd][ee];
+        const double vals[3] = {v.x, v.y, sS[dd][ee]};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            int D[kDigits];
+            digits_of(vals[t], ex[(int64_t)t * w + e], D);
+#pragma unroll
+            for (int i = 0; i < kDigits; ++i)
+                out[(((int64_t)t * kDigits + i) * w + e) * Kpad + d] = __float2bfloat16_rn((float)D[i]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ products
+
+struct TcProdArgs {
+    int nk;                                   // k blocks with outputs
+    int kblocks;                              // 64-wide K blocks
+    int64_t tile0[PCV_MAX_PHOTONS + 2];       // first tile of each block
+    int rows_low[PCV_MAX_PHOTONS + 1];        // 1: rows are low-side entries P, columns high-side Q
+    int tn[PCV_MAX_PHOTONS + 1];              // tile width (16..64)
+    int64_t rows[PCV_MAX_PHOTONS + 1], cols[PCV_MAX_PHOTONS + 1];
+    int64_t row_off[PCV_MAX_PHOTONS + 1], col_off[PCV_MAX_PHOTONS + 1];   // level offsets in their side
+    int64_t lowoff[PCV_MAX_PHOTONS + 1];      // level offset of P (for lowbase)
+    const int64_t* lowbase;
+    const int* ex_low;                        // [3][wlow]
+    const int* ex_high;                       // [3][whigh]
+    int64_t wlow, whigh;
+    double2* acc;                             // running Re/Im; the amplitudes at the end
+    double* prob;
+    int* error;
+};
+
+__device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(sm_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sm_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sm_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity)
+{
+    const uint32_t a = sm_addr(bar);
+    for (long long i = 0; i < kMaxPolls; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n"
+            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                            int u)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(sm_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(u), "r"(sm_addr(bar))
+        : "memory");
+}
+
+// K-major tile in the 128-byte swizzle layout written by TMA: rows of 128 B,
+// 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(const void* p)
+{
+    const uint64_t addr = sm_addr(p);
+    uint64_t d = 0;
+    d |= (addr & 0x3FFFF) >> 4;
+    d |= (uint64_t)(16 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_for(int n)
+{
+    uint32_t d = 0;
+    d |= 1u << 4;
+    d |= 1u << 7;
+    d |= 1u << 10;
+    d |= (uint32_t)(n >> 3) << 17;
+    d |= (uint32_t)(TBM >> 4) << 24;
+    return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(sm_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ double pow2(int e)      // 2^e for -1022 <= e <= 1023
+{
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_constant__ CUtensorMap low_cols,
+                  const __grid_constant__ CUtensorMap high_rows, const __grid_constant__ CUtensorMap high_cols,
+                  const TcProdArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* bset = base;                                // kBSets x 64 KB
+    unsigned char* aslot = base + kBSets * kBBytes;            // kASlots x 16 KB
+    __shared__ __align__(8) uint64_t bfull[kBSets], bempty[kBSets], afull[kASlots], aempty[kASlots];
+    __shared__ __align__(8) uint64_t accfull, accempty;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // tile -> (k block, row tile, column tile); column tiles vary fastest
+    const int64_t tile = blockIdx.x;
+    int kb = 0;
+    while (kb + 1 < a.nk && a.tile0[kb + 1] <= tile) ++kb;
+    const int tn = a.tn[kb];
+    const int64_t ctiles = (a.cols[kb] + tn - 1) / tn;
+    const int64_t lt = tile - a.tile0[kb];
+    const int64_t r0 = (lt / ctiles) * TBM, c0 = (lt % ctiles) * tn;
+    const bool rl = a.rows_low[kb] != 0;
+    const CUtensorMap* rmap = rl ? &low_rows : &high_rows;
+    const CUtensorMap* cmap = rl ? &high_cols : &low_cols;
+    const int rentry = (int)(a.row_off[kb] + r0), centry = (int)(a.col_off[kb] + c0);
+
+    if (tid == 0) {
+        for (int s = 0; s < kBSets; ++s) {
+            bar_init(&bfull[s], 1);
+            bar_init(&bempty[s], 1);
+        }
+        for (int s = 0; s < kASlots; ++s) {
+            bar_init(&afull[s], 1);
+            bar_init(&aempty[s], 1);
+        }
+        bar_init(&accfull, 1);
+        bar_init(&accempty, 128);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(rmap) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(cmap) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sm_addr(&tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const int nkb = a.kblocks;
+
+    if (tid == 0) {
+        // ---------------- TMA producer
+        uint32_t na = 0, nb = 0;
+        for (int t = 0; t < 3 && !s_fail; ++t) {
+            for (int c = 0; c < nkb && !s_fail; ++c) {
+                const uint32_t bs = nb % kBSets;
+                if (nb >= (uint32_t)kBSets && !bar_wait(&bempty[bs], ((nb / kBSets) - 1) & 1)) { s_fail = 1; break; }
+                bar_expect_tx(&bfull[bs], kBBytes);
+                for (int j = 0; j < kDigits; ++j)
+                    tma_load_4d(bset + bs * kBBytes + j * kBSliceBytes, cmap, &bfull[bs], c * TBK, centry, j, t);
+                ++nb;
+                for (int i = 0; i < kDigits; ++i) {
+                    const uint32_t as = na % kASlots;
+                    if (na >= (uint32_t)kASlots && !bar_wait(&aempty[as], ((na / kASlots) - 1) & 1)) { s_fail = 1; break; }
+                    bar_expect_tx(&afull[as], kABytes);
+                    tma_load_4d(aslot + as * kABytes, rmap, &afull[as], c * TBK, rentry, i, t);
+                    ++na;
+                }
+            }
+        }
+    } else if (tid == 32) {
+        // ---------------- MMA issuer
+        const uint32_t idesc = idesc_for(tn);
+        uint32_t na = 0, nb = 0;
+        for (int t = 0; t < 3 && !s_fail; ++t) {
+            if (t > 0 && !bar_wait(&accempty, (t - 1) & 1)) { s_fail = 2; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            for (int c = 0; c < nkb && !s_fail; ++c) {
+                const uint32_t bs = nb % kBSets;
+                if (!bar_wait(&bfull[bs], (nb / kBSets) & 1)) { s_fail = 2; break; }
+                const unsigned char* sb = bset + bs * kBBytes;
+                for (int i = 0; i < kDigits; ++i) {
+                    const uint32_t as = na % kASlots;
+                    if (!bar_wait(&afull[as], (na / kASlots) & 1)) { s_fail = 2; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const unsigned char* sa = aslot + as * kABytes;
+                    for (int j = 0; j + i < kDigits; ++j) {
+                        const uint32_t acc_t = tmem + (uint32_t)((i + j) * TBN);
+#pragma unroll
+                        for (int kk = 0; kk < TBK / 16; ++kk)
+                            mma_f16(acc_t, sdesc(sa + kk * 32), sdesc(sb + j * kBSliceBytes + kk * 32), idesc,
+                                    (c == 0 && i == 0 && kk == 0) ? 0u : 1u);
+                    }
+                    mma_commit(&aempty[as]);
+                    ++na;
+                }
+                mma_commit(&bempty[bs]);
+                ++nb;
+            }
+            mma_commit(&accfull);
+        }
+    } else if (warp >= 2) {
+        // ---------------- drain: warp w owns TMEM lanes 32 (w mod 4) .. + 31
+        const int q4 = warp & 3;
+        const int64_t row = r0 + q4 * 32 + lane;
+        const bool rv = row < a.rows[kb];
+        const int* ex_r = rl ? a.ex_low : a.ex_high;
+        const int* ex_c = rl ? a.ex_high : a.ex_low;
+        const int64_t wr = rl ? a.wlow : a.whigh, wc = rl ? a.whigh : a.wlow;
+        for (int t = 0; t < 3; ++t) {
+            const bool ok = bar_wait(&accfull, t & 1);
+            if (!ok) {
+                if (lane == 0) s_fail = 3;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int er = rv ? ex_r[(int64_t)t * wr + a.row_off[kb] + row] : kNoExp;
+            for (int cc = 0; cc < tn; cc += 16) {
+                long long hi[16], lo[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) hi[q] = lo[q] = 0;
+#pragma unroll
+                for (int d = 0; d < kDigits; ++d) {
+                    uint32_t r[16];
+                    const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * TBN + cc);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];\n"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const long long v = (long long)__float2int_rn(__uint_as_float(r[q]));
+                        if (d < 4) hi[q] = hi[q] * 128 + v;
+                        else lo[q] = lo[q] * 128 + v;
+                    }
+                }
+                if (!rv) continue;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int64_t col = c0 + cc + q;
+                    if (col >= a.cols[kb]) continue;
+                    const int ec = ex_c[(int64_t)t * wc + a.col_off[kb] + col];
+                    double x = 0.0;
+                    if (er != kNoExp && ec != kNoExp) {
+                        const int sc = er + ec - 14;
+                        x = fma((double)lo[q], pow2(sc - 49), (double)hi[q] * pow2(sc - 21));
+                    }
+                    const int64_t P = rl ? row : col, Q = rl ? col : row;
+                    const int64_t o = a.lowbase[a.lowoff[kb] + P] + Q;
+                    if (t == 0) {
+                        a.acc[o] = make_double2(x, -x);
+                    } else if (t == 1) {
+                        const double2 v = a.acc[o];
+                        a.acc[o] = make_double2(v.x - x, v.y - x);
+                    } else {
+                        double2 v = a.acc[o];
+                        v.y += x;
+                        a.acc[o] = v;
+                        if (a.prob) a.prob[o] = fma(v.x, v.x, v.y * v.y);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            bar_arrive(&accempty);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    if (tid == 0 && s_fail && a.error) atomicExch(a.error, s_fail);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
+std::once_flag g_enc_once;
+bool g_tc_attr[64] = {};
+
+cudaError_t get_enc()
+{
+    std::call_once(g_enc_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    return g_enc ? cudaSuccess : cudaErrorNotSupported;
+}
+
+// 4-D map over the digit tensor [3][8][w][Kpad] (bf16), box 64 (K) x rows.
+cudaError_t make_digit_map(CUtensorMap* map, const void* base, int64_t w, int Kpad, int box_rows)
+{
+    const cuuint64_t dims[4] = {(cuuint64_t)Kpad, (cuuint64_t)w, (cuuint64_t)kDigits, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)Kpad * 2, (cuuint64_t)w * Kpad * 2, (cuuint64_t)kDigits * w * Kpad * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)TBK, (cuuint32_t)box_rows, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = g_enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int64_t binom_tc(int a, int b)
+{
+    if (b < 0 || a < 0 || b > a) return 0;
+    unsigned __int128 c = 1;
+    for (int i = 1; i <= b; ++i) c = c * (unsigned __int128)(a - b + i) / (unsigned __int128)i;
+    return (int64_t)c;
+}
+
+int64_t msets_tc(int w, int k) { return k == 0 ? 1 : (w <= 0 ? 0 : binom_tc(w + k - 1, k)); }
+
+}  // namespace
+
+int tc_pad_k(int K) { return ((K + TBK - 1) / TBK) * TBK; }
+
+int64_t tc_workspace(int64_t wlow, int64_t whigh, int K)
+{
+    const int Kp = tc_pad_k(K);
+    return (int64_t)(al256((size_t)3 * kDigits * wlow * Kp * 2) + al256((size_t)3 * kDigits * whigh * Kp * 2) +
+                     al256((size_t)3 * wlow * sizeof(int)) + al256((size_t)3 * whigh * sizeof(int)) + 256);
+}
+
+cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
+{
+    cudaError_t e = get_enc();
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !g_tc_attr[dev]) {
+        e = cudaFuncSetAttribute(tc_product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        g_tc_attr[dev] = true;
+    }
+    const int K = in.K, Kp = tc_pad_k(K);
+    char* w = (char*)in.ws;
+    __nv_bfloat16* dlow = (__nv_bfloat16*)w;     w += al256((size_t)3 * kDigits * in.wlow * Kp * 2);
+    __nv_bfloat16* dhigh = (__nv_bfloat16*)w;    w += al256((size_t)3 * kDigits * in.whigh * Kp * 2);
+    int* exlow = (int*)w;                        w += al256((size_t)3 * in.wlow * sizeof(int));
+    int* exhigh = (int*)w;
+    // digits of both sides (timed as their own stage when profiling is on)
+    stage_end(kStageGemm, s);
+    stage_begin(kStageSplit, s);
+    for (int side = 0; side < 2; ++side) {
+        const double2* T = side == 0 ? in.Tlow : in.Thigh;
+        const double* S = side == 0 ? in.Slow : in.Shigh;
+        const int64_t ww = side == 0 ? in.wlow : in.whigh;
+        int* ex = side == 0 ? exlow : exhigh;
+        __nv_bfloat16* dg = side == 0 ? dlow : dhigh;
+        split_exp_kernel<<<(unsigned)((ww + 255) / 256), 256, 0, s>>>(T, S, ww, K, ex);
+        split_digits_kernel<<<dim3((unsigned)((ww + 31) / 32), (unsigned)(Kp / 64)), 256, 0, s>>>(T, S, ww, K, Kp, ex, dg);
+        note_launches(2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    stage_end(kStageSplit, s);
+    stage_begin(kStageGemm, s);
+    CUtensorMap lr, lc, hr, hc;
+    if ((e = make_digit_map(&lr, dlow, in.wlow, Kp, TBM)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&lc, dlow, in.wlow, Kp, TBN)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&hr, dhigh, in.whigh, Kp, TBM)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&hc, dhigh, in.whigh, Kp, TBN)) != cudaSuccess) return e;
+    TcProdArgs a;
+    a.nk = 0;
+    a.kblocks = Kp / TBK;
+    int64_t tiles = 0;
+    for (int k = 0; k <= in.n; ++k) {
+        const int64_t M = msets_tc(in.h, k), N = msets_tc(in.m - in.h, in.n - k);
+        if (M == 0 || N == 0) continue;
+        const bool rl = M >= N;
+        const int64_t rows = rl ? M : N, cols = rl ? N : M;
+        const int tn = cols >= TBN ? TBN : (int)((cols + 15) / 16) * 16;
+        a.rows_low[a.nk] = rl ? 1 : 0;
+        a.tn[a.nk] = tn;
+        a.rows[a.nk] = rows;
+        a.cols[a.nk] = cols;
+        a.row_off[a.nk] = rl ? in.lowoff[k] : in.highoff[in.n - k];
+        a.col_off[a.nk] = rl ? in.highoff[in.n - k] : in.lowoff[k];
+        a.lowoff[a.nk] = in.lowoff[k];
+        a.tile0[a.nk] = tiles;
+        tiles += ((rows + TBM - 1) / TBM) * ((cols + tn - 1) / tn);
+        a.nk++;
+    }
+    a.tile0[a.nk] = tiles;
+    if (tiles == 0) return cudaSuccess;
+    if (tiles > INT32_MAX || in.wlow + TBM > INT32_MAX || in.whigh + TBM > INT32_MAX) return cudaErrorInvalidConfiguration;
+    a.lowbase = in.lowbase;
+    a.ex_low = exlow;
+    a.ex_high = exhigh;
+    a.wlow = in.wlow;
+    a.whigh = in.whigh;
+    a.acc = in.acc;
+    a.prob = in.prob;
+    a.error = in.error;
+    tc_product_kernel<<<(unsigned)tiles, kThreads, kSmemBytes, s>>>(lr, lc, hr, hc, a);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace pcv

@@ -583,10 +583,45 @@ int pcv_distribution_slos(const pcv_c64* U, int B, int m, const uint8_t* input_o
     return e == cudaSuccess ? PCV_OK : cuda_fail(e, "state expansion");
 }
 
+int64_t pcv_distribution_tc_workspace(int m, int n)
+{
+    if (m < 1 || m > PCV_MAX_MODES || n < 1 || n > 10) return fail(PCV_EINVAL, "tensor-core products need 1 <= n <= 10");
+    if (msets(m, n) < 0) return fail(PCV_ERANGE, "output space too large");
+    pcv::Plan p;
+    p.m = m;
+    p.n = n;
+    pcv::DistPlan dp;
+    const int64_t r = pcv::dist_plan_tc(p, true, &dp);
+    return r < 0 ? fail(PCV_ERANGE, "workspace size overflows") : r;
+}
+
+static int distribution_tc(const pcv_c64* U, int m, const uint8_t* input_occ, double* prob, pcv_c64* amp,
+                           void* workspace, int64_t workspace_bytes, void* stream)
+{
+    pcv::Plan p;
+    int rc = make_plan(U, m, input_occ, &p);
+    if (rc) return rc;
+    if (p.n < 1 || p.n > 10) return fail(PCV_EINVAL, "tensor-core products need 1 <= n <= 10 (n=%d)", p.n);
+    if (!amp && !prob) return fail(PCV_EINVAL, "amp and prob are both NULL");
+    if (amp && !aligned(amp, 16)) return fail(PCV_EINVAL, "amp is not 16-byte aligned");
+    if (prob && !aligned(prob, 8)) return fail(PCV_EINVAL, "prob is not 8-byte aligned");
+    if (workspace && !aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
+    if (msets(m, p.n) < 0) return fail(PCV_ERANGE, "output space too large");
+    pcv::DistPlan dp;
+    const int64_t need = pcv::dist_plan_tc(p, amp == nullptr, &dp);
+    if (need < 0) return fail(PCV_ERANGE, "workspace size overflows");
+    if (!workspace || need > workspace_bytes)
+        return fail(PCV_ENOMEM, "workspace of %lld bytes needed, %lld given", (long long)need, (long long)workspace_bytes);
+    cudaError_t e = pcv::launch_glynn_dist(p, dp, (const double2*)U, prob, (double2*)amp, workspace, (cudaStream_t)stream);
+    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "tensor-core factorised distribution");
+}
+
 int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                         double* prob, pcv_c64* amp, int algo, int param,
                         void* workspace, int64_t workspace_bytes, void* stream)
 {
+    if (algo == PCV_ALGO_FACTOR_TC)
+        return distribution_tc(U, m, input_occ, prob, amp, workspace, workspace_bytes, stream);
     if (algo == PCV_ALGO_SLOS)
         return pcv_distribution_slos(U, 1, m, input_occ, prob, amp, workspace, workspace_bytes, stream);
     if (algo == PCV_ALGO_AUTO || algo == PCV_ALGO_FACTOR)

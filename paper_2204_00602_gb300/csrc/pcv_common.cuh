@@ -103,7 +103,7 @@ cudaError_t build_cum_table(const int64_t* mc, int m, int kmax, int64_t* cum, cu
 // Per-stage timing (pcv_api.cu): when enabled, stage_begin/stage_end record
 // CUDA events on the launching stream around a group of launches; the times
 // are read back by pcv_profile_read.  note_launches counts kernel launches.
-enum Stage { kStageTables = 0, kStageGemm = 1, kStagePlain = 2, kStageCount = 8 };
+enum Stage { kStageTables = 0, kStageGemm = 1, kStagePlain = 2, kStageSplit = 3, kStageCount = 8 };
 void stage_begin(int stage, cudaStream_t s);
 void stage_end(int stage, cudaStream_t s);
 void note_launches(int64_t k);
@@ -185,8 +185,32 @@ struct DistPlan {
     int64_t wlow, whigh;      // entries of all levels per side: C(h+n, n), C(m-h+n, n)
     int64_t lowoff[PCV_MAX_PHOTONS + 2], highoff[PCV_MAX_PHOTONS + 2];
     size_t ws_table, ws_base, ws_acc, ws_y, ws_tl, ws_sl, ws_th, ws_sh, ws_total;
+    bool tc = false;          // products on the tensor cores (glynn_tc.cu)
+    size_t ws_tc = 0;
 };
+// The single-pass plan for the tensor-core products (B = 1): the FP64 tables
+// of all sign vectors, an amplitude buffer when the caller wants
+// probabilities only, and the digit tensors.  Returns the bytes, -1 on overflow.
+int64_t dist_plan_tc(const Plan& p, bool need_amp_buffer, DistPlan* dp);
 int64_t dist_plan(const Plan& p, int B, int64_t ws_bytes, bool need_acc, DistPlan* dp);
+
+// Product stage on the tensor cores with exact digit splitting (glynn_tc.cu):
+// one batch entry, all K = 2^{n-1} sign vectors in one pass.
+struct TcInputs {
+    const double2* Tlow; const double* Slow;      // [K][wlow]
+    const double2* Thigh; const double* Shigh;    // [K][whigh]
+    int64_t wlow, whigh;
+    int K, n, m, h;
+    int64_t lowoff[PCV_MAX_PHOTONS + 2], highoff[PCV_MAX_PHOTONS + 2];
+    const int64_t* lowbase;
+    double2* acc;                                 // amplitudes (written)
+    double* prob;                                 // or null
+    void* ws;                                     // tc_workspace bytes
+    int* error;                                   // device flag, or null
+};
+int tc_pad_k(int K);
+int64_t tc_workspace(int64_t wlow, int64_t whigh, int K);
+cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s);
 cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* U,
                               double* prob, double2* amp, void* ws, cudaStream_t s);
 }  // namespace pcv
