@@ -343,9 +343,10 @@ int64_t dist_plan_tc(const Plan& p, bool need_amp_buffer, DistPlan* dp)
     if (dist_plan(p, 1, INT64_MAX / 4, false, dp) < 0) return -1;
     const int64_t dmax = p.n > 0 ? (1ll << (p.n - 1)) : 1;
     if (dp->kc != dmax) return -1;
-    dp->ws_acc = need_amp_buffer ? align256((size_t)dp->total * sizeof(double2)) : 0;
+    (void)need_amp_buffer;                   // the products go to their own buffer
+    dp->ws_acc = 0;
     dp->tc = true;
-    dp->ws_tc = (size_t)tc_workspace(dp->wlow, dp->whigh, (int)dmax);
+    dp->ws_tc = (size_t)tc_workspace(dp->wlow, dp->whigh, (int)dmax, dp->total);
     dp->ws_total = dp->ws_table + dp->ws_base + dp->ws_acc + dp->ws_y + dp->ws_tl + dp->ws_sl + dp->ws_th + dp->ws_sh +
                    dp->ws_tc;
     return (int64_t)dp->ws_total;
@@ -448,8 +449,7 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
             }
         }
         stage_end(kStageTables, s);
-        stage_begin(kStageGemm, s);
-        if (dp.tc) {
+        if (dp.tc) {                          // times its own split and product stages
             TcInputs ti;
             ti.Tlow = Tlow; ti.Slow = Slow; ti.Thigh = Thigh; ti.Shigh = Shigh;
             ti.wlow = dp.wlow; ti.whigh = dp.whigh;
@@ -459,14 +459,15 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
                 ti.highoff[k] = dp.highoff[k];
             }
             ti.lowbase = lowbase;
-            ti.acc = accbuf;
+            ti.total = dp.total;
+            ti.amp = amp;
             ti.prob = prob;
             ti.ws = tcws;
             ti.error = nullptr;
             if ((e = launch_tc_products(ti, s)) != cudaSuccess) return e;
-            stage_end(kStageGemm, s);
             continue;
         }
+        stage_begin(kStageGemm, s);
         g.first = ch == 0;
         g.last = ch == nchunks - 1;
         gemm_kernel<<<dim3((unsigned)tiles, (unsigned)B), 256, 0, s>>>(g);

@@ -28,21 +28,22 @@
 //
 // Kernels: split_exp_kernel (the row exponents, integer max of the exponent
 // fields), split_digits_kernel (digits as BF16, laid out [t][digit][entry][K]
-// for TMA), and tc_product_kernel: one CTA per 128 x N output tile of one k
-// (N = 16..64), six warps:
+// for TMA), tc_product_kernel: one persistent CTA per SM walking 128 x N
+// output tiles of one k each (N = 16..64), ten warps, and tc_combine_kernel
+// (Re, Im and |a|^2):
 //   warp 0  TMA producer: per 64-wide K block, the 8 digit slices of the
 //           column operand (64 rows each, one 64 KB set, double-buffered),
 //           then the 8 digit slices of the row operand one at a time
-//           (16 KB slots, triple-buffered), 128B swizzle;
+//           (16 KB slots, six in flight), 128B swizzle;
 //   warp 1  MMA issuer: for row digit i, tcgen05.mma kind::f16 (M=128, N,
 //           K=16) with every column digit j <= 7 - i into the TMEM
 //           accumulator of diagonal i + j (8 accumulators x 64 columns =
 //           all 512 TMEM columns); commits free the slots;
-//   warps 2-5  drain: after each of the three products, tcgen05.ld of the 8
-//           diagonals (warp w owns TMEM lanes 32 (w mod 4) ..), integer
-//           combination, FP64 scaling, and the running Re/Im of the outputs
-//           in global memory (written at t1, updated at t2 and t3, with the
-//           probability at the end), at canonical index lowbase(P) + rank(Q).
+//   warps 2-9  drain: after each of the three products, tcgen05.ld of the 8
+//           diagonals (warp w owns TMEM lanes 32 (w mod 4) .., two warps per
+//           lane group split the columns), integer combination, FP64 scaling,
+//           and a plain store of the product at canonical index
+//           lowbase(P) + rank(Q) of its [3][outputs] buffer.
 // Every mbarrier wait is bounded; on a time-out the kernel records an error
 // code and returns after releasing its tensor memory.
 
@@ -59,12 +60,12 @@ namespace {
 
 constexpr int kDigits = 8;
 constexpr int TBM = 128, TBN = 64, TBK = 64;
-constexpr int kASlots = 3, kBSets = 2;
+constexpr int kASlots = 6, kBSets = 2;
 constexpr uint32_t kABytes = TBM * TBK * 2;             // 16 KB: one digit slice of the row operand
 constexpr uint32_t kBSliceBytes = TBN * TBK * 2;        // 8 KB: one digit slice of the column operand
 constexpr uint32_t kBBytes = kDigits * kBSliceBytes;    // 64 KB: all digit slices of the column operand
 constexpr uint32_t kSmemBytes = kBSets * kBBytes + kASlots * kABytes + 1024;
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;                            // warp 0 TMA, warp 1 MMA, warps 2-9 drain
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kMaxPolls = 1ll << 26;
 constexpr int kNoExp = -100000;                          // an all-zero row
@@ -93,25 +94,46 @@ __global__ void split_exp_kernel(const double2* __restrict__ T, const double* __
 }
 
 // Balanced base-128 digits of round(x 2^{56-E}), most significant first.
+// The magnitude M < 2^56 is cut into 28-bit halves so that the digit loop runs
+// on 32-bit integers; the digits of -M are those of M negated.
 __device__ __forceinline__ void digits_of(double x, int E, int* D)
 {
     const long long bits = __double_as_longlong(x);
     const int ef = (int)((bits >> 52) & 0x7FF);
-    long long X = 0;
+    unsigned long long M = 0;
     if (ef != 0 && E != kNoExp) {
-        const long long mant = (bits & ((1ll << 52) - 1)) | (1ll << 52);
-        const int sh = ef - 1019 - E;                      // X = mant 2^{sh}, sh <= 3
-        if (sh >= 0) X = mant << sh;
-        else if (sh > -60) X = (mant + (1ll << (-sh - 1))) >> (-sh);
-        if (bits < 0) X = -X;
+        const unsigned long long mant = (unsigned long long)(bits & ((1ll << 52) - 1)) | (1ull << 52);
+        const int sh = ef - 1019 - E;                      // M = mant 2^{sh}, sh <= 3
+        if (sh >= 0) M = mant << sh;
+        else if (sh > -60) M = (mant + (1ull << (-sh - 1))) >> (-sh);
     }
+    int v = (int)(M & ((1u << 28) - 1));
+    int w = (int)(M >> 28);
 #pragma unroll
-    for (int i = kDigits - 1; i >= 1; --i) {
-        const long long d = ((X + 64) & 127) - 64;
-        D[i] = (int)d;
-        X = (X - d) >> 7;
+    for (int i = kDigits - 1; i >= 4; --i) {
+        const int d = ((v + 64) & 127) - 64;
+        D[i] = d;
+        v = (v - d) >> 7;
     }
-    D[0] = (int)X;
+    w += v;                                                // carry out of the low half
+#pragma unroll
+    for (int i = 3; i >= 1; --i) {
+        const int d = ((w + 64) & 127) - 64;
+        D[i] = d;
+        w = (w - d) >> 7;
+    }
+    D[0] = w;
+    if (bits < 0) {
+#pragma unroll
+        for (int i = 0; i < kDigits; ++i) D[i] = -D[i];
+    }
+}
+
+// BF16 bits of a small integer (|d| < 2^22): exact through FP32, whose low
+// 16 bits are then zero.
+__device__ __forceinline__ uint32_t bf16_bits(int d)
+{
+    return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
 }
 
 // One block: 32 entries x 64 sign vectors of one side.  Loads are coalesced
@@ -138,21 +160,28 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const double2* __rest
         sS[r][tx] = s;
     }
     __syncthreads();
-    // thread -> (entry ee, sign vectors dd and dd + 32)
-    for (int q = threadIdx.x; q < 32 * 64; q += 256) {
-        const int dd = q & 63, ee = q >> 6;
+    // item -> (entry ee, 4 consecutive sign vectors): one 8-byte store per
+    // product and digit, 128 contiguous bytes per entry and warp
+    for (int q = threadIdx.x; q < 32 * 16; q += 256) {
+        const int ee = q >> 4, dq = (q & 15) * 4;
         const int64_t e = e0 + ee;
-        const int d = d0 + dd;
-        if (e >= w || d >= Kpad) continue;
-        const double2 v = sT[dd][ee];
-        const double vals[3] = {v.x, v.y, sS[dd][ee]};
+        if (e >= w || d0 + dq >= Kpad) continue;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            int D[kDigits];
-            digits_of(vals[t], ex[(int64_t)t * w + e], D);
+            const int E = ex[(int64_t)t * w + e];
+            int D[4][kDigits];
 #pragma unroll
-            for (int i = 0; i < kDigits; ++i)
-                out[(((int64_t)t * kDigits + i) * w + e) * Kpad + d] = __float2bfloat16_rn((float)D[i]);
+            for (int u = 0; u < 4; ++u) {
+                const double v = t == 0 ? sT[dq + u][ee].x : (t == 1 ? sT[dq + u][ee].y : sS[dq + u][ee]);
+                digits_of(v, E, D[u]);
+            }
+#pragma unroll
+            for (int i = 0; i < kDigits; ++i) {
+                uint2 pk;
+                pk.x = bf16_bits(D[0][i]) | (bf16_bits(D[1][i]) << 16);
+                pk.y = bf16_bits(D[2][i]) | (bf16_bits(D[3][i]) << 16);
+                *reinterpret_cast<uint2*>(out + (((int64_t)t * kDigits + i) * w + e) * Kpad + d0 + dq) = pk;
+            }
         }
     }
 }
@@ -163,6 +192,7 @@ struct TcProdArgs {
     int nk;                                   // k blocks with outputs
     int kblocks;                              // 64-wide K blocks
     int64_t tile0[PCV_MAX_PHOTONS + 2];       // first tile of each block
+    int64_t tiles;                            // all tiles
     int rows_low[PCV_MAX_PHOTONS + 1];        // 1: rows are low-side entries P, columns high-side Q
     int tn[PCV_MAX_PHOTONS + 1];              // tile width (16..64)
     int64_t rows[PCV_MAX_PHOTONS + 1], cols[PCV_MAX_PHOTONS + 1];
@@ -172,8 +202,8 @@ struct TcProdArgs {
     const int* ex_low;                        // [3][wlow]
     const int* ex_high;                       // [3][whigh]
     int64_t wlow, whigh;
-    double2* acc;                             // running Re/Im; the amplitudes at the end
-    double* prob;
+    double* xt;                               // [3][total]: the three real products per output
+    int64_t total;
     int* error;
 };
 
@@ -267,6 +297,38 @@ __device__ __forceinline__ double pow2(int e)      // 2^e for -1022 <= e <= 1023
     return __longlong_as_double((long long)(1023 + e) << 52);
 }
 
+// A tile's place: k block, first row and column, width, and which side the
+// rows come from.  Tiles are numbered k block by k block, column tiles
+// fastest, so CTAs that run at the same time share row digits.
+struct TileInfo {
+    int kb, tn;
+    int64_t r0, c0;
+    bool rl;
+    int rentry, centry;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const TcProdArgs& a, int64_t tile)
+{
+    TileInfo ti;
+    int kb = 0;
+    while (kb + 1 < a.nk && a.tile0[kb + 1] <= tile) ++kb;
+    ti.kb = kb;
+    ti.tn = a.tn[kb];
+    const int64_t ctiles = (a.cols[kb] + ti.tn - 1) / ti.tn;
+    const int64_t lt = tile - a.tile0[kb];
+    ti.r0 = (lt / ctiles) * TBM;
+    ti.c0 = (lt % ctiles) * ti.tn;
+    ti.rl = a.rows_low[kb] != 0;
+    ti.rentry = (int)(a.row_off[kb] + ti.r0);
+    ti.centry = (int)(a.col_off[kb] + ti.c0);
+    return ti;
+}
+
+// Persistent: CTA b takes tiles b, b + grid, b + 2 grid, ...  The work of a
+// CTA is a sequence of chunks q = (tile, product t, 64-wide K block c); the
+// producer issues chunk q + 1's column digits after chunk q's third row digit
+// (by then chunk q - 1, the last user of that buffer, is nearly done), and
+// the next tile's loads while the drain finishes the last one.
 __global__ void __launch_bounds__(kThreads, 1)
 tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_constant__ CUtensorMap low_cols,
                   const __grid_constant__ CUtensorMap high_rows, const __grid_constant__ CUtensorMap high_cols,
@@ -282,18 +344,9 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
     __shared__ int s_fail;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // tile -> (k block, row tile, column tile); column tiles vary fastest
-    const int64_t tile = blockIdx.x;
-    int kb = 0;
-    while (kb + 1 < a.nk && a.tile0[kb + 1] <= tile) ++kb;
-    const int tn = a.tn[kb];
-    const int64_t ctiles = (a.cols[kb] + tn - 1) / tn;
-    const int64_t lt = tile - a.tile0[kb];
-    const int64_t r0 = (lt / ctiles) * TBM, c0 = (lt % ctiles) * tn;
-    const bool rl = a.rows_low[kb] != 0;
-    const CUtensorMap* rmap = rl ? &low_rows : &high_rows;
-    const CUtensorMap* cmap = rl ? &high_cols : &low_cols;
-    const int rentry = (int)(a.row_off[kb] + r0), centry = (int)(a.col_off[kb] + c0);
+    const int nkb = a.kblocks;
+    const int64_t my_tiles = a.tiles > (int64_t)blockIdx.x ? (a.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t nchunks = my_tiles * 3 * nkb;
 
     if (tid == 0) {
         for (int s = 0; s < kBSets; ++s) {
@@ -305,11 +358,13 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             bar_init(&aempty[s], 1);
         }
         bar_init(&accfull, 1);
-        bar_init(&accempty, 128);
+        bar_init(&accempty, 256);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(rmap) : "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(cmap) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&low_rows) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&low_cols) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&high_rows) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&high_cols) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sm_addr(&tmem_base)),
@@ -321,126 +376,144 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const int nkb = a.kblocks;
 
     if (tid == 0) {
         // ---------------- TMA producer
-        uint32_t na = 0, nb = 0;
-        for (int t = 0; t < 3 && !s_fail; ++t) {
-            for (int c = 0; c < nkb && !s_fail; ++c) {
-                const uint32_t bs = nb % kBSets;
-                if (nb >= (uint32_t)kBSets && !bar_wait(&bempty[bs], ((nb / kBSets) - 1) & 1)) { s_fail = 1; break; }
-                bar_expect_tx(&bfull[bs], kBBytes);
-                for (int j = 0; j < kDigits; ++j)
-                    tma_load_4d(bset + bs * kBBytes + j * kBSliceBytes, cmap, &bfull[bs], c * TBK, centry, j, t);
-                ++nb;
-                for (int i = 0; i < kDigits; ++i) {
-                    const uint32_t as = na % kASlots;
-                    if (na >= (uint32_t)kASlots && !bar_wait(&aempty[as], ((na / kASlots) - 1) & 1)) { s_fail = 1; break; }
-                    bar_expect_tx(&afull[as], kABytes);
-                    tma_load_4d(aslot + as * kABytes, rmap, &afull[as], c * TBK, rentry, i, t);
-                    ++na;
-                }
+        uint32_t na = 0;
+        auto issue_b = [&](int64_t q) -> bool {
+            const int64_t it = q / (3 * nkb), rem = q % (3 * nkb);
+            const int t = (int)(rem / nkb), c = (int)(rem % nkb);
+            const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
+            const CUtensorMap* cmap = ti.rl ? &high_cols : &low_cols;
+            const uint32_t bs = (uint32_t)(q % kBSets);
+            if (q >= kBSets && !bar_wait(&bempty[bs], (uint32_t)((q / kBSets) - 1) & 1)) return false;
+            bar_expect_tx(&bfull[bs], kBBytes);
+            for (int j = 0; j < kDigits; ++j)
+                tma_load_4d(bset + bs * kBBytes + j * kBSliceBytes, cmap, &bfull[bs], c * TBK, ti.centry, j, t);
+            return true;
+        };
+        if (nchunks > 0 && !issue_b(0)) s_fail = 1;
+        for (int64_t q = 0; q < nchunks && !s_fail; ++q) {
+            const int64_t it = q / (3 * nkb), rem = q % (3 * nkb);
+            const int t = (int)(rem / nkb), c = (int)(rem % nkb);
+            const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
+            const CUtensorMap* rmap = ti.rl ? &low_rows : &high_rows;
+            for (int i = 0; i < kDigits; ++i) {
+                const uint32_t as = na % kASlots;
+                if (na >= (uint32_t)kASlots && !bar_wait(&aempty[as], ((na / kASlots) - 1) & 1)) { s_fail = 1; break; }
+                bar_expect_tx(&afull[as], kABytes);
+                tma_load_4d(aslot + as * kABytes, rmap, &afull[as], c * TBK, ti.rentry, i, t);
+                ++na;
+                if (i == 2 && q + 1 < nchunks && !issue_b(q + 1)) { s_fail = 1; break; }
             }
         }
     } else if (tid == 32) {
         // ---------------- MMA issuer
-        const uint32_t idesc = idesc_for(tn);
-        uint32_t na = 0, nb = 0;
-        for (int t = 0; t < 3 && !s_fail; ++t) {
-            if (t > 0 && !bar_wait(&accempty, (t - 1) & 1)) { s_fail = 2; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            for (int c = 0; c < nkb && !s_fail; ++c) {
-                const uint32_t bs = nb % kBSets;
-                if (!bar_wait(&bfull[bs], (nb / kBSets) & 1)) { s_fail = 2; break; }
-                const unsigned char* sb = bset + bs * kBBytes;
-                for (int i = 0; i < kDigits; ++i) {
-                    const uint32_t as = na % kASlots;
-                    if (!bar_wait(&afull[as], (na / kASlots) & 1)) { s_fail = 2; break; }
-                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const unsigned char* sa = aslot + as * kABytes;
-                    for (int j = 0; j + i < kDigits; ++j) {
-                        const uint32_t acc_t = tmem + (uint32_t)((i + j) * TBN);
-#pragma unroll
-                        for (int kk = 0; kk < TBK / 16; ++kk)
-                            mma_f16(acc_t, sdesc(sa + kk * 32), sdesc(sb + j * kBSliceBytes + kk * 32), idesc,
-                                    (c == 0 && i == 0 && kk == 0) ? 0u : 1u);
-                    }
-                    mma_commit(&aempty[as]);
-                    ++na;
-                }
-                mma_commit(&bempty[bs]);
-                ++nb;
+        uint32_t na = 0;
+        uint32_t idesc = 0;
+        for (int64_t q = 0; q < nchunks && !s_fail; ++q) {
+            const int64_t it = q / (3 * nkb), rem = q % (3 * nkb);
+            const int c = (int)(rem % nkb);
+            const int64_t g = q / nkb;                                   // pass number of this CTA
+            if (c == 0) {
+                if (rem == 0) idesc = idesc_for(tile_info(a, blockIdx.x + it * gridDim.x).tn);
+                if (g > 0 && !bar_wait(&accempty, (uint32_t)(g - 1) & 1)) { s_fail = 2; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             }
-            mma_commit(&accfull);
+            const uint32_t bs = (uint32_t)(q % kBSets);
+            if (!bar_wait(&bfull[bs], (uint32_t)(q / kBSets) & 1)) { s_fail = 2; break; }
+            // descriptors are linear in the address (16-byte units in the low
+            // bits): one per slice, plus 2 per 16-wide K step
+            const uint64_t db0 = sdesc(bset + bs * kBBytes);
+            for (int i = 0; i < kDigits; ++i) {
+                const uint32_t as = na % kASlots;
+                if (!bar_wait(&afull[as], (na / kASlots) & 1)) { s_fail = 2; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint64_t da = sdesc(aslot + as * kABytes);
+                const uint32_t first = (c == 0 && i == 0) ? 0u : 1u;
+#pragma unroll
+                for (int j = 0; j < kDigits; ++j) {
+                    if (j + i >= kDigits) break;
+                    const uint32_t acc_t = tmem + (uint32_t)((i + j) * TBN);
+                    const uint64_t db = db0 + (uint64_t)(j * (kBSliceBytes >> 4));
+                    mma_f16(acc_t, da, db, idesc, first);
+                    mma_f16(acc_t, da + 2, db + 2, idesc, 1u);
+                    mma_f16(acc_t, da + 4, db + 4, idesc, 1u);
+                    mma_f16(acc_t, da + 6, db + 6, idesc, 1u);
+                }
+                mma_commit(&aempty[as]);
+                ++na;
+            }
+            mma_commit(&bempty[bs]);
+            if (c == nkb - 1) mma_commit(&accfull);
         }
     } else if (warp >= 2) {
-        // ---------------- drain: warp w owns TMEM lanes 32 (w mod 4) .. + 31
+        // ---------------- drain: warp w owns TMEM lanes 32 (w mod 4) .. + 31;
+        // warps 2-5 take columns [0, 32), warps 6-9 columns [32, 64)
         const int q4 = warp & 3;
-        const int64_t row = r0 + q4 * 32 + lane;
-        const bool rv = row < a.rows[kb];
-        const int* ex_r = rl ? a.ex_low : a.ex_high;
-        const int* ex_c = rl ? a.ex_high : a.ex_low;
-        const int64_t wr = rl ? a.wlow : a.whigh, wc = rl ? a.whigh : a.wlow;
-        for (int t = 0; t < 3; ++t) {
-            const bool ok = bar_wait(&accfull, t & 1);
-            if (!ok) {
-                if (lane == 0) s_fail = 3;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const int er = rv ? ex_r[(int64_t)t * wr + a.row_off[kb] + row] : kNoExp;
-            for (int cc = 0; cc < tn; cc += 16) {
-                long long hi[16], lo[16];
+        const int cbase = warp < 6 ? 0 : 32;
+        bool alive = true;
+        for (int64_t it = 0; it < my_tiles && alive; ++it) {
+            const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
+            const int kb = ti.kb, tn = ti.tn;
+            const bool rl = ti.rl;
+            const int64_t row = ti.r0 + q4 * 32 + lane;
+            const bool rv = row < a.rows[kb];
+            const int* ex_r = rl ? a.ex_low : a.ex_high;
+            const int* ex_c = rl ? a.ex_high : a.ex_low;
+            const int64_t wr = rl ? a.wlow : a.whigh, wc = rl ? a.whigh : a.wlow;
+            const int64_t pbase = rl && rv ? a.lowbase[a.lowoff[kb] + row] : 0;
+            for (int t = 0; t < 3; ++t) {
+                const int64_t g = it * 3 + t;
+                if (!bar_wait(&accfull, (uint32_t)g & 1)) {
+                    if (lane == 0) s_fail = 3;
+                    alive = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const int er = rv ? ex_r[(int64_t)t * wr + a.row_off[kb] + row] : kNoExp;
+                double* xt = a.xt + (int64_t)t * a.total;
+                for (int cc = cbase; cc < tn && cc < cbase + 32; cc += 16) {
+                    long long hi[16], lo[16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) hi[q] = lo[q] = 0;
+                    for (int q = 0; q < 16; ++q) hi[q] = lo[q] = 0;
 #pragma unroll
-                for (int d = 0; d < kDigits; ++d) {
-                    uint32_t r[16];
-                    const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * TBN + cc);
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-                        "%15}, [%16];\n"
-                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                          "=r"(r[14]), "=r"(r[15])
-                        : "r"(taddr));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    for (int d = 0; d < kDigits; ++d) {
+                        uint32_t r[16];
+                        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * TBN + cc);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                            "%14,%15}, [%16];\n"
+                            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                              "=r"(r[14]), "=r"(r[15])
+                            : "r"(taddr));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const long long v = (long long)__float2int_rn(__uint_as_float(r[q]));
+                            if (d < 4) hi[q] = hi[q] * 128 + v;
+                            else lo[q] = lo[q] * 128 + v;
+                        }
+                    }
+                    if (!rv) continue;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        const long long v = (long long)__float2int_rn(__uint_as_float(r[q]));
-                        if (d < 4) hi[q] = hi[q] * 128 + v;
-                        else lo[q] = lo[q] * 128 + v;
+                        const int64_t col = ti.c0 + cc + q;
+                        if (col >= a.cols[kb]) continue;
+                        const int ec = ex_c[(int64_t)t * wc + a.col_off[kb] + col];
+                        double x = 0.0;
+                        if (er != kNoExp && ec != kNoExp) {
+                            const int sc = er + ec - 14;
+                            x = fma((double)lo[q], pow2(sc - 49), (double)hi[q] * pow2(sc - 21));
+                        }
+                        const int64_t o = rl ? pbase + col : a.lowbase[a.lowoff[kb] + col] + row;
+                        xt[o] = x;
                     }
                 }
-                if (!rv) continue;
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int64_t col = c0 + cc + q;
-                    if (col >= a.cols[kb]) continue;
-                    const int ec = ex_c[(int64_t)t * wc + a.col_off[kb] + col];
-                    double x = 0.0;
-                    if (er != kNoExp && ec != kNoExp) {
-                        const int sc = er + ec - 14;
-                        x = fma((double)lo[q], pow2(sc - 49), (double)hi[q] * pow2(sc - 21));
-                    }
-                    const int64_t P = rl ? row : col, Q = rl ? col : row;
-                    const int64_t o = a.lowbase[a.lowoff[kb] + P] + Q;
-                    if (t == 0) {
-                        a.acc[o] = make_double2(x, -x);
-                    } else if (t == 1) {
-                        const double2 v = a.acc[o];
-                        a.acc[o] = make_double2(v.x - x, v.y - x);
-                    } else {
-                        double2 v = a.acc[o];
-                        v.y += x;
-                        a.acc[o] = v;
-                        if (a.prob) a.prob[o] = fma(v.x, v.x, v.y * v.y);
-                    }
-                }
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                bar_arrive(&accempty);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            bar_arrive(&accempty);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -448,6 +521,18 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
     if (tid == 0 && s_fail && a.error) atomicExch(a.error, s_fail);
+}
+
+// a = (t1 - t2) + i (t3 - t1 - t2), p = |a|^2
+__global__ void tc_combine_kernel(const double* __restrict__ xt, int64_t total, double2* __restrict__ amp,
+                                  double* __restrict__ prob)
+{
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= total) return;
+    const double t1 = xt[o], t2 = xt[total + o], t3 = xt[2 * total + o];
+    const double2 v = make_double2(t1 - t2, t3 - t1 - t2);
+    if (amp) amp[o] = v;
+    if (prob) prob[o] = fma(v.x, v.x, v.y * v.y);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
@@ -495,11 +580,12 @@ int64_t msets_tc(int w, int k) { return k == 0 ? 1 : (w <= 0 ? 0 : binom_tc(w + 
 
 int tc_pad_k(int K) { return ((K + TBK - 1) / TBK) * TBK; }
 
-int64_t tc_workspace(int64_t wlow, int64_t whigh, int K)
+int64_t tc_workspace(int64_t wlow, int64_t whigh, int K, int64_t total)
 {
     const int Kp = tc_pad_k(K);
     return (int64_t)(al256((size_t)3 * kDigits * wlow * Kp * 2) + al256((size_t)3 * kDigits * whigh * Kp * 2) +
-                     al256((size_t)3 * wlow * sizeof(int)) + al256((size_t)3 * whigh * sizeof(int)) + 256);
+                     al256((size_t)3 * wlow * sizeof(int)) + al256((size_t)3 * whigh * sizeof(int)) +
+                     al256((size_t)3 * total * sizeof(double)) + 256);
 }
 
 cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
@@ -518,9 +604,9 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     __nv_bfloat16* dlow = (__nv_bfloat16*)w;     w += al256((size_t)3 * kDigits * in.wlow * Kp * 2);
     __nv_bfloat16* dhigh = (__nv_bfloat16*)w;    w += al256((size_t)3 * kDigits * in.whigh * Kp * 2);
     int* exlow = (int*)w;                        w += al256((size_t)3 * in.wlow * sizeof(int));
-    int* exhigh = (int*)w;
+    int* exhigh = (int*)w;                       w += al256((size_t)3 * in.whigh * sizeof(int));
+    double* xt = (double*)w;
     // digits of both sides (timed as their own stage when profiling is on)
-    stage_end(kStageGemm, s);
     stage_begin(kStageSplit, s);
     for (int side = 0; side < 2; ++side) {
         const double2* T = side == 0 ? in.Tlow : in.Thigh;
@@ -562,18 +648,29 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         a.nk++;
     }
     a.tile0[a.nk] = tiles;
-    if (tiles == 0) return cudaSuccess;
+    if (tiles == 0) {
+        stage_end(kStageGemm, s);
+        return cudaSuccess;
+    }
     if (tiles > INT32_MAX || in.wlow + TBM > INT32_MAX || in.whigh + TBM > INT32_MAX) return cudaErrorInvalidConfiguration;
     a.lowbase = in.lowbase;
     a.ex_low = exlow;
     a.ex_high = exhigh;
     a.wlow = in.wlow;
     a.whigh = in.whigh;
-    a.acc = in.acc;
-    a.prob = in.prob;
+    a.xt = xt;
+    a.total = in.total;
     a.error = in.error;
-    tc_product_kernel<<<(unsigned)tiles, kThreads, kSmemBytes, s>>>(lr, lc, hr, hc, a);
+    a.tiles = tiles;
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const unsigned grid = (unsigned)(tiles < (int64_t)sms ? tiles : sms);
+    tc_product_kernel<<<grid, kThreads, kSmemBytes, s>>>(lr, lc, hr, hc, a);
     note_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    tc_combine_kernel<<<(unsigned)((in.total + 255) / 256), 256, 0, s>>>(xt, in.total, in.amp, in.prob);
+    note_launches(1);
+    stage_end(kStageGemm, s);
     return cudaGetLastError();
 }
 
