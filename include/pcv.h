@@ -488,7 +488,7 @@ int pcv_fp64_probe(double* out, int blocks, int threads, int iters, void* stream
  * record CUDA events on the launching stream around each stage of a call
  * (stage 0: factorised-distribution tables, 1: factorised-distribution
  * products, 2: plain Glynn kernels, 3: digit splitting of the tensor-core
- * products).  pcv_profile_read waits for the recorded
+ * products, 4: the FP64 blocks beside the tensor-core products).  pcv_profile_read waits for the recorded
  * events, writes the accumulated milliseconds and call counts of the first
  * `nstages` stages to ms[] and calls[] (host) and resets them.
  * pcv_launch_count returns the number of kernels the library has launched

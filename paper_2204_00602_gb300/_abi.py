@@ -379,7 +379,7 @@ def pcv_fp64_probe(out, blocks, threads, iters, stream):
     return _call("pcv_fp64_probe", ptr(out), blocks, threads, iters, stream)
 
 
-STAGES = ("dist_tables", "dist_products", "glynn_plain", "tc_split")
+STAGES = ("dist_tables", "dist_products", "glynn_plain", "tc_split", "tc_edge_fp64")
 
 
 def pcv_profile_enable(on: bool):

@@ -258,6 +258,42 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs a)
     }
 }
 
+// The blocks with one entry on one side (k = 0: P empty; k = n: Q empty):
+// a(S) = sum_d f(d) v_s(d) for one fixed entry f and every entry s of the
+// other side's level; one thread per output, the fixed entry broadcast, the
+// strip loads coalesced.  3 DFMA per output and sign vector, as gemm_kernel.
+struct EdgeArgs {
+    const double2* F; const double* Fs; int64_t wF;     // fixed entry (column 0 of its level)
+    const double2* S; const double* Ss; int64_t wS;     // strip level
+    int64_t count;                                       // strip entries
+    int kc;
+    const int64_t* lowbase;
+    int64_t lowidx;                                      // low-table index of P (k = 0) or of the strip level (k = n)
+    int strip_is_low;                                    // 1 for k = n
+    double2* amp;
+    double* prob;
+};
+
+__global__ void __launch_bounds__(256) edge_kernel(const EdgeArgs a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.count) return;
+    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    for (int q = 0; q < a.kc; ++q) {
+        const double2 f = __ldg(a.F + (int64_t)q * a.wF);
+        const double fs = __ldg(a.Fs + (int64_t)q * a.wF);
+        const double2 v = __ldg(a.S + (int64_t)q * a.wS + i);
+        const double vs = __ldg(a.Ss + (int64_t)q * a.wS + i);
+        t1 = fma(f.x, v.x, t1);
+        t2 = fma(f.y, v.y, t2);
+        t3 = fma(fs, vs, t3);
+    }
+    const double2 v = make_double2(t1 - t2, t3 - t1 - t2);
+    const int64_t o = a.strip_is_low ? a.lowbase[a.lowidx + i] : a.lowbase[a.lowidx] + i;
+    if (a.amp) a.amp[o] = v;
+    if (a.prob) a.prob[o] = fma(v.x, v.x, v.y * v.y);
+}
+
 int64_t binom_host(int a, int b)
 {
     if (b < 0 || a < 0 || b > a) return 0;
@@ -465,6 +501,34 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
             ti.ws = tcws;
             ti.error = nullptr;
             if ((e = launch_tc_products(ti, s)) != cudaSuccess) return e;
+            // the k = 0 and k = n blocks (one entry on one side) in FP64
+            stage_begin(kStageEdge, s);
+            for (int k = 0; k <= n; k += n) {
+                EdgeArgs ea;
+                ea.kc = dp.kc;
+                ea.lowbase = lowbase;
+                ea.amp = amp;
+                ea.prob = prob;
+                if (k == 0) {                      // P = {} (low level 0), strip: high level n
+                    ea.F = Tlow + dp.lowoff[0]; ea.Fs = Slow + dp.lowoff[0]; ea.wF = dp.wlow;
+                    ea.S = Thigh + dp.highoff[n]; ea.Ss = Shigh + dp.highoff[n]; ea.wS = dp.whigh;
+                    ea.count = mset(m - dp.h, n);
+                    ea.lowidx = dp.lowoff[0];
+                    ea.strip_is_low = 0;
+                } else {                           // Q = {} (high level 0), strip: low level n
+                    ea.F = Thigh + dp.highoff[0]; ea.Fs = Shigh + dp.highoff[0]; ea.wF = dp.whigh;
+                    ea.S = Tlow + dp.lowoff[n]; ea.Ss = Slow + dp.lowoff[n]; ea.wS = dp.wlow;
+                    ea.count = mset(dp.h, n);
+                    ea.lowidx = dp.lowoff[n];
+                    ea.strip_is_low = 1;
+                }
+                if (ea.count > 0) {
+                    edge_kernel<<<(unsigned)((ea.count + 255) / 256), 256, 0, s>>>(ea);
+                    note_launches(1);
+                    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                }
+            }
+            stage_end(kStageEdge, s);
             continue;
         }
         stage_begin(kStageGemm, s);

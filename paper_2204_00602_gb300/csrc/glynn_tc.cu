@@ -76,27 +76,29 @@ __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_l
 
 // E_t(entry) for t = re, im, re+im: the smallest E with max |x| <= 2^{E-1}
 // (from the largest exponent field; a power of two costs one spare bit).
-__global__ void split_exp_kernel(const double2* __restrict__ T, const double* __restrict__ Sm, int64_t w, int K,
-                                 int* __restrict__ ex)
+// (T, Sm: [K][stride] tables from their first digitised entry; w entries.)
+__global__ void split_exp_kernel(const double2* __restrict__ T, const double* __restrict__ Sm, int64_t stride,
+                                 int64_t w, int K, int* __restrict__ ex)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= w) return;
     int f0 = 0, f1 = 0, f2 = 0;
     for (int d = 0; d < K; ++d) {
-        const double2 v = T[(int64_t)d * w + e];
+        const double2 v = T[(int64_t)d * stride + e];
         f0 = max(f0, exp_field(v.x));
         f1 = max(f1, exp_field(v.y));
-        f2 = max(f2, exp_field(Sm[(int64_t)d * w + e]));
+        f2 = max(f2, exp_field(Sm[(int64_t)d * stride + e]));
     }
     ex[e] = f0 ? f0 - 1021 : kNoExp;
     ex[w + e] = f1 ? f1 - 1021 : kNoExp;
     ex[2 * w + e] = f2 ? f2 - 1021 : kNoExp;
 }
 
-// Balanced base-128 digits of round(x 2^{56-E}), most significant first.
-// The magnitude M < 2^56 is cut into 28-bit halves so that the digit loop runs
-// on 32-bit integers; the digits of -M are those of M negated.
-__device__ __forceinline__ void digits_of(double x, int E, int* D)
+// Balanced base-128 digits of round(x 2^{56-E}), most significant first,
+// packed one per byte (two's complement; digit i in byte i).  The magnitude
+// M < 2^56 is cut into 28-bit halves so that the digit loop runs on 32-bit
+// integers; the digits of -M are those of M negated.
+__device__ __forceinline__ unsigned long long digits_of(double x, int E)
 {
     const long long bits = __double_as_longlong(x);
     const int ef = (int)((bits >> 52) & 0x7FF);
@@ -107,81 +109,76 @@ __device__ __forceinline__ void digits_of(double x, int E, int* D)
         if (sh >= 0) M = mant << sh;
         else if (sh > -60) M = (mant + (1ull << (-sh - 1))) >> (-sh);
     }
+    const int neg = bits < 0 ? 1 : 0;
     int v = (int)(M & ((1u << 28) - 1));
     int w = (int)(M >> 28);
+    uint32_t lo = 0, hi = 0;                               // bytes 4..7 and 0..3
 #pragma unroll
     for (int i = kDigits - 1; i >= 4; --i) {
         const int d = ((v + 64) & 127) - 64;
-        D[i] = d;
+        lo |= (uint32_t)((neg ? -d : d) & 0xFF) << (8 * (i - 4));
         v = (v - d) >> 7;
     }
     w += v;                                                // carry out of the low half
 #pragma unroll
     for (int i = 3; i >= 1; --i) {
         const int d = ((w + 64) & 127) - 64;
-        D[i] = d;
+        hi |= (uint32_t)((neg ? -d : d) & 0xFF) << (8 * i);
         w = (w - d) >> 7;
     }
-    D[0] = w;
-    if (bits < 0) {
-#pragma unroll
-        for (int i = 0; i < kDigits; ++i) D[i] = -D[i];
-    }
+    hi |= (uint32_t)((neg ? -w : w) & 0xFF);
+    return ((unsigned long long)lo << 32) | hi;
 }
 
-// BF16 bits of a small integer (|d| < 2^22): exact through FP32, whose low
-// 16 bits are then zero.
-__device__ __forceinline__ uint32_t bf16_bits(int d)
+// BF16 bits of digit i of a packed word (|d| <= 64): exact through FP32,
+// whose low 16 bits are then zero.
+__device__ __forceinline__ uint32_t digit_bf16(unsigned long long packed, int i)
 {
+    const int d = (int)(signed char)(packed >> (8 * i));
     return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
 }
 
-// One block: 32 entries x 64 sign vectors of one side.  Loads are coalesced
-// along entries, stores along sign vectors (the digit tensors are K-major).
+// One warp: 4 consecutive entries x 32 consecutive sign vectors (lane ->
+// entry lane & 3, sign vectors 4 (lane >> 2) .. + 3).  Loads take 64-byte
+// segments of the tables; each product and digit is one 8-byte store per
+// lane (64-byte segments along K of the digit tensors).  No shared memory.
 __global__ void __launch_bounds__(256) split_digits_kernel(const double2* __restrict__ T, const double* __restrict__ Sm,
-                                                           int64_t w, int K, int Kpad, const int* __restrict__ ex,
-                                                           __nv_bfloat16* __restrict__ out)
+                                                           int64_t stride, int64_t w, int K, int Kpad,
+                                                           const int* __restrict__ ex, __nv_bfloat16* __restrict__ out)
 {
-    __shared__ double2 sT[64][33];
-    __shared__ double sS[64][33];
-    const int64_t e0 = (int64_t)blockIdx.x * 32;
-    const int d0 = blockIdx.y * 64;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;     // 32 x 8
-    for (int r = ty; r < 64; r += 8) {
-        const int d = d0 + r;
-        const int64_t e = e0 + tx;
-        double2 v = make_double2(0.0, 0.0);
-        double s = 0.0;
-        if (d < K && e < w) {
-            v = T[(int64_t)d * w + e];
-            s = Sm[(int64_t)d * w + e];
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int ndg = Kpad / 32;
+    const int64_t eg = gw / ndg;
+    const int dg = (int)(gw % ndg);
+    const int64_t e = eg * 4 + (lane & 3);
+    const int d0 = dg * 32 + (lane >> 2) * 4;
+    if (e >= w) return;
+    double vr[4], vi[4], vs[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int d = d0 + u;
+        if (d < K) {
+            const double2 v = T[(int64_t)d * stride + e];
+            vr[u] = v.x;
+            vi[u] = v.y;
+            vs[u] = Sm[(int64_t)d * stride + e];
+        } else {
+            vr[u] = vi[u] = vs[u] = 0.0;
         }
-        sT[r][tx] = v;
-        sS[r][tx] = s;
     }
-    __syncthreads();
-    // item -> (entry ee, 4 consecutive sign vectors): one 8-byte store per
-    // product and digit, 128 contiguous bytes per entry and warp
-    for (int q = threadIdx.x; q < 32 * 16; q += 256) {
-        const int ee = q >> 4, dq = (q & 15) * 4;
-        const int64_t e = e0 + ee;
-        if (e >= w || d0 + dq >= Kpad) continue;
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int E = ex[(int64_t)t * w + e];
-            int D[4][kDigits];
+    for (int t = 0; t < 3; ++t) {
+        const int E = ex[(int64_t)t * w + e];
+        unsigned long long pk[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const double v = t == 0 ? sT[dq + u][ee].x : (t == 1 ? sT[dq + u][ee].y : sS[dq + u][ee]);
-                digits_of(v, E, D[u]);
-            }
+        for (int u = 0; u < 4; ++u) pk[u] = digits_of(t == 0 ? vr[u] : (t == 1 ? vi[u] : vs[u]), E);
 #pragma unroll
-            for (int i = 0; i < kDigits; ++i) {
-                uint2 pk;
-                pk.x = bf16_bits(D[0][i]) | (bf16_bits(D[1][i]) << 16);
-                pk.y = bf16_bits(D[2][i]) | (bf16_bits(D[3][i]) << 16);
-                *reinterpret_cast<uint2*>(out + (((int64_t)t * kDigits + i) * w + e) * Kpad + d0 + dq) = pk;
-            }
+        for (int i = 0; i < kDigits; ++i) {
+            uint2 st;
+            st.x = digit_bf16(pk[0], i) | (digit_bf16(pk[1], i) << 16);
+            st.y = digit_bf16(pk[2], i) | (digit_bf16(pk[3], i) << 16);
+            *reinterpret_cast<uint2*>(out + (((int64_t)t * kDigits + i) * w + e) * Kpad + d0) = st;
         }
     }
 }
@@ -600,37 +597,44 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         g_tc_attr[dev] = true;
     }
     const int K = in.K, Kp = tc_pad_k(K);
+    // the blocks k = 1 .. n-1 use table levels 1 .. n-1 of each side (the
+    // k = 0 and k = n blocks, one entry on one side, are left to the caller)
+    const int64_t lb = in.lowoff[1], lcnt = in.n >= 2 ? in.lowoff[in.n] - lb : 0;
+    const int64_t hb = in.highoff[1], hcnt = in.n >= 2 ? in.highoff[in.n] - hb : 0;
     char* w = (char*)in.ws;
     __nv_bfloat16* dlow = (__nv_bfloat16*)w;     w += al256((size_t)3 * kDigits * in.wlow * Kp * 2);
     __nv_bfloat16* dhigh = (__nv_bfloat16*)w;    w += al256((size_t)3 * kDigits * in.whigh * Kp * 2);
     int* exlow = (int*)w;                        w += al256((size_t)3 * in.wlow * sizeof(int));
     int* exhigh = (int*)w;                       w += al256((size_t)3 * in.whigh * sizeof(int));
     double* xt = (double*)w;
+    if (lcnt == 0 || hcnt == 0) return cudaSuccess;
     // digits of both sides (timed as their own stage when profiling is on)
     stage_begin(kStageSplit, s);
     for (int side = 0; side < 2; ++side) {
         const double2* T = side == 0 ? in.Tlow : in.Thigh;
         const double* S = side == 0 ? in.Slow : in.Shigh;
-        const int64_t ww = side == 0 ? in.wlow : in.whigh;
+        const int64_t stride = side == 0 ? in.wlow : in.whigh;
+        const int64_t eb = side == 0 ? lb : hb, ww = side == 0 ? lcnt : hcnt;
         int* ex = side == 0 ? exlow : exhigh;
         __nv_bfloat16* dg = side == 0 ? dlow : dhigh;
-        split_exp_kernel<<<(unsigned)((ww + 255) / 256), 256, 0, s>>>(T, S, ww, K, ex);
-        split_digits_kernel<<<dim3((unsigned)((ww + 31) / 32), (unsigned)(Kp / 64)), 256, 0, s>>>(T, S, ww, K, Kp, ex, dg);
+        split_exp_kernel<<<(unsigned)((ww + 255) / 256), 256, 0, s>>>(T + eb, S + eb, stride, ww, K, ex);
+        const int64_t warps = ((ww + 3) / 4) * (Kp / 32);
+        split_digits_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(T + eb, S + eb, stride, ww, K, Kp, ex, dg);
         note_launches(2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     stage_end(kStageSplit, s);
     stage_begin(kStageGemm, s);
     CUtensorMap lr, lc, hr, hc;
-    if ((e = make_digit_map(&lr, dlow, in.wlow, Kp, TBM)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&lc, dlow, in.wlow, Kp, TBN)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&hr, dhigh, in.whigh, Kp, TBM)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&hc, dhigh, in.whigh, Kp, TBN)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&lr, dlow, lcnt, Kp, TBM)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&lc, dlow, lcnt, Kp, TBN)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&hr, dhigh, hcnt, Kp, TBM)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&hc, dhigh, hcnt, Kp, TBN)) != cudaSuccess) return e;
     TcProdArgs a;
     a.nk = 0;
     a.kblocks = Kp / TBK;
     int64_t tiles = 0;
-    for (int k = 0; k <= in.n; ++k) {
+    for (int k = 1; k < in.n; ++k) {
         const int64_t M = msets_tc(in.h, k), N = msets_tc(in.m - in.h, in.n - k);
         if (M == 0 || N == 0) continue;
         const bool rl = M >= N;
@@ -640,8 +644,8 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         a.tn[a.nk] = tn;
         a.rows[a.nk] = rows;
         a.cols[a.nk] = cols;
-        a.row_off[a.nk] = rl ? in.lowoff[k] : in.highoff[in.n - k];
-        a.col_off[a.nk] = rl ? in.highoff[in.n - k] : in.lowoff[k];
+        a.row_off[a.nk] = rl ? in.lowoff[k] - lb : in.highoff[in.n - k] - hb;
+        a.col_off[a.nk] = rl ? in.highoff[in.n - k] - hb : in.lowoff[k] - lb;
         a.lowoff[a.nk] = in.lowoff[k];
         a.tile0[a.nk] = tiles;
         tiles += ((rows + TBM - 1) / TBM) * ((cols + tn - 1) / tn);
@@ -652,12 +656,12 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         stage_end(kStageGemm, s);
         return cudaSuccess;
     }
-    if (tiles > INT32_MAX || in.wlow + TBM > INT32_MAX || in.whigh + TBM > INT32_MAX) return cudaErrorInvalidConfiguration;
+    if (tiles > INT32_MAX || lcnt + TBM > INT32_MAX || hcnt + TBM > INT32_MAX) return cudaErrorInvalidConfiguration;
     a.lowbase = in.lowbase;
     a.ex_low = exlow;
     a.ex_high = exhigh;
-    a.wlow = in.wlow;
-    a.whigh = in.whigh;
+    a.wlow = lcnt;                            // entries of the digit tensors (exponent stride)
+    a.whigh = hcnt;
     a.xt = xt;
     a.total = in.total;
     a.error = in.error;

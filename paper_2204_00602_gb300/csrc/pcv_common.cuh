@@ -103,7 +103,7 @@ cudaError_t build_cum_table(const int64_t* mc, int m, int kmax, int64_t* cum, cu
 // Per-stage timing (pcv_api.cu): when enabled, stage_begin/stage_end record
 // CUDA events on the launching stream around a group of launches; the times
 // are read back by pcv_profile_read.  note_launches counts kernel launches.
-enum Stage { kStageTables = 0, kStageGemm = 1, kStagePlain = 2, kStageSplit = 3, kStageCount = 8 };
+enum Stage { kStageTables = 0, kStageGemm = 1, kStagePlain = 2, kStageSplit = 3, kStageEdge = 4, kStageCount = 8 };
 void stage_begin(int stage, cudaStream_t s);
 void stage_end(int stage, cudaStream_t s);
 void note_launches(int64_t k);
