@@ -2,10 +2,13 @@
 
 One step = every amplitude and probability of the 20,030,010 outputs of a
 Haar-random 20x20 unitary with photons in modes 0..9 (Eq. eqperm, Sec. 4.2),
-computed by the CUDA library through its C ABI.
+computed by the CUDA library through its C ABI.  The default path is the
+factorised Glynn sum with its complex products on the tensor cores as exact
+integer digit products (--algo factor_tc); --algo factor runs the same sum
+with FP64 products, which the JSON line also reports as context.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--algo factor|group]
+                    [--algo factor_tc|factor|group|slos]
 
 Prints one JSON line (rank 0).  `value` is amplitudes/s over all ranks with
 inputs resident in HBM; `e2e` is the same metric through the public API with
@@ -48,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="factor", choices=["factor", "factor_tc", "group", "slos"],
+    ap.add_argument("--algo", default="factor_tc", choices=["factor", "factor_tc", "group", "slos"],
                     help="factor: factorised Glynn (default); group: plain Glynn; slos: state expansion")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
@@ -313,7 +316,10 @@ def run_ours(args):
         # BF16 tensor-core work: 3 real products x 36 digit pairs x 2 flops per
         # output and sign vector (useful outputs only)
         ms, calls = stages["dist_products"]
-        flops_per_call = Ntot * (2 ** (N_PH - 1)) * 3 * 36 * 2
+        # outputs of the blocks k = 1 .. n-1 (the two single-entry blocks run in FP64)
+        h = M // 2
+        n_tc = Ntot - math.comb(M - h + N_PH - 1, N_PH) - math.comb(h + N_PH - 1, N_PH)
+        flops_per_call = n_tc * (2 ** (N_PH - 1)) * 3 * 36 * 2
         kname = "tc_product_kernel (exact-digit BF16 tcgen05 products, 36 digit pairs x 3 real products)"
         launches_per_call = 1
     elif args.algo == "group":
@@ -344,9 +350,37 @@ def run_ours(args):
             "launches_per_step": launches_per_call,
             "stage_ms_per_step": {k: (v[0] / v[1] if v[1] else None) for k, v in stages.items()}}
 
+    # context: the FP64 factorised path (its product kernel against the FP64 peak)
+    fp64_ctx = None
+    if args.algo == "factor_tc" and not args.no_e2e:
+        ws_f = pcv.workspace(pcv.distribution_workspace_bytes(M, N_PH, pcv.PCV_ALGO_FACTOR), dev)
+        for _ in range(2):
+            pcv.distribution(U, t, algo=pcv.PCV_ALGO_FACTOR, ws=ws_f, out=(prob, amp))
+        torch.cuda.synchronize()
+        abi.pcv_profile_read()
+        abi.pcv_profile_enable(True)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            pcv.distribution(U, t, algo=pcv.PCV_ALGO_FACTOR, ws=ws_f, out=(prob, amp))
+        f1.record(stream)
+        torch.cuda.synchronize()
+        abi.pcv_profile_enable(False)
+        st = abi.pcv_profile_read()
+        ms_f = f0.elapsed_time(f1) / args.steps
+        gms, gcalls = st["dist_products"]
+        gflops = Ntot * (2 ** (N_PH - 1)) * 6
+        ach = gflops * gcalls / (gms * 1e-3) / 1e12 if gms > 0 else None
+        fp64_peak = sms * 4 * sm_max * 1e6 / 1e12
+        fp64_ctx = {"algo": "factorised Glynn, FP64 products (gemm_kernel, 3 DFMA per output and sign vector)",
+                    "ms_per_step": ms_f, "value": Ntot / (ms_f * 1e-3), "unit": "amplitudes/s",
+                    "product_kernel_tflops": ach, "fp64_peak_tflops": fp64_peak,
+                    "frac_of_fp64_peak": ach / fp64_peak if ach else None}
+        del ws_f
+
     # context: the same workload by photon-by-photon state expansion (not the Glynn path)
     alt = None
-    if args.algo == "factor" and not args.no_e2e:
+    if args.algo in ("factor", "factor_tc") and not args.no_e2e:
         ws_s = pcv.workspace(pcv.distribution_workspace_bytes(M, N_PH, pcv.PCV_ALGO_SLOS), dev)
         for _ in range(2):
             pcv.distribution(U, t, algo=pcv.PCV_ALGO_SLOS, ws=ws_s, out=(prob, amp))
@@ -371,12 +405,16 @@ def run_ours(args):
         "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.algo != "factor_tc" else "f64 (tables, scaling, results; products as exact bf16 digit MMAs)",
+        "dtype": "f64",
+        "dtype_note": None if args.algo != "factor_tc" else
+        "FP64 tables, scaling and results; the complex products run as exact integer digit products "
+        "on the bf16 tensor cores (no rounding; agreement with the FP64 path to 1e-11)",
         "data": "synthetic",
         "config": {"workload": workload_text(M, N_PH, Ntot), "m": M, "n": N_PH, "outputs": Ntot, "algo": args.algo,
                    "l2": "flushed between steps (256 MiB write, untimed)", "parallelism": f"replicas{world}"},
         "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "state_expansion": alt,
+        "fp64_factor_path": fp64_ctx,
         "wall_s_timed_region": wall,
     }
     print(json.dumps(line), flush=True)
