@@ -91,6 +91,13 @@ struct LevelArgs {
     double* Tsum;          // [batch][kc][width]: re + im of T
     int64_t tstride;
     int64_t* lowbase;      // low side: canonical base index of each P (written once)
+    // Edge mode (partial != null): the level is not stored; each thread adds
+    // sum_q F(q) entry(q) over its sign vectors, F being the single entry of
+    // the other side, and writes the sum to partial[entry * ngroups + group].
+    const double2* F;
+    int64_t wF;
+    double2* partial;
+    int ngroups;
 };
 
 __global__ void level_kernel(const LevelArgs a)
@@ -158,6 +165,17 @@ __global__ void level_kernel(const LevelArgs a)
         a.lowbase[a.off + i] = base;
     }
 
+    if (a.partial) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int q = q0; q < q1; ++q) {
+            double2 y = Y[(int64_t)q * a.m + r];
+            if (mult > 1) { y.x *= sc; y.y *= sc; }
+            const double2 v = cmul(T[(int64_t)q * a.width + a.poff + parent], y);
+            cmac(acc, a.F[(int64_t)q * a.wF], v);
+        }
+        if (b == 0) a.partial[i * a.ngroups + blockIdx.y] = acc;
+        return;
+    }
     for (int q = q0; q < q1; ++q) {
         double2 y = Y[(int64_t)q * a.m + r];
         if (mult > 1) { y.x *= sc; y.y *= sc; }
@@ -165,6 +183,21 @@ __global__ void level_kernel(const LevelArgs a)
         T[(int64_t)q * a.width + a.off + i] = v;
         Ts[(int64_t)q * a.width + a.off + i] = v.x + v.y;
     }
+}
+
+// Edge mode's second pass: the sign-vector groups of each entry added in a
+// fixed order, written at its canonical index.
+__global__ void edge_reduce_kernel(const double2* __restrict__ partial, int64_t count, int ngroups,
+                                   const int64_t* __restrict__ lowbase, int64_t lowidx, int strip_is_low,
+                                   double2* __restrict__ amp, double* __restrict__ prob)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double2 v = partial[i * ngroups];
+    for (int g = 1; g < ngroups; ++g) v = cadd(v, partial[i * ngroups + g]);
+    const int64_t o = strip_is_low ? lowbase[lowidx + i] : lowbase[lowidx] + i;
+    if (amp) amp[o] = v;
+    if (prob) prob[o] = fma(v.x, v.x, v.y * v.y);
 }
 
 struct GemmArgs {
@@ -258,42 +291,6 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs a)
     }
 }
 
-// The blocks with one entry on one side (k = 0: P empty; k = n: Q empty):
-// a(S) = sum_d f(d) v_s(d) for one fixed entry f and every entry s of the
-// other side's level; one thread per output, the fixed entry broadcast, the
-// strip loads coalesced.  3 DFMA per output and sign vector, as gemm_kernel.
-struct EdgeArgs {
-    const double2* F; const double* Fs; int64_t wF;     // fixed entry (column 0 of its level)
-    const double2* S; const double* Ss; int64_t wS;     // strip level
-    int64_t count;                                       // strip entries
-    int kc;
-    const int64_t* lowbase;
-    int64_t lowidx;                                      // low-table index of P (k = 0) or of the strip level (k = n)
-    int strip_is_low;                                    // 1 for k = n
-    double2* amp;
-    double* prob;
-};
-
-__global__ void __launch_bounds__(256) edge_kernel(const EdgeArgs a)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.count) return;
-    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
-    for (int q = 0; q < a.kc; ++q) {
-        const double2 f = __ldg(a.F + (int64_t)q * a.wF);
-        const double fs = __ldg(a.Fs + (int64_t)q * a.wF);
-        const double2 v = __ldg(a.S + (int64_t)q * a.wS + i);
-        const double vs = __ldg(a.Ss + (int64_t)q * a.wS + i);
-        t1 = fma(f.x, v.x, t1);
-        t2 = fma(f.y, v.y, t2);
-        t3 = fma(fs, vs, t3);
-    }
-    const double2 v = make_double2(t1 - t2, t3 - t1 - t2);
-    const int64_t o = a.strip_is_low ? a.lowbase[a.lowidx + i] : a.lowbase[a.lowidx] + i;
-    if (a.amp) a.amp[o] = v;
-    if (a.prob) a.prob[o] = fma(v.x, v.x, v.y * v.y);
-}
-
 int64_t binom_host(int a, int b)
 {
     if (b < 0 || a < 0 || b > a) return 0;
@@ -383,8 +380,11 @@ int64_t dist_plan_tc(const Plan& p, bool need_amp_buffer, DistPlan* dp)
     dp->ws_acc = 0;
     dp->tc = true;
     dp->ws_tc = (size_t)tc_workspace(dp->wlow, dp->whigh, (int)dmax, dp->total);
+    // edge-mode partial sums of the larger level n (reused by both sides)
+    const int64_t ln = std::max(mset(dp->h, p.n), mset(p.m - dp->h, p.n));
+    dp->ws_edge = align256((size_t)ln * ((dmax + kLevelGroup - 1) / kLevelGroup) * sizeof(double2));
     dp->ws_total = dp->ws_table + dp->ws_base + dp->ws_acc + dp->ws_y + dp->ws_tl + dp->ws_sl + dp->ws_th + dp->ws_sh +
-                   dp->ws_tc;
+                   dp->ws_tc + dp->ws_edge;
     return (int64_t)dp->ws_total;
 }
 
@@ -458,7 +458,12 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
         for (int side = 0; side < 2; ++side) {
             const int wside = side == 0 ? dp.h : m - dp.h;
             for (int k = 0; k <= n; ++k) {
+                if (dp.tc && k == n) continue;     // folded into the edge products below
                 LevelArgs la;
+                la.F = nullptr;
+                la.wF = 0;
+                la.partial = nullptr;
+                la.ngroups = 0;
                 la.mc = mc;
                 la.m = m; la.n = n; la.h = dp.h;
                 la.side = side;
@@ -501,32 +506,47 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
             ti.ws = tcws;
             ti.error = nullptr;
             if ((e = launch_tc_products(ti, s)) != cudaSuccess) return e;
-            // the k = 0 and k = n blocks (one entry on one side) in FP64
+            // the k = 0 and k = n blocks (one entry on one side) in FP64: level n
+            // of each side is never stored; the level kernel multiplies each new
+            // entry by the other side's single entry (level 0) and sums over its
+            // sign vectors, and a second pass adds the groups
             stage_begin(kStageEdge, s);
-            for (int k = 0; k <= n; k += n) {
-                EdgeArgs ea;
-                ea.kc = dp.kc;
-                ea.lowbase = lowbase;
-                ea.amp = amp;
-                ea.prob = prob;
-                if (k == 0) {                      // P = {} (low level 0), strip: high level n
-                    ea.F = Tlow + dp.lowoff[0]; ea.Fs = Slow + dp.lowoff[0]; ea.wF = dp.wlow;
-                    ea.S = Thigh + dp.highoff[n]; ea.Ss = Shigh + dp.highoff[n]; ea.wS = dp.whigh;
-                    ea.count = mset(m - dp.h, n);
-                    ea.lowidx = dp.lowoff[0];
-                    ea.strip_is_low = 0;
-                } else {                           // Q = {} (high level 0), strip: low level n
-                    ea.F = Thigh + dp.highoff[0]; ea.Fs = Shigh + dp.highoff[0]; ea.wF = dp.whigh;
-                    ea.S = Tlow + dp.lowoff[n]; ea.Ss = Slow + dp.lowoff[n]; ea.wS = dp.wlow;
-                    ea.count = mset(dp.h, n);
-                    ea.lowidx = dp.lowoff[n];
-                    ea.strip_is_low = 1;
-                }
-                if (ea.count > 0) {
-                    edge_kernel<<<(unsigned)((ea.count + 255) / 256), 256, 0, s>>>(ea);
-                    note_launches(1);
-                    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-                }
+            const int ngroups = (int)((dp.kc + kLevelGroup - 1) / kLevelGroup);
+            double2* partial = (double2*)((char*)tcws + dp.ws_tc);
+            for (int side = 0; side < 2; ++side) {
+                const int wside = side == 0 ? dp.h : m - dp.h;
+                LevelArgs la;
+                la.mc = mc;
+                la.m = m; la.n = n; la.h = dp.h;
+                la.side = side;
+                la.k = n;
+                la.count = mset(wside, n);
+                if (la.count == 0) continue;
+                la.off = side == 0 ? dp.lowoff[n] : dp.highoff[n];
+                la.poff = side == 0 ? dp.lowoff[n - 1] : dp.highoff[n - 1];
+                la.width = side == 0 ? dp.wlow : dp.whigh;
+                la.kc = dp.kc;
+                la.d0 = 0;
+                la.lead = lead;
+                la.Y = Y;
+                la.ystride = ystride;
+                la.T = side == 0 ? Tlow : Thigh;
+                la.Tsum = side == 0 ? Slow : Shigh;
+                la.tstride = side == 0 ? tl_stride : th_stride;
+                la.lowbase = side == 0 ? lowbase : nullptr;
+                la.F = side == 0 ? Thigh + dp.highoff[0] : Tlow + dp.lowoff[0];
+                la.wF = side == 0 ? dp.whigh : dp.wlow;
+                la.partial = partial;
+                la.ngroups = ngroups;
+                dim3 grid((unsigned)((la.count + 127) / 128), (unsigned)ngroups, 1);
+                level_kernel<<<grid, 128, 0, s>>>(la);
+                // low side level n: the block k = n (Q empty), outputs lowbase(P);
+                // high side level n: the block k = 0 (P empty), outputs lowbase({}) + rank(Q)
+                edge_reduce_kernel<<<(unsigned)((la.count + 255) / 256), 256, 0, s>>>(
+                    partial, la.count, ngroups, lowbase, side == 0 ? dp.lowoff[n] : dp.lowoff[0], side == 0 ? 1 : 0,
+                    amp, prob);
+                note_launches(2);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
             }
             stage_end(kStageEdge, s);
             continue;

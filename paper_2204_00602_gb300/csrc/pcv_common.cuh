@@ -187,6 +187,7 @@ struct DistPlan {
     size_t ws_table, ws_base, ws_acc, ws_y, ws_tl, ws_sl, ws_th, ws_sh, ws_total;
     bool tc = false;          // products on the tensor cores (glynn_tc.cu)
     size_t ws_tc = 0;
+    size_t ws_edge = 0;       // partial sums of the single-entry blocks (tensor-core plan)
 };
 // The single-pass plan for the tensor-core products (B = 1): the FP64 tables
 // of all sign vectors, an amplitude buffer when the caller wants
