@@ -316,9 +316,13 @@ def run_ours(args):
         # BF16 tensor-core work: 3 real products x 36 digit pairs x 2 flops per
         # output and sign vector (useful outputs only)
         ms, calls = stages["dist_products"]
-        # outputs of the blocks k = 1 .. n-1 (the two single-entry blocks run in FP64)
-        h = M // 2
-        n_tc = Ntot - math.comb(M - h + N_PH - 1, N_PH) - math.comb(h + N_PH - 1, N_PH)
+        # every output goes through the tensor cores when n >= 2 and m >= 2 (the
+        # single-entry blocks k = 0 and k = n as products of level n-1 with one
+        # vector per mode; products whose mode is below the row's largest are
+        # computed and dropped, not counted); else those two blocks run in FP64
+        h = max(1, M // 2)
+        n_tc = Ntot if (N_PH >= 2 and M - h >= 1) else \
+            Ntot - math.comb(M - h + N_PH - 1, N_PH) - math.comb(h + N_PH - 1, N_PH)
         flops_per_call = n_tc * (2 ** (N_PH - 1)) * 3 * 36 * 2
         kname = "tc_product_kernel (exact-digit BF16 tcgen05 products, 36 digit pairs x 3 real products)"
         launches_per_call = 1

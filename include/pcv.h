@@ -191,9 +191,9 @@ int pcv_amplitudes_batched_ex(const pcv_batch_desc* descs, int n_circ, int64_t t
                               void* workspace, int64_t workspace_bytes, void* stream);
 
 /* Workspace bytes of pcv_distribution_ex with PCV_ALGO_FACTOR_TC (1 <= n <= 10):
- * the FP64 factor tables of all sign vectors, an amplitude buffer (used when
- * amp is NULL) and the digit tensors (48 bytes per table entry and sign
- * vector). */
+ * the FP64 factor tables of all sign vectors, the digit tensors (48 bytes
+ * per table entry and sign vector), two FP64 products per output, and the
+ * vectors and per-row data of the single-entry blocks. */
 int64_t pcv_distribution_tc_workspace(int m, int n);
 
 /* Workspace bytes pcv_distribution needs for m modes and n photons with the
@@ -251,9 +251,13 @@ int pcv_distribution_slos(const pcv_c64* U, int B, int m, const uint8_t* input_o
  * Ozaki, Ogita, Oishi and Rump, 2012); digit products are exact in BF16 and
  * each diagonal of digit pairs sums to at most 2^24, so its FP32 tensor-core
  * accumulation is exact; the diagonals are recombined in 64-bit integers and
- * scaled in FP64.  Results agree with the FP64 path to double precision.
- * The paper has no such variant (its back-ends run on CPUs).  n <= 10
- * (2^{n-1} <= 512 keeps each diagonal sum below 2^24). */
+ * rounded once to FP64 (round to nearest even) with integer operations.
+ * The blocks with every photon on one side (k = 0, k = n) are products of
+ * that side's level n-1 with one vector per mode, y_r(d) times the other
+ * side's single entry; the output of R' + r is kept for r >= max R'.  With
+ * n = 1 or m = 1 those two blocks run in FP64.  Results agree with the FP64
+ * path to double precision.  The paper has no such variant (its back-ends
+ * run on CPUs).  n <= 10 (2^{n-1} <= 512 keeps each diagonal sum below 2^24). */
 int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                         double* prob, pcv_c64* amp, int algo, int param,
                         void* workspace, int64_t workspace_bytes, void* stream);
@@ -488,7 +492,8 @@ int pcv_fp64_probe(double* out, int blocks, int threads, int iters, void* stream
  * record CUDA events on the launching stream around each stage of a call
  * (stage 0: factorised-distribution tables, 1: factorised-distribution
  * products, 2: plain Glynn kernels, 3: digit splitting of the tensor-core
- * products, 4: the FP64 blocks beside the tensor-core products).  pcv_profile_read waits for the recorded
+ * products, 4: the FP64 single-entry blocks beside the tensor-core products,
+ * n = 1 or m = 1 only).  pcv_profile_read waits for the recorded
  * events, writes the accumulated milliseconds and call counts of the first
  * `nstages` stages to ms[] and calls[] (host) and resets them.
  * pcv_launch_count returns the number of kernels the library has launched

@@ -379,10 +379,13 @@ int64_t dist_plan_tc(const Plan& p, bool need_amp_buffer, DistPlan* dp)
     (void)need_amp_buffer;                   // the products go to their own buffer
     dp->ws_acc = 0;
     dp->tc = true;
-    dp->ws_tc = (size_t)tc_workspace(dp->wlow, dp->whigh, (int)dmax, dp->total);
-    // edge-mode partial sums of the larger level n (reused by both sides)
+    dp->ws_tc = (size_t)tc_workspace(dp->wlow, dp->whigh, (int)dmax, dp->total, p.m);
+    // the single-entry blocks run on the tensor cores with the other blocks
+    // when both sides have levels 1 .. n-1 (n >= 2, m >= 2), else in FP64
+    // (edge-mode partial sums of the larger level n, reused by both sides)
     const int64_t ln = std::max(mset(dp->h, p.n), mset(p.m - dp->h, p.n));
-    dp->ws_edge = align256((size_t)ln * ((dmax + kLevelGroup - 1) / kLevelGroup) * sizeof(double2));
+    const bool tc_edges = p.n >= 2 && p.m - dp->h >= 1;
+    dp->ws_edge = !tc_edges ? align256((size_t)ln * ((dmax + kLevelGroup - 1) / kLevelGroup) * sizeof(double2)) : 0;
     dp->ws_total = dp->ws_table + dp->ws_base + dp->ws_acc + dp->ws_y + dp->ws_tl + dp->ws_sl + dp->ws_th + dp->ws_sh +
                    dp->ws_tc + dp->ws_edge;
     return (int64_t)dp->ws_total;
@@ -500,16 +503,19 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
                 ti.highoff[k] = dp.highoff[k];
             }
             ti.lowbase = lowbase;
+            ti.Y = Y;
+            ti.mc = mc;
             ti.total = dp.total;
             ti.amp = amp;
             ti.prob = prob;
             ti.ws = tcws;
             ti.error = nullptr;
             if ((e = launch_tc_products(ti, s)) != cudaSuccess) return e;
-            // the k = 0 and k = n blocks (one entry on one side) in FP64: level n
-            // of each side is never stored; the level kernel multiplies each new
-            // entry by the other side's single entry (level 0) and sums over its
-            // sign vectors, and a second pass adds the groups
+            if (n >= 2 && m - dp.h >= 1) continue;
+            // n = 1 or m = 1: the k = 0 and k = n blocks (one entry on one side) in FP64:
+            // level n of each side is never stored; the level kernel multiplies
+            // each new entry by the other side's single entry (level 0) and sums
+            // over its sign vectors, and a second pass adds the groups
             stage_begin(kStageEdge, s);
             const int ngroups = (int)((dp.kc + kLevelGroup - 1) / kLevelGroup);
             double2* partial = (double2*)((char*)tcws + dp.ws_tc);

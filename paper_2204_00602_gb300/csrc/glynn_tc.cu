@@ -28,22 +28,27 @@
 //
 // Kernels: split_exp_kernel (the row exponents, integer max of the exponent
 // fields), split_digits_kernel (digits as BF16, laid out [t][digit][entry][K]
-// for TMA), tc_product_kernel: one persistent CTA per SM walking 128 x N
-// output tiles of one k each (N = 16..64), ten warps, and tc_combine_kernel
-// (Re, Im and |a|^2):
+// for TMA), and tc_product_kernel: one persistent CTA per SM walking 128 x N
+// output tiles of one k each (N = 16..64), ten warps:
 //   warp 0  TMA producer: per 64-wide K block, the 8 digit slices of the
-//           column operand (64 rows each, one 64 KB set, double-buffered),
-//           then the 8 digit slices of the row operand one at a time
-//           (16 KB slots, six in flight), 128B swizzle;
-//   warp 1  MMA issuer: for row digit i, tcgen05.mma kind::f16 (M=128, N,
-//           K=16) with every column digit j <= 7 - i into the TMEM
-//           accumulator of diagonal i + j (8 accumulators x 64 columns =
-//           all 512 TMEM columns); commits free the slots;
+//           column operand (N rows each, packed one after the other in a
+//           64 KB set, double-buffered), then the 8 digit slices of the row
+//           operand one at a time (16 KB slots, six in flight), 128B swizzle;
+//   warp 1  MMA issuer: the accumulator of diagonal d sits at TMEM columns
+//           d N .. d N + N - 1, so the products of row digit i with column
+//           digits j = j0 .. j1 land on the contiguous columns (i + j0) N ..
+//           (i + j1 + 1) N - 1: one tcgen05.mma kind::f16 (M=128, K=16) with
+//           the packed column slices j0 .. j1 as a single operand of width
+//           (j1 - j0 + 1) N <= 256 covers them all.  A row slice is then read
+//           from shared memory once or twice per K step instead of 8 - i
+//           times; commits free the slots;
 //   warps 2-9  drain: after each of the three products, tcgen05.ld of the 8
 //           diagonals (warp w owns TMEM lanes 32 (w mod 4) .., two warps per
-//           lane group split the columns), integer combination, FP64 scaling,
-//           and a plain store of the product at canonical index
-//           lowbase(P) + rank(Q) of its [3][outputs] buffer.
+//           lane group split the columns), integer combination and FP64
+//           scaling; the accumulators are handed back to the MMA before any
+//           store.  t1 and t2 are stored at canonical index lowbase(P) +
+//           rank(Q) of a [2][outputs] buffer; after t3 the thread that
+//           stored them forms the amplitude and |a|^2 in place.
 // Every mbarrier wait is bounded; on a time-out the kernel records an error
 // code and returns after releasing its tensor memory.
 
@@ -62,8 +67,9 @@ constexpr int kDigits = 8;
 constexpr int TBM = 128, TBN = 64, TBK = 64;
 constexpr int kASlots = 6, kBSets = 2;
 constexpr uint32_t kABytes = TBM * TBK * 2;             // 16 KB: one digit slice of the row operand
-constexpr uint32_t kBSliceBytes = TBN * TBK * 2;        // 8 KB: one digit slice of the column operand
-constexpr uint32_t kBBytes = kDigits * kBSliceBytes;    // 64 KB: all digit slices of the column operand
+constexpr uint32_t kRowBytes = TBK * 2;                 // one 64-wide K row of a slice: 128 B
+constexpr uint32_t kBBytes = kDigits * TBN * kRowBytes; // 64 KB: all digit slices of the column operand
+constexpr int kBSub = 16;                               // rows per column load when N < 64
 constexpr uint32_t kSmemBytes = kBSets * kBBytes + kASlots * kABytes + 1024;
 constexpr int kThreads = 320;                            // warp 0 TMA, warp 1 MMA, warps 2-9 drain
 constexpr uint32_t kTmemCols = 512;
@@ -185,22 +191,36 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const double2* __rest
 
 // ------------------------------------------------------------ products
 
+constexpr int kMaxBlocks = PCV_MAX_PHOTONS + 2;     // k = 1 .. n-1 and the two single-entry blocks
+
 struct TcProdArgs {
-    int nk;                                   // k blocks with outputs
+    int nk;                                   // blocks with outputs
     int kblocks;                              // 64-wide K blocks
-    int64_t tile0[PCV_MAX_PHOTONS + 2];       // first tile of each block
+    int64_t tile0[kMaxBlocks + 1];            // first tile of each block
     int64_t tiles;                            // all tiles
-    int rows_low[PCV_MAX_PHOTONS + 1];        // 1: rows are low-side entries P, columns high-side Q
-    int tn[PCV_MAX_PHOTONS + 1];              // tile width (16..64)
-    int64_t rows[PCV_MAX_PHOTONS + 1], cols[PCV_MAX_PHOTONS + 1];
-    int64_t row_off[PCV_MAX_PHOTONS + 1], col_off[PCV_MAX_PHOTONS + 1];   // level offsets in their side
-    int64_t lowoff[PCV_MAX_PHOTONS + 1];      // level offset of P (for lowbase)
+    int rows_low[kMaxBlocks];                 // 1: rows are low-side entries P, columns high-side Q
+    int edge[kMaxBlocks];                     // 1: single-entry block (k = 0 or k = n), see below
+    int tn[kMaxBlocks];                       // tile width (16..64)
+    int64_t rows[kMaxBlocks], cols[kMaxBlocks];
+    int64_t row_off[kMaxBlocks], col_off[kMaxBlocks];   // entry offsets in the digit tensors
+    int64_t lowoff[kMaxBlocks];               // level offset of P (for lowbase)
     const int64_t* lowbase;
     const int* ex_low;                        // [3][wlow]
     const int* ex_high;                       // [3][whigh]
     int64_t wlow, whigh;
-    double* xt;                               // [3][total]: the three real products per output
+    // Single-entry blocks, by the side s of their rows (0 low, 1 high): the
+    // rows are the level n-1 entries R' of side s, the columns the modes r of
+    // side s with the vectors v_r of that side (digits under the v maps), and
+    // the output of (R', r), r >= max R', is entry R' + r of level n:
+    // index efirst[s][R'] + r - max R', scaled by esc[s][R'] when r = max R'.
+    const int* ex_v[2];                       // [3][modes of side s]
+    const int64_t* efirst[2];
+    const int* emax[2];
+    const double* esc[2];
+    double* xt;                               // [2][total]: the real products t1, t2 per output
     int64_t total;
+    double2* amp;                             // amplitudes, or null
+    double* prob;                             // probabilities, or null
     int* error;
 };
 
@@ -236,6 +256,13 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity)
         if (done) return true;
     }
     return false;
+}
+
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int x, int y, int z, int u)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];\n" ::"l"(map), "r"(x), "r"(y),
+                 "r"(z), "r"(u)
+                 : "memory");
 }
 
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
@@ -294,13 +321,69 @@ __device__ __forceinline__ double pow2(int e)      // 2^e for -1022 <= e <= 1023
     return __longlong_as_double((long long)(1023 + e) << 52);
 }
 
+// RN(Z 2^s) for the exact integer Z = zh 2^28 + zl (0 <= zl < 2^28, |Z| <
+// 2^75), from 64-bit integer operations only (FP64 arithmetic is scarce on
+// this part): |Z| is shifted so that its leading one is bit 63 of a word, the
+// top 53 bits are kept and rounded to nearest even, with the bits shifted out
+// of the word as a sticky bit.  Z = hi 2^28 + lo is the combination of the
+// diagonal sums, so this is the value fma(lo, 2^s, hi 2^{s+28}) rounds to.
+// Returns false if the result would not be a normal number; the caller then
+// takes the FP64 expression.
+__device__ __forceinline__ bool scale_packed(long long zh, uint32_t zl, int s, double& out)
+{
+    const bool neg = zh < 0;
+    unsigned long long mh;                                 // |Z| = mh 2^28 + ml
+    uint32_t ml;
+    if (!neg) {
+        mh = (unsigned long long)zh;
+        ml = zl;
+    } else if (zl == 0) {
+        mh = (unsigned long long)(-zh);
+        ml = 0;
+    } else {
+        mh = (unsigned long long)(-zh) - 1;
+        ml = (1u << 28) - zl;
+    }
+    if (mh == 0) {
+        if (ml == 0) {
+            out = 0.0;
+            return true;
+        }
+        mh = ml;
+        ml = 0;
+        s -= 28;
+    }
+    const int lz = __clzll((long long)mh);
+    const int sh = lz - 28;
+    unsigned long long T = mh << lz;
+    bool sticky = false;
+    if (sh >= 0) {
+        T |= (unsigned long long)ml << sh;
+    } else {
+        T |= (unsigned long long)(ml >> (-sh));
+        sticky = (ml & ((1u << (-sh)) - 1)) != 0;
+    }
+    unsigned long long mant = T >> 11;
+    const uint32_t rb = (uint32_t)(T & 0x7FF);
+    if (rb > 0x400 || (rb == 0x400 && (sticky || (mant & 1)))) ++mant;
+    int ef = s + (64 - lz + 28) + 1022;                    // |Z| has 64 - lz + 28 bits
+    if (mant >> 53) {
+        mant >>= 1;
+        ++ef;
+    }
+    if (ef < 1 || ef > 2046) return false;
+    out = __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)ef << 52) |
+                                           (mant & ((1ull << 52) - 1))));
+    return true;
+}
+
 // A tile's place: k block, first row and column, width, and which side the
 // rows come from.  Tiles are numbered k block by k block, column tiles
 // fastest, so CTAs that run at the same time share row digits.
 struct TileInfo {
     int kb, tn;
     int64_t r0, c0;
-    bool rl;
+    bool rl, edge;
     int rentry, centry;
 };
 
@@ -316,6 +399,7 @@ __device__ __forceinline__ TileInfo tile_info(const TcProdArgs& a, int64_t tile)
     ti.r0 = (lt / ctiles) * TBM;
     ti.c0 = (lt % ctiles) * ti.tn;
     ti.rl = a.rows_low[kb] != 0;
+    ti.edge = a.edge[kb] != 0;
     ti.rentry = (int)(a.row_off[kb] + ti.r0);
     ti.centry = (int)(a.col_off[kb] + ti.c0);
     return ti;
@@ -329,6 +413,8 @@ __device__ __forceinline__ TileInfo tile_info(const TcProdArgs& a, int64_t tile)
 __global__ void __launch_bounds__(kThreads, 1)
 tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_constant__ CUtensorMap low_cols,
                   const __grid_constant__ CUtensorMap high_rows, const __grid_constant__ CUtensorMap high_cols,
+                  const __grid_constant__ CUtensorMap low_cols16, const __grid_constant__ CUtensorMap high_cols16,
+                  const __grid_constant__ CUtensorMap vlow16, const __grid_constant__ CUtensorMap vhigh16,
                   const TcProdArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -362,6 +448,10 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(&low_cols) : "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(&high_rows) : "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(&high_cols) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&low_cols16) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&high_cols16) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&vlow16) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&vhigh16) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sm_addr(&tmem_base)),
@@ -381,12 +471,22 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             const int64_t it = q / (3 * nkb), rem = q % (3 * nkb);
             const int t = (int)(rem / nkb), c = (int)(rem % nkb);
             const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
-            const CUtensorMap* cmap = ti.rl ? &high_cols : &low_cols;
             const uint32_t bs = (uint32_t)(q % kBSets);
             if (q >= kBSets && !bar_wait(&bempty[bs], (uint32_t)((q / kBSets) - 1) & 1)) return false;
-            bar_expect_tx(&bfull[bs], kBBytes);
-            for (int j = 0; j < kDigits; ++j)
-                tma_load_4d(bset + bs * kBBytes + j * kBSliceBytes, cmap, &bfull[bs], c * TBK, ti.centry, j, t);
+            // slice j at rows j N .. j N + N - 1 of the set: one 64-row box, or
+            // N / 16 boxes of 16 rows
+            unsigned char* dst = bset + bs * kBBytes;
+            bar_expect_tx(&bfull[bs], (uint32_t)(kDigits * ti.tn) * kRowBytes);
+            if (ti.tn == TBN && !ti.edge) {
+                const CUtensorMap* cmap = ti.rl ? &high_cols : &low_cols;
+                for (int j = 0; j < kDigits; ++j)
+                    tma_load_4d(dst + j * TBN * kRowBytes, cmap, &bfull[bs], c * TBK, ti.centry, j, t);
+            } else {
+                const CUtensorMap* cmap = ti.edge ? (ti.rl ? &vlow16 : &vhigh16) : (ti.rl ? &high_cols16 : &low_cols16);
+                for (int j = 0; j < kDigits; ++j)
+                    for (int r = 0; r < ti.tn; r += kBSub)
+                        tma_load_4d(dst + (j * ti.tn + r) * kRowBytes, cmap, &bfull[bs], c * TBK, ti.centry + r, j, t);
+            }
             return true;
         };
         if (nchunks > 0 && !issue_b(0)) s_fail = 1;
@@ -395,6 +495,15 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             const int t = (int)(rem / nkb), c = (int)(rem % nkb);
             const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
             const CUtensorMap* rmap = ti.rl ? &low_rows : &high_rows;
+            if (q + 2 < nchunks) {
+                // row digits of chunk q + 2 into L2, so that their loads
+                // (issued a few slices ahead of the MMA) do not wait on DRAM
+                const int64_t q2 = q + 2, it2 = q2 / (3 * nkb), rem2 = q2 % (3 * nkb);
+                const TileInfo t2 = tile_info(a, blockIdx.x + it2 * gridDim.x);
+                const CUtensorMap* m2 = t2.rl ? &low_rows : &high_rows;
+                for (int i = 0; i < kDigits; ++i)
+                    tma_prefetch_4d(m2, (int)(rem2 % nkb) * TBK, t2.rentry, i, (int)(rem2 / nkb));
+            }
             for (int i = 0; i < kDigits; ++i) {
                 const uint32_t as = na % kASlots;
                 if (na >= (uint32_t)kASlots && !bar_wait(&aempty[as], ((na / kASlots) - 1) & 1)) { s_fail = 1; break; }
@@ -407,13 +516,16 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
     } else if (tid == 32) {
         // ---------------- MMA issuer
         uint32_t na = 0;
-        uint32_t idesc = 0;
+        int tn = TBN, per = 4;
         for (int64_t q = 0; q < nchunks && !s_fail; ++q) {
             const int64_t it = q / (3 * nkb), rem = q % (3 * nkb);
             const int c = (int)(rem % nkb);
             const int64_t g = q / nkb;                                   // pass number of this CTA
             if (c == 0) {
-                if (rem == 0) idesc = idesc_for(tile_info(a, blockIdx.x + it * gridDim.x).tn);
+                if (rem == 0) {
+                    tn = tile_info(a, blockIdx.x + it * gridDim.x).tn;
+                    per = min(kDigits, 256 / tn);                        // column slices per MMA
+                }
                 if (g > 0 && !bar_wait(&accempty, (uint32_t)(g - 1) & 1)) { s_fail = 2; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             }
@@ -428,11 +540,11 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint64_t da = sdesc(aslot + as * kABytes);
                 const uint32_t first = (c == 0 && i == 0) ? 0u : 1u;
-#pragma unroll
-                for (int j = 0; j < kDigits; ++j) {
-                    if (j + i >= kDigits) break;
-                    const uint32_t acc_t = tmem + (uint32_t)((i + j) * TBN);
-                    const uint64_t db = db0 + (uint64_t)(j * (kBSliceBytes >> 4));
+                for (int j0 = 0; j0 < kDigits - i; j0 += per) {
+                    const int ns = min(per, kDigits - i - j0);
+                    const uint32_t idesc = idesc_for(ns * tn);
+                    const uint32_t acc_t = tmem + (uint32_t)((i + j0) * tn);
+                    const uint64_t db = db0 + (uint64_t)((j0 * tn * kRowBytes) >> 4);
                     mma_f16(acc_t, da, db, idesc, first);
                     mma_f16(acc_t, da + 2, db + 2, idesc, 1u);
                     mma_f16(acc_t, da + 4, db + 4, idesc, 1u);
@@ -446,9 +558,10 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
         }
     } else if (warp >= 2) {
         // ---------------- drain: warp w owns TMEM lanes 32 (w mod 4) .. + 31;
-        // warps 2-5 take columns [0, 32), warps 6-9 columns [32, 64)
+        // warps 2-5 take the 16-column chunks at 0 and 32, warps 6-9 those at
+        // 16 and 48 (so a 32-wide tile keeps all eight busy)
         const int q4 = warp & 3;
-        const int cbase = warp < 6 ? 0 : 32;
+        const int cbase = warp < 6 ? 0 : 16;
         bool alive = true;
         for (int64_t it = 0; it < my_tiles && alive; ++it) {
             const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
@@ -456,28 +569,48 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             const bool rl = ti.rl;
             const int64_t row = ti.r0 + q4 * 32 + lane;
             const bool rv = row < a.rows[kb];
+            const bool edge = ti.edge;
+            const int side = rl ? 0 : 1;
             const int* ex_r = rl ? a.ex_low : a.ex_high;
-            const int* ex_c = rl ? a.ex_high : a.ex_low;
-            const int64_t wr = rl ? a.wlow : a.whigh, wc = rl ? a.whigh : a.wlow;
-            const int64_t pbase = rl && rv ? a.lowbase[a.lowoff[kb] + row] : 0;
+            const int* ex_c = edge ? a.ex_v[side] : (rl ? a.ex_high : a.ex_low);
+            const int64_t wr = rl ? a.wlow : a.whigh, wc = edge ? a.cols[kb] : (rl ? a.whigh : a.wlow);
+            int64_t pbase = 0;                     // lowbase(P), or efirst(R') - max R' for an edge row
+            int emx = 0;
+            double esc = 1.0;
+            if (rv && edge) {
+                emx = a.emax[side][row];
+                esc = a.esc[side][row];
+                pbase = a.efirst[side][row] - emx;
+            } else if (rv && rl) {
+                pbase = a.lowbase[a.lowoff[kb] + row];
+            }
             for (int t = 0; t < 3; ++t) {
                 const int64_t g = it * 3 + t;
+                const int er = rv ? ex_r[(int64_t)t * wr + a.row_off[kb] + row] : kNoExp;
                 if (!bar_wait(&accfull, (uint32_t)g & 1)) {
                     if (lane == 0) s_fail = 3;
                     alive = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const int er = rv ? ex_r[(int64_t)t * wr + a.row_off[kb] + row] : kNoExp;
-                double* xt = a.xt + (int64_t)t * a.total;
-                for (int cc = cbase; cc < tn && cc < cbase + 32; cc += 16) {
+                // read the 8 diagonals of this warp's columns (16-wide chunks
+                // cc = 0, 32 for warps 2-5 and 16, 48 for warps 6-9) and
+                // combine them on the integer pipe into Z = zh 2^28 + zl, then
+                // hand the accumulators back to the MMA; the rounding to FP64
+                // and the stores come after
+                long long zh[2][16];
+                uint32_t zl[2][16];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int cc = cbase + 32 * h;
+                    if (cc >= tn) continue;
                     long long hi[16], lo[16];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) hi[q] = lo[q] = 0;
 #pragma unroll
                     for (int d = 0; d < kDigits; ++d) {
                         uint32_t r[16];
-                        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * TBN + cc);
+                        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * tn + cc);
                         asm volatile(
                             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
                             "%14,%15}, [%16];\n"
@@ -493,23 +626,47 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                             else lo[q] = lo[q] * 128 + v;
                         }
                     }
-                    if (!rv) continue;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        const int64_t col = ti.c0 + cc + q;
-                        if (col >= a.cols[kb]) continue;
-                        const int ec = ex_c[(int64_t)t * wc + a.col_off[kb] + col];
-                        double x = 0.0;
-                        if (er != kNoExp && ec != kNoExp) {
-                            const int sc = er + ec - 14;
-                            x = fma((double)lo[q], pow2(sc - 49), (double)hi[q] * pow2(sc - 21));
-                        }
-                        const int64_t o = rl ? pbase + col : a.lowbase[a.lowoff[kb] + col] + row;
-                        xt[o] = x;
+                        zh[h][q] = hi[q] + (lo[q] >> 28);
+                        zl[h][q] = (uint32_t)(lo[q] & ((1ll << 28) - 1));
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                 bar_arrive(&accempty);
+                if (!rv) continue;
+                // t1 and t2 go to the workspace; with t3, the same thread
+                // forms a = (t1 - t2) + i (t3 - t1 - t2) and |a|^2
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int cc = cbase + 32 * h;
+                    if (cc >= tn) continue;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int64_t col = ti.c0 + cc + q;
+                        if (col >= a.cols[kb] || (edge && col < emx)) continue;
+                        const int ec = ex_c[(int64_t)t * wc + a.col_off[kb] + col];
+                        double x = 0.0;
+                        if (er != kNoExp && ec != kNoExp) {
+                            const int sc = er + ec - 14;
+                            if (!scale_packed(zh[h][q], zl[h][q], sc - 49, x))
+                                x = fma((double)zl[h][q], pow2(sc - 49), (double)zh[h][q] * pow2(sc - 21));
+                        }
+                        const int64_t o = (rl || edge) ? pbase + col : a.lowbase[a.lowoff[kb] + col] + row;
+                        if (t < 2) {
+                            a.xt[(int64_t)t * a.total + o] = x;
+                        } else {
+                            const double t1 = a.xt[o], t2 = a.xt[a.total + o];
+                            double re = t1 - t2, im = x - t1 - t2;
+                            if (edge && col == emx) {          // 1 / sqrt(multiplicity of r in R' + r)
+                                re *= esc;
+                                im *= esc;
+                            }
+                            if (a.amp) a.amp[o] = make_double2(re, im);
+                            if (a.prob) a.prob[o] = fma(re, re, im * im);
+                        }
+                    }
+                }
             }
         }
     }
@@ -520,16 +677,63 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
     if (tid == 0 && s_fail && a.error) atomicExch(a.error, s_fail);
 }
 
-// a = (t1 - t2) + i (t3 - t1 - t2), p = |a|^2
-__global__ void tc_combine_kernel(const double* __restrict__ xt, int64_t total, double2* __restrict__ amp,
-                                  double* __restrict__ prob)
+// Column vectors of the single-entry blocks, per sign vector d and mode r:
+//   low side  (block k = n, rows P'):  v_r(d) = y_r(d) beta_{}(d),
+//   high side (block k = 0, rows Q'):  v_r(d) = alpha_{}(d) y_{h+r}(d),
+// so that sum_d entry_{R'}(d) v_r(d) is the output of R' + r up to the
+// 1/sqrt(multiplicity) that level n would have applied.  [K][modes] each,
+// with re + im beside them for the third product.
+__global__ void edge_vectors_kernel(const double2* __restrict__ Y, int m, int h, int K, const double2* __restrict__ Tl0,
+                                    int64_t wlow, const double2* __restrict__ Th0, int64_t whigh,
+                                    double2* __restrict__ Vl, double* __restrict__ Sl, double2* __restrict__ Vh,
+                                    double* __restrict__ Sh)
 {
-    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= total) return;
-    const double t1 = xt[o], t2 = xt[total + o], t3 = xt[2 * total + o];
-    const double2 v = make_double2(t1 - t2, t3 - t1 - t2);
-    if (amp) amp[o] = v;
-    if (prob) prob[o] = fma(v.x, v.x, v.y * v.y);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)K * m) return;
+    const int64_t q = i / m;
+    const int r = (int)(i % m);
+    const double2 y = Y[q * m + r];
+    if (r < h) {
+        const double2 v = cmul(y, Th0[q * whigh]);
+        Vl[q * h + r] = v;
+        Sl[q * h + r] = v.x + v.y;
+    } else {
+        const double2 v = cmul(Tl0[q * wlow], y);
+        Vh[q * (m - h) + (r - h)] = v;
+        Sh[q * (m - h) + (r - h)] = v.x + v.y;
+    }
+}
+
+// Per level n-1 entry R' of one side (modes in [0, w), shifted by `shift` in
+// the output): its largest mode, the canonical output index of R' + max R',
+// and 1/sqrt(multiplicity of max R' in R' + max R').  Low side: the output
+// index among all n-photon outputs; high side: lowbase({}) + rank of Q'+max.
+__global__ void edge_info_kernel(MultisetTable mc, int m, int n, int h, int side, int64_t count,
+                                 int64_t* __restrict__ first, int* __restrict__ mx, double* __restrict__ sc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int w = side == 0 ? h : m - h;
+    int modes[PCV_MAX_PHOTONS];
+    unrank_multiset<PCV_MAX_PHOTONS>(mc, w, n - 1, i, modes);
+    const int top = modes[n - 2];
+    int mult = 1;
+    for (int p = n - 2; p >= 0 && modes[p] == top; --p) ++mult;
+    modes[n - 1] = top;
+    int64_t o = 0;
+    if (side == 0) {
+        int prev = 0;
+        for (int p = 0; p < n; ++p) {
+            for (int v = prev; v < modes[p]; ++v) o += mc(m - v, n - p - 1);
+            prev = modes[p];
+        }
+    } else {
+        for (int v = 0; v < h; ++v) o += mc(m - v, n - 1);
+        o += rank_multiset(mc, w, n, modes);
+    }
+    first[i] = o;
+    mx[i] = top;
+    sc[i] = inv_sqrt_int(mult);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
@@ -577,12 +781,45 @@ int64_t msets_tc(int w, int k) { return k == 0 ? 1 : (w <= 0 ? 0 : binom_tc(w + 
 
 int tc_pad_k(int K) { return ((K + TBK - 1) / TBK) * TBK; }
 
-int64_t tc_workspace(int64_t wlow, int64_t whigh, int K, int64_t total)
+namespace {
+
+// Workspace layout: digits, exponents and products of the two sides, then
+// the column vectors of the single-entry blocks (sized by m for both sides)
+// with their digits and exponents, and the per-row data of those blocks
+// (sized by every entry of a side).
+struct TcLayout {
+    size_t dlow, dhigh, exlow, exhigh, xt, v, sv, dv, exv, efirst_l, emax_l, esc_l, efirst_h, emax_h, esc_h, total;
+};
+
+TcLayout tc_layout(int64_t wlow, int64_t whigh, int K, int64_t total, int m)
 {
-    const int Kp = tc_pad_k(K);
-    return (int64_t)(al256((size_t)3 * kDigits * wlow * Kp * 2) + al256((size_t)3 * kDigits * whigh * Kp * 2) +
-                     al256((size_t)3 * wlow * sizeof(int)) + al256((size_t)3 * whigh * sizeof(int)) +
-                     al256((size_t)3 * total * sizeof(double)) + 256);
+    const size_t Kp = (size_t)tc_pad_k(K);
+    TcLayout L;
+    L.dlow = al256((size_t)3 * kDigits * wlow * Kp * 2);
+    L.dhigh = al256((size_t)3 * kDigits * whigh * Kp * 2);
+    L.exlow = al256((size_t)3 * wlow * sizeof(int));
+    L.exhigh = al256((size_t)3 * whigh * sizeof(int));
+    L.xt = al256((size_t)2 * total * sizeof(double));
+    L.v = al256((size_t)K * m * sizeof(double2));
+    L.sv = al256((size_t)K * m * sizeof(double));
+    L.dv = al256((size_t)3 * kDigits * m * Kp * 2);
+    L.exv = al256((size_t)3 * m * sizeof(int));
+    L.efirst_l = al256((size_t)wlow * sizeof(int64_t));
+    L.emax_l = al256((size_t)wlow * sizeof(int));
+    L.esc_l = al256((size_t)wlow * sizeof(double));
+    L.efirst_h = al256((size_t)whigh * sizeof(int64_t));
+    L.emax_h = al256((size_t)whigh * sizeof(int));
+    L.esc_h = al256((size_t)whigh * sizeof(double));
+    L.total = L.dlow + L.dhigh + L.exlow + L.exhigh + L.xt + 2 * (L.v + L.sv + L.dv + L.exv) + L.efirst_l + L.emax_l +
+              L.esc_l + L.efirst_h + L.emax_h + L.esc_h + 256;
+    return L;
+}
+
+}  // namespace
+
+int64_t tc_workspace(int64_t wlow, int64_t whigh, int K, int64_t total, int m)
+{
+    return (int64_t)tc_layout(wlow, whigh, K, total, m).total;
 }
 
 cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
@@ -596,17 +833,37 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         if (e != cudaSuccess) return e;
         g_tc_attr[dev] = true;
     }
-    const int K = in.K, Kp = tc_pad_k(K);
-    // the blocks k = 1 .. n-1 use table levels 1 .. n-1 of each side (the
-    // k = 0 and k = n blocks, one entry on one side, are left to the caller)
-    const int64_t lb = in.lowoff[1], lcnt = in.n >= 2 ? in.lowoff[in.n] - lb : 0;
-    const int64_t hb = in.highoff[1], hcnt = in.n >= 2 ? in.highoff[in.n] - hb : 0;
+    const int K = in.K, Kp = tc_pad_k(K), n = in.n, m = in.m, h = in.h;
+    // the blocks k = 1 .. n-1 use table levels 1 .. n-1 of each side; the
+    // single-entry blocks k = 0 and k = n use level n-1 of one side
+    const int64_t lb = in.lowoff[1], lcnt = n >= 2 ? in.lowoff[n] - lb : 0;
+    const int64_t hb = in.highoff[1], hcnt = n >= 2 ? in.highoff[n] - hb : 0;
+    const TcLayout L = tc_layout(in.wlow, in.whigh, K, in.total, m);
     char* w = (char*)in.ws;
-    __nv_bfloat16* dlow = (__nv_bfloat16*)w;     w += al256((size_t)3 * kDigits * in.wlow * Kp * 2);
-    __nv_bfloat16* dhigh = (__nv_bfloat16*)w;    w += al256((size_t)3 * kDigits * in.whigh * Kp * 2);
-    int* exlow = (int*)w;                        w += al256((size_t)3 * in.wlow * sizeof(int));
-    int* exhigh = (int*)w;                       w += al256((size_t)3 * in.whigh * sizeof(int));
-    double* xt = (double*)w;
+    __nv_bfloat16* dlow = (__nv_bfloat16*)w;     w += L.dlow;
+    __nv_bfloat16* dhigh = (__nv_bfloat16*)w;    w += L.dhigh;
+    int* exlow = (int*)w;                        w += L.exlow;
+    int* exhigh = (int*)w;                       w += L.exhigh;
+    double* xt = (double*)w;                     w += L.xt;
+    double2* V[2];
+    double* SV[2];
+    __nv_bfloat16* DV[2];
+    int* EXV[2];
+    for (int side = 0; side < 2; ++side) {
+        V[side] = (double2*)w;                   w += L.v;
+        SV[side] = (double*)w;                   w += L.sv;
+        DV[side] = (__nv_bfloat16*)w;            w += L.dv;
+        EXV[side] = (int*)w;                     w += L.exv;
+    }
+    int64_t* efirst[2];
+    int* emax[2];
+    double* esc[2];
+    efirst[0] = (int64_t*)w;                     w += L.efirst_l;
+    emax[0] = (int*)w;                           w += L.emax_l;
+    esc[0] = (double*)w;                         w += L.esc_l;
+    efirst[1] = (int64_t*)w;                     w += L.efirst_h;
+    emax[1] = (int*)w;                           w += L.emax_h;
+    esc[1] = (double*)w;                         w += L.esc_h;
     if (lcnt == 0 || hcnt == 0) return cudaSuccess;
     // digits of both sides (timed as their own stage when profiling is on)
     stage_begin(kStageSplit, s);
@@ -623,13 +880,34 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         note_launches(2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    // single-entry blocks: the column vectors of both sides, their digits, and
+    // the output data of every level n-1 entry
+    edge_vectors_kernel<<<(unsigned)(((int64_t)K * m + 255) / 256), 256, 0, s>>>(
+        in.Y, m, h, K, in.Tlow + in.lowoff[0], in.wlow, in.Thigh + in.highoff[0], in.whigh, V[0], SV[0], V[1], SV[1]);
+    note_launches(1);
+    for (int side = 0; side < 2; ++side) {
+        const int64_t ww = side == 0 ? h : m - h;
+        split_exp_kernel<<<(unsigned)((ww + 255) / 256), 256, 0, s>>>(V[side], SV[side], ww, ww, K, EXV[side]);
+        const int64_t warps = ((ww + 3) / 4) * (Kp / 32);
+        split_digits_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(V[side], SV[side], ww, ww, K, Kp, EXV[side],
+                                                                          DV[side]);
+        const int64_t cnt = side == 0 ? in.lowoff[n] - in.lowoff[n - 1] : in.highoff[n] - in.highoff[n - 1];
+        edge_info_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(in.mc, m, n, h, side, cnt, efirst[side],
+                                                                         emax[side], esc[side]);
+        note_launches(3);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     stage_end(kStageSplit, s);
     stage_begin(kStageGemm, s);
-    CUtensorMap lr, lc, hr, hc;
+    CUtensorMap lr, lc, hr, hc, lc16, hc16, vl16, vh16;
+    if ((e = make_digit_map(&vl16, DV[0], h, Kp, kBSub)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&vh16, DV[1], m - h, Kp, kBSub)) != cudaSuccess) return e;
     if ((e = make_digit_map(&lr, dlow, lcnt, Kp, TBM)) != cudaSuccess) return e;
     if ((e = make_digit_map(&lc, dlow, lcnt, Kp, TBN)) != cudaSuccess) return e;
     if ((e = make_digit_map(&hr, dhigh, hcnt, Kp, TBM)) != cudaSuccess) return e;
     if ((e = make_digit_map(&hc, dhigh, hcnt, Kp, TBN)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&lc16, dlow, lcnt, Kp, kBSub)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&hc16, dhigh, hcnt, Kp, kBSub)) != cudaSuccess) return e;
     TcProdArgs a;
     a.nk = 0;
     a.kblocks = Kp / TBK;
@@ -641,12 +919,32 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         const int64_t rows = rl ? M : N, cols = rl ? N : M;
         const int tn = cols >= TBN ? TBN : (int)((cols + 15) / 16) * 16;
         a.rows_low[a.nk] = rl ? 1 : 0;
+        a.edge[a.nk] = 0;
         a.tn[a.nk] = tn;
         a.rows[a.nk] = rows;
         a.cols[a.nk] = cols;
         a.row_off[a.nk] = rl ? in.lowoff[k] - lb : in.highoff[in.n - k] - hb;
         a.col_off[a.nk] = rl ? in.highoff[in.n - k] - hb : in.lowoff[k] - lb;
         a.lowoff[a.nk] = in.lowoff[k];
+        a.tile0[a.nk] = tiles;
+        tiles += ((rows + TBM - 1) / TBM) * ((cols + tn - 1) / tn);
+        a.nk++;
+    }
+    // the single-entry blocks: rows = level n-1 of a side, columns = its modes
+    // (side 0: outputs with every photon low, k = n; side 1: k = 0)
+    for (int side = 0; side < 2; ++side) {
+        const int64_t rows = side == 0 ? in.lowoff[n] - in.lowoff[n - 1] : in.highoff[n] - in.highoff[n - 1];
+        const int64_t cols = side == 0 ? h : m - h;
+        if (rows == 0 || cols == 0) continue;
+        const int tn = cols >= TBN ? TBN : (int)((cols + 15) / 16) * 16;
+        a.rows_low[a.nk] = side == 0 ? 1 : 0;
+        a.edge[a.nk] = 1;
+        a.tn[a.nk] = tn;
+        a.rows[a.nk] = rows;
+        a.cols[a.nk] = cols;
+        a.row_off[a.nk] = side == 0 ? in.lowoff[n - 1] - lb : in.highoff[n - 1] - hb;
+        a.col_off[a.nk] = 0;
+        a.lowoff[a.nk] = 0;
         a.tile0[a.nk] = tiles;
         tiles += ((rows + TBM - 1) / TBM) * ((cols + tn - 1) / tn);
         a.nk++;
@@ -664,15 +962,20 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     a.whigh = hcnt;
     a.xt = xt;
     a.total = in.total;
+    a.amp = in.amp;
+    a.prob = in.prob;
+    for (int side = 0; side < 2; ++side) {
+        a.ex_v[side] = EXV[side];
+        a.efirst[side] = efirst[side];
+        a.emax[side] = emax[side];
+        a.esc[side] = esc[side];
+    }
     a.error = in.error;
     a.tiles = tiles;
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const unsigned grid = (unsigned)(tiles < (int64_t)sms ? tiles : sms);
-    tc_product_kernel<<<grid, kThreads, kSmemBytes, s>>>(lr, lc, hr, hc, a);
-    note_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    tc_combine_kernel<<<(unsigned)((in.total + 255) / 256), 256, 0, s>>>(xt, in.total, in.amp, in.prob);
+    tc_product_kernel<<<grid, kThreads, kSmemBytes, s>>>(lr, lc, hr, hc, lc16, hc16, vl16, vh16, a);
     note_launches(1);
     stage_end(kStageGemm, s);
     return cudaGetLastError();

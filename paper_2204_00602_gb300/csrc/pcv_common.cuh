@@ -204,6 +204,8 @@ struct TcInputs {
     int K, n, m, h;
     int64_t lowoff[PCV_MAX_PHOTONS + 2], highoff[PCV_MAX_PHOTONS + 2];
     const int64_t* lowbase;
+    const double2* Y;                             // [K][m] row sums y_r(d)
+    MultisetTable mc;                             // multiset counts (a <= m, k <= n)
     int64_t total;                                // outputs
     double2* amp;                                 // amplitudes (written), or null
     double* prob;                                 // or null
@@ -211,7 +213,7 @@ struct TcInputs {
     int* error;                                   // device flag, or null
 };
 int tc_pad_k(int K);
-int64_t tc_workspace(int64_t wlow, int64_t whigh, int K, int64_t total);
+int64_t tc_workspace(int64_t wlow, int64_t whigh, int K, int64_t total, int m);
 cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s);
 cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* U,
                               double* prob, double2* amp, void* ws, cudaStream_t s);
