@@ -379,13 +379,21 @@ int64_t dist_plan_tc(const Plan& p, bool need_amp_buffer, DistPlan* dp)
     (void)need_amp_buffer;                   // the products go to their own buffer
     dp->ws_acc = 0;
     dp->tc = true;
-    dp->ws_tc = (size_t)tc_workspace(dp->wlow, dp->whigh, (int)dmax, dp->total, p.m);
-    // the single-entry blocks run on the tensor cores with the other blocks
-    // when both sides have levels 1 .. n-1 (n >= 2, m >= 2), else in FP64
-    // (edge-mode partial sums of the larger level n, reused by both sides)
-    const int64_t ln = std::max(mset(dp->h, p.n), mset(p.m - dp->h, p.n));
-    const bool tc_edges = p.n >= 2 && p.m - dp->h >= 1;
-    dp->ws_edge = !tc_edges ? align256((size_t)ln * ((dmax + kLevelGroup - 1) / kLevelGroup) * sizeof(double2)) : 0;
+    // n >= 2 with both sides non-empty: tables, digits and every output block
+    // in glynn_tc.cu (no FP64 tables in this file's layout); else (n = 1 or
+    // m = 1, no block has entries on both sides) only the single-entry blocks
+    // in FP64: the tables of levels < n and edge-mode partial sums of the
+    // larger level n, reused by both sides
+    const bool tc_all = p.n >= 2 && p.m - dp->h >= 1;
+    if (tc_all) {
+        dp->ws_tl = dp->ws_sl = dp->ws_th = dp->ws_sh = 0;
+        dp->ws_tc = (size_t)tc_workspace(p.m, p.n, (int)dmax, dp->total, dp->lowoff, dp->highoff);
+        dp->ws_edge = 0;
+    } else {
+        dp->ws_tc = 0;
+        const int64_t ln = std::max(mset(dp->h, p.n), mset(p.m - dp->h, p.n));
+        dp->ws_edge = align256((size_t)ln * ((dmax + kLevelGroup - 1) / kLevelGroup) * sizeof(double2));
+    }
     dp->ws_total = dp->ws_table + dp->ws_base + dp->ws_acc + dp->ws_y + dp->ws_tl + dp->ws_sl + dp->ws_th + dp->ws_sh +
                    dp->ws_tc + dp->ws_edge;
     return (int64_t)dp->ws_total;
@@ -458,6 +466,28 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
             note_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
+        if (dp.tc && n >= 2 && m - dp.h >= 1) {
+            // tables, digits and products on the tensor-core path
+            TcInputs ti;
+            ti.K = (int)dp.kc; ti.n = n; ti.m = m; ti.h = dp.h;
+            for (int k = 0; k <= PCV_MAX_PHOTONS + 1; ++k) {
+                ti.lowoff[k] = dp.lowoff[k];
+                ti.highoff[k] = dp.highoff[k];
+            }
+            ti.lowbase = lowbase;
+            ti.Y = Y;
+            ti.mc = mc;
+            ti.lead = lead;
+            ti.total = dp.total;
+            ti.amp = amp;
+            ti.prob = prob;
+            ti.ws = tcws;
+            ti.error = nullptr;
+            if ((e = launch_tc_tables(ti, s)) != cudaSuccess) return e;
+            stage_end(kStageTables, s);
+            if ((e = launch_tc_products(ti, s)) != cudaSuccess) return e;
+            continue;
+        }
         for (int side = 0; side < 2; ++side) {
             const int wside = side == 0 ? dp.h : m - dp.h;
             for (int k = 0; k <= n; ++k) {
@@ -493,25 +523,7 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
             }
         }
         stage_end(kStageTables, s);
-        if (dp.tc) {                          // times its own split and product stages
-            TcInputs ti;
-            ti.Tlow = Tlow; ti.Slow = Slow; ti.Thigh = Thigh; ti.Shigh = Shigh;
-            ti.wlow = dp.wlow; ti.whigh = dp.whigh;
-            ti.K = (int)dp.kc; ti.n = n; ti.m = m; ti.h = dp.h;
-            for (int k = 0; k <= PCV_MAX_PHOTONS + 1; ++k) {
-                ti.lowoff[k] = dp.lowoff[k];
-                ti.highoff[k] = dp.highoff[k];
-            }
-            ti.lowbase = lowbase;
-            ti.Y = Y;
-            ti.mc = mc;
-            ti.total = dp.total;
-            ti.amp = amp;
-            ti.prob = prob;
-            ti.ws = tcws;
-            ti.error = nullptr;
-            if ((e = launch_tc_products(ti, s)) != cudaSuccess) return e;
-            if (n >= 2 && m - dp.h >= 1) continue;
+        if (dp.tc) {
             // n = 1 or m = 1: the k = 0 and k = n blocks (one entry on one side) in FP64:
             // level n of each side is never stored; the level kernel multiplies
             // each new entry by the other side's single entry (level 0) and sums

@@ -100,11 +100,9 @@ __global__ void split_exp_kernel(const double2* __restrict__ T, const double* __
     ex[2 * w + e] = f2 ? f2 - 1021 : kNoExp;
 }
 
-// Balanced base-128 digits of round(x 2^{56-E}), most significant first,
-// packed one per byte (two's complement; digit i in byte i).  The magnitude
-// M < 2^56 is cut into 28-bit halves so that the digit loop runs on 32-bit
-// integers; the digits of -M are those of M negated.
-__device__ __forceinline__ unsigned long long digits_of(double x, int E)
+// X = round(x 2^{56-E}) as a signed integer, |X| <= 2^55 (the magnitude
+// rounded half up; 0 for x = 0 or an all-zero row).
+__device__ __forceinline__ long long fixed_of(double x, int E)
 {
     const long long bits = __double_as_longlong(x);
     const int ef = (int)((bits >> 52) & 0x7FF);
@@ -115,33 +113,166 @@ __device__ __forceinline__ unsigned long long digits_of(double x, int E)
         if (sh >= 0) M = mant << sh;
         else if (sh > -60) M = (mant + (1ull << (-sh - 1))) >> (-sh);
     }
-    const int neg = bits < 0 ? 1 : 0;
-    int v = (int)(M & ((1u << 28) - 1));
-    int w = (int)(M >> 28);
-    uint32_t lo = 0, hi = 0;                               // bytes 4..7 and 0..3
-#pragma unroll
-    for (int i = kDigits - 1; i >= 4; --i) {
-        const int d = ((v + 64) & 127) - 64;
-        lo |= (uint32_t)((neg ? -d : d) & 0xFF) << (8 * (i - 4));
-        v = (v - d) >> 7;
-    }
-    w += v;                                                // carry out of the low half
-#pragma unroll
-    for (int i = 3; i >= 1; --i) {
-        const int d = ((w + 64) & 127) - 64;
-        hi |= (uint32_t)((neg ? -d : d) & 0xFF) << (8 * i);
-        w = (w - d) >> 7;
-    }
-    hi |= (uint32_t)((neg ? -w : w) & 0xFF);
-    return ((unsigned long long)lo << 32) | hi;
+    return bits < 0 ? -(long long)M : (long long)M;
 }
 
-// BF16 bits of digit i of a packed word (|d| <= 64): exact through FP32,
-// whose low 16 bits are then zero.
-__device__ __forceinline__ uint32_t digit_bf16(unsigned long long packed, int i)
+// Balanced base-128 digits of X, most significant first, X = sum_i D_i
+// 128^{7-i}: with C = 64 (1 + 128 + ... + 128^7), the word P = X + C is
+// non-negative and below 2^57, and D_i = u_i - 64 for its 7-bit fields u_i
+// (the top field, bits 49 and up, unmasked), so |D_i| <= 64 with no carry
+// chain.  digit_bf16 returns the BF16 bits of D_i: u_i - 64 is formed
+// exactly in FP32 (1.5 2^23 + u_i, minus 1.5 2^23 + 64), whose low 16 bits
+// are then zero.
+constexpr unsigned long long kDigitOffset = 0x0081020408102040ull;   // 64 in every 7-bit field
+
+__device__ __forceinline__ unsigned long long digit_word(long long X) { return (unsigned long long)(X + (long long)kDigitOffset); }
+
+__device__ __forceinline__ uint32_t digit_bf16(unsigned long long P, int i)
 {
-    const int d = (int)(signed char)(packed >> (8 * i));
-    return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
+    const uint32_t u = i == 0 ? (uint32_t)(P >> 49) : (uint32_t)((P >> (7 * (7 - i))) & 127u);
+    return __float_as_uint(__uint_as_float(0x4B400000u | u) - 12582976.0f) >> 16;
+}
+
+// ------------------------------------------------------------ fused tables
+
+// One level k >= 1 of one side's factor table, built and split in one pass
+// (the tables are never stored in the [sign vector][entry] layout of the
+// FP64 path): entry(P)(d) = entry(P minus its last mode r)(d) y_r(d) /
+// sqrt(multiplicity of r in P), level 0 being sigma(d) 2^{-(n-1)} norm_t on
+// the low side and 1 on the high side.  One warp per entry P, lane l holding
+// sign vectors PER l .. PER l + PER - 1 (PER = Kpad / 32; those >= K are
+// zero): the three row exponents (re, im, re + im) are warp maxima, so the
+// digits [3][8][entry][Kpad] are written in the same pass.  Levels below
+// n - 1 also keep the complex entries, entry-major [entry][K], as the parents
+// of the next level.  Low side: writes lowbase of each entry.
+struct TcLevelArgs {
+    MultisetTable mc;
+    int m, n, h, side, k, K, Kpad;
+    int64_t count;                       // entries of level k
+    double lead;                         // 2^{-(n-1)} norm_t
+    const double2* Ys;                   // [n-1][m][K]: y_r(d) / sqrt(mult), mult = 1 .. n-1
+    const double2* parent;               // level k-1, [entry][K] (k >= 2)
+    double2* out;                        // level k, [entry][K], or null
+    int64_t dig_off, wdig;               // entry offset of level k in the digit tensor; its entries
+    __nv_bfloat16* digits;               // [3][8][wdig][Kpad]
+    int* ex;                             // [3][wdig]
+    int64_t* lowbase;                    // low side: at lowoff_k + entry, else null
+    int64_t lowoff_k;
+};
+
+// Ys[mult-1][r][d] = y_r(d) / sqrt(mult) (mult = 1: y_r(d) itself), the
+// factor a level entry whose last mode r occurs mult times takes from its
+// parent; sign vectors contiguous per (mult, r).
+__global__ void scaled_rowsums_kernel(const double2* __restrict__ Y, int m, int K, int nmult, double2* __restrict__ Ys)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nmult * m * K) return;
+    const int mu = (int)(i / ((int64_t)m * K));
+    const int64_t rem = i % ((int64_t)m * K);
+    const int r = (int)(rem / K), q = (int)(rem % K);
+    double2 y = Y[(int64_t)q * m + r];
+    if (mu > 0) {
+        const double sc = inv_sqrt_int(mu + 1);
+        y.x *= sc;
+        y.y *= sc;
+    }
+    Ys[i] = y;
+}
+
+template <int PER>
+__device__ __forceinline__ void store_digit_run(__nv_bfloat16* dst, const unsigned long long* pk, int i)
+{
+    uint32_t wv[PER / 2];
+#pragma unroll
+    for (int u = 0; u < PER / 2; ++u) wv[u] = digit_bf16(pk[2 * u], i) | (digit_bf16(pk[2 * u + 1], i) << 16);
+    if constexpr (PER == 8) {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    } else if constexpr (PER == 4) {
+        *reinterpret_cast<uint2*>(dst) = make_uint2(wv[0], wv[1]);
+    } else {
+        *reinterpret_cast<uint32_t*>(dst) = wv[0];
+    }
+}
+
+template <int PER>
+__global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
+{
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= a.count) return;                              // whole warps
+    const int w = a.side == 0 ? a.h : a.m - a.h;
+    const int shift = a.side == 0 ? 0 : a.h;
+    int modes[PCV_MAX_PHOTONS];
+    unrank_multiset<PCV_MAX_PHOTONS>(a.mc, w, a.k, e, modes);
+    const int last = modes[a.k - 1];
+    int mult = 1;
+    for (int p = a.k - 2; p >= 0 && modes[p] == last; --p) ++mult;
+    const int r = last + shift;
+    const double2* yr = a.Ys + ((int64_t)(mult - 1) * a.m + r) * a.K;
+    const int64_t parent = a.k > 1 ? rank_multiset(a.mc, w, a.k - 1, modes) : 0;
+    if (a.lowbase && lane == 0) {
+        // canonical index of the first output with prefix P and the rest in [h, m)
+        int64_t base = 0;
+        int prev = 0;
+        for (int p = 0; p < a.k; ++p) {
+            for (int v = prev; v < modes[p]; ++v) base += a.mc(a.m - v, a.n - p - 1);
+            prev = modes[p];
+        }
+        if (a.k < a.n)
+            for (int v = prev; v < a.h; ++v) base += a.mc(a.m - v, a.n - a.k - 1);
+        a.lowbase[a.lowoff_k + e] = base;
+    }
+    double2 v[PER];
+    double sv[PER];
+    int f0 = 0, f1 = 0, f2 = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int q = lane * PER + j;
+        v[j] = make_double2(0.0, 0.0);
+        if (q < a.K) {
+            const double2 y = yr[q];
+            double2 pv;
+            if (a.k == 1) {
+                double lv = 1.0;
+                if (a.side == 0) {
+                    const uint64_t d = (uint64_t)q;
+                    lv = (__popcll(d ^ (d >> 1)) & 1) ? -a.lead : a.lead;
+                }
+                pv = make_double2(lv, 0.0);
+            } else {
+                pv = a.parent[parent * a.K + q];
+            }
+            v[j] = cmul(pv, y);
+            if (a.out) a.out[e * a.K + q] = v[j];
+        }
+        sv[j] = v[j].x + v[j].y;
+        f0 = max(f0, exp_field(v[j].x));
+        f1 = max(f1, exp_field(v[j].y));
+        f2 = max(f2, exp_field(sv[j]));
+    }
+    f0 = __reduce_max_sync(0xffffffffu, f0);
+    f1 = __reduce_max_sync(0xffffffffu, f1);
+    f2 = __reduce_max_sync(0xffffffffu, f2);
+    const int64_t ent = a.dig_off + e;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const int f = t == 0 ? f0 : (t == 1 ? f1 : f2);
+        const int E = f ? f - 1021 : kNoExp;
+        if (lane == 0) a.ex[(int64_t)t * a.wdig + ent] = E;
+        // runs of at most 8 sign vectors (16-byte stores), to bound registers
+        constexpr int RUN = PER < 8 ? PER : 8;
+#pragma unroll
+        for (int j0 = 0; j0 < PER; j0 += RUN) {
+            unsigned long long pk[RUN];
+#pragma unroll
+            for (int j = 0; j < RUN; ++j)
+                pk[j] = digit_word(fixed_of(t == 0 ? v[j0 + j].x : (t == 1 ? v[j0 + j].y : sv[j0 + j]), E));
+#pragma unroll
+            for (int i = 0; i < kDigits; ++i)
+                store_digit_run<RUN>(a.digits + (((int64_t)t * kDigits + i) * a.wdig + ent) * a.Kpad + lane * PER + j0,
+                                     pk, i);
+        }
+    }
 }
 
 // One warp: 4 consecutive entries x 32 consecutive sign vectors (lane ->
@@ -178,7 +309,7 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const double2* __rest
         const int E = ex[(int64_t)t * w + e];
         unsigned long long pk[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) pk[u] = digits_of(t == 0 ? vr[u] : (t == 1 ? vi[u] : vs[u]), E);
+        for (int u = 0; u < 4; ++u) pk[u] = digit_word(fixed_of(t == 0 ? vr[u] : (t == 1 ? vi[u] : vs[u]), E));
 #pragma unroll
         for (int i = 0; i < kDigits; ++i) {
             uint2 st;
@@ -683,8 +814,7 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
 // so that sum_d entry_{R'}(d) v_r(d) is the output of R' + r up to the
 // 1/sqrt(multiplicity) that level n would have applied.  [K][modes] each,
 // with re + im beside them for the third product.
-__global__ void edge_vectors_kernel(const double2* __restrict__ Y, int m, int h, int K, const double2* __restrict__ Tl0,
-                                    int64_t wlow, const double2* __restrict__ Th0, int64_t whigh,
+__global__ void edge_vectors_kernel(const double2* __restrict__ Y, int m, int h, int K, double lead,
                                     double2* __restrict__ Vl, double* __restrict__ Sl, double2* __restrict__ Vh,
                                     double* __restrict__ Sh)
 {
@@ -693,12 +823,14 @@ __global__ void edge_vectors_kernel(const double2* __restrict__ Y, int m, int h,
     const int64_t q = i / m;
     const int r = (int)(i % m);
     const double2 y = Y[q * m + r];
-    if (r < h) {
-        const double2 v = cmul(y, Th0[q * whigh]);
+    if (r < h) {                                           // beta_{}(d) = 1
+        const double2 v = cmul(y, make_double2(1.0, 0.0));
         Vl[q * h + r] = v;
         Sl[q * h + r] = v.x + v.y;
-    } else {
-        const double2 v = cmul(Tl0[q * wlow], y);
+    } else {                                               // alpha_{}(d) = sigma(d) 2^{-(n-1)} norm_t
+        const uint64_t d = (uint64_t)q;
+        const double2 t0 = make_double2((__popcll(d ^ (d >> 1)) & 1) ? -lead : lead, 0.0);
+        const double2 v = cmul(t0, y);
         Vh[q * (m - h) + (r - h)] = v;
         Sh[q * (m - h) + (r - h)] = v.x + v.y;
     }
@@ -783,43 +915,144 @@ int tc_pad_k(int K) { return ((K + TBK - 1) / TBK) * TBK; }
 
 namespace {
 
-// Workspace layout: digits, exponents and products of the two sides, then
-// the column vectors of the single-entry blocks (sized by m for both sides)
-// with their digits and exponents, and the per-row data of those blocks
-// (sized by every entry of a side).
+// Workspace layout: digits and exponents of table levels 1 .. n-1 of the two
+// sides, the entry-major complex entries of levels 1 .. n-2 (parents), two
+// products per output, the column vectors of the single-entry blocks (sized
+// by m for both sides) with their digits and exponents, and the per-row data
+// of those blocks (sized by levels 1 .. n-1).
 struct TcLayout {
-    size_t dlow, dhigh, exlow, exhigh, xt, v, sv, dv, exv, efirst_l, emax_l, esc_l, efirst_h, emax_h, esc_h, total;
+    int64_t lcnt, hcnt, plow, phigh;
+    size_t dlow, dhigh, exlow, exhigh, tpl, tph, ys, xt, v, sv, dv, exv, efirst_l, emax_l, esc_l, efirst_h, emax_h, esc_h,
+        total;
 };
 
-TcLayout tc_layout(int64_t wlow, int64_t whigh, int K, int64_t total, int m)
+TcLayout tc_layout(int m, int n, int K, int64_t total, const int64_t* lowoff, const int64_t* highoff)
 {
     const size_t Kp = (size_t)tc_pad_k(K);
     TcLayout L;
-    L.dlow = al256((size_t)3 * kDigits * wlow * Kp * 2);
-    L.dhigh = al256((size_t)3 * kDigits * whigh * Kp * 2);
-    L.exlow = al256((size_t)3 * wlow * sizeof(int));
-    L.exhigh = al256((size_t)3 * whigh * sizeof(int));
+    L.lcnt = n >= 2 ? lowoff[n] - lowoff[1] : 0;
+    L.hcnt = n >= 2 ? highoff[n] - highoff[1] : 0;
+    L.plow = n >= 3 ? lowoff[n - 1] - lowoff[1] : 0;
+    L.phigh = n >= 3 ? highoff[n - 1] - highoff[1] : 0;
+    L.dlow = al256((size_t)3 * kDigits * L.lcnt * Kp * 2);
+    L.dhigh = al256((size_t)3 * kDigits * L.hcnt * Kp * 2);
+    L.exlow = al256((size_t)3 * L.lcnt * sizeof(int));
+    L.exhigh = al256((size_t)3 * L.hcnt * sizeof(int));
+    L.tpl = al256((size_t)L.plow * K * sizeof(double2));
+    L.tph = al256((size_t)L.phigh * K * sizeof(double2));
+    L.ys = al256((size_t)(n > 1 ? n - 1 : 1) * m * K * sizeof(double2));
     L.xt = al256((size_t)2 * total * sizeof(double));
     L.v = al256((size_t)K * m * sizeof(double2));
     L.sv = al256((size_t)K * m * sizeof(double));
     L.dv = al256((size_t)3 * kDigits * m * Kp * 2);
     L.exv = al256((size_t)3 * m * sizeof(int));
-    L.efirst_l = al256((size_t)wlow * sizeof(int64_t));
-    L.emax_l = al256((size_t)wlow * sizeof(int));
-    L.esc_l = al256((size_t)wlow * sizeof(double));
-    L.efirst_h = al256((size_t)whigh * sizeof(int64_t));
-    L.emax_h = al256((size_t)whigh * sizeof(int));
-    L.esc_h = al256((size_t)whigh * sizeof(double));
-    L.total = L.dlow + L.dhigh + L.exlow + L.exhigh + L.xt + 2 * (L.v + L.sv + L.dv + L.exv) + L.efirst_l + L.emax_l +
-              L.esc_l + L.efirst_h + L.emax_h + L.esc_h + 256;
+    L.efirst_l = al256((size_t)L.lcnt * sizeof(int64_t));
+    L.emax_l = al256((size_t)L.lcnt * sizeof(int));
+    L.esc_l = al256((size_t)L.lcnt * sizeof(double));
+    L.efirst_h = al256((size_t)L.hcnt * sizeof(int64_t));
+    L.emax_h = al256((size_t)L.hcnt * sizeof(int));
+    L.esc_h = al256((size_t)L.hcnt * sizeof(double));
+    L.total = L.dlow + L.dhigh + L.exlow + L.exhigh + L.tpl + L.tph + L.ys + L.xt + 2 * (L.v + L.sv + L.dv + L.exv) +
+              L.efirst_l + L.emax_l + L.esc_l + L.efirst_h + L.emax_h + L.esc_h + 256;
     return L;
+}
+
+struct TcBuffers {
+    __nv_bfloat16* dig[2];
+    int* ex[2];
+    double2* par[2];
+    double2* ys;
+    double* xt;
+    double2* V[2];
+    double* SV[2];
+    __nv_bfloat16* DV[2];
+    int* EXV[2];
+    int64_t* efirst[2];
+    int* emax[2];
+    double* esc[2];
+};
+
+TcBuffers tc_buffers(const TcLayout& L, void* ws)
+{
+    TcBuffers B;
+    char* w = (char*)ws;
+    B.dig[0] = (__nv_bfloat16*)w;    w += L.dlow;
+    B.dig[1] = (__nv_bfloat16*)w;    w += L.dhigh;
+    B.ex[0] = (int*)w;               w += L.exlow;
+    B.ex[1] = (int*)w;               w += L.exhigh;
+    B.par[0] = (double2*)w;          w += L.tpl;
+    B.par[1] = (double2*)w;          w += L.tph;
+    B.ys = (double2*)w;              w += L.ys;
+    B.xt = (double*)w;               w += L.xt;
+    for (int side = 0; side < 2; ++side) {
+        B.V[side] = (double2*)w;     w += L.v;
+        B.SV[side] = (double*)w;     w += L.sv;
+        B.DV[side] = (__nv_bfloat16*)w;  w += L.dv;
+        B.EXV[side] = (int*)w;       w += L.exv;
+    }
+    B.efirst[0] = (int64_t*)w;       w += L.efirst_l;
+    B.emax[0] = (int*)w;             w += L.emax_l;
+    B.esc[0] = (double*)w;           w += L.esc_l;
+    B.efirst[1] = (int64_t*)w;       w += L.efirst_h;
+    B.emax[1] = (int*)w;             w += L.emax_h;
+    B.esc[1] = (double*)w;           w += L.esc_h;
+    return B;
+}
+
+template <int PER>
+cudaError_t launch_level(const TcLevelArgs& la, cudaStream_t s)
+{
+    const int64_t threads = la.count * 32;
+    tc_level_kernel<PER><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(la);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-int64_t tc_workspace(int64_t wlow, int64_t whigh, int K, int64_t total, int m)
+int64_t tc_workspace(int m, int n, int K, int64_t total, const int64_t* lowoff, const int64_t* highoff)
 {
-    return (int64_t)tc_layout(wlow, whigh, K, total, m).total;
+    return (int64_t)tc_layout(m, n, K, total, lowoff, highoff).total;
+}
+
+cudaError_t launch_tc_tables(const TcInputs& in, cudaStream_t s)
+{
+    const int K = in.K, Kp = tc_pad_k(K), n = in.n;
+    if (n < 2 || Kp > 512) return cudaErrorInvalidValue;
+    const TcLayout L = tc_layout(in.m, n, K, in.total, in.lowoff, in.highoff);
+    const TcBuffers B = tc_buffers(L, in.ws);
+    const int64_t nys = (int64_t)(n - 1) * in.m * K;
+    scaled_rowsums_kernel<<<(unsigned)((nys + 255) / 256), 256, 0, s>>>(in.Y, in.m, K, n - 1, B.ys);
+    note_launches(1);
+    for (int side = 0; side < 2; ++side) {
+        const int64_t* off = side == 0 ? in.lowoff : in.highoff;
+        for (int k = 1; k < n; ++k) {
+            TcLevelArgs la;
+            la.mc = in.mc;
+            la.m = in.m; la.n = n; la.h = in.h; la.side = side; la.k = k; la.K = K; la.Kpad = Kp;
+            la.count = off[k + 1] - off[k];
+            if (la.count == 0) continue;
+            la.lead = in.lead;
+            la.Ys = B.ys;
+            la.parent = k >= 2 ? B.par[side] + (off[k - 1] - off[1]) * K : nullptr;
+            la.out = k <= n - 2 ? B.par[side] + (off[k] - off[1]) * K : nullptr;
+            la.dig_off = off[k] - off[1];
+            la.wdig = side == 0 ? L.lcnt : L.hcnt;
+            la.digits = B.dig[side];
+            la.ex = B.ex[side];
+            la.lowbase = side == 0 ? in.lowbase : nullptr;
+            la.lowoff_k = off[k];
+            cudaError_t e;
+            switch (Kp / 32) {
+                case 2: e = launch_level<2>(la, s); break;
+                case 4: e = launch_level<4>(la, s); break;
+                case 8: e = launch_level<8>(la, s); break;
+                default: e = launch_level<16>(la, s); break;
+            }
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
@@ -834,56 +1067,30 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         g_tc_attr[dev] = true;
     }
     const int K = in.K, Kp = tc_pad_k(K), n = in.n, m = in.m, h = in.h;
+    if (n < 2 || m - h < 1) return cudaErrorInvalidValue;
     // the blocks k = 1 .. n-1 use table levels 1 .. n-1 of each side; the
     // single-entry blocks k = 0 and k = n use level n-1 of one side
-    const int64_t lb = in.lowoff[1], lcnt = n >= 2 ? in.lowoff[n] - lb : 0;
-    const int64_t hb = in.highoff[1], hcnt = n >= 2 ? in.highoff[n] - hb : 0;
-    const TcLayout L = tc_layout(in.wlow, in.whigh, K, in.total, m);
-    char* w = (char*)in.ws;
-    __nv_bfloat16* dlow = (__nv_bfloat16*)w;     w += L.dlow;
-    __nv_bfloat16* dhigh = (__nv_bfloat16*)w;    w += L.dhigh;
-    int* exlow = (int*)w;                        w += L.exlow;
-    int* exhigh = (int*)w;                       w += L.exhigh;
-    double* xt = (double*)w;                     w += L.xt;
-    double2* V[2];
-    double* SV[2];
-    __nv_bfloat16* DV[2];
-    int* EXV[2];
-    for (int side = 0; side < 2; ++side) {
-        V[side] = (double2*)w;                   w += L.v;
-        SV[side] = (double*)w;                   w += L.sv;
-        DV[side] = (__nv_bfloat16*)w;            w += L.dv;
-        EXV[side] = (int*)w;                     w += L.exv;
-    }
-    int64_t* efirst[2];
-    int* emax[2];
-    double* esc[2];
-    efirst[0] = (int64_t*)w;                     w += L.efirst_l;
-    emax[0] = (int*)w;                           w += L.emax_l;
-    esc[0] = (double*)w;                         w += L.esc_l;
-    efirst[1] = (int64_t*)w;                     w += L.efirst_h;
-    emax[1] = (int*)w;                           w += L.emax_h;
-    esc[1] = (double*)w;                         w += L.esc_h;
-    if (lcnt == 0 || hcnt == 0) return cudaSuccess;
-    // digits of both sides (timed as their own stage when profiling is on)
-    stage_begin(kStageSplit, s);
-    for (int side = 0; side < 2; ++side) {
-        const double2* T = side == 0 ? in.Tlow : in.Thigh;
-        const double* S = side == 0 ? in.Slow : in.Shigh;
-        const int64_t stride = side == 0 ? in.wlow : in.whigh;
-        const int64_t eb = side == 0 ? lb : hb, ww = side == 0 ? lcnt : hcnt;
-        int* ex = side == 0 ? exlow : exhigh;
-        __nv_bfloat16* dg = side == 0 ? dlow : dhigh;
-        split_exp_kernel<<<(unsigned)((ww + 255) / 256), 256, 0, s>>>(T + eb, S + eb, stride, ww, K, ex);
-        const int64_t warps = ((ww + 3) / 4) * (Kp / 32);
-        split_digits_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(T + eb, S + eb, stride, ww, K, Kp, ex, dg);
-        note_launches(2);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    const int64_t lb = in.lowoff[1], hb = in.highoff[1];
+    const TcLayout L = tc_layout(m, n, K, in.total, in.lowoff, in.highoff);
+    const TcBuffers B = tc_buffers(L, in.ws);
+    const int64_t lcnt = L.lcnt, hcnt = L.hcnt;
+    __nv_bfloat16* dlow = B.dig[0];
+    __nv_bfloat16* dhigh = B.dig[1];
+    int* exlow = B.ex[0];
+    int* exhigh = B.ex[1];
+    double* xt = B.xt;
+    double2* const* V = B.V;
+    double* const* SV = B.SV;
+    __nv_bfloat16* const* DV = B.DV;
+    int* const* EXV = B.EXV;
+    int64_t* const* efirst = B.efirst;
+    int* const* emax = B.emax;
+    double* const* esc = B.esc;
     // single-entry blocks: the column vectors of both sides, their digits, and
-    // the output data of every level n-1 entry
-    edge_vectors_kernel<<<(unsigned)(((int64_t)K * m + 255) / 256), 256, 0, s>>>(
-        in.Y, m, h, K, in.Tlow + in.lowoff[0], in.wlow, in.Thigh + in.highoff[0], in.whigh, V[0], SV[0], V[1], SV[1]);
+    // the output data of every level n-1 entry (timed as the split stage)
+    stage_begin(kStageSplit, s);
+    edge_vectors_kernel<<<(unsigned)(((int64_t)K * m + 255) / 256), 256, 0, s>>>(in.Y, m, h, K, in.lead, V[0], SV[0],
+                                                                                    V[1], SV[1]);
     note_launches(1);
     for (int side = 0; side < 2; ++side) {
         const int64_t ww = side == 0 ? h : m - h;

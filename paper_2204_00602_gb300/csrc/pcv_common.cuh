@@ -195,17 +195,19 @@ struct DistPlan {
 int64_t dist_plan_tc(const Plan& p, bool need_amp_buffer, DistPlan* dp);
 int64_t dist_plan(const Plan& p, int B, int64_t ws_bytes, bool need_acc, DistPlan* dp);
 
-// Product stage on the tensor cores with exact digit splitting (glynn_tc.cu):
-// one batch entry, all K = 2^{n-1} sign vectors in one pass.
+// Tables and products on the tensor cores with exact digit splitting
+// (glynn_tc.cu): one batch entry, all K = 2^{n-1} <= 512 sign vectors in one
+// pass, n >= 2 and both sides non-empty.  launch_tc_tables builds table
+// levels 1 .. n-1 of both sides from the row sums and writes their digits
+// (and lowbase of the low side); launch_tc_products runs every output block,
+// k = 0 .. n, and writes amp / prob.
 struct TcInputs {
-    const double2* Tlow; const double* Slow;      // [K][wlow]
-    const double2* Thigh; const double* Shigh;    // [K][whigh]
-    int64_t wlow, whigh;
     int K, n, m, h;
     int64_t lowoff[PCV_MAX_PHOTONS + 2], highoff[PCV_MAX_PHOTONS + 2];
-    const int64_t* lowbase;
+    int64_t* lowbase;                             // low side, written by launch_tc_tables
     const double2* Y;                             // [K][m] row sums y_r(d)
     MultisetTable mc;                             // multiset counts (a <= m, k <= n)
+    double lead;                                  // 2^{-(n-1)} norm_t
     int64_t total;                                // outputs
     double2* amp;                                 // amplitudes (written), or null
     double* prob;                                 // or null
@@ -213,7 +215,8 @@ struct TcInputs {
     int* error;                                   // device flag, or null
 };
 int tc_pad_k(int K);
-int64_t tc_workspace(int64_t wlow, int64_t whigh, int K, int64_t total, int m);
+int64_t tc_workspace(int m, int n, int K, int64_t total, const int64_t* lowoff, const int64_t* highoff);
+cudaError_t launch_tc_tables(const TcInputs& in, cudaStream_t s);
 cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s);
 cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* U,
                               double* prob, double2* amp, void* ws, cudaStream_t s);
