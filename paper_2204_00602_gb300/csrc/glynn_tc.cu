@@ -33,7 +33,9 @@
 //   warp 0  TMA producer: per 64-wide K block, the 8 digit slices of the
 //           column operand (N rows each, packed one after the other in a
 //           64 KB set, double-buffered), then the 8 digit slices of the row
-//           operand one at a time (16 KB slots, six in flight), 128B swizzle;
+//           operand one at a time (16 KB slots, six in flight, digits in the
+//           order 0 7 1 6 2 5 3 4), 128B swizzle; the row digits two K blocks
+//           ahead are prefetched into L2;
 //   warp 1  MMA issuer: the accumulator of diagonal d sits at TMEM columns
 //           d N .. d N + N - 1, so the products of row digit i with column
 //           digits j = j0 .. j1 land on the contiguous columns (i + j0) N ..
@@ -139,10 +141,11 @@ __device__ __forceinline__ uint32_t digit_bf16(unsigned long long P, int i)
 // (the tables are never stored in the [sign vector][entry] layout of the
 // FP64 path): entry(P)(d) = entry(P minus its last mode r)(d) y_r(d) /
 // sqrt(multiplicity of r in P), level 0 being sigma(d) 2^{-(n-1)} norm_t on
-// the low side and 1 on the high side.  One warp per entry P, lane l holding
-// sign vectors PER l .. PER l + PER - 1 (PER = Kpad / 32; those >= K are
-// zero): the three row exponents (re, im, re + im) are warp maxima, so the
-// digits [3][8][entry][Kpad] are written in the same pass.  Levels below
+// the low side and 1 on the high side.  One warp per entry P (two when
+// Kpad = 512), each lane holding Kpad / 32 (8) sign vectors (those >= K are
+// zero): the three row exponents (re, im, re + im) are maxima over the
+// entry's warps, so the digits [3][8][entry][Kpad] are written in the same
+// pass.  Levels below
 // n - 1 also keep the complex entries, entry-major [entry][K], as the parents
 // of the next level.  Low side: writes lowbase of each entry.
 struct TcLevelArgs {
@@ -194,42 +197,54 @@ __device__ __forceinline__ void store_digit_run(__nv_bfloat16* dst, const unsign
     }
 }
 
-template <int PER>
+template <int PER, int WPE>
 __global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
 {
-    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (e >= a.count) return;                              // whole warps
+    // WPE warps per entry (4 / WPE entries per block), warp `part` holding
+    // sign vectors part 32 PER .. (part + 1) 32 PER - 1
+    __shared__ int s_f[4][3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int part = warp % WPE;
+    const int64_t e = (int64_t)blockIdx.x * (4 / WPE) + warp / WPE;
+    const bool valid = e < a.count;
     const int w = a.side == 0 ? a.h : a.m - a.h;
     const int shift = a.side == 0 ? 0 : a.h;
     int modes[PCV_MAX_PHOTONS];
-    unrank_multiset<PCV_MAX_PHOTONS>(a.mc, w, a.k, e, modes);
-    const int last = modes[a.k - 1];
-    int mult = 1;
-    for (int p = a.k - 2; p >= 0 && modes[p] == last; --p) ++mult;
-    const int r = last + shift;
-    const double2* yr = a.Ys + ((int64_t)(mult - 1) * a.m + r) * a.K;
-    const int64_t parent = a.k > 1 ? rank_multiset(a.mc, w, a.k - 1, modes) : 0;
-    if (a.lowbase && lane == 0) {
-        // canonical index of the first output with prefix P and the rest in [h, m)
-        int64_t base = 0;
-        int prev = 0;
-        for (int p = 0; p < a.k; ++p) {
-            for (int v = prev; v < modes[p]; ++v) base += a.mc(a.m - v, a.n - p - 1);
-            prev = modes[p];
+    int mult = 1, r = 0;
+    int64_t parent = 0;
+    if (valid) {
+        unrank_multiset<PCV_MAX_PHOTONS>(a.mc, w, a.k, e, modes);
+        const int last = modes[a.k - 1];
+        for (int p = a.k - 2; p >= 0 && modes[p] == last; --p) ++mult;
+        r = last + shift;
+        parent = a.k > 1 ? rank_multiset(a.mc, w, a.k - 1, modes) : 0;
+        if (a.lowbase && lane == 0 && part == 0) {
+            // canonical index of the first output with prefix P and the rest in [h, m)
+            int64_t base = 0;
+            int prev = 0;
+            for (int p = 0; p < a.k; ++p) {
+                for (int v = prev; v < modes[p]; ++v) base += a.mc(a.m - v, a.n - p - 1);
+                prev = modes[p];
+            }
+            if (a.k < a.n)
+                for (int v = prev; v < a.h; ++v) base += a.mc(a.m - v, a.n - a.k - 1);
+            a.lowbase[a.lowoff_k + e] = base;
         }
-        if (a.k < a.n)
-            for (int v = prev; v < a.h; ++v) base += a.mc(a.m - v, a.n - a.k - 1);
-        a.lowbase[a.lowoff_k + e] = base;
     }
+    const double2* yr = a.Ys + ((int64_t)(mult - 1) * a.m + r) * a.K;
+    // lane l holds runs of RUN consecutive sign vectors, run j0 / RUN at
+    // j0 32 + l RUN of this warp's range, so that each 16-byte digit store of
+    // a warp covers 512 contiguous bytes
+    constexpr int RUN = PER < 8 ? PER : 8;
+    const int qbase = part * 32 * PER;
     double2 v[PER];
     double sv[PER];
     int f0 = 0, f1 = 0, f2 = 0;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-        const int q = lane * PER + j;
+        const int q = qbase + (j / RUN) * 32 * RUN + lane * RUN + (j % RUN);
         v[j] = make_double2(0.0, 0.0);
-        if (q < a.K) {
+        if (valid && q < a.K) {
             const double2 y = yr[q];
             double2 pv;
             if (a.k == 1) {
@@ -253,14 +268,28 @@ __global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
     f0 = __reduce_max_sync(0xffffffffu, f0);
     f1 = __reduce_max_sync(0xffffffffu, f1);
     f2 = __reduce_max_sync(0xffffffffu, f2);
+    if constexpr (WPE > 1) {
+        if (lane == 0) {
+            s_f[warp][0] = f0;
+            s_f[warp][1] = f1;
+            s_f[warp][2] = f2;
+        }
+        __syncthreads();
+        const int w0 = warp - part;
+#pragma unroll
+        for (int u = 0; u < WPE; ++u) {
+            f0 = max(f0, s_f[w0 + u][0]);
+            f1 = max(f1, s_f[w0 + u][1]);
+            f2 = max(f2, s_f[w0 + u][2]);
+        }
+    }
+    if (!valid) return;
     const int64_t ent = a.dig_off + e;
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
         const int f = t == 0 ? f0 : (t == 1 ? f1 : f2);
         const int E = f ? f - 1021 : kNoExp;
-        if (lane == 0) a.ex[(int64_t)t * a.wdig + ent] = E;
-        // runs of at most 8 sign vectors (16-byte stores), to bound registers
-        constexpr int RUN = PER < 8 ? PER : 8;
+        if (lane == 0 && part == 0) a.ex[(int64_t)t * a.wdig + ent] = E;
 #pragma unroll
         for (int j0 = 0; j0 < PER; j0 += RUN) {
             unsigned long long pk[RUN];
@@ -269,7 +298,8 @@ __global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
                 pk[j] = digit_word(fixed_of(t == 0 ? v[j0 + j].x : (t == 1 ? v[j0 + j].y : sv[j0 + j]), E));
 #pragma unroll
             for (int i = 0; i < kDigits; ++i)
-                store_digit_run<RUN>(a.digits + (((int64_t)t * kDigits + i) * a.wdig + ent) * a.Kpad + lane * PER + j0,
+                store_digit_run<RUN>(a.digits + (((int64_t)t * kDigits + i) * a.wdig + ent) * a.Kpad + qbase + j0 * 32 +
+                                         lane * RUN,
                                      pk, i);
         }
     }
@@ -508,6 +538,13 @@ __device__ __forceinline__ bool scale_packed(long long zh, uint32_t zl, int s, d
     return true;
 }
 
+// Row digits in the order 0, 7, 1, 6, 2, 5, 3, 4: digit i is multiplied by
+// 8 - i column digits, so alternating long and short products keeps the MMA
+// time between consecutive row-digit loads even (the slots then stay about
+// equally far ahead of the MMA).  Digit 0 comes first: its products start
+// every diagonal.
+__device__ __forceinline__ int slice_order(int ii) { return (ii & 1) ? kDigits - 1 - (ii >> 1) : (ii >> 1); }
+
 // A tile's place: k block, first row and column, width, and which side the
 // rows come from.  Tiles are numbered k block by k block, column tiles
 // fastest, so CTAs that run at the same time share row digits.
@@ -635,13 +672,13 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                 for (int i = 0; i < kDigits; ++i)
                     tma_prefetch_4d(m2, (int)(rem2 % nkb) * TBK, t2.rentry, i, (int)(rem2 / nkb));
             }
-            for (int i = 0; i < kDigits; ++i) {
+            for (int ii = 0; ii < kDigits; ++ii) {
                 const uint32_t as = na % kASlots;
                 if (na >= (uint32_t)kASlots && !bar_wait(&aempty[as], ((na / kASlots) - 1) & 1)) { s_fail = 1; break; }
                 bar_expect_tx(&afull[as], kABytes);
-                tma_load_4d(aslot + as * kABytes, rmap, &afull[as], c * TBK, ti.rentry, i, t);
+                tma_load_4d(aslot + as * kABytes, rmap, &afull[as], c * TBK, ti.rentry, slice_order(ii), t);
                 ++na;
-                if (i == 2 && q + 1 < nchunks && !issue_b(q + 1)) { s_fail = 1; break; }
+                if (ii == 2 && q + 1 < nchunks && !issue_b(q + 1)) { s_fail = 1; break; }
             }
         }
     } else if (tid == 32) {
@@ -665,12 +702,13 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             // descriptors are linear in the address (16-byte units in the low
             // bits): one per slice, plus 2 per 16-wide K step
             const uint64_t db0 = sdesc(bset + bs * kBBytes);
-            for (int i = 0; i < kDigits; ++i) {
+            for (int ii = 0; ii < kDigits; ++ii) {
+                const int i = slice_order(ii);
                 const uint32_t as = na % kASlots;
                 if (!bar_wait(&afull[as], (na / kASlots) & 1)) { s_fail = 2; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint64_t da = sdesc(aslot + as * kABytes);
-                const uint32_t first = (c == 0 && i == 0) ? 0u : 1u;
+                const uint32_t first = (c == 0 && ii == 0) ? 0u : 1u;
                 for (int j0 = 0; j0 < kDigits - i; j0 += per) {
                     const int ns = min(per, kDigits - i - j0);
                     const uint32_t idesc = idesc_for(ns * tn);
@@ -999,11 +1037,11 @@ TcBuffers tc_buffers(const TcLayout& L, void* ws)
     return B;
 }
 
-template <int PER>
+template <int PER, int WPE>
 cudaError_t launch_level(const TcLevelArgs& la, cudaStream_t s)
 {
-    const int64_t threads = la.count * 32;
-    tc_level_kernel<PER><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(la);
+    const int64_t blocks = (la.count + (4 / WPE) - 1) / (4 / WPE);
+    tc_level_kernel<PER, WPE><<<(unsigned)blocks, 128, 0, s>>>(la);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -1044,10 +1082,10 @@ cudaError_t launch_tc_tables(const TcInputs& in, cudaStream_t s)
             la.lowoff_k = off[k];
             cudaError_t e;
             switch (Kp / 32) {
-                case 2: e = launch_level<2>(la, s); break;
-                case 4: e = launch_level<4>(la, s); break;
-                case 8: e = launch_level<8>(la, s); break;
-                default: e = launch_level<16>(la, s); break;
+                case 2: e = launch_level<2, 1>(la, s); break;
+                case 4: e = launch_level<4, 1>(la, s); break;
+                case 8: e = launch_level<8, 1>(la, s); break;
+                default: e = launch_level<8, 2>(la, s); break;
             }
             if (e != cudaSuccess) return e;
         }
