@@ -360,7 +360,11 @@ struct TcProdArgs {
     int64_t tile0[kMaxBlocks + 1];            // first tile of each block
     int64_t tiles;                            // all tiles
     int rows_low[kMaxBlocks];                 // 1: rows are low-side entries P, columns high-side Q
-    int edge[kMaxBlocks];                     // 1: single-entry block (k = 0 or k = n), see below
+    // Columns of a block: [0, ncol) from the other side's table levels
+    // (col_off), then [ecol0, ecol0 + ecols) single-entry columns (see below);
+    // a block k = 1 or k = n-1 whose rows are level n-1 carries the
+    // single-entry columns of that side when both fit one tile
+    int ncol[kMaxBlocks], ecol0[kMaxBlocks], ecols[kMaxBlocks];
     int tn[kMaxBlocks];                       // tile width (16..64)
     int64_t rows[kMaxBlocks], cols[kMaxBlocks];
     int64_t row_off[kMaxBlocks], col_off[kMaxBlocks];   // entry offsets in the digit tensors
@@ -551,7 +555,7 @@ __device__ __forceinline__ int slice_order(int ii) { return (ii & 1) ? kDigits -
 struct TileInfo {
     int kb, tn;
     int64_t r0, c0;
-    bool rl, edge;
+    bool rl;
     int rentry, centry;
 };
 
@@ -567,7 +571,6 @@ __device__ __forceinline__ TileInfo tile_info(const TcProdArgs& a, int64_t tile)
     ti.r0 = (lt / ctiles) * TBM;
     ti.c0 = (lt % ctiles) * ti.tn;
     ti.rl = a.rows_low[kb] != 0;
-    ti.edge = a.edge[kb] != 0;
     ti.rentry = (int)(a.row_off[kb] + ti.r0);
     ti.centry = (int)(a.col_off[kb] + ti.c0);
     return ti;
@@ -645,15 +648,24 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             // N / 16 boxes of 16 rows
             unsigned char* dst = bset + bs * kBBytes;
             bar_expect_tx(&bfull[bs], (uint32_t)(kDigits * ti.tn) * kRowBytes);
-            if (ti.tn == TBN && !ti.edge) {
+            if (ti.tn == TBN && a.ecols[ti.kb] == 0) {
                 const CUtensorMap* cmap = ti.rl ? &high_cols : &low_cols;
                 for (int j = 0; j < kDigits; ++j)
                     tma_load_4d(dst + j * TBN * kRowBytes, cmap, &bfull[bs], c * TBK, ti.centry, j, t);
             } else {
-                const CUtensorMap* cmap = ti.edge ? (ti.rl ? &vlow16 : &vhigh16) : (ti.rl ? &high_cols16 : &low_cols16);
+                // 16-row boxes; those at or past ecol0 come from the vectors
+                // of the single-entry columns (ecol0 is a multiple of 16)
+                const int e0 = a.ecol0[ti.kb];
+                const CUtensorMap* nmap = ti.rl ? &high_cols16 : &low_cols16;
+                const CUtensorMap* vmap = ti.rl ? &vlow16 : &vhigh16;
                 for (int j = 0; j < kDigits; ++j)
-                    for (int r = 0; r < ti.tn; r += kBSub)
-                        tma_load_4d(dst + (j * ti.tn + r) * kRowBytes, cmap, &bfull[bs], c * TBK, ti.centry + r, j, t);
+                    for (int r = 0; r < ti.tn; r += kBSub) {
+                        const int lc = (int)ti.c0 + r;
+                        if (lc < e0)
+                            tma_load_4d(dst + (j * ti.tn + r) * kRowBytes, nmap, &bfull[bs], c * TBK, ti.centry + r, j, t);
+                        else
+                            tma_load_4d(dst + (j * ti.tn + r) * kRowBytes, vmap, &bfull[bs], c * TBK, lc - e0, j, t);
+                    }
             }
             return true;
         };
@@ -738,21 +750,22 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             const bool rl = ti.rl;
             const int64_t row = ti.r0 + q4 * 32 + lane;
             const bool rv = row < a.rows[kb];
-            const bool edge = ti.edge;
             const int side = rl ? 0 : 1;
             const int* ex_r = rl ? a.ex_low : a.ex_high;
-            const int* ex_c = edge ? a.ex_v[side] : (rl ? a.ex_high : a.ex_low);
-            const int64_t wr = rl ? a.wlow : a.whigh, wc = edge ? a.cols[kb] : (rl ? a.whigh : a.wlow);
-            int64_t pbase = 0;                     // lowbase(P), or efirst(R') - max R' for an edge row
+            const int* ex_c = rl ? a.ex_high : a.ex_low;
+            const int* ex_e = a.ex_v[side];
+            const int64_t wr = rl ? a.wlow : a.whigh, wc = rl ? a.whigh : a.wlow;
+            const int ncol = a.ncol[kb], e0 = a.ecol0[kb], necol = a.ecols[kb];
+            int64_t pbase = 0;                     // lowbase(P) of a low-side row
+            int64_t ebase = 0;                     // efirst(R') - max R' of a level n-1 row
             int emx = 0;
             double esc = 1.0;
-            if (rv && edge) {
+            if (rv && necol > 0) {
                 emx = a.emax[side][row];
                 esc = a.esc[side][row];
-                pbase = a.efirst[side][row] - emx;
-            } else if (rv && rl) {
-                pbase = a.lowbase[a.lowoff[kb] + row];
+                ebase = a.efirst[side][row] - emx;
             }
+            if (rv && rl && ncol > 0) pbase = a.lowbase[a.lowoff[kb] + row];
             for (int t = 0; t < 3; ++t) {
                 const int64_t g = it * 3 + t;
                 const int er = rv ? ex_r[(int64_t)t * wr + a.row_off[kb] + row] : kNoExp;
@@ -813,21 +826,23 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const int64_t col = ti.c0 + cc + q;
-                        if (col >= a.cols[kb] || (edge && col < emx)) continue;
-                        const int ec = ex_c[(int64_t)t * wc + a.col_off[kb] + col];
+                        const bool is_e = col >= e0;       // a single-entry column: mode ce of this side
+                        const int64_t ce = col - e0;
+                        if (is_e ? (ce >= necol || ce < emx) : (col >= ncol)) continue;
+                        const int ec = is_e ? ex_e[(int64_t)t * necol + ce] : ex_c[(int64_t)t * wc + a.col_off[kb] + col];
                         double x = 0.0;
                         if (er != kNoExp && ec != kNoExp) {
                             const int sc = er + ec - 14;
                             if (!scale_packed(zh[h][q], zl[h][q], sc - 49, x))
                                 x = fma((double)zl[h][q], pow2(sc - 49), (double)zh[h][q] * pow2(sc - 21));
                         }
-                        const int64_t o = (rl || edge) ? pbase + col : a.lowbase[a.lowoff[kb] + col] + row;
+                        const int64_t o = is_e ? ebase + ce : (rl ? pbase + col : a.lowbase[a.lowoff[kb] + col] + row);
                         if (t < 2) {
                             a.xt[(int64_t)t * a.total + o] = x;
                         } else {
                             const double t1 = a.xt[o], t2 = a.xt[a.total + o];
                             double re = t1 - t2, im = x - t1 - t2;
-                            if (edge && col == emx) {          // 1 / sqrt(multiplicity of r in R' + r)
+                            if (is_e && ce == emx) {           // 1 / sqrt(multiplicity of r in R' + r)
                                 re *= esc;
                                 im *= esc;
                             }
@@ -1156,43 +1171,60 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     TcProdArgs a;
     a.nk = 0;
     a.kblocks = Kp / TBK;
-    int64_t tiles = 0;
+    auto round16 = [](int64_t x) { return (int)((x + 15) / 16) * 16; };
     for (int k = 1; k < in.n; ++k) {
         const int64_t M = msets_tc(in.h, k), N = msets_tc(in.m - in.h, in.n - k);
         if (M == 0 || N == 0) continue;
         const bool rl = M >= N;
         const int64_t rows = rl ? M : N, cols = rl ? N : M;
-        const int tn = cols >= TBN ? TBN : (int)((cols + 15) / 16) * 16;
         a.rows_low[a.nk] = rl ? 1 : 0;
-        a.edge[a.nk] = 0;
-        a.tn[a.nk] = tn;
+        a.tn[a.nk] = cols >= TBN ? TBN : round16(cols);
         a.rows[a.nk] = rows;
         a.cols[a.nk] = cols;
+        a.ncol[a.nk] = (int)std::min<int64_t>(cols, INT32_MAX);
+        a.ecol0[a.nk] = (int)std::min<int64_t>(cols, INT32_MAX);
+        a.ecols[a.nk] = 0;
         a.row_off[a.nk] = rl ? in.lowoff[k] - lb : in.highoff[in.n - k] - hb;
         a.col_off[a.nk] = rl ? in.highoff[in.n - k] - hb : in.lowoff[k] - lb;
         a.lowoff[a.nk] = in.lowoff[k];
-        a.tile0[a.nk] = tiles;
-        tiles += ((rows + TBM - 1) / TBM) * ((cols + tn - 1) / tn);
         a.nk++;
     }
-    // the single-entry blocks: rows = level n-1 of a side, columns = its modes
-    // (side 0: outputs with every photon low, k = n; side 1: k = 0)
+    // the single-entry columns: rows = level n-1 of a side, columns = its
+    // modes (side 0: outputs with every photon low, k = n; side 1: k = 0),
+    // merged into the block with the same rows when both fit one tile
     for (int side = 0; side < 2; ++side) {
         const int64_t rows = side == 0 ? in.lowoff[n] - in.lowoff[n - 1] : in.highoff[n] - in.highoff[n - 1];
-        const int64_t cols = side == 0 ? h : m - h;
-        if (rows == 0 || cols == 0) continue;
-        const int tn = cols >= TBN ? TBN : (int)((cols + 15) / 16) * 16;
+        const int ecols = side == 0 ? h : m - h;
+        if (rows == 0 || ecols == 0) continue;
+        const int64_t roff = side == 0 ? in.lowoff[n - 1] - lb : in.highoff[n - 1] - hb;
+        int host = -1;
+        for (int b = 0; b < a.nk; ++b)
+            if (a.rows_low[b] == (side == 0 ? 1 : 0) && a.row_off[b] == roff && a.ecols[b] == 0 &&
+                round16(a.ncol[b]) + round16(ecols) <= TBN)
+                host = b;
+        if (host >= 0) {
+            a.ecol0[host] = round16(a.ncol[host]);
+            a.ecols[host] = ecols;
+            a.cols[host] = a.ecol0[host] + ecols;
+            a.tn[host] = a.ecol0[host] + round16(ecols);
+            continue;
+        }
         a.rows_low[a.nk] = side == 0 ? 1 : 0;
-        a.edge[a.nk] = 1;
-        a.tn[a.nk] = tn;
+        a.tn[a.nk] = ecols >= TBN ? TBN : round16(ecols);
         a.rows[a.nk] = rows;
-        a.cols[a.nk] = cols;
-        a.row_off[a.nk] = side == 0 ? in.lowoff[n - 1] - lb : in.highoff[n - 1] - hb;
+        a.cols[a.nk] = ecols;
+        a.ncol[a.nk] = 0;
+        a.ecol0[a.nk] = 0;
+        a.ecols[a.nk] = ecols;
+        a.row_off[a.nk] = roff;
         a.col_off[a.nk] = 0;
         a.lowoff[a.nk] = 0;
-        a.tile0[a.nk] = tiles;
-        tiles += ((rows + TBM - 1) / TBM) * ((cols + tn - 1) / tn);
         a.nk++;
+    }
+    int64_t tiles = 0;
+    for (int b = 0; b < a.nk; ++b) {
+        a.tile0[b] = tiles;
+        tiles += ((a.rows[b] + TBM - 1) / TBM) * ((a.cols[b] + a.tn[b] - 1) / a.tn[b]);
     }
     a.tile0[a.nk] = tiles;
     if (tiles == 0) {
