@@ -122,17 +122,23 @@ __device__ __forceinline__ long long fixed_of(double x, int E)
 // 128^{7-i}: with C = 64 (1 + 128 + ... + 128^7), the word P = X + C is
 // non-negative and below 2^57, and D_i = u_i - 64 for its 7-bit fields u_i
 // (the top field, bits 49 and up, unmasked), so |D_i| <= 64 with no carry
-// chain.  digit_bf16 returns the BF16 bits of D_i: u_i - 64 is formed
-// exactly in FP32 (1.5 2^23 + u_i, minus 1.5 2^23 + 64), whose low 16 bits
-// are then zero.
+// chain.  digit_f32 returns D_i = u_i - 64 as FP32 bits, formed exactly
+// (1.5 2^23 + u_i, minus 1.5 2^23 + 64); their low 16 bits are zero, so the
+// high half is D_i in BF16, and bf16_pair packs two of them into a word.
 constexpr unsigned long long kDigitOffset = 0x0081020408102040ull;   // 64 in every 7-bit field
 
 __device__ __forceinline__ unsigned long long digit_word(long long X) { return (unsigned long long)(X + (long long)kDigitOffset); }
 
-__device__ __forceinline__ uint32_t digit_bf16(unsigned long long P, int i)
+__device__ __forceinline__ uint32_t digit_f32(unsigned long long P, int i)
 {
     const uint32_t u = i == 0 ? (uint32_t)(P >> 49) : (uint32_t)((P >> (7 * (7 - i))) & 127u);
-    return __float_as_uint(__uint_as_float(0x4B400000u | u) - 12582976.0f) >> 16;
+    return __float_as_uint(__uint_as_float(0x4B400000u | u) - 12582976.0f);
+}
+
+// BF16 of digit i of P0 in the low half, of P1 in the high half
+__device__ __forceinline__ uint32_t bf16_pair(unsigned long long P0, unsigned long long P1, int i)
+{
+    return __byte_perm(digit_f32(P0, i), digit_f32(P1, i), 0x7632);
 }
 
 // ------------------------------------------------------------ fused tables
@@ -187,7 +193,7 @@ __device__ __forceinline__ void store_digit_run(__nv_bfloat16* dst, const unsign
 {
     uint32_t wv[PER / 2];
 #pragma unroll
-    for (int u = 0; u < PER / 2; ++u) wv[u] = digit_bf16(pk[2 * u], i) | (digit_bf16(pk[2 * u + 1], i) << 16);
+    for (int u = 0; u < PER / 2; ++u) wv[u] = bf16_pair(pk[2 * u], pk[2 * u + 1], i);
     if constexpr (PER == 8) {
         *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
     } else if constexpr (PER == 4) {
@@ -209,25 +215,33 @@ __global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
     const bool valid = e < a.count;
     const int w = a.side == 0 ? a.h : a.m - a.h;
     const int shift = a.side == 0 ? 0 : a.h;
-    int modes[PCV_MAX_PHOTONS];
     int mult = 1, r = 0;
     int64_t parent = 0;
     if (valid) {
-        unrank_multiset<PCV_MAX_PHOTONS>(a.mc, w, a.k, e, modes);
-        const int last = modes[a.k - 1];
-        for (int p = a.k - 2; p >= 0 && modes[p] == last; --p) ++mult;
-        r = last + shift;
-        parent = a.k > 1 ? rank_multiset(a.mc, w, a.k - 1, modes) : 0;
-        if (a.lowbase && lane == 0 && part == 0) {
-            // canonical index of the first output with prefix P and the rest in [h, m)
-            int64_t base = 0;
-            int prev = 0;
-            for (int p = 0; p < a.k; ++p) {
-                for (int v = prev; v < modes[p]; ++v) base += a.mc(a.m - v, a.n - p - 1);
-                prev = modes[p];
+        // unrank P (non-decreasing modes, lexicographic order) and, in the same
+        // walk, the rank of P minus its last mode among (k-1)-multisets, the
+        // run length of the last mode, and (low side) the canonical index of
+        // the first output with prefix P and the rest in [h, m)
+        const bool want_base = a.lowbase && lane == 0 && part == 0;
+        int64_t idx = e, base = 0;
+        int v = 0, prevmode = -1;
+        for (int p = 0; p < a.k; ++p) {
+            const int rest = a.k - p - 1;
+            for (;;) {
+                const int64_t c = a.mc(w - v, rest);
+                if (idx < c) break;
+                idx -= c;
+                if (p < a.k - 1) parent += a.mc(w - v, a.k - 2 - p);
+                if (want_base) base += a.mc(a.m - v, a.n - p - 1);
+                ++v;
             }
+            mult = v == prevmode ? mult + 1 : 1;
+            prevmode = v;
+        }
+        r = v + shift;
+        if (want_base) {
             if (a.k < a.n)
-                for (int v = prev; v < a.h; ++v) base += a.mc(a.m - v, a.n - a.k - 1);
+                for (int u = v; u < a.h; ++u) base += a.mc(a.m - u, a.n - a.k - 1);
             a.lowbase[a.lowoff_k + e] = base;
         }
     }
@@ -343,8 +357,8 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const double2* __rest
 #pragma unroll
         for (int i = 0; i < kDigits; ++i) {
             uint2 st;
-            st.x = digit_bf16(pk[0], i) | (digit_bf16(pk[1], i) << 16);
-            st.y = digit_bf16(pk[2], i) | (digit_bf16(pk[3], i) << 16);
+            st.x = bf16_pair(pk[0], pk[1], i);
+            st.y = bf16_pair(pk[2], pk[3], i);
             *reinterpret_cast<uint2*>(out + (((int64_t)t * kDigits + i) * w + e) * Kpad + d0) = st;
         }
     }
