@@ -85,21 +85,28 @@ __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_l
 // E_t(entry) for t = re, im, re+im: the smallest E with max |x| <= 2^{E-1}
 // (from the largest exponent field; a power of two costs one spare bit).
 // (T, Sm: [K][stride] tables from their first digitised entry; w entries.)
+// One warp per entry, lanes over the sign vectors.
 __global__ void split_exp_kernel(const double2* __restrict__ T, const double* __restrict__ Sm, int64_t stride,
                                  int64_t w, int K, int* __restrict__ ex)
 {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= w) return;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= w) return;                                    // whole warps
     int f0 = 0, f1 = 0, f2 = 0;
-    for (int d = 0; d < K; ++d) {
+    for (int d = lane; d < K; d += 32) {
         const double2 v = T[(int64_t)d * stride + e];
         f0 = max(f0, exp_field(v.x));
         f1 = max(f1, exp_field(v.y));
         f2 = max(f2, exp_field(Sm[(int64_t)d * stride + e]));
     }
-    ex[e] = f0 ? f0 - 1021 : kNoExp;
-    ex[w + e] = f1 ? f1 - 1021 : kNoExp;
-    ex[2 * w + e] = f2 ? f2 - 1021 : kNoExp;
+    f0 = __reduce_max_sync(0xffffffffu, f0);
+    f1 = __reduce_max_sync(0xffffffffu, f1);
+    f2 = __reduce_max_sync(0xffffffffu, f2);
+    if (lane == 0) {
+        ex[e] = f0 ? f0 - 1021 : kNoExp;
+        ex[w + e] = f1 ? f1 - 1021 : kNoExp;
+        ex[2 * w + e] = f2 ? f2 - 1021 : kNoExp;
+    }
 }
 
 // X = round(x 2^{56-E}) as a signed integer, |X| <= 2^55 (the magnitude
@@ -1161,7 +1168,7 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     note_launches(1);
     for (int side = 0; side < 2; ++side) {
         const int64_t ww = side == 0 ? h : m - h;
-        split_exp_kernel<<<(unsigned)((ww + 255) / 256), 256, 0, s>>>(V[side], SV[side], ww, ww, K, EXV[side]);
+        split_exp_kernel<<<(unsigned)((ww * 32 + 255) / 256), 256, 0, s>>>(V[side], SV[side], ww, ww, K, EXV[side]);
         const int64_t warps = ((ww + 3) / 4) * (Kp / 32);
         split_digits_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(V[side], SV[side], ww, ww, K, Kp, EXV[side],
                                                                           DV[side]);
