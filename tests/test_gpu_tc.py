@@ -49,6 +49,32 @@ def test_tc_distribution_matches_oracle(pcv, m, n, t):
     assert np.allclose(prob, np.abs(amp) ** 2, rtol=1e-14, atol=0)
 
 
+@pytest.mark.parametrize("m,n,t", [
+    (40, 3, None),          # single-entry columns merged into the k = 1 and k = n-1 tiles (32 + 32 wide)
+    (70, 2, None),          # 35 + 35 columns do not fit one tile: separate single-entry blocks
+    (5, 4, [0, 4, 0, 0, 0]),    # all photons in one input mode (a repeated column)
+    (2, 3, [2, 1]),          # one mode per side
+    (1, 3, [3]),             # m = 1: no high side, the single-entry blocks in FP64
+    (30, 4, "modes 0 2 6 29"),   # photons spread over both sides, K = 8
+])
+def test_tc_block_shapes_match_oracle(pcv, m, n, t):
+    """Shapes that exercise how the blocks are formed: merged and separate
+    single-entry columns, tile widths 16..64, one side with a single mode,
+    and the FP64 fallback."""
+    U = pin.haar_unitary(m, 7400 + 17 * m + n)
+    if t is None:
+        t = pin.single_photon_input(m, n)
+    elif isinstance(t, str):
+        t = pin.single_photon_input(m, n, modes=[int(v) for v in t.split()[1:]])
+    else:
+        t = np.array(t, np.uint8)
+    p_ref, a_ref = oracle.distribution(U, t)
+    prob, amp = tc_dist(pcv, U, t)
+    assert amp_err(amp, a_ref, m, n) <= 1e-10
+    assert 0.5 * np.abs(prob - p_ref).sum() <= 1e-12
+    assert abs(prob.sum() - 1.0) <= 1e-12
+
+
 def test_tc_probabilities_only(pcv):
     m, n = 10, 5
     U = pin.haar_unitary(m, 7101)
