@@ -40,9 +40,13 @@ def workload_text(m, n, count):
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2, written between timed steps
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, m=20 n=10,
-# from one ncu capture of the current kernel (dram__bytes_read.sum 15.49 GB +
-# dram__bytes_write.sum 0.51 GB); None when no capture of the current kernel exists.
+# from one ncu capture of the current kernel; None when no capture of the
+# current kernel exists.  FP64 products (gemm_kernel): dram__bytes_read.sum
+# 15.49 GB + dram__bytes_write.sum 0.51 GB.  Tensor-core products
+# (tc_product_kernel): 6.805 GB read + 0.903 GB written (one-pass capture of
+# the full workload, profiles/tc_products_m20n10.md).
 NCU_TRAFFIC_PER_LAUNCH = 16.00e9
+NCU_TRAFFIC_TC_PER_LAUNCH = 7.708e9
 
 
 def parse():
@@ -350,7 +354,8 @@ def run_ours(args):
             "frac": achieved / peak_tflops if achieved else None,
             "peak_source": peak_src,
             "fp64_probe_tflops": probe_tflops,
-            "traffic": NCU_TRAFFIC_PER_LAUNCH if (M, N_PH, args.algo) == (20, 10, "factor") else None,
+            "traffic": (NCU_TRAFFIC_PER_LAUNCH if (M, N_PH, args.algo) == (20, 10, "factor") else
+                        NCU_TRAFFIC_TC_PER_LAUNCH if (M, N_PH, args.algo) == (20, 10, "factor_tc") else None),
             "launches_per_step": launches_per_call,
             "stage_ms_per_step": {k: (v[0] / v[1] if v[1] else None) for k, v in stages.items()}}
 
