@@ -55,3 +55,26 @@ def test_online_refinement_lowers_the_surrogate_tvd():
     _, _, refined = opt.surrogate_loop(prob, copy(), ph0, 200, check_every=10, tvd_tol=1e-3, refine_steps=20)
     assert refined["refine_steps"] == 20 and refined["checks"] == 20
     assert refined["median_tvd_seen"] < plain["median_tvd_seen"], (plain, refined)
+
+
+def test_anchored_loop_limits():
+    # the anchored loop with a tolerance no check meets takes exact steps
+    # throughout and follows the exact loop; with no network and an infinite
+    # tolerance it takes one exact step per interval and reuses its gradient
+    from paper_2204_00602_gb300 import optimize as opt
+    from paper_2204_00602_gb300.surrogate import MLP, init_weights
+    prob = opt.MeshProblem(B=16)
+    ph0 = torch.from_numpy(np.random.default_rng(3).uniform(0, 2 * np.pi, (16, prob.P))).cuda()
+    ph_e, _ = opt.exact_loop(prob, ph0, 40)
+    Ws, bs = init_weights(9)
+    net = MLP(Ws, bs, lr=1e-3)
+    ph_a, _, info = opt.anchored_loop(prob, net, ph0, 40, check_every=5, tvd_tol=-1.0)
+    assert info["exact_steps"] == 40 and info["checks"] == 7
+    # the same exact steps; the adjoint scatters dL/dU with atomic adds, so the
+    # two runs differ in rounding, which Adam's normalisation amplifies over
+    # the steps: compare where they end, not the bits
+    la, le = prob.loss(ph_a), prob.loss(ph_e)
+    assert torch.allclose(la, le, rtol=1e-2, atol=0), (la, le)
+    ph_s, _, info = opt.anchored_loop(prob, None, ph0, 40, check_every=5, tvd_tol=float("inf"))
+    assert info["exact_steps"] == 8 and not info["network"]
+    assert torch.all(prob.loss(ph_s) < prob.loss(ph0))
