@@ -1,7 +1,8 @@
-// Product stage of the factorised full distribution on the BF16 tensor cores,
-// with exact integer arithmetic.
+// The factorised full distribution with its products on the BF16 tensor
+// cores, in exact integer arithmetic: table levels, digit splitting and the
+// products of every block k = 0..n.
 //
-// After the factor tables are built (glynn_dist.cu), every output is
+// With the row sums y_r(d) (glynn_dist.cu), every output is
 //     a(S) = sum_d alpha_P(d) beta_Q(d),
 // for each k a complex matrix product over the K = 2^{n-1} sign vectors, done
 // as three real products (Gauss): t1 = Ar Br, t2 = Ai Bi, t3 = (Ar+Ai)(Br+Bi),
@@ -22,14 +23,26 @@
 //     diagonal exactly, in any order the tensor core adds them;
 //   * diagonals d = 0..7 are kept (36 digit pairs); the dropped ones weigh
 //     2^{-56} and less relative to the row and column scales;
-//   * the 8 diagonal sums (exact integers) are combined on the integer pipe,
-//     hi = sum_{d<4} acc_d 128^{3-d}, lo = sum_{d>=4} acc_d 128^{7-d}, and
-//     x_t = 2^{E_row + E_col - 14} (hi 2^{-21} + lo 2^{-49}) in FP64.
+//   * the 8 diagonal sums (exact integers) are combined on the integer pipe
+//     into Z = hi 2^28 + lo, hi = sum_{d<4} acc_d 128^{3-d}, lo = sum_{d>=4}
+//     acc_d 128^{7-d}, and x_t = Z 2^{E_row + E_col - 63} is rounded once to
+//     FP64 with integer operations (scale_packed).
 //
-// Kernels: split_exp_kernel (the row exponents, integer max of the exponent
-// fields), split_digits_kernel (digits as BF16, laid out [t][digit][entry][K]
-// for TMA), and tc_product_kernel: one persistent CTA per SM walking 128 x N
-// output tiles of one k each (N = 16..64), ten warps:
+// Kernels:
+//   tc_level_kernel     table levels 1..n-1 of each side, built in FP64 from
+//                       the parent level and written as BF16 digits, laid out
+//                       [t][digit][entry][K] for TMA (levels <= n-2 also keep
+//                       their complex entries as the next level's parents);
+//   split_exp_kernel, split_digits_kernel, edge_vectors_kernel,
+//   edge_info_kernel    the single-entry blocks (k = 0, k = n): level n is
+//                       level n-1 times y_r / sqrt(multiplicity), so these
+//                       blocks are products of level n-1 with one vector per
+//                       mode; the vectors are split here, and each level n-1
+//                       entry gets its output index and scale;
+//   tc_product_kernel   one persistent CTA per SM walking 128 x N output
+//                       tiles of one block each (N = 16..64; the single-entry
+//                       columns ride in the tile of the block k = 1 or n-1
+//                       with the same rows when both fit), ten warps:
 //   warp 0  TMA producer: per 64-wide K block, the 8 digit slices of the
 //           column operand (N rows each, packed one after the other in a
 //           64 KB set, double-buffered), then the 8 digit slices of the row
@@ -46,11 +59,11 @@
 //           times; commits free the slots;
 //   warps 2-9  drain: after each of the three products, tcgen05.ld of the 8
 //           diagonals (warp w owns TMEM lanes 32 (w mod 4) .., two warps per
-//           lane group split the columns), integer combination and FP64
-//           scaling; the accumulators are handed back to the MMA before any
-//           store.  t1 and t2 are stored at canonical index lowbase(P) +
-//           rank(Q) of a [2][outputs] buffer; after t3 the thread that
-//           stored them forms the amplitude and |a|^2 in place.
+//           lane group split the columns) and the integer combination; the
+//           accumulators are then handed back to the MMA, and the rounding
+//           and stores follow.  t1 and t2 are stored at the output's
+//           canonical index in a [2][outputs] buffer; after t3 the thread
+//           that stored them forms the amplitude and |a|^2 in place.
 // Every mbarrier wait is bounded; on a time-out the kernel records an error
 // code and returns after releasing its tensor memory.
 
