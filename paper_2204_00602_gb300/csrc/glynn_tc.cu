@@ -167,9 +167,9 @@ __device__ __forceinline__ uint32_t bf16_pair(unsigned long long P0, unsigned lo
 // (the tables are never stored in the [sign vector][entry] layout of the
 // FP64 path): entry(P)(d) = entry(P minus its last mode r)(d) y_r(d) /
 // sqrt(multiplicity of r in P), level 0 being sigma(d) 2^{-(n-1)} norm_t on
-// the low side and 1 on the high side.  One warp per entry P (two when
-// Kpad = 512), each lane holding Kpad / 32 (8) sign vectors (those >= K are
-// zero): the three row exponents (re, im, re + im) are maxima over the
+// the low side and 1 on the high side.  Kpad / 128 warps per entry P (one
+// for Kpad <= 128), each lane holding 4 sign vectors (2 at Kpad = 64; those
+// >= K are zero): the three row exponents (re, im, re + im) are maxima over the
 // entry's warps, so the digits [3][8][entry][Kpad] are written in the same
 // pass.  Levels below
 // n - 1 also keep the complex entries, entry-major [entry][K], as the parents
@@ -1131,10 +1131,10 @@ cudaError_t launch_tc_tables(const TcInputs& in, cudaStream_t s)
             la.lowoff_k = off[k];
             cudaError_t e;
             switch (Kp / 32) {
-                case 2: e = launch_level<2, 1>(la, s); break;
-                case 4: e = launch_level<4, 1>(la, s); break;
-                case 8: e = launch_level<8, 1>(la, s); break;
-                default: e = launch_level<8, 2>(la, s); break;
+                case 2: e = launch_level<2, 1>(la, s); break;           // Kpad = 64
+                case 4: e = launch_level<4, 1>(la, s); break;           // 128
+                case 8: e = launch_level<4, 2>(la, s); break;           // 256
+                default: e = launch_level<4, 4>(la, s); break;          // 512
             }
             if (e != cudaSuccess) return e;
         }

@@ -56,6 +56,8 @@ def test_tc_distribution_matches_oracle(pcv, m, n, t):
     (2, 3, [2, 1]),          # one mode per side
     (1, 3, [3]),             # m = 1: no high side, the single-entry blocks in FP64
     (30, 4, "modes 0 2 6 29"),   # photons spread over both sides, K = 8
+    (10, 8, None),           # K = 128: one warp per table entry
+    (10, 9, None),           # K = 256: two warps per table entry
 ])
 def test_tc_block_shapes_match_oracle(pcv, m, n, t):
     """Shapes that exercise how the blocks are formed: merged and separate
