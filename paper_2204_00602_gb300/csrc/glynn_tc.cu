@@ -47,8 +47,7 @@
 //           column operand (N rows each, packed one after the other in a
 //           64 KB set, double-buffered), then the 8 digit slices of the row
 //           operand one at a time (16 KB slots, six in flight, digits in the
-//           order 0 7 1 6 2 5 3 4), 128B swizzle; the row digits two K blocks
-//           ahead are prefetched into L2;
+//           order 0 7 1 6 2 5 3 4), 128B swizzle;
 //   warp 1  MMA issuer: the accumulator of diagonal d sits at TMEM columns
 //           d N .. d N + N - 1, so the products of row digit i with column
 //           digits j = j0 .. j1 land on the contiguous columns (i + j0) N ..
@@ -457,13 +456,6 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int x, int y, int z, int u)
-{
-    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];\n" ::"l"(map), "r"(x), "r"(y),
-                 "r"(z), "r"(u)
-                 : "memory");
-}
-
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
                                             int u)
 {
@@ -634,7 +626,7 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nkb = a.kblocks;
     const int64_t my_tiles = a.tiles > (int64_t)blockIdx.x ? (a.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t nchunks = my_tiles * 3 * nkb;
+    const uint32_t nchunks = (uint32_t)(my_tiles * 3 * nkb);      // < 2^31 (checked on the host)
 
     if (tid == 0) {
         for (int s = 0; s < kBSets; ++s) {
@@ -671,105 +663,125 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
 
     if (tid == 0) {
         // ---------------- TMA producer
+        // chunk q = (tile it, product t, K block c), in that nesting; the tile
+        // of the next chunk is looked up once, when the chunk crosses into it
         uint32_t na = 0;
-        auto issue_b = [&](int64_t q) -> bool {
-            const int64_t it = q / (3 * nkb), rem = q % (3 * nkb);
-            const int t = (int)(rem / nkb), c = (int)(rem % nkb);
-            const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
-            const uint32_t bs = (uint32_t)(q % kBSets);
-            if (q >= kBSets && !bar_wait(&bempty[bs], (uint32_t)((q / kBSets) - 1) & 1)) return false;
+        auto issue_b = [&](uint32_t q, const TileInfo& tb, int t, int c) -> bool {
+            const uint32_t bs = q % kBSets;
+            if (q >= kBSets && !bar_wait(&bempty[bs], ((q / kBSets) - 1) & 1)) return false;
             // slice j at rows j N .. j N + N - 1 of the set: one 64-row box, or
             // N / 16 boxes of 16 rows
             unsigned char* dst = bset + bs * kBBytes;
-            bar_expect_tx(&bfull[bs], (uint32_t)(kDigits * ti.tn) * kRowBytes);
-            if (ti.tn == TBN && a.ecols[ti.kb] == 0) {
-                const CUtensorMap* cmap = ti.rl ? &high_cols : &low_cols;
+            bar_expect_tx(&bfull[bs], (uint32_t)(kDigits * tb.tn) * kRowBytes);
+            if (tb.tn == TBN && a.ecols[tb.kb] == 0) {
+                const CUtensorMap* cmap = tb.rl ? &high_cols : &low_cols;
                 for (int j = 0; j < kDigits; ++j)
-                    tma_load_4d(dst + j * TBN * kRowBytes, cmap, &bfull[bs], c * TBK, ti.centry, j, t);
+                    tma_load_4d(dst + j * TBN * kRowBytes, cmap, &bfull[bs], c * TBK, tb.centry, j, t);
             } else {
                 // 16-row boxes; those at or past ecol0 come from the vectors
                 // of the single-entry columns (ecol0 is a multiple of 16)
-                const int e0 = a.ecol0[ti.kb];
-                const CUtensorMap* nmap = ti.rl ? &high_cols16 : &low_cols16;
-                const CUtensorMap* vmap = ti.rl ? &vlow16 : &vhigh16;
+                const int e0 = a.ecol0[tb.kb];
+                const CUtensorMap* nmap = tb.rl ? &high_cols16 : &low_cols16;
+                const CUtensorMap* vmap = tb.rl ? &vlow16 : &vhigh16;
                 for (int j = 0; j < kDigits; ++j)
-                    for (int r = 0; r < ti.tn; r += kBSub) {
-                        const int lc = (int)ti.c0 + r;
+                    for (int r = 0; r < tb.tn; r += kBSub) {
+                        const int lc = (int)tb.c0 + r;
                         if (lc < e0)
-                            tma_load_4d(dst + (j * ti.tn + r) * kRowBytes, nmap, &bfull[bs], c * TBK, ti.centry + r, j, t);
+                            tma_load_4d(dst + (j * tb.tn + r) * kRowBytes, nmap, &bfull[bs], c * TBK, tb.centry + r, j, t);
                         else
-                            tma_load_4d(dst + (j * ti.tn + r) * kRowBytes, vmap, &bfull[bs], c * TBK, lc - e0, j, t);
+                            tma_load_4d(dst + (j * tb.tn + r) * kRowBytes, vmap, &bfull[bs], c * TBK, lc - e0, j, t);
                     }
             }
             return true;
         };
-        if (nchunks > 0 && !issue_b(0)) s_fail = 1;
-        for (int64_t q = 0; q < nchunks && !s_fail; ++q) {
-            const int64_t it = q / (3 * nkb), rem = q % (3 * nkb);
-            const int t = (int)(rem / nkb), c = (int)(rem % nkb);
-            const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
+        TileInfo ti = {}, tnext = {};
+        if (my_tiles > 0) {
+            ti = tile_info(a, blockIdx.x);
+            if (!issue_b(0, ti, 0, 0)) s_fail = 1;
+        }
+        uint32_t q = 0;
+        for (int64_t it = 0; it < my_tiles && !s_fail; ++it) {
+            if (it > 0) ti = tnext;
             const CUtensorMap* rmap = ti.rl ? &low_rows : &high_rows;
-            if (q + 2 < nchunks) {
-                // row digits of chunk q + 2 into L2, so that their loads
-                // (issued a few slices ahead of the MMA) do not wait on DRAM
-                const int64_t q2 = q + 2, it2 = q2 / (3 * nkb), rem2 = q2 % (3 * nkb);
-                const TileInfo t2 = tile_info(a, blockIdx.x + it2 * gridDim.x);
-                const CUtensorMap* m2 = t2.rl ? &low_rows : &high_rows;
-                for (int i = 0; i < kDigits; ++i)
-                    tma_prefetch_4d(m2, (int)(rem2 % nkb) * TBK, t2.rentry, i, (int)(rem2 / nkb));
-            }
-            for (int ii = 0; ii < kDigits; ++ii) {
-                const uint32_t as = na % kASlots;
-                if (na >= (uint32_t)kASlots && !bar_wait(&aempty[as], ((na / kASlots) - 1) & 1)) { s_fail = 1; break; }
-                bar_expect_tx(&afull[as], kABytes);
-                tma_load_4d(aslot + as * kABytes, rmap, &afull[as], c * TBK, ti.rentry, slice_order(ii), t);
-                ++na;
-                if (ii == 2 && q + 1 < nchunks && !issue_b(q + 1)) { s_fail = 1; break; }
+            for (int t = 0; t < 3 && !s_fail; ++t) {
+                for (int c = 0; c < nkb && !s_fail; ++c, ++q) {
+                    int tn1 = t, cn1 = c + 1;                       // the chunk after this one
+                    bool next_tile = false;
+                    if (cn1 == nkb) {
+                        cn1 = 0;
+                        if (++tn1 == 3) {
+                            tn1 = 0;
+                            next_tile = true;
+                        }
+                    }
+                    for (int ii = 0; ii < kDigits; ++ii) {
+                        const uint32_t as = na % kASlots;
+                        if (na >= (uint32_t)kASlots && !bar_wait(&aempty[as], ((na / kASlots) - 1) & 1)) {
+                            s_fail = 1;
+                            break;
+                        }
+                        bar_expect_tx(&afull[as], kABytes);
+                        tma_load_4d(aslot + as * kABytes, rmap, &afull[as], c * TBK, ti.rentry, slice_order(ii), t);
+                        ++na;
+                        if (ii == 2 && q + 1 < nchunks) {
+                            if (next_tile) tnext = tile_info(a, blockIdx.x + (it + 1) * gridDim.x);
+                            if (!issue_b(q + 1, next_tile ? tnext : ti, tn1, cn1)) {
+                                s_fail = 1;
+                                break;
+                            }
+                        }
+                    }
+                }
             }
         }
     } else if (tid == 32) {
         // ---------------- MMA issuer
-        uint32_t na = 0;
-        int tn = TBN, per = 4;
-        for (int64_t q = 0; q < nchunks && !s_fail; ++q) {
-            const int64_t it = q / (3 * nkb), rem = q % (3 * nkb);
-            const int c = (int)(rem % nkb);
-            const int64_t g = q / nkb;                                   // pass number of this CTA
-            if (c == 0) {
-                if (rem == 0) {
-                    tn = tile_info(a, blockIdx.x + it * gridDim.x).tn;
-                    per = min(kDigits, 256 / tn);                        // column slices per MMA
+        uint32_t na = 0, q = 0, g = 0;                               // slices, chunks, passes
+        for (int64_t it = 0; it < my_tiles && !s_fail; ++it) {
+            const int tn = tile_info(a, blockIdx.x + it * gridDim.x).tn;
+            const int per = min(kDigits, 256 / tn);                      // column slices per MMA
+            for (int t = 0; t < 3 && !s_fail; ++t, ++g) {
+                if (g > 0 && !bar_wait(&accempty, (g - 1) & 1)) {
+                    s_fail = 2;
+                    break;
                 }
-                if (g > 0 && !bar_wait(&accempty, (uint32_t)(g - 1) & 1)) { s_fail = 2; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            }
-            const uint32_t bs = (uint32_t)(q % kBSets);
-            if (!bar_wait(&bfull[bs], (uint32_t)(q / kBSets) & 1)) { s_fail = 2; break; }
-            // descriptors are linear in the address (16-byte units in the low
-            // bits): one per slice, plus 2 per 16-wide K step
-            const uint64_t db0 = sdesc(bset + bs * kBBytes);
-            for (int ii = 0; ii < kDigits; ++ii) {
-                const int i = slice_order(ii);
-                const uint32_t as = na % kASlots;
-                if (!bar_wait(&afull[as], (na / kASlots) & 1)) { s_fail = 2; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const uint64_t da = sdesc(aslot + as * kABytes);
-                const uint32_t first = (c == 0 && ii == 0) ? 0u : 1u;
-                for (int j0 = 0; j0 < kDigits - i; j0 += per) {
-                    const int ns = min(per, kDigits - i - j0);
-                    const uint32_t idesc = idesc_for(ns * tn);
-                    const uint32_t acc_t = tmem + (uint32_t)((i + j0) * tn);
-                    const uint64_t db = db0 + (uint64_t)((j0 * tn * kRowBytes) >> 4);
-                    mma_f16(acc_t, da, db, idesc, first);
-                    mma_f16(acc_t, da + 2, db + 2, idesc, 1u);
-                    mma_f16(acc_t, da + 4, db + 4, idesc, 1u);
-                    mma_f16(acc_t, da + 6, db + 6, idesc, 1u);
+                for (int c = 0; c < nkb && !s_fail; ++c, ++q) {
+                    const uint32_t bs = q % kBSets;
+                    if (!bar_wait(&bfull[bs], (q / kBSets) & 1)) {
+                        s_fail = 2;
+                        break;
+                    }
+                    // descriptors are linear in the address (16-byte units in
+                    // the low bits): one per slice, plus 2 per 16-wide K step
+                    const uint64_t db0 = sdesc(bset + bs * kBBytes);
+                    for (int ii = 0; ii < kDigits; ++ii) {
+                        const int i = slice_order(ii);
+                        const uint32_t as = na % kASlots;
+                        if (!bar_wait(&afull[as], (na / kASlots) & 1)) {
+                            s_fail = 2;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                        const uint64_t da = sdesc(aslot + as * kABytes);
+                        const uint32_t first = (c == 0 && ii == 0) ? 0u : 1u;
+                        for (int j0 = 0; j0 < kDigits - i; j0 += per) {
+                            const int ns = min(per, kDigits - i - j0);
+                            const uint32_t idesc = idesc_for(ns * tn);
+                            const uint32_t acc_t = tmem + (uint32_t)((i + j0) * tn);
+                            const uint64_t db = db0 + (uint64_t)((j0 * tn * kRowBytes) >> 4);
+                            mma_f16(acc_t, da, db, idesc, first);
+                            mma_f16(acc_t, da + 2, db + 2, idesc, 1u);
+                            mma_f16(acc_t, da + 4, db + 4, idesc, 1u);
+                            mma_f16(acc_t, da + 6, db + 6, idesc, 1u);
+                        }
+                        mma_commit(&aempty[as]);
+                        ++na;
+                    }
+                    mma_commit(&bempty[bs]);
                 }
-                mma_commit(&aempty[as]);
-                ++na;
+                if (!s_fail) mma_commit(&accfull);
             }
-            mma_commit(&bempty[bs]);
-            if (c == nkb - 1) mma_commit(&accfull);
         }
     } else if (warp >= 2) {
         // ---------------- drain: warp w owns TMEM lanes 32 (w mod 4) .. + 31;
@@ -1265,7 +1277,8 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         stage_end(kStageGemm, s);
         return cudaSuccess;
     }
-    if (tiles > INT32_MAX || lcnt + TBM > INT32_MAX || hcnt + TBM > INT32_MAX) return cudaErrorInvalidConfiguration;
+    if (tiles * 3 * a.kblocks > INT32_MAX || lcnt + TBM > INT32_MAX || hcnt + TBM > INT32_MAX)
+        return cudaErrorInvalidConfiguration;
     a.lowbase = in.lowbase;
     a.ex_low = exlow;
     a.ex_high = exhigh;
