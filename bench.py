@@ -43,10 +43,10 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2, written between timed steps
 # from one ncu capture of the current kernel; None when no capture of the
 # current kernel exists.  FP64 products (gemm_kernel): dram__bytes_read.sum
 # 15.49 GB + dram__bytes_write.sum 0.51 GB.  Tensor-core products
-# (tc_product_kernel): 6.805 GB read + 0.903 GB written (one-pass capture of
+# (tc_product_kernel): 5.854 GB read + 0.872 GB written (one-pass capture of
 # the full workload, profiles/tc_products_m20n10.md).
 NCU_TRAFFIC_PER_LAUNCH = 16.00e9
-NCU_TRAFFIC_TC_PER_LAUNCH = 7.708e9
+NCU_TRAFFIC_TC_PER_LAUNCH = 6.726e9
 
 
 def parse():
