@@ -490,9 +490,10 @@ int pcv_fp64_probe(double* out, int blocks, int threads, int iters, void* stream
 
 /* Stage timing for measurement.  pcv_profile_enable(1) makes the library
  * record CUDA events on the launching stream around each stage of a call
- * (stage 0: factorised-distribution tables, 1: factorised-distribution
- * products, 2: plain Glynn kernels, 3: digit splitting of the tensor-core
- * products, 4: the FP64 single-entry blocks beside the tensor-core products,
+ * (stage 0: factorised-distribution tables, with PCV_ALGO_FACTOR_TC their
+ * digits too, 1: factorised-distribution products, 2: plain Glynn kernels,
+ * 3: PCV_ALGO_FACTOR_TC's per-mode vectors of the single-entry columns and
+ * their digits, 4: the FP64 single-entry blocks of PCV_ALGO_FACTOR_TC,
  * n = 1 or m = 1 only).  pcv_profile_read waits for the recorded
  * events, writes the accumulated milliseconds and call counts of the first
  * `nstages` stages to ms[] and calls[] (host) and resets them.
