@@ -191,3 +191,17 @@ def test_distinguishability_arguments_are_checked():
     assert _abi.pcv_distribution_source_size(6, 3) == sum(math.comb(6 + k - 1, k) for k in range(4))
     cls[0, 0], cls[1, 1] = 2, 1
     assert _abi.pcv_distribution_classes_workspace(4, 2, cls) > 0
+
+
+def test_tensor_core_workspace_sizes(lib):
+    # host-only: the factorised tensor-core path's workspace (digit tensors of
+    # table levels 1..n-1, parents, two products per output, single-entry data)
+    from paper_2204_00602_gb300 import _abi
+    ws = _abi.pcv_distribution_tc_workspace(20, 10)
+    # 2 sides x 92,377 entries x 3 products x 8 digits x 512 sign vectors x 2 B
+    digits = 2 * 92377 * 3 * 8 * 512 * 2
+    assert digits < ws < digits + 1.1e9, ws
+    assert _abi.pcv_distribution_tc_workspace(20, 9) < ws
+    assert _abi.pcv_distribution_tc_workspace(12, 6) > 0
+    with pytest.raises(_abi.PcvError):
+        _abi.pcv_distribution_tc_workspace(20, 11)              # K = 2^{n-1} <= 512
