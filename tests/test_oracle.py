@@ -358,6 +358,53 @@ def test_clements_mesh_is_unitary_with_66_mzis():
     assert np.abs(U.conj().T @ U - np.eye(12)).max() < 1e-14
 
 
+# A mesh whose MZIs are each in the cross state (phi_a = 0, phi_b = 0: the
+# 2x2 block [[0, i], [i, 0]]) or the bar state (phi_a = pi, phi_b = 0: the
+# block [[-1, 0], [0, 1]]) is a permutation matrix with phases.  The matrices
+# below were traced by hand, following each input photon through the MZIs in
+# the order they act (the first MZI of the list acts first), so a reversed
+# composition order, a swapped column parity or a transposed result fails
+# them: every unitary mesh passes the unitarity test above, these do not.
+CROSS, BAR = (0.0, 0.0), (np.pi, 0.0)
+
+
+def test_clements_layout_written_out():
+    # column c acts on the pairs (k, k+1) with k = c mod 2, c mod 2 + 2, ...
+    assert oracle.clements_pairs(3) == [0, 1, 0]
+    assert oracle.clements_pairs(4) == [0, 2, 1, 0, 2, 1]
+
+
+def test_mesh_cross_bar_three_modes_is_a_three_cycle():
+    # MZIs on (0,1), (1,2), (0,1): cross, cross, bar.  Photon 0: -> 1 (i) -> 2
+    # (i): U[2][0] = -1.  Photon 1: -> 0 (i), bar gives -1 on mode 0: U[0][1] =
+    # -i.  Photon 2: -> 1 (i), bar leaves mode 1: U[1][2] = i.
+    U = oracle.mesh(np.array([*CROSS, *CROSS, *BAR]))
+    want = np.array([[0, -1j, 0], [0, 0, 1j], [-1, 0, 0]])
+    assert np.abs(U - want).max() < 1e-15
+
+
+def test_mesh_cross_bar_four_modes():
+    # MZIs on (0,1), (2,3), (1,2), (0,1), (2,3), (1,2): cross, bar, cross, bar,
+    # bar, cross.  Photon 0: -> 1 (i) -> 2 (i), bar on (2,3) as the upper mode
+    # (-1), -> 1 (i): U[1][0] = i.  Photon 1: -> 0 (i), bar on (0,1) as the
+    # upper mode (-1): U[0][1] = -i.  Photon 2: bar as the upper mode (-1),
+    # -> 1 (i), bar on (0,1) as the lower mode (1), -> 2 (i): U[2][2] = 1.
+    # Photon 3: two bars as the lower mode: U[3][3] = 1.
+    U = oracle.mesh(np.array([*CROSS, *BAR, *CROSS, *BAR, *BAR, *CROSS]))
+    want = np.array([[0, -1j, 0, 0], [1j, 0, 0, 0], [0, 0, 1, 0], [0, 0, 0, 1]])
+    assert np.abs(U - want).max() < 1e-15
+
+
+@pytest.mark.parametrize("m", [4, 12])
+def test_mesh_all_cross_reverses_the_modes(m):
+    # every MZI crossed: the m columns of the rectangular mesh carry photon k to
+    # mode m-1-k through m-1 crossings (m(m-1)/2 MZIs, two photons each), so
+    # U = i^(m-1) times the anti-diagonal
+    U = oracle.mesh(np.tile(np.array(CROSS), m * (m - 1) // 2))
+    want = (1j ** (m - 1)) * np.fliplr(np.eye(m))
+    assert np.abs(U - want).max() < 1e-14
+
+
 def test_tvd_and_kl_basics():
     p = pin.dirichlet_target(50, 1)
     q = pin.dirichlet_target(50, 2)
