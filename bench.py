@@ -2,13 +2,14 @@
 
 One step = every amplitude and probability of the 20,030,010 outputs of a
 Haar-random 20x20 unitary with photons in modes 0..9 (Eq. eqperm, Sec. 4.2),
-computed by the CUDA library through its C ABI.  The default path is the
-factorised Glynn sum with its complex products on the tensor cores as exact
-integer digit products (--algo factor_tc); --algo factor runs the same sum
-with FP64 products, which the JSON line also reports as context.
+computed by the CUDA library through its C ABI entry point pcv_distribution.
+At this size that call takes the factorised Glynn sum with its complex
+products on the tensor cores as exact integer digit products (--algo auto,
+the default, = factor_tc here); --algo factor runs the same sum with FP64
+products, which the JSON line also reports as context.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--algo factor_tc|factor|group|slos]
+                    [--algo auto|factor_tc|factor|group|slos]
 
 Prints one JSON line (rank 0).  `value` is amplitudes/s over all ranks with
 inputs resident in HBM; `e2e` is the same metric through the public API with
@@ -39,14 +40,33 @@ def workload_text(m, n, count):
             "outputs, complex FP64 amplitudes and probabilities")
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2, written between timed steps
 
-# DRAM bytes (read + write) of one launch of the dominant kernel, m=20 n=10,
-# from one ncu capture of the current kernel; None when no capture of the
-# current kernel exists.  FP64 products (gemm_kernel): dram__bytes_read.sum
-# 15.49 GB + dram__bytes_write.sum 0.51 GB.  Tensor-core products
-# (tc_product_kernel): 5.854 GB read + 0.872 GB written (one-pass capture of
-# the full workload, profiles/tc_products_m20n10.md).
-NCU_TRAFFIC_PER_LAUNCH = 16.00e9
-NCU_TRAFFIC_TC_PER_LAUNCH = 6.726e9
+# Per-launch DRAM traffic of the dominant kernels comes from ncu records
+# committed beside the profile summaries; each names the SHA-256 of the CUDA
+# source it was taken from, and a record whose source has changed since is
+# not used (traffic = null).
+TRAFFIC_RECORDS = {"factor_tc": ("tc_product_kernel_traffic.txt", "glynn_tc.cu"),
+                   "factor": ("gemm_kernel_traffic.txt", "glynn_dist.cu")}
+
+
+def recorded_traffic(algo: str, m: int, n: int):
+    """(bytes per launch, note) from the kernel's traffic record, or (None, why)."""
+    import hashlib
+    if algo not in TRAFFIC_RECORDS:
+        return None, "no traffic record for this kernel"
+    rec, src = TRAFFIC_RECORDS[algo]
+    try:
+        with open(os.path.join(ROOT, "profiles", rec)) as f:
+            kv = dict(line.split(":", 1) for line in f if ":" in line and not line.startswith("#"))
+        kv = {k.strip(): v.strip() for k, v in kv.items()}
+        with open(os.path.join(ROOT, "paper_2204_00602_gb300", "csrc", src), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None, "no traffic record for this kernel"
+    if kv.get("source_sha256") != sha:
+        return None, f"the kernel changed since its ncu traffic record ({rec})"
+    if (int(kv.get("m", -1)), int(kv.get("n", -1))) != (m, n):
+        return None, f"the traffic record is for another workload ({rec})"
+    return float(kv["read_bytes"]) + float(kv["write_bytes"]), f"ncu record {rec} of the current source"
 
 
 def parse():
@@ -55,8 +75,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="factor_tc", choices=["factor", "factor_tc", "group", "slos"],
-                    help="factor: factorised Glynn (default); group: plain Glynn; slos: state expansion")
+    ap.add_argument("--algo", default="auto", choices=["auto", "factor", "factor_tc", "group", "slos"],
+                    help="auto: pcv_distribution's own choice (default); factor / factor_tc: factorised Glynn "
+                         "with FP64 / tensor-core products; group: plain Glynn; slos: state expansion")
+    ap.add_argument("--shard", action="store_true",
+                    help="split ONE distribution into contiguous canonical output ranges, one per rank "
+                         "(pcv_distribution_range; strong scaling) instead of one distribution per rank")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -194,20 +218,35 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
 
-    U_h = pin.haar_unitary(M, rank_unitary_seed(rank))
+    U_h = pin.haar_unitary(M, rank_unitary_seed(0 if args.shard else rank))
     t = pin.single_photon_input(M, N_PH)
     Ntot = pcv.num_outputs(M, N_PH)
-    algo = {"factor": pcv.PCV_ALGO_FACTOR, "factor_tc": pcv.PCV_ALGO_FACTOR_TC, "group": pcv.PCV_ALGO_GROUP,
-            "slos": pcv.PCV_ALGO_SLOS}[args.algo]
+    algo = {"auto": pcv.PCV_ALGO_AUTO, "factor": pcv.PCV_ALGO_FACTOR, "factor_tc": pcv.PCV_ALGO_FACTOR_TC,
+            "group": pcv.PCV_ALGO_GROUP, "slos": pcv.PCV_ALGO_SLOS}[args.algo]
     param = 32 if args.algo == "group" else 0
     U = torch.from_numpy(U_h).to(dev)
-    prob = torch.empty(Ntot, dtype=torch.float64, device=dev)
-    amp = torch.empty(Ntot, dtype=torch.complex128, device=dev)
-    ws = pcv.workspace(pcv.distribution_workspace_bytes(M, N_PH, algo, param), dev)
+    # --shard: this rank's canonical range [lo, hi) of the one distribution
+    lo, hi = (Ntot * rank // world, Ntot * (rank + 1) // world) if args.shard else (0, Ntot)
+    if args.shard and args.algo not in ("auto", "factor", "factor_tc"):
+        raise SystemExit("--shard runs the factorised distribution (algo auto, factor or factor_tc)")
+    prob = torch.empty(hi - lo, dtype=torch.float64, device=dev)
+    amp = torch.empty(hi - lo, dtype=torch.complex128, device=dev)
+    ws_bytes = pcv.distribution_workspace_bytes(M, N_PH, algo, param)
+    ws = pcv.workspace(ws_bytes, dev)
+    # the path pcv_distribution takes with this workspace (the roofline's kernel)
+    kind = args.algo
+    if args.algo == "auto":
+        kind = "factor_tc" if abi.pcv_distribution_auto_algo(M, N_PH, ws_bytes) == pcv.PCV_ALGO_FACTOR_TC else "factor"
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    def dist_call(Uc, out):
+        if args.shard:
+            pcv.distribution_range(Uc, t, lo, hi, ws=ws, out=out)
+        else:
+            pcv.distribution(Uc, t, algo=algo, param=param, ws=ws, out=out)
+
     def step():
-        pcv.distribution(U, t, algo=algo, param=param, ws=ws, out=(prob, amp))
+        dist_call(U, (prob, amp))
 
     for _ in range(args.warmup):
         step()
@@ -250,10 +289,13 @@ def run_ours(args):
     abi.pcv_profile_enable(False)
     stages = abi.pcv_profile_read()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if args.algo in ("auto", "factor", "factor_tc"):
+        abi.pcv_distribution_status(ws, stream.cuda_stream)      # raises if a bounded wait gave up
     t_dev = max_over_ranks(sum(step_ms) / 1e3, world, dev)
     if world > 1:
         torch.distributed.barrier()
-    value = whole_job_rate(Ntot, args.steps, world, t_dev)
+    # weak: every rank a whole distribution; strong (--shard): one between them
+    value = Ntot * args.steps / t_dev if args.shard else whole_job_rate(Ntot, args.steps, world, t_dev)
 
     # ---------------- end to end through the public API with host buffers
     e2e = None
@@ -277,7 +319,7 @@ def run_ours(args):
             b = i % 2
             U_d.copy_(U_pin, non_blocking=True)
             stream.wait_event(copied[b])                  # buffer b's previous D2H has finished
-            pcv.distribution(U_d, t, algo=algo, param=param, ws=ws, out=dev_out[b])
+            dist_call(U_d, dev_out[b])
             computed[b].record(stream)
             copy_stream.wait_event(computed[b])
             with torch.cuda.stream(copy_stream):
@@ -298,7 +340,8 @@ def run_ours(args):
         ee.record(stream)
         torch.cuda.synchronize()
         te = max_over_ranks(es.elapsed_time(ee) / 1e3, world, dev)
-        e2e = {"value": whole_job_rate(Ntot, args.steps, world, te), "unit": "amplitudes/s",
+        e2e = {"value": (Ntot * args.steps / te) if args.shard else whole_job_rate(Ntot, args.steps, world, te),
+               "unit": "amplitudes/s",
                "h2d_bytes_per_step": U_pin.numel() * 16,
                "d2h_bytes_per_step": host_out[0][0].numel() * 8 + host_out[0][1].numel() * 16,
                "pipeline": "results double-buffered; the D2H of step i overlaps the compute of step i+1"}
@@ -311,12 +354,12 @@ def run_ours(args):
     # ---------------- roofline of the dominant kernel (FP64 ALU bound)
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak_tflops = sms * 4 * sm_max * 1e6 / 1e12        # 2 DFMA/clk/SM x 2 flop
-    if args.algo == "factor":
+    if kind == "factor":
         ms, calls = stages["dist_products"]
-        flops_per_call = Ntot * (2 ** (N_PH - 1)) * 6     # 3 DFMA per output and sign vector
+        flops_per_call = (hi - lo) * (2 ** (N_PH - 1)) * 6     # 3 DFMA per output and sign vector
         kname = "gemm_kernel (factorised Glynn products, 3 DFMA per output and sign vector)"
         launches_per_call = 1
-    elif args.algo == "factor_tc":
+    elif kind == "factor_tc":
         # BF16 tensor-core work: 3 real products x 36 digit pairs x 2 flops per
         # output and sign vector (useful outputs only)
         ms, calls = stages["dist_products"]
@@ -325,12 +368,12 @@ def run_ours(args):
         # vector per mode; products whose mode is below the row's largest are
         # computed and dropped, not counted); else those two blocks run in FP64
         h = max(1, M // 2)
-        n_tc = Ntot if (N_PH >= 2 and M - h >= 1) else \
+        n_tc = (hi - lo) if (N_PH >= 2 and M - h >= 1) else \
             Ntot - math.comb(M - h + N_PH - 1, N_PH) - math.comb(h + N_PH - 1, N_PH)
         flops_per_call = n_tc * (2 ** (N_PH - 1)) * 3 * 36 * 2
         kname = "tc_product_kernel (exact-digit BF16 tcgen05 products, 36 digit pairs x 3 real products)"
         launches_per_call = 1
-    elif args.algo == "group":
+    elif kind == "group":
         ms, calls = stages["glynn_plain"]
         flops_per_call = Ntot * (2 ** (N_PH - 1)) * (8 * N_PH - 4)
         kname = "glynn_group_kernel<10,32> (plain Glynn)"
@@ -347,21 +390,21 @@ def run_ours(args):
     achieved = flops_per_call * calls / (ms * 1e-3) / 1e12 if ms > 0 and flops_per_call else None
     peak_src = f"derived: {sms} SMs x 2 DFMA/clk x 2 flop x {sm_max:.0f} MHz (FP64 ALU)"
     bound = "alu"
-    if args.algo == "factor_tc":
+    if kind == "factor_tc":
         peak_tflops, bound = measured_bf16_peak(), "tensor"
         peak_src = "MEASURED_PEAKS.json bf16_tflops (burst cuBLAS bf16 GEMM, measured)"
+    traffic, traffic_note = recorded_traffic(kind, M, N_PH)
     roof = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops if achieved else None,
             "peak_source": peak_src,
             "fp64_probe_tflops": probe_tflops,
-            "traffic": (NCU_TRAFFIC_PER_LAUNCH if (M, N_PH, args.algo) == (20, 10, "factor") else
-                        NCU_TRAFFIC_TC_PER_LAUNCH if (M, N_PH, args.algo) == (20, 10, "factor_tc") else None),
+            "traffic": traffic, "traffic_source": traffic_note,
             "launches_per_step": launches_per_call,
             "stage_ms_per_step": {k: (v[0] / v[1] if v[1] else None) for k, v in stages.items()}}
 
     # context: the FP64 factorised path (its product kernel against the FP64 peak)
     fp64_ctx = None
-    if args.algo == "factor_tc" and not args.no_e2e:
+    if kind == "factor_tc" and not args.no_e2e:
         ws_f = pcv.workspace(pcv.distribution_workspace_bytes(M, N_PH, pcv.PCV_ALGO_FACTOR), dev)
         for _ in range(2):
             pcv.distribution(U, t, algo=pcv.PCV_ALGO_FACTOR, ws=ws_f, out=(prob, amp))
@@ -389,7 +432,7 @@ def run_ours(args):
 
     # context: the same workload by photon-by-photon state expansion (not the Glynn path)
     alt = None
-    if args.algo in ("factor", "factor_tc") and not args.no_e2e:
+    if kind in ("factor", "factor_tc") and not args.no_e2e:
         ws_s = pcv.workspace(pcv.distribution_workspace_bytes(M, N_PH, pcv.PCV_ALGO_SLOS), dev)
         for _ in range(2):
             pcv.distribution(U, t, algo=pcv.PCV_ALGO_SLOS, ws=ws_s, out=(prob, amp))
@@ -412,15 +455,18 @@ def run_ours(args):
     line = {
         "metric": f"amplitudes/s (m={M} n={N_PH} full distribution, complex FP64)",
         "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "strong" if args.shard else "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "dtype_note": None if args.algo != "factor_tc" else
+        "dtype_note": None if kind != "factor_tc" else
         "FP64 tables, scaling and results; the complex products run as exact integer digit products "
         "on the bf16 tensor cores (no rounding; agreement with the FP64 path to 1e-11)",
         "data": "synthetic",
-        "config": {"workload": workload_text(M, N_PH, Ntot), "m": M, "n": N_PH, "outputs": Ntot, "algo": args.algo,
-                   "l2": "flushed between steps (256 MiB write, untimed)", "parallelism": f"replicas{world}"},
+        "config": {"workload": workload_text(M, N_PH, Ntot), "m": M, "n": N_PH, "outputs": Ntot, "algo": kind,
+                   "entry_point": "pcv_distribution" if args.algo == "auto" else "pcv_distribution_ex",
+                   "l2": "flushed between steps (256 MiB write, untimed)",
+                   "parallelism": f"output-range shards x{world}" if args.shard else f"replicas{world}"},
         "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "state_expansion": alt,
         "fp64_factor_path": fp64_ctx,

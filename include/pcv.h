@@ -197,23 +197,60 @@ int pcv_amplitudes_batched_ex(const pcv_batch_desc* descs, int n_circ, int64_t t
 int64_t pcv_distribution_tc_workspace(int m, int n);
 
 /* Workspace bytes pcv_distribution needs for m modes and n photons with the
- * default plan.  A smaller workspace (>= pcv_distribution_workspace_min) is
- * accepted and processed in more passes. */
+ * default plan: for 2 <= n <= 10 and m >= 2 the single-pass plan of the
+ * tensor-core products (= pcv_distribution_tc_workspace), otherwise the FP64
+ * plan.  A smaller workspace (>= pcv_distribution_workspace_min) is accepted:
+ * pcv_distribution then takes the FP64 products, in more passes if needed. */
 int64_t pcv_distribution_workspace(int m, int n);
 int64_t pcv_distribution_workspace_min(int m, int n);
+
+/* The algorithm pcv_distribution (PCV_ALGO_AUTO) runs for m modes, n photons
+ * and a workspace of workspace_bytes: PCV_ALGO_FACTOR_TC when 2 <= n <= 10,
+ * m >= 2 and workspace_bytes >= pcv_distribution_tc_workspace(m, n), else
+ * PCV_ALGO_FACTOR.  Both give the same amplitudes to double precision.  Returns
+ * the algorithm code, or PCV_EINVAL for sizes out of range.  No counterpart in
+ * the paper. */
+int pcv_distribution_auto_algo(int m, int n, int64_t workspace_bytes);
 
 /* Every output of S_{m,n} in canonical order (the SLOS back-end's full
  * distribution, Sec. 3.2.3, computed here from Eq. eqperm).
  *   prob  device, C(m+n-1,n) doubles (written) or NULL
  *   amp   device, C(m+n-1,n) pcv_c64 (written) or NULL; not both NULL
- * The default algorithm factorises Glynn's sum: with sign vectors on the
- * input photons, every output shares the per-mode row sums
+ * The algorithm factorises Glynn's sum: with sign vectors on the input
+ * photons, every output shares the per-mode row sums
  * y_r(d) = sum_j d_j U[r][c_j], and a(S) = sum_d (sign, scale) prod_r y_r(d)^{s_r};
  * the product splits into the modes below and above m/2, so each output costs
- * one complex multiply-add per sign vector. */
+ * one complex multiply-add per sign vector.  Those products run on the tensor
+ * cores in exact integer arithmetic (PCV_ALGO_FACTOR_TC below) when the input
+ * has 2..10 photons and the workspace holds that plan, else as FP64 multiply-
+ * adds (PCV_ALGO_FACTOR); pcv_distribution_auto_algo tells which. */
 int pcv_distribution(const pcv_c64* U, int m, const uint8_t* input_occ,
                      double* prob, pcv_c64* amp,
                      void* workspace, int64_t workspace_bytes, void* stream);
+
+/* The outputs of pcv_distribution with canonical index in [begin, end), for
+ * splitting one distribution across devices or processes (each takes a
+ * contiguous range of the canonical order, 0 <= begin <= end <=
+ * C(m+n-1,n)).  Output i is written at prob[i - begin] and amp[i - begin]
+ * (end - begin entries each; either may be NULL, not both).  Same algorithm
+ * choice, workspace and errors as pcv_distribution, and the same result for
+ * every output, bit for bit: the ranges of a partition of [0, C(m+n-1,n))
+ * together give exactly pcv_distribution's arrays.  Work scales with the
+ * range for the products; the per-mode row sums and factor tables (about a
+ * third of the time at m=20, n=10) are built whole by every call.  The paper
+ * has no counterpart (its workers split samples, Sec. 4.2). */
+int pcv_distribution_range(const pcv_c64* U, int m, const uint8_t* input_occ, int64_t begin, int64_t end,
+                           double* prob, pcv_c64* amp, void* workspace, int64_t workspace_bytes, void* stream);
+
+/* Host-only view of how pcv_distribution_range splits its work.  Let P be
+ * the photons of an output in modes [0, h), h = max(1, m / 2), a multiset of
+ * size k ranked at its level k in canonical order.  The outputs sharing P
+ * form one contiguous block of the canonical order, and at a fixed k the
+ * blocks follow P's rank, so [begin, end) meets the blocks of the P of ranks
+ * [pa[k], pb[k]) at each k = 0..n (empty when pa[k] == pb[k]); those are the
+ * rows or columns of the products the range computes.  pa, pb: host arrays of
+ * n + 1 entries (written).  Errors as pcv_distribution_range. */
+int pcv_distribution_range_plan(int m, int n, int64_t begin, int64_t end, int64_t* pa, int64_t* pb);
 
 /* Full distributions of B unitaries with the same input state (the
  * factorised algorithm of pcv_distribution, all B in the same launches).
@@ -479,6 +516,29 @@ int pcv_exp_f32_to_f64(const float* in, int64_t count, double* out, void* stream
 int pcv_distribution_static(const pcv_c64* U, int m, const uint8_t* input_occ,
                             double* prob, pcv_c64* amp, void* stream);
 int64_t pcv_distribution_static_max_bytes(void);
+
+/* ------------------------------------------------ failure detection */
+
+/* Status of the last pcv_distribution / pcv_distribution_ex /
+ * pcv_distribution_batched call that used `workspace` (device): waits for
+ * `stream` (the call's stream), then returns PCV_OK, or PCV_ETIMEOUT when a
+ * bounded wait inside the tensor-core product kernel gave up, in which case
+ * the outputs of that call are not valid (pcv_last_error names the role that
+ * gave up).  The first 256 bytes of a distribution workspace hold this status
+ * word; each call sets it to zero before its kernels run.  The kernels never
+ * wait on other blocks or devices, so a time-out means a stalled copy or
+ * tensor-core operation inside one block; the block then waits, again with a
+ * bound, for its own copies and MMAs in flight, releases its tensor memory and
+ * returns.  No counterpart in the paper. */
+int pcv_distribution_status(const void* workspace, void* stream);
+
+/* Number of polls after which one mbarrier wait of the tensor-core kernels
+ * (distribution products, pcv_gemm_bf16_tc) gives up: polls >= 1 sets it for
+ * later launches, 0 restores each kernel's default (2^26 and 2^22 polls).  A
+ * small value makes the waits run out, so the time-out path can be exercised
+ * without a fault; it is a testing aid.  Returns PCV_OK or PCV_EINVAL (polls
+ * < 0).  No counterpart in the paper. */
+int pcv_set_wait_limit(int64_t polls);
 
 /* -------------------------------------------------- measurement helpers */
 

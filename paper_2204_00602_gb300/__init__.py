@@ -19,7 +19,7 @@ from ._abi import (PCV_ALGO_AUTO, PCV_ALGO_BLOCK, PCV_ALGO_FACTOR, PCV_ALGO_GROU
                    PCV_MAX_PHOTONS, PcvError)
 
 __all__ = ["amplitudes", "amplitudes_batched", "BatchPlan", "distribution", "distribution_batched",
-           "distribution_classes", "source_distribution", "sample", "num_outputs", "unrank", "rank",
+           "distribution_range", "distribution_status", "distribution_classes", "source_distribution", "sample", "num_outputs", "unrank", "rank",
            "fp64_probe", "PcvError", "PCV_ALGO_AUTO", "PCV_ALGO_GROUP", "PCV_ALGO_BLOCK", "PCV_ALGO_FACTOR",
            "PCV_ALGO_TILE", "PCV_ALGO_SLOS", "PCV_ALGO_MULT", "PCV_ALGO_FACTOR_TC", "abi"]
 
@@ -151,8 +151,10 @@ def amplitudes_batched(circuits, want_prob: bool = True, algo: int = PCV_ALGO_AU
 
 
 def distribution_workspace_bytes(m: int, n: int, algo: int = PCV_ALGO_AUTO, param: int = 0) -> int:
-    if algo in (PCV_ALGO_AUTO, PCV_ALGO_FACTOR):
+    if algo == PCV_ALGO_AUTO:
         return abi.pcv_distribution_workspace(m, n)
+    if algo == PCV_ALGO_FACTOR:
+        return abi.pcv_distribution_batched_workspace(1, m, n)
     if algo == PCV_ALGO_SLOS:
         return abi.pcv_distribution_slos_workspace(1, m, n)
     if algo == PCV_ALGO_FACTOR_TC:
@@ -182,9 +184,41 @@ def distribution(U: torch.Tensor, input_occ, *, want_amp: bool = True, algo: int
         amp = torch.empty(N, dtype=torch.complex128, device=U.device) if want_amp else None
     if ws is None:
         ws = workspace(distribution_workspace_bytes(m, n, algo, param), U.device)
-    abi.pcv_distribution_ex(U, m, t, prob, amp, algo, param, ws, 0 if ws is None else ws.numel(),
-                            _stream(U.device))
+    nbytes = 0 if ws is None else ws.numel()
+    if algo == PCV_ALGO_AUTO:
+        abi.pcv_distribution(U, m, t, prob, amp, ws, nbytes, _stream(U.device))
+    else:
+        abi.pcv_distribution_ex(U, m, t, prob, amp, algo, param, ws, nbytes, _stream(U.device))
     return prob, amp
+
+
+def distribution_range(U: torch.Tensor, input_occ, begin: int, end: int, *, want_amp: bool = True,
+                       ws: torch.Tensor | None = None, out=None):
+    """The outputs of `distribution` with canonical index in [begin, end):
+    (prob float64 [end - begin], amp complex128 [end - begin] or None), output
+    i at position i - begin.  The ranges of a partition of [0, N) together
+    give exactly `distribution`'s arrays."""
+    m = _check_U(U)
+    t = _host_occ(input_occ, m)
+    n = int(t.sum())
+    U = U.contiguous()
+    if out is not None:
+        prob, amp = out
+    else:
+        prob = torch.empty(end - begin, dtype=torch.float64, device=U.device)
+        amp = torch.empty(end - begin, dtype=torch.complex128, device=U.device) if want_amp else None
+    if ws is None:
+        ws = workspace(abi.pcv_distribution_workspace(m, n), U.device)
+    abi.pcv_distribution_range(U, m, t, begin, end, prob, amp, ws, 0 if ws is None else ws.numel(),
+                               _stream(U.device))
+    return prob, amp
+
+
+def distribution_status(ws: torch.Tensor) -> int:
+    """Wait for the current stream, then PCV_OK, or PcvError(PCV_ETIMEOUT) if a
+    bounded wait of the tensor-core kernels gave up in the last distribution
+    call that used workspace `ws`."""
+    return abi.pcv_distribution_status(ws, _stream(ws.device))
 
 
 def distribution_classes(U: torch.Tensor, classes, ws: torch.Tensor | None = None) -> torch.Tensor:

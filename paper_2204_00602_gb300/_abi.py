@@ -54,8 +54,11 @@ SIGNATURES = {
     "pcv_distribution_workspace": (_i64, [_i, _i]),
     "pcv_distribution_tc_workspace": (_i64, [_i, _i]),
     "pcv_distribution_workspace_min": (_i64, [_i, _i]),
+    "pcv_distribution_auto_algo": (_i, [_i, _i, _i64]),
     "pcv_distribution": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
     "pcv_distribution_ex": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _vp, _i64, _vp]),
+    "pcv_distribution_range": (_i, [_vp, _i, _vp, _i64, _i64, _vp, _vp, _vp, _i64, _vp]),
+    "pcv_distribution_range_plan": (_i, [_i, _i, _i64, _i64, _vp, _vp]),
     "pcv_distribution_batched_workspace": (_i64, [_i, _i, _i]),
     "pcv_distribution_batched": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
     "pcv_distribution_slos_workspace": (_i64, [_i, _i, _i]),
@@ -101,6 +104,8 @@ SIGNATURES = {
     "pcv_profile_enable": (_i, [_i]),
     "pcv_profile_read": (_i, [_vp, _vp, _i]),
     "pcv_launch_count": (_i64, []),
+    "pcv_distribution_status": (_i, [_vp, _vp]),
+    "pcv_set_wait_limit": (_i, [_i64]),
 }
 
 for _name, (_res, _args) in SIGNATURES.items():
@@ -185,8 +190,27 @@ def pcv_distribution_tc_workspace(m, n) -> int:
     return _call("pcv_distribution_tc_workspace", m, n)
 
 
+def pcv_distribution_auto_algo(m, n, workspace_bytes) -> int:
+    return _call("pcv_distribution_auto_algo", m, n, workspace_bytes)
+
+
 def pcv_distribution_workspace_min(m, n) -> int:
     return _call("pcv_distribution_workspace_min", m, n)
+
+
+def pcv_distribution_range(U, m, input_occ, begin, end, prob, amp, workspace, workspace_bytes, stream):
+    return _call("pcv_distribution_range", ptr(U), m, ptr(input_occ), begin, end, ptr(prob), ptr(amp),
+                 ptr(workspace), workspace_bytes, stream)
+
+
+def pcv_distribution_range_plan(m, n, begin, end):
+    """[(pa[k], pb[k]) for k = 0..n]: the ranks of the low-side multisets whose
+    outputs meet [begin, end)."""
+    import numpy as np
+    pa = np.zeros(n + 1, dtype=np.int64)
+    pb = np.zeros(n + 1, dtype=np.int64)
+    _call("pcv_distribution_range_plan", m, n, begin, end, pa.ctypes.data, pb.ctypes.data)
+    return list(zip(pa.tolist(), pb.tolist()))
 
 
 def pcv_distribution(U, m, input_occ, prob, amp, workspace, workspace_bytes, stream):
@@ -397,3 +421,11 @@ def pcv_profile_read():
 
 def pcv_launch_count() -> int:
     return int(_lib.pcv_launch_count())
+
+
+def pcv_distribution_status(workspace, stream):
+    return _call("pcv_distribution_status", ptr(workspace), stream)
+
+
+def pcv_set_wait_limit(polls):
+    return _call("pcv_set_wait_limit", polls)

@@ -189,15 +189,16 @@ __global__ void level_kernel(const LevelArgs a)
 // fixed order, written at its canonical index.
 __global__ void edge_reduce_kernel(const double2* __restrict__ partial, int64_t count, int ngroups,
                                    const int64_t* __restrict__ lowbase, int64_t lowidx, int strip_is_low,
-                                   double2* __restrict__ amp, double* __restrict__ prob)
+                                   int64_t lo, int64_t hi, double2* __restrict__ amp, double* __restrict__ prob)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
+    const int64_t o = strip_is_low ? lowbase[lowidx + i] : lowbase[lowidx] + i;
+    if (o < lo || o >= hi) return;
     double2 v = partial[i * ngroups];
     for (int g = 1; g < ngroups; ++g) v = cadd(v, partial[i * ngroups + g]);
-    const int64_t o = strip_is_low ? lowbase[lowidx + i] : lowbase[lowidx] + i;
-    if (amp) amp[o] = v;
-    if (prob) prob[o] = fma(v.x, v.x, v.y * v.y);
+    if (amp) amp[o - lo] = v;
+    if (prob) prob[o - lo] = fma(v.x, v.x, v.y * v.y);
 }
 
 struct GemmArgs {
@@ -208,12 +209,16 @@ struct GemmArgs {
     int64_t wlow, whigh, tstride_low, tstride_high;
     int64_t lowoff[PCV_MAX_PHOTONS + 1], highoff[PCV_MAX_PHOTONS + 1];  // per k: level k low, level n-k high
     int64_t M[PCV_MAX_PHOTONS + 1], N[PCV_MAX_PHOTONS + 1];
+    // entries of the fixed and strip sides this launch covers, per k: one of
+    // them is the range of P whose outputs meet [lo, hi), the other complete
+    int64_t fb[PCV_MAX_PHOTONS + 1], fe[PCV_MAX_PHOTONS + 1], sb[PCV_MAX_PHOTONS + 1], se[PCV_MAX_PHOTONS + 1];
     int64_t tile0[PCV_MAX_PHOTONS + 2];   // first tile of each k
     int nk;
     const int64_t* lowbase;
     int kc;
     int first, last;       // first / last chunk of sign vectors
-    int64_t out_stride;    // outputs per batch entry
+    int64_t lo, hi;        // outputs written: canonical [lo, hi), at o - lo
+    int64_t out_stride;    // outputs per batch entry (hi - lo)
     double2* acc;          // running sums between chunks (= amp when amplitudes are wanted)
     double2* amp;
     double* prob;
@@ -230,12 +235,12 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs a)
     while (k + 1 < a.nk && a.tile0[k + 1] <= tile) ++k;
     const int64_t M = a.M[k], N = a.N[k];
     const bool qstrip = N >= M;
-    const int64_t nfixed = qstrip ? M : N, nstrip = qstrip ? N : M;
-    const int64_t strip_tiles = (nstrip + 32 * kStrip - 1) / (32 * kStrip);
+    const int64_t strip_tiles = (a.se[k] - a.sb[k] + 32 * kStrip - 1) / (32 * kStrip);
     const int64_t lt = tile - a.tile0[k];
-    const int64_t fixed = (lt / strip_tiles) * kWarps + warp;
-    if (fixed >= nfixed) return;
-    const int64_t s0 = (lt % strip_tiles) * (32 * kStrip) + lane;
+    const int64_t fixed = a.fb[k] + (lt / strip_tiles) * kWarps + warp;
+    if (fixed >= a.fe[k]) return;
+    const int64_t nstrip = a.se[k];
+    const int64_t s0 = a.sb[k] + (lt % strip_tiles) * (32 * kStrip) + lane;
     const int b = blockIdx.y;
 
     const double2* Tl = a.Tlow + (size_t)b * a.tstride_low + a.lowoff[k];
@@ -282,12 +287,13 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs a)
     double* prob = a.prob ? a.prob + (size_t)b * a.out_stride : nullptr;
 #pragma unroll
     for (int t = 0; t < kStrip; ++t) {
-        if (!sv[t]) continue;
+        if (!sv[t] || oidx[t] < a.lo || oidx[t] >= a.hi) continue;
+        const int64_t o = oidx[t] - a.lo;
         double2 v = make_double2(t1[t] - t2[t], t3[t] - t1[t] - t2[t]);
-        if (!a.first) v = cadd(v, acc[oidx[t]]);
-        if (!a.last) { acc[oidx[t]] = v; continue; }
-        if (amp) amp[oidx[t]] = v;
-        if (prob) prob[oidx[t]] = fma(v.x, v.x, v.y * v.y);
+        if (!a.first) v = cadd(v, acc[o]);
+        if (!a.last) { acc[o] = v; continue; }
+        if (amp) amp[o] = v;
+        if (prob) prob[o] = fma(v.x, v.x, v.y * v.y);
     }
 }
 
@@ -308,12 +314,13 @@ int64_t mset(int w, int k) { return k == 0 ? 1 : (w <= 0 ? 0 : binom_host(w + k 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t table, base, acc, y, tl, sl, th, sh, total;
+    size_t status, table, base, acc, y, tl, sl, th, sh, total;
 };
 
 Layout layout(int m, int n, int B, int64_t lo, int64_t hi, int64_t total, bool need_acc, int64_t kc)
 {
     Layout L;
+    L.status = 256;                          // the call's status word (pcv_distribution_status)
     L.table = align256((size_t)(m + 1) * (n + 1) * sizeof(int64_t));
     L.base = align256((size_t)lo * sizeof(int64_t));
     L.acc = need_acc ? align256((size_t)B * total * sizeof(double2)) : 0;
@@ -322,11 +329,85 @@ Layout layout(int m, int n, int B, int64_t lo, int64_t hi, int64_t total, bool n
     L.sl = align256((size_t)B * kc * lo * sizeof(double));
     L.th = align256((size_t)B * kc * hi * sizeof(double2));
     L.sh = align256((size_t)B * kc * hi * sizeof(double));
-    L.total = L.table + L.base + L.acc + L.y + L.tl + L.sl + L.th + L.sh;
+    L.total = L.status + L.table + L.base + L.acc + L.y + L.tl + L.sl + L.th + L.sh;
     return L;
 }
 
+// Host copies of the multiset walks: unrank a size-k multiset over w modes,
+// and the rank of a non-decreasing mode list.
+void host_unrank(int w, int k, int64_t idx, int* modes)
+{
+    int v = 0;
+    for (int p = 0; p < k; ++p) {
+        for (;;) {
+            const int64_t c = mset(w - v, k - p - 1);
+            if (idx < c) break;
+            idx -= c;
+            ++v;
+        }
+        modes[p] = v;
+    }
+}
+
+int64_t host_rank(int w, int k, const int* modes)
+{
+    int64_t r = 0;
+    int prev = 0;
+    for (int p = 0; p < k; ++p) {
+        for (int v = prev; v < modes[p]; ++v) r += mset(w - v, k - p - 1);
+        prev = modes[p];
+    }
+    return r;
+}
+
 }  // namespace
+
+int64_t host_lowbase(int m, int n, int h, int k, int64_t rank)
+{
+    int modes[PCV_MAX_PHOTONS];
+    host_unrank(h, k, rank, modes);
+    int64_t base = 0;
+    int prev = 0;
+    for (int p = 0; p < k; ++p) {
+        for (int v = prev; v < modes[p]; ++v) base += mset(m - v, n - p - 1);
+        prev = modes[p];
+    }
+    if (k < n)
+        for (int v = prev; v < h; ++v) base += mset(m - v, n - k - 1);
+    return base;
+}
+
+int64_t host_parent_rank(int w, int k, int64_t rank)
+{
+    int modes[PCV_MAX_PHOTONS];
+    host_unrank(w, k, rank, modes);
+    return host_rank(w, k - 1, modes);
+}
+
+void p_ranges(int m, int n, int h, int64_t lo, int64_t hi, PRanges* r)
+{
+    for (int k = 0; k <= n; ++k) {
+        const int64_t cnt = mset(h, k), blk = mset(m - h, n - k);
+        r->pa[k] = r->pb[k] = 0;
+        if (cnt <= 0 || blk <= 0 || lo >= hi) continue;
+        // lowbase grows with P's rank at a fixed level: bisect for the first
+        // block that ends after lo and the first that starts at or after hi
+        int64_t a0 = 0, a1 = cnt;
+        while (a0 < a1) {
+            const int64_t mid = a0 + (a1 - a0) / 2;
+            if (host_lowbase(m, n, h, k, mid) + blk > lo) a1 = mid;
+            else a0 = mid + 1;
+        }
+        int64_t b0 = a0, b1 = cnt;
+        while (b0 < b1) {
+            const int64_t mid = b0 + (b1 - b0) / 2;
+            if (host_lowbase(m, n, h, k, mid) >= hi) b1 = mid;
+            else b0 = mid + 1;
+        }
+        r->pa[k] = a0;
+        r->pb[k] = b0;
+    }
+}
 
 // Plan the workspace: the largest power-of-two chunk of sign vectors whose
 // tables fit into ws_bytes (ws_bytes < 0: the default budget of 8 GiB).
@@ -359,6 +440,7 @@ int64_t dist_plan(const Plan& p, int B, int64_t ws_bytes, bool need_acc, DistPla
     while (kc > 1 && layout(m, n, B, lo, hi, total, need_acc && kc < dmax, kc).total > budget) kc >>= 1;
     const Layout L = layout(m, n, B, lo, hi, total, need_acc && kc < dmax, kc);
     dp->kc = (int)kc;
+    dp->ws_status = L.status;
     dp->ws_table = L.table;
     dp->ws_base = L.base;
     dp->ws_acc = L.acc;
@@ -368,6 +450,8 @@ int64_t dist_plan(const Plan& p, int B, int64_t ws_bytes, bool need_acc, DistPla
     dp->ws_th = L.th;
     dp->ws_sh = L.sh;
     dp->ws_total = L.total;
+    dp->lo = 0;
+    dp->hi = total;
     return (int64_t)L.total;
 }
 
@@ -394,8 +478,8 @@ int64_t dist_plan_tc(const Plan& p, bool need_amp_buffer, DistPlan* dp)
         const int64_t ln = std::max(mset(dp->h, p.n), mset(p.m - dp->h, p.n));
         dp->ws_edge = align256((size_t)ln * ((dmax + kLevelGroup - 1) / kLevelGroup) * sizeof(double2));
     }
-    dp->ws_total = dp->ws_table + dp->ws_base + dp->ws_acc + dp->ws_y + dp->ws_tl + dp->ws_sl + dp->ws_th + dp->ws_sh +
-                   dp->ws_tc + dp->ws_edge;
+    dp->ws_total = dp->ws_status + dp->ws_table + dp->ws_base + dp->ws_acc + dp->ws_y + dp->ws_tl + dp->ws_sl +
+                   dp->ws_th + dp->ws_sh + dp->ws_tc + dp->ws_edge;
     return (int64_t)dp->ws_total;
 }
 
@@ -404,6 +488,7 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
 {
     const int m = p.m, n = p.n, B = dp.B;
     char* w = (char*)ws;
+    int* status = (int*)w;                   w += dp.ws_status;
     int64_t* table = (int64_t*)w;            w += dp.ws_table;
     int64_t* lowbase = (int64_t*)w;          w += dp.ws_base;
     double2* accbuf = dp.ws_acc ? (double2*)w : amp;  w += dp.ws_acc;
@@ -415,8 +500,11 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
     void* tcws = w;
     if (dp.tc && (B != 1 || dp.kc != (1ll << (n - 1)))) return cudaErrorInvalidValue;
 
-    cudaError_t e = build_multiset_table(table, m, n, s);
+    // the status word starts each call at zero; a tensor-core kernel whose
+    // bounded wait gives up writes its role code there
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
+    if ((e = build_multiset_table(table, m, n, s)) != cudaSuccess) return e;
     MultisetTable mc{table, n};
     ColList cols;
     for (int j = 0; j < PCV_MAX_PHOTONS; ++j) cols.c[j] = p.cols[j];
@@ -433,7 +521,12 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
     g.tstride_low = tl_stride; g.tstride_high = th_stride;
     g.lowbase = lowbase;
     g.kc = dp.kc;
-    g.out_stride = dp.total;
+    const int64_t lo = dp.lo, hi = dp.hi < 0 ? dp.total : dp.hi;
+    g.lo = lo;
+    g.hi = hi;
+    g.out_stride = hi - lo;
+    PRanges pr;
+    p_ranges(m, n, dp.h, lo, hi, &pr);
     g.acc = accbuf;
     g.amp = amp;
     g.prob = prob;
@@ -441,15 +534,20 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
     int64_t tiles = 0;
     for (int k = 0; k <= n; ++k) {
         const int64_t M = mset(dp.h, k), N = mset(m - dp.h, n - k);
-        if (M == 0 || N == 0) continue;
+        if (M == 0 || N == 0 || pr.pa[k] >= pr.pb[k]) continue;
         const bool qstrip = N >= M;
-        const int64_t nstrip = qstrip ? N : M, nfixed = qstrip ? M : N;
+        // the P side (fixed when qstrip) covers only the P whose outputs meet [lo, hi)
+        g.fb[g.nk] = qstrip ? pr.pa[k] : 0;
+        g.fe[g.nk] = qstrip ? pr.pb[k] : N;
+        g.sb[g.nk] = qstrip ? 0 : pr.pa[k];
+        g.se[g.nk] = qstrip ? N : pr.pb[k];
         g.lowoff[g.nk] = dp.lowoff[k];
         g.highoff[g.nk] = dp.highoff[n - k];
         g.M[g.nk] = M;
         g.N[g.nk] = N;
         g.tile0[g.nk] = tiles;
-        tiles += ((nstrip + 32 * kStrip - 1) / (32 * kStrip)) * ((nfixed + kWarps - 1) / kWarps);
+        tiles += ((g.se[g.nk] - g.sb[g.nk] + 32 * kStrip - 1) / (32 * kStrip)) *
+                 ((g.fe[g.nk] - g.fb[g.nk] + kWarps - 1) / kWarps);
         g.nk++;
     }
     g.tile0[g.nk] = tiles;
@@ -482,7 +580,9 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
             ti.amp = amp;
             ti.prob = prob;
             ti.ws = tcws;
-            ti.error = nullptr;
+            ti.error = status;
+            ti.lo = lo;
+            ti.hi = hi;
             if ((e = launch_tc_tables(ti, s)) != cudaSuccess) return e;
             stage_end(kStageTables, s);
             if ((e = launch_tc_products(ti, s)) != cudaSuccess) return e;
@@ -562,7 +662,7 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
                 // high side level n: the block k = 0 (P empty), outputs lowbase({}) + rank(Q)
                 edge_reduce_kernel<<<(unsigned)((la.count + 255) / 256), 256, 0, s>>>(
                     partial, la.count, ngroups, lowbase, side == 0 ? dp.lowoff[n] : dp.lowoff[0], side == 0 ? 1 : 0,
-                    amp, prob);
+                    lo, hi, amp, prob);
                 note_launches(2);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
             }
@@ -572,9 +672,11 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
         stage_begin(kStageGemm, s);
         g.first = ch == 0;
         g.last = ch == nchunks - 1;
-        gemm_kernel<<<dim3((unsigned)tiles, (unsigned)B), 256, 0, s>>>(g);
-        note_launches(1);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (tiles > 0) {                      // none when [lo, hi) is empty
+            gemm_kernel<<<dim3((unsigned)tiles, (unsigned)B), 256, 0, s>>>(g);
+            note_launches(1);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         stage_end(kStageGemm, s);
     }
     return cudaSuccess;

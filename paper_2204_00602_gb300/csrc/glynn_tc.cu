@@ -73,6 +73,7 @@
 #include <mutex>
 
 #include "pcv_common.cuh"
+#include "tc_ptx.cuh"
 
 namespace pcv {
 namespace {
@@ -87,7 +88,7 @@ constexpr int kBSub = 16;                               // rows per column load 
 constexpr uint32_t kSmemBytes = kBSets * kBBytes + kASlots * kABytes + 1024;
 constexpr int kThreads = 320;                            // warp 0 TMA, warp 1 MMA, warps 2-9 drain
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kMaxPolls = 1ll << 26;
+constexpr long long kMaxPolls = 1ll << 26;               // default bound of one mbarrier wait
 constexpr int kNoExp = -100000;                          // an all-zero row
 
 // ------------------------------------------------------------ splitting
@@ -399,7 +400,9 @@ struct TcProdArgs {
     // single-entry columns of that side when both fit one tile
     int ncol[kMaxBlocks], ecol0[kMaxBlocks], ecols[kMaxBlocks];
     int tn[kMaxBlocks];                       // tile width (16..64)
-    int64_t rows[kMaxBlocks], cols[kMaxBlocks];
+    // tiles cover rows [rows0, rows) and columns [cols0, cols) of the block:
+    // all of it, or the rows or columns of the P whose outputs meet [lo, hi)
+    int64_t rows0[kMaxBlocks], rows[kMaxBlocks], cols0[kMaxBlocks], cols[kMaxBlocks];
     int64_t row_off[kMaxBlocks], col_off[kMaxBlocks];   // entry offsets in the digit tensors
     int64_t lowoff[kMaxBlocks];               // level offset of P (for lowbase)
     const int64_t* lowbase;
@@ -415,97 +418,23 @@ struct TcProdArgs {
     const int64_t* efirst[2];
     const int* emax[2];
     const double* esc[2];
-    double* xt;                               // [2][total]: the real products t1, t2 per output
-    int64_t total;
+    double* xt;                               // [2][hi - lo]: the real products t1, t2 per output
+    int64_t lo, hi;                           // outputs [lo, hi) are written, at o - lo
     double2* amp;                             // amplitudes, or null
     double* prob;                             // probabilities, or null
-    int* error;
+    int* error;                               // set to the role that gave up (1 producer, 2 MMA, 3 drain,
+                                              // 4 clean-up), or null
+    long long max_polls;                      // bound of one mbarrier wait
 };
 
-__device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(sm_addr(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sm_addr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sm_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity)
-{
-    const uint32_t a = sm_addr(bar);
-    for (long long i = 0; i < kMaxPolls; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n"
-            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
-                                            int u)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];\n" ::"r"(sm_addr(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(z), "r"(u), "r"(sm_addr(bar))
-        : "memory");
-}
-
-// K-major tile in the 128-byte swizzle layout written by TMA: rows of 128 B,
-// 8-row atoms 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(const void* p)
-{
-    const uint64_t addr = sm_addr(p);
-    uint64_t d = 0;
-    d |= (addr & 0x3FFFF) >> 4;
-    d |= (uint64_t)(16 >> 4) << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = n.
-__device__ __forceinline__ uint32_t idesc_for(int n)
-{
-    uint32_t d = 0;
-    d |= 1u << 4;
-    d |= 1u << 7;
-    d |= 1u << 10;
-    d |= (uint32_t)(n >> 3) << 17;
-    d |= (uint32_t)(TBM >> 4) << 24;
-    return d;
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(sm_addr(bar))
-                 : "memory");
-}
+using tcx::mbar_arrive;
+using tcx::mbar_expect_tx;
+using tcx::mbar_init;
+using tcx::mbar_wait;
+using tcx::mma_bf16;
+using tcx::mma_commit;
+using tcx::sdesc_sw128;
+using tcx::tma_load_4d;
 
 __device__ __forceinline__ double pow2(int e)      // 2^e for -1022 <= e <= 1023
 {
@@ -592,10 +521,10 @@ __device__ __forceinline__ TileInfo tile_info(const TcProdArgs& a, int64_t tile)
     while (kb + 1 < a.nk && a.tile0[kb + 1] <= tile) ++kb;
     ti.kb = kb;
     ti.tn = a.tn[kb];
-    const int64_t ctiles = (a.cols[kb] + ti.tn - 1) / ti.tn;
+    const int64_t ctiles = (a.cols[kb] - a.cols0[kb] + ti.tn - 1) / ti.tn;
     const int64_t lt = tile - a.tile0[kb];
-    ti.r0 = (lt / ctiles) * TBM;
-    ti.c0 = (lt % ctiles) * ti.tn;
+    ti.r0 = a.rows0[kb] + (lt / ctiles) * TBM;
+    ti.c0 = a.cols0[kb] + (lt % ctiles) * ti.tn;
     ti.rl = a.rows_low[kb] != 0;
     ti.rentry = (int)(a.row_off[kb] + ti.r0);
     ti.centry = (int)(a.col_off[kb] + ti.c0);
@@ -619,7 +548,7 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
     unsigned char* bset = base;                                // kBSets x 64 KB
     unsigned char* aslot = base + kBSets * kBBytes;            // kASlots x 16 KB
     __shared__ __align__(8) uint64_t bfull[kBSets], bempty[kBSets], afull[kASlots], aempty[kASlots];
-    __shared__ __align__(8) uint64_t accfull, accempty;
+    __shared__ __align__(8) uint64_t accfull, accempty, mma_done;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
 
@@ -630,49 +559,46 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
 
     if (tid == 0) {
         for (int s = 0; s < kBSets; ++s) {
-            bar_init(&bfull[s], 1);
-            bar_init(&bempty[s], 1);
+            mbar_init(&bfull[s], 1);
+            mbar_init(&bempty[s], 1);
         }
         for (int s = 0; s < kASlots; ++s) {
-            bar_init(&afull[s], 1);
-            bar_init(&aempty[s], 1);
+            mbar_init(&afull[s], 1);
+            mbar_init(&aempty[s], 1);
         }
-        bar_init(&accfull, 1);
-        bar_init(&accempty, 256);
+        mbar_init(&accfull, 1);
+        mbar_init(&accempty, 256);
+        mbar_init(&mma_done, 1);
         s_fail = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&low_rows) : "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&low_cols) : "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&high_rows) : "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&high_cols) : "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&low_cols16) : "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&high_cols16) : "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&vlow16) : "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&vhigh16) : "memory");
+        tcx::mbar_fence_init();
+        tcx::prefetch_tmap(&low_rows);
+        tcx::prefetch_tmap(&low_cols);
+        tcx::prefetch_tmap(&high_rows);
+        tcx::prefetch_tmap(&high_cols);
+        tcx::prefetch_tmap(&low_cols16);
+        tcx::prefetch_tmap(&high_cols16);
+        tcx::prefetch_tmap(&vlow16);
+        tcx::prefetch_tmap(&vhigh16);
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sm_addr(&tmem_base)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    if (warp == 1) tcx::tmem_alloc(&tmem_base, kTmemCols);
+    tcx::fence_before_sync();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    tcx::fence_after_sync();
     const uint32_t tmem = tmem_base;
+    const long long polls = a.max_polls;
 
     if (tid == 0) {
         // ---------------- TMA producer
         // chunk q = (tile it, product t, K block c), in that nesting; the tile
         // of the next chunk is looked up once, when the chunk crosses into it
-        uint32_t na = 0;
+        uint32_t na = 0, nb = 0;                                      // row and column loads issued
         auto issue_b = [&](uint32_t q, const TileInfo& tb, int t, int c) -> bool {
             const uint32_t bs = q % kBSets;
-            if (q >= kBSets && !bar_wait(&bempty[bs], ((q / kBSets) - 1) & 1)) return false;
+            if (q >= kBSets && !mbar_wait(&bempty[bs], ((q / kBSets) - 1) & 1, polls)) return false;
             // slice j at rows j N .. j N + N - 1 of the set: one 64-row box, or
             // N / 16 boxes of 16 rows
             unsigned char* dst = bset + bs * kBBytes;
-            bar_expect_tx(&bfull[bs], (uint32_t)(kDigits * tb.tn) * kRowBytes);
+            mbar_expect_tx(&bfull[bs], (uint32_t)(kDigits * tb.tn) * kRowBytes);
             if (tb.tn == TBN && a.ecols[tb.kb] == 0) {
                 const CUtensorMap* cmap = tb.rl ? &high_cols : &low_cols;
                 for (int j = 0; j < kDigits; ++j)
@@ -692,6 +618,7 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                             tma_load_4d(dst + (j * tb.tn + r) * kRowBytes, vmap, &bfull[bs], c * TBK, lc - e0, j, t);
                     }
             }
+            nb = q + 1;
             return true;
         };
         TileInfo ti = {}, tnext = {};
@@ -716,11 +643,11 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                     }
                     for (int ii = 0; ii < kDigits; ++ii) {
                         const uint32_t as = na % kASlots;
-                        if (na >= (uint32_t)kASlots && !bar_wait(&aempty[as], ((na / kASlots) - 1) & 1)) {
+                        if (na >= (uint32_t)kASlots && !mbar_wait(&aempty[as], ((na / kASlots) - 1) & 1, polls)) {
                             s_fail = 1;
                             break;
                         }
-                        bar_expect_tx(&afull[as], kABytes);
+                        mbar_expect_tx(&afull[as], kABytes);
                         tma_load_4d(aslot + as * kABytes, rmap, &afull[as], c * TBK, ti.rentry, slice_order(ii), t);
                         ++na;
                         if (ii == 2 && q + 1 < nchunks) {
@@ -734,6 +661,11 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                 }
             }
         }
+        // every load issued lands in this CTA's shared memory: wait for the
+        // ones no consumer waited for before the CTA may exit
+        const bool rows_in = tcx::wait_issued(afull, kASlots, na);
+        const bool cols_in = tcx::wait_issued(bfull, kBSets, nb);
+        if (!(rows_in && cols_in) && !s_fail) s_fail = 4;
     } else if (tid == 32) {
         // ---------------- MMA issuer
         uint32_t na = 0, q = 0, g = 0;                               // slices, chunks, passes
@@ -741,39 +673,39 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             const int tn = tile_info(a, blockIdx.x + it * gridDim.x).tn;
             const int per = min(kDigits, 256 / tn);                      // column slices per MMA
             for (int t = 0; t < 3 && !s_fail; ++t, ++g) {
-                if (g > 0 && !bar_wait(&accempty, (g - 1) & 1)) {
+                if (g > 0 && !mbar_wait(&accempty, (g - 1) & 1, polls)) {
                     s_fail = 2;
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                tcx::fence_after_sync();
                 for (int c = 0; c < nkb && !s_fail; ++c, ++q) {
                     const uint32_t bs = q % kBSets;
-                    if (!bar_wait(&bfull[bs], (q / kBSets) & 1)) {
+                    if (!mbar_wait(&bfull[bs], (q / kBSets) & 1, polls)) {
                         s_fail = 2;
                         break;
                     }
                     // descriptors are linear in the address (16-byte units in
                     // the low bits): one per slice, plus 2 per 16-wide K step
-                    const uint64_t db0 = sdesc(bset + bs * kBBytes);
+                    const uint64_t db0 = sdesc_sw128(bset + bs * kBBytes);
                     for (int ii = 0; ii < kDigits; ++ii) {
                         const int i = slice_order(ii);
                         const uint32_t as = na % kASlots;
-                        if (!bar_wait(&afull[as], (na / kASlots) & 1)) {
+                        if (!mbar_wait(&afull[as], (na / kASlots) & 1, polls)) {
                             s_fail = 2;
                             break;
                         }
-                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                        const uint64_t da = sdesc(aslot + as * kABytes);
+                        tcx::fence_after_sync();
+                        const uint64_t da = sdesc_sw128(aslot + as * kABytes);
                         const uint32_t first = (c == 0 && ii == 0) ? 0u : 1u;
                         for (int j0 = 0; j0 < kDigits - i; j0 += per) {
                             const int ns = min(per, kDigits - i - j0);
-                            const uint32_t idesc = idesc_for(ns * tn);
+                            const uint32_t idesc = tcx::idesc_bf16(TBM, ns * tn);
                             const uint32_t acc_t = tmem + (uint32_t)((i + j0) * tn);
                             const uint64_t db = db0 + (uint64_t)((j0 * tn * kRowBytes) >> 4);
-                            mma_f16(acc_t, da, db, idesc, first);
-                            mma_f16(acc_t, da + 2, db + 2, idesc, 1u);
-                            mma_f16(acc_t, da + 4, db + 4, idesc, 1u);
-                            mma_f16(acc_t, da + 6, db + 6, idesc, 1u);
+                            mma_bf16(acc_t, da, db, idesc, first);
+                            mma_bf16(acc_t, da + 2, db + 2, idesc, 1u);
+                            mma_bf16(acc_t, da + 4, db + 4, idesc, 1u);
+                            mma_bf16(acc_t, da + 6, db + 6, idesc, 1u);
                         }
                         mma_commit(&aempty[as]);
                         ++na;
@@ -782,6 +714,11 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                 }
                 if (!s_fail) mma_commit(&accfull);
             }
+        }
+        // the MMAs issued are complete before the tensor memory is released
+        if (na > 0) {
+            mma_commit(&mma_done);
+            if (!mbar_wait(&mma_done, 0, tcx::kCleanupPolls) && !s_fail) s_fail = 4;
         }
     } else if (warp >= 2) {
         // ---------------- drain: warp w owns TMEM lanes 32 (w mod 4) .. + 31;
@@ -815,12 +752,12 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             for (int t = 0; t < 3; ++t) {
                 const int64_t g = it * 3 + t;
                 const int er = rv ? ex_r[(int64_t)t * wr + a.row_off[kb] + row] : kNoExp;
-                if (!bar_wait(&accfull, (uint32_t)g & 1)) {
+                if (!mbar_wait(&accfull, (uint32_t)g & 1, polls)) {
                     if (lane == 0) s_fail = 3;
                     alive = false;
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                tcx::fence_after_sync();
                 // read the 8 diagonals of this warp's columns (16-wide chunks
                 // cc = 0, 32 for warps 2-5 and 16, 48 for warps 6-9) and
                 // combine them on the integer pipe into Z = zh 2^28 + zl, then
@@ -860,8 +797,8 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                         zl[h][q] = (uint32_t)(lo[q] & ((1ll << 28) - 1));
                     }
                 }
-                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                bar_arrive(&accempty);
+                tcx::fence_before_sync();
+                mbar_arrive(&accempty);
                 if (!rv) continue;
                 // t1 and t2 go to the workspace; with t3, the same thread
                 // forms a = (t1 - t2) + i (t3 - t1 - t2) and |a|^2
@@ -882,11 +819,13 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                             if (!scale_packed(zh[h][q], zl[h][q], sc - 49, x))
                                 x = fma((double)zl[h][q], pow2(sc - 49), (double)zh[h][q] * pow2(sc - 21));
                         }
-                        const int64_t o = is_e ? ebase + ce : (rl ? pbase + col : a.lowbase[a.lowoff[kb] + col] + row);
+                        const int64_t og = is_e ? ebase + ce : (rl ? pbase + col : a.lowbase[a.lowoff[kb] + col] + row);
+                        if (og < a.lo || og >= a.hi) continue;
+                        const int64_t o = og - a.lo, span = a.hi - a.lo;
                         if (t < 2) {
-                            a.xt[(int64_t)t * a.total + o] = x;
+                            a.xt[(int64_t)t * span + o] = x;
                         } else {
-                            const double t1 = a.xt[o], t2 = a.xt[a.total + o];
+                            const double t1 = a.xt[o], t2 = a.xt[span + o];
                             double re = t1 - t2, im = x - t1 - t2;
                             if (is_e && ce == emx) {           // 1 / sqrt(multiplicity of r in R' + r)
                                 re *= esc;
@@ -900,10 +839,9 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    tcx::fence_before_sync();
     __syncthreads();
-    if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    if (warp == 1) tcx::tmem_dealloc(tmem, kTmemCols);
     if (tid == 0 && s_fail && a.error) atomicExch(a.error, s_fail);
 }
 
@@ -1218,18 +1156,27 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     a.nk = 0;
     a.kblocks = Kp / TBK;
     auto round16 = [](int64_t x) { return (int)((x + 15) / 16) * 16; };
+    // outputs [lo, hi): per k the ranks of the P whose outputs meet the range
+    PRanges pr;
+    p_ranges(m, n, h, in.lo, in.hi, &pr);
+    int64_t fullcols[kMaxBlocks];                 // columns of each block before any restriction
     for (int k = 1; k < in.n; ++k) {
         const int64_t M = msets_tc(in.h, k), N = msets_tc(in.m - in.h, in.n - k);
         if (M == 0 || N == 0) continue;
         const bool rl = M >= N;
         const int64_t rows = rl ? M : N, cols = rl ? N : M;
+        const bool any = pr.pa[k] < pr.pb[k];
         a.rows_low[a.nk] = rl ? 1 : 0;
         a.tn[a.nk] = cols >= TBN ? TBN : round16(cols);
-        a.rows[a.nk] = rows;
-        a.cols[a.nk] = cols;
-        a.ncol[a.nk] = (int)std::min<int64_t>(cols, INT32_MAX);
+        // the P side (rows when rl, else columns) restricted to [pa, pb)
+        a.rows0[a.nk] = rl ? pr.pa[k] : 0;
+        a.rows[a.nk] = !any ? a.rows0[a.nk] : (rl ? pr.pb[k] : rows);
+        a.cols0[a.nk] = rl ? 0 : pr.pa[k];
+        a.cols[a.nk] = !any ? a.cols0[a.nk] : (rl ? cols : pr.pb[k]);
+        a.ncol[a.nk] = (int)std::min<int64_t>(a.cols[a.nk], INT32_MAX);
         a.ecol0[a.nk] = (int)std::min<int64_t>(cols, INT32_MAX);
         a.ecols[a.nk] = 0;
+        fullcols[a.nk] = cols;
         a.row_off[a.nk] = rl ? in.lowoff[k] - lb : in.highoff[in.n - k] - hb;
         a.col_off[a.nk] = rl ? in.highoff[in.n - k] - hb : in.lowoff[k] - lb;
         a.lowoff[a.nk] = in.lowoff[k];
@@ -1237,41 +1184,92 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     }
     // the single-entry columns: rows = level n-1 of a side, columns = its
     // modes (side 0: outputs with every photon low, k = n; side 1: k = 0),
-    // merged into the block with the same rows when both fit one tile
+    // merged into the block with the same rows when both fit one tile.  The
+    // rows that reach [lo, hi): side 0, the parents (level n-1) of the level-n
+    // P in range; side 1, the parents of the Q of the block P = {} in range.
     for (int side = 0; side < 2; ++side) {
         const int64_t rows = side == 0 ? in.lowoff[n] - in.lowoff[n - 1] : in.highoff[n] - in.highoff[n - 1];
         const int ecols = side == 0 ? h : m - h;
         if (rows == 0 || ecols == 0) continue;
+        int64_t r0 = 0, r1 = 0;
+        if (side == 0) {
+            if (pr.pa[n] < pr.pb[n]) {
+                r0 = host_parent_rank(h, n, pr.pa[n]);
+                r1 = host_parent_rank(h, n, pr.pb[n] - 1) + 1;
+            }
+        } else {
+            const int64_t base = host_lowbase(m, n, h, 0, 0);
+            const int64_t c = std::max(in.lo, base) - base, d = std::min(in.hi, in.total) - base;
+            if (c < d) {
+                r0 = host_parent_rank(m - h, n, c);
+                r1 = host_parent_rank(m - h, n, d - 1) + 1;
+            }
+        }
+        if (r0 >= r1) continue;
         const int64_t roff = side == 0 ? in.lowoff[n - 1] - lb : in.highoff[n - 1] - hb;
         int host = -1;
         for (int b = 0; b < a.nk; ++b)
             if (a.rows_low[b] == (side == 0 ? 1 : 0) && a.row_off[b] == roff && a.ecols[b] == 0 &&
-                round16(a.ncol[b]) + round16(ecols) <= TBN)
+                round16(fullcols[b]) + round16(ecols) <= TBN)
                 host = b;
         if (host >= 0) {
-            a.ecol0[host] = round16(a.ncol[host]);
+            // one column tile: every column of the host block, then the modes
+            a.ecol0[host] = round16(fullcols[host]);
             a.ecols[host] = ecols;
+            a.ncol[host] = (int)fullcols[host];
+            a.cols0[host] = 0;
             a.cols[host] = a.ecol0[host] + ecols;
             a.tn[host] = a.ecol0[host] + round16(ecols);
+            if (a.rows[host] <= a.rows0[host]) {
+                a.rows0[host] = r0;
+                a.rows[host] = r1;
+            } else {
+                a.rows0[host] = std::min(a.rows0[host], r0);
+                a.rows[host] = std::max(a.rows[host], r1);
+            }
             continue;
         }
         a.rows_low[a.nk] = side == 0 ? 1 : 0;
         a.tn[a.nk] = ecols >= TBN ? TBN : round16(ecols);
-        a.rows[a.nk] = rows;
+        a.rows0[a.nk] = r0;
+        a.rows[a.nk] = r1;
+        a.cols0[a.nk] = 0;
         a.cols[a.nk] = ecols;
         a.ncol[a.nk] = 0;
         a.ecol0[a.nk] = 0;
         a.ecols[a.nk] = ecols;
+        fullcols[a.nk] = ecols;
         a.row_off[a.nk] = roff;
         a.col_off[a.nk] = 0;
         a.lowoff[a.nk] = 0;
         a.nk++;
     }
+    // blocks without tiles are dropped
     int64_t tiles = 0;
+    int nb = 0;
     for (int b = 0; b < a.nk; ++b) {
-        a.tile0[b] = tiles;
-        tiles += ((a.rows[b] + TBM - 1) / TBM) * ((a.cols[b] + a.tn[b] - 1) / a.tn[b]);
+        const int64_t rt = a.rows[b] > a.rows0[b] ? (a.rows[b] - a.rows0[b] + TBM - 1) / TBM : 0;
+        const int64_t ct = a.cols[b] > a.cols0[b] ? (a.cols[b] - a.cols0[b] + a.tn[b] - 1) / a.tn[b] : 0;
+        if (rt * ct == 0) continue;
+        if (nb != b) {
+            a.rows_low[nb] = a.rows_low[b];
+            a.tn[nb] = a.tn[b];
+            a.rows0[nb] = a.rows0[b];
+            a.rows[nb] = a.rows[b];
+            a.cols0[nb] = a.cols0[b];
+            a.cols[nb] = a.cols[b];
+            a.ncol[nb] = a.ncol[b];
+            a.ecol0[nb] = a.ecol0[b];
+            a.ecols[nb] = a.ecols[b];
+            a.row_off[nb] = a.row_off[b];
+            a.col_off[nb] = a.col_off[b];
+            a.lowoff[nb] = a.lowoff[b];
+        }
+        a.tile0[nb] = tiles;
+        tiles += rt * ct;
+        ++nb;
     }
+    a.nk = nb;
     a.tile0[a.nk] = tiles;
     if (tiles == 0) {
         stage_end(kStageGemm, s);
@@ -1285,7 +1283,8 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     a.wlow = lcnt;                            // entries of the digit tensors (exponent stride)
     a.whigh = hcnt;
     a.xt = xt;
-    a.total = in.total;
+    a.lo = in.lo;
+    a.hi = in.hi;
     a.amp = in.amp;
     a.prob = in.prob;
     for (int side = 0; side < 2; ++side) {
@@ -1295,6 +1294,7 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         a.esc[side] = esc[side];
     }
     a.error = in.error;
+    a.max_polls = wait_limit(kMaxPolls);
     a.tiles = tiles;
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;

@@ -28,6 +28,7 @@
 #include <mutex>
 
 #include "pcv_common.cuh"
+#include "tc_ptx.cuh"
 
 namespace pcv {
 
@@ -37,7 +38,7 @@ constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;   // 97 KB: t
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_STAGE_BYTES = (TC_BM + TC_BN) * TC_BK * 2;     // 32 KB per stage
 constexpr uint32_t TC_TMEM_COLS = 128;
-constexpr long long TC_MAX_POLLS = 1ll << 22;                        // bounded polling (~seconds at most)
+constexpr long long TC_MAX_POLLS = 1ll << 22;                        // default bound of one mbarrier wait
 
 struct TcArgs {
     int M, N, K;
@@ -46,73 +47,15 @@ struct TcArgs {
     float* outf; int ldo;
     __nv_bfloat16* outb; int ldob;
     const float* pre; int ldp;
-    int* error;                       // set to a nonzero code when a wait gives up
+    int* error;                       // set to the role that gave up (1 loads, 2 MMA, 3 epilogue, 4 clean-up)
+    long long max_polls;              // bound of one mbarrier wait
 };
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Bounded wait on phase `parity`; returns false when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
-{
-    const uint32_t a = smem_addr(bar);
-    for (long long i = 0; i < TC_MAX_POLLS; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n"
-            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
-            "r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzle
-// layout written by TMA: rows of 128 B, 8-row atoms 1024 B apart.
-__device__ __forceinline__ uint64_t smem_desc(const void* p)
-{
-    const uint64_t addr = smem_addr(p);
-    uint64_t d = 0;
-    d |= (addr & 0x3FFFF) >> 4;                 // start address, bits 0-13
-    d |= (uint64_t)(16 >> 4) << 16;             // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M=128, N=128.
-__device__ __forceinline__ uint32_t instr_desc()
-{
-    uint32_t d = 0;
-    d |= 1u << 4;                               // accumulator format: FP32
-    d |= 1u << 7;                               // A format: BF16
-    d |= 1u << 10;                              // B format: BF16
-    d |= (uint32_t)(TC_BN >> 3) << 17;          // N / 8
-    d |= (uint32_t)(TC_BM >> 4) << 24;          // M / 16
-    return d;
-}
+using tcx::mbar_expect_tx;
+using tcx::mbar_init;
+using tcx::mbar_wait;
+using tcx::sdesc_sw128;
+using tcx::tma_load_2d;
 
 __device__ __forceinline__ float gelu_tc(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_tc(float x)
@@ -126,7 +69,7 @@ gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned ring of stages: [A 128x64 | B 128x64] bf16 each
     unsigned char* ring = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
+    __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar, mma_done;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
 
@@ -140,66 +83,63 @@ gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&done_bar, 1);
+        mbar_init(&mma_done, 1);
         s_fail = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&mapA) : "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&mapB) : "memory");
+        tcx::mbar_fence_init();
+        tcx::prefetch_tmap(&mapA);
+        tcx::prefetch_tmap(&mapB);
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_base)),
-                     "r"(TC_TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    if (warp == 1) tcx::tmem_alloc(&tmem_base, TC_TMEM_COLS);
+    tcx::fence_before_sync();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    tcx::fence_after_sync();
     const uint32_t tmem = tmem_base;
+    const long long polls = a.max_polls;
 
     if (tid == 0) {
         // ---------------- TMA producer
+        int issued = 0;
         for (int kt = 0; kt < nk && !s_fail; ++kt) {
             const int s = kt % TC_STAGES;
-            if (kt >= TC_STAGES && !mbar_wait(&empty_bar[s], ((kt / TC_STAGES) - 1) & 1)) { s_fail = 1; break; }
+            if (kt >= TC_STAGES && !mbar_wait(&empty_bar[s], ((kt / TC_STAGES) - 1) & 1, polls)) { s_fail = 1; break; }
             unsigned char* sa = ring + s * TC_STAGE_BYTES;
             unsigned char* sb = sa + TC_BM * TC_BK * 2;
             mbar_expect_tx(&full_bar[s], TC_STAGE_BYTES);
             tma_load_2d(sa, &mapA, &full_bar[s], kt * TC_BK, m0);
             tma_load_2d(sb, &mapB, &full_bar[s], kt * TC_BK, n0);
+            ++issued;
         }
+        // the loads issued land in this CTA's shared memory before it may exit
+        if (!tcx::wait_issued(full_bar, TC_STAGES, (uint32_t)issued) && !s_fail) s_fail = 4;
     } else if (tid == 32) {
         // ---------------- MMA issuer
-        const uint32_t idesc = instr_desc();
+        const uint32_t idesc = tcx::idesc_bf16(TC_BM, TC_BN);
+        bool all = true;
         for (int kt = 0; kt < nk; ++kt) {
             const int s = kt % TC_STAGES;
-            if (!mbar_wait(&full_bar[s], (kt / TC_STAGES) & 1)) { s_fail = 2; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            if (!mbar_wait(&full_bar[s], (kt / TC_STAGES) & 1, polls)) { s_fail = 2; all = false; break; }
+            tcx::fence_after_sync();
             const unsigned char* sa = ring + s * TC_STAGE_BYTES;
             const unsigned char* sb = sa + TC_BM * TC_BK * 2;
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                const uint64_t ad = smem_desc(sa + kk * 32);      // 16 bf16 = 32 B along K
-                const uint64_t bd = smem_desc(sb + kk * 32);
-                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                    : "memory");
+                const uint64_t ad = sdesc_sw128(sa + kk * 32);      // 16 bf16 = 32 B along K
+                const uint64_t bd = sdesc_sw128(sb + kk * 32);
+                tcx::mma_bf16(tmem, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             smem_addr(&empty_bar[s]))
-                         : "memory");
+            tcx::mma_commit(&empty_bar[s]);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                         smem_addr(&done_bar))
-                     : "memory");
+        // a complete accumulation goes to the epilogue; in every case the MMAs
+        // issued finish before the tensor memory is released
+        if (all) tcx::mma_commit(&done_bar);
+        tcx::mma_commit(&mma_done);
+        if (!mbar_wait(&mma_done, 0, tcx::kCleanupPolls) && !s_fail) s_fail = 4;
     }
 
     // ---------------- epilogue (all warps)
-    const bool ok = mbar_wait(&done_bar, 0);
+    const bool ok = mbar_wait(&done_bar, 0, polls);
     if (!ok && lane == 0) s_fail = 3;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    tcx::fence_after_sync();
     __syncwarp();
     if (ok) {
         // Each warp moves its 32 rows x 32 columns through a padded shared tile
@@ -247,10 +187,9 @@ gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
             __syncwarp();
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    tcx::fence_before_sync();
     __syncthreads();
-    if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    if (warp == 1) tcx::tmem_dealloc(tmem, TC_TMEM_COLS);
     if (tid == 0 && s_fail && a.error) atomicExch(a.error, s_fail);
 }
 
@@ -307,6 +246,7 @@ cudaError_t launch_gemm_bf16_tc(const void* A, int lda, const void* B, int ldb, 
     a.M = M; a.N = N; a.K = K; a.mode = mode;
     a.bias = bias; a.outf = outf; a.ldo = ldo; a.outb = (__nv_bfloat16*)outb; a.ldob = ldob; a.pre = pre; a.ldp = ldp;
     a.error = error;
+    a.max_polls = wait_limit(TC_MAX_POLLS);
     dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
     gemm_bf16_tc_kernel<<<grid, TC_THREADS, gemm_tc_smem(), s>>>(ma, mb, a);
     note_launches(1);

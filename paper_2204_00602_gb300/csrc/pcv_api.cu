@@ -178,6 +178,7 @@ struct StageTimer {
 };
 StageTimer g_timer;
 std::atomic<int64_t> g_launches{0};
+std::atomic<long long> g_wait_polls{0};      // 0: each kernel's default bound
 
 }  // namespace
 
@@ -205,6 +206,11 @@ void stage_end(int stage, cudaStream_t s)
 }
 void note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 void set_error(const char* msg) { g_err = msg; }
+long long wait_limit(long long dflt)
+{
+    const long long v = g_wait_polls.load(std::memory_order_relaxed);
+    return v > 0 ? v : dflt;
+}
 }  // namespace pcv
 
 extern "C" {
@@ -241,6 +247,29 @@ int pcv_profile_read(double* ms, int64_t* calls, int nstages)
 }
 
 int64_t pcv_launch_count(void) { return g_launches.load(); }
+
+int pcv_set_wait_limit(int64_t polls)
+{
+    if (polls < 0) return fail(PCV_EINVAL, "wait limit %lld < 0", (long long)polls);
+    g_wait_polls.store((long long)polls, std::memory_order_relaxed);
+    return PCV_OK;
+}
+
+int pcv_distribution_status(const void* workspace, void* stream)
+{
+    if (!workspace) return fail(PCV_EINVAL, "workspace is NULL");
+    int code = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&code, workspace, sizeof code, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the distribution status");
+    if (code != 0)
+        return fail(PCV_ETIMEOUT,
+                    "a bounded wait of the tensor-core product kernel gave up (role %d: 1 loads, 2 MMA issue, "
+                    "3 accumulator drain, 4 clean-up); the outputs of that call are not valid",
+                    code);
+    return PCV_OK;
+}
 
 const char* pcv_last_error(void) { return g_err.c_str(); }
 
@@ -499,7 +528,39 @@ int64_t pcv_distribution_batched_workspace(int B, int m, int n)
     return r < 0 ? fail(PCV_ERANGE, "workspace size overflows") : r;
 }
 
-int64_t pcv_distribution_workspace(int m, int n) { return pcv_distribution_batched_workspace(1, m, n); }
+// Single-pass tensor-core plan of one distribution (no error message on
+// failure): its bytes, or -1 when the path does not apply or overflows.
+static int64_t tc_ws_bytes(int m, int n)
+{
+    if (m < 2 || m > PCV_MAX_MODES || n < 2 || n > 10 || msets(m, n) < 0) return -1;
+    pcv::Plan p;
+    p.m = m;
+    p.n = n;
+    pcv::DistPlan dp;
+    return pcv::dist_plan_tc(p, true, &dp);
+}
+
+// PCV_ALGO_AUTO for one full distribution: the tensor-core products when the
+// input has 2..10 photons over m >= 2 modes and the workspace holds their
+// single-pass plan, else the FP64 products (which accept any workspace down to
+// pcv_distribution_workspace_min).
+static int auto_dist_algo(int m, int n, int64_t workspace_bytes)
+{
+    const int64_t tc = tc_ws_bytes(m, n);
+    return (tc >= 0 && workspace_bytes >= tc) ? PCV_ALGO_FACTOR_TC : PCV_ALGO_FACTOR;
+}
+
+int64_t pcv_distribution_workspace(int m, int n)
+{
+    const int64_t tc = tc_ws_bytes(m, n);
+    return tc >= 0 ? tc : pcv_distribution_batched_workspace(1, m, n);
+}
+
+int pcv_distribution_auto_algo(int m, int n, int64_t workspace_bytes)
+{
+    if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "bad sizes");
+    return auto_dist_algo(m, n, workspace_bytes);
+}
 
 int64_t pcv_distribution_workspace_min(int m, int n)
 {
@@ -509,9 +570,10 @@ int64_t pcv_distribution_workspace_min(int m, int n)
     return r < 0 ? fail(PCV_ERANGE, "workspace size overflows") : r;
 }
 
-int pcv_distribution_batched(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
-                             double* prob, pcv_c64* amp,
-                             void* workspace, int64_t workspace_bytes, void* stream)
+// The factorised distribution with FP64 products for the outputs [lo, hi)
+// (hi < 0: all) of B unitaries; arguments as pcv_distribution_batched.
+static int distribution_factor(const pcv_c64* U, int B, int m, const uint8_t* input_occ, int64_t lo, int64_t hi,
+                               double* prob, pcv_c64* amp, void* workspace, int64_t workspace_bytes, void* stream)
 {
     pcv::Plan p;
     int rc = make_plan(U, m, input_occ, &p);
@@ -523,8 +585,12 @@ int pcv_distribution_batched(const pcv_c64* U, int B, int m, const uint8_t* inpu
     if (workspace && !aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
     const int64_t N = msets(m, p.n);
     if (N < 0) return fail(PCV_ERANGE, "output space C(%d,%d) too large", m + p.n - 1, p.n);
+    if (hi < 0) hi = N;
+    if (lo < 0 || lo > hi || hi > N)
+        return fail(PCV_EINVAL, "output range [%lld, %lld) outside [0, %lld]", (long long)lo, (long long)hi, (long long)N);
+    if (lo == hi) return PCV_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (p.n == 0) {
+    if (p.n == 0) {                               // one output, index 0 (lo = 0, hi = 1 here)
         for (int b = 0; b < B; ++b) {
             cudaError_t e = pcv::launch_glynn_group(p, (const double2*)U, nullptr, nullptr, 0, 1,
                                                     amp ? (double2*)amp + b : nullptr, prob ? prob + b : nullptr, 1, s);
@@ -538,8 +604,18 @@ int pcv_distribution_batched(const pcv_c64* U, int B, int m, const uint8_t* inpu
     if (!workspace || need > workspace_bytes)
         return fail(PCV_ENOMEM, "workspace of at least %lld bytes needed, %lld given",
                     (long long)dist_ws(B, m, p.n, PCV_ALGO_FACTOR, 0, amp == nullptr, 0, nullptr), (long long)workspace_bytes);
+    if (B > 1 && (lo != 0 || hi != N)) return fail(PCV_EINVAL, "output ranges take one unitary");
+    dp.lo = lo;
+    dp.hi = hi;
     cudaError_t e = pcv::launch_glynn_dist(p, dp, (const double2*)U, prob, (double2*)amp, workspace, s);
     return e == cudaSuccess ? PCV_OK : cuda_fail(e, "factorised distribution");
+}
+
+int pcv_distribution_batched(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
+                             double* prob, pcv_c64* amp,
+                             void* workspace, int64_t workspace_bytes, void* stream)
+{
+    return distribution_factor(U, B, m, input_occ, 0, -1, prob, amp, workspace, workspace_bytes, stream);
 }
 
 int64_t pcv_distribution_slos_workspace(int B, int m, int n)
@@ -595,8 +671,10 @@ int64_t pcv_distribution_tc_workspace(int m, int n)
     return r < 0 ? fail(PCV_ERANGE, "workspace size overflows") : r;
 }
 
-static int distribution_tc(const pcv_c64* U, int m, const uint8_t* input_occ, double* prob, pcv_c64* amp,
-                           void* workspace, int64_t workspace_bytes, void* stream)
+// The factorised distribution with tensor-core products for the outputs
+// [lo, hi) (hi < 0: all), written at prob[o - lo], amp[o - lo].
+static int distribution_tc(const pcv_c64* U, int m, const uint8_t* input_occ, int64_t lo, int64_t hi, double* prob,
+                           pcv_c64* amp, void* workspace, int64_t workspace_bytes, void* stream)
 {
     pcv::Plan p;
     int rc = make_plan(U, m, input_occ, &p);
@@ -606,12 +684,19 @@ static int distribution_tc(const pcv_c64* U, int m, const uint8_t* input_occ, do
     if (amp && !aligned(amp, 16)) return fail(PCV_EINVAL, "amp is not 16-byte aligned");
     if (prob && !aligned(prob, 8)) return fail(PCV_EINVAL, "prob is not 8-byte aligned");
     if (workspace && !aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
-    if (msets(m, p.n) < 0) return fail(PCV_ERANGE, "output space too large");
+    const int64_t N = msets(m, p.n);
+    if (N < 0) return fail(PCV_ERANGE, "output space too large");
+    if (hi < 0) hi = N;
+    if (lo < 0 || lo > hi || hi > N)
+        return fail(PCV_EINVAL, "output range [%lld, %lld) outside [0, %lld]", (long long)lo, (long long)hi, (long long)N);
     pcv::DistPlan dp;
     const int64_t need = pcv::dist_plan_tc(p, amp == nullptr, &dp);
     if (need < 0) return fail(PCV_ERANGE, "workspace size overflows");
     if (!workspace || need > workspace_bytes)
         return fail(PCV_ENOMEM, "workspace of %lld bytes needed, %lld given", (long long)need, (long long)workspace_bytes);
+    if (lo == hi) return PCV_OK;
+    dp.lo = lo;
+    dp.hi = hi;
     cudaError_t e = pcv::launch_glynn_dist(p, dp, (const double2*)U, prob, (double2*)amp, workspace, (cudaStream_t)stream);
     return e == cudaSuccess ? PCV_OK : cuda_fail(e, "tensor-core factorised distribution");
 }
@@ -620,8 +705,13 @@ int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                         double* prob, pcv_c64* amp, int algo, int param,
                         void* workspace, int64_t workspace_bytes, void* stream)
 {
+    if (algo == PCV_ALGO_AUTO && m >= 1 && m <= PCV_MAX_MODES && input_occ) {
+        int n = 0;
+        for (int i = 0; i < m; ++i) n += input_occ[i];
+        algo = auto_dist_algo(m, n, workspace ? workspace_bytes : 0);
+    }
     if (algo == PCV_ALGO_FACTOR_TC)
-        return distribution_tc(U, m, input_occ, prob, amp, workspace, workspace_bytes, stream);
+        return distribution_tc(U, m, input_occ, 0, -1, prob, amp, workspace, workspace_bytes, stream);
     if (algo == PCV_ALGO_SLOS)
         return pcv_distribution_slos(U, 1, m, input_occ, prob, amp, workspace, workspace_bytes, stream);
     if (algo == PCV_ALGO_AUTO || algo == PCV_ALGO_FACTOR)
@@ -665,6 +755,35 @@ int pcv_distribution(const pcv_c64* U, int m, const uint8_t* input_occ,
                      void* workspace, int64_t workspace_bytes, void* stream)
 {
     return pcv_distribution_ex(U, m, input_occ, prob, amp, PCV_ALGO_AUTO, 0, workspace, workspace_bytes, stream);
+}
+
+int pcv_distribution_range_plan(int m, int n, int64_t begin, int64_t end, int64_t* pa, int64_t* pb)
+{
+    if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS || !pa || !pb) return fail(PCV_EINVAL, "bad sizes");
+    const int64_t N = msets(m, n);
+    if (N < 0) return fail(PCV_ERANGE, "output space too large");
+    if (begin < 0 || end < begin || end > N)
+        return fail(PCV_EINVAL, "output range [%lld, %lld) outside [0, %lld]", (long long)begin, (long long)end,
+                    (long long)N);
+    pcv::PRanges r;
+    pcv::p_ranges(m, n, std::max(1, m / 2), begin, end, &r);
+    for (int k = 0; k <= n; ++k) {
+        pa[k] = r.pa[k];
+        pb[k] = r.pb[k];
+    }
+    return PCV_OK;
+}
+
+int pcv_distribution_range(const pcv_c64* U, int m, const uint8_t* input_occ, int64_t begin, int64_t end,
+                           double* prob, pcv_c64* amp, void* workspace, int64_t workspace_bytes, void* stream)
+{
+    if (begin < 0 || end < begin) return fail(PCV_EINVAL, "output range [%lld, %lld)", (long long)begin, (long long)end);
+    int n = 0;
+    if (m >= 1 && m <= PCV_MAX_MODES && input_occ)
+        for (int i = 0; i < m; ++i) n += input_occ[i];
+    if (auto_dist_algo(m, n, workspace ? workspace_bytes : 0) == PCV_ALGO_FACTOR_TC)
+        return distribution_tc(U, m, input_occ, begin, end, prob, amp, workspace, workspace_bytes, stream);
+    return distribution_factor(U, 1, m, input_occ, begin, end, prob, amp, workspace, workspace_bytes, stream);
 }
 
 // ------------------------------------------------------------- adjoint

@@ -108,6 +108,9 @@ void stage_begin(int stage, cudaStream_t s);
 void stage_end(int stage, cudaStream_t s);
 void note_launches(int64_t k);
 void set_error(const char* msg);      // message returned by pcv_last_error
+// Bound of one mbarrier wait in the tensor-core kernels: `dflt` unless
+// pcv_set_wait_limit set another.
+long long wait_limit(long long dflt);
 
 // Plain Glynn kernels (glynn_plain.cu)
 cudaError_t launch_glynn_group(const Plan& p, const double2* U, const uint8_t* out_occ,
@@ -184,11 +187,28 @@ struct DistPlan {
     int64_t total;            // outputs per batch entry
     int64_t wlow, whigh;      // entries of all levels per side: C(h+n, n), C(m-h+n, n)
     int64_t lowoff[PCV_MAX_PHOTONS + 2], highoff[PCV_MAX_PHOTONS + 2];
-    size_t ws_table, ws_base, ws_acc, ws_y, ws_tl, ws_sl, ws_th, ws_sh, ws_total;
+    size_t ws_status, ws_table, ws_base, ws_acc, ws_y, ws_tl, ws_sl, ws_th, ws_sh, ws_total;
     bool tc = false;          // products on the tensor cores (glynn_tc.cu)
     size_t ws_tc = 0;
     size_t ws_edge = 0;       // partial sums of the single-entry blocks (tensor-core plan)
+    // The outputs computed: canonical indices [lo, hi) (the whole space by
+    // default), written at prob[o - lo], amp[o - lo].
+    int64_t lo = 0, hi = -1;
 };
+
+// Outputs in a canonical index range, grouped by the low-side multiset P
+// (modes [0, h)): all outputs with low part P form one contiguous block of the
+// canonical order, starting at lowbase(P) with msets(m - h, n - |P|) entries,
+// and within one size k the blocks follow P's rank.  So [lo, hi) meets, for
+// each k, the P of ranks [pa[k], pb[k]) at level k (empty when pa >= pb).
+struct PRanges {
+    int64_t pa[PCV_MAX_PHOTONS + 1], pb[PCV_MAX_PHOTONS + 1];
+};
+void p_ranges(int m, int n, int h, int64_t lo, int64_t hi, PRanges* r);
+// canonical index of the first output whose low part is the level-k multiset of rank `rank`
+int64_t host_lowbase(int m, int n, int h, int k, int64_t rank);
+// rank at level k-1 of the level-k multiset of rank `rank` (over w modes) without its last mode
+int64_t host_parent_rank(int w, int k, int64_t rank);
 // The single-pass plan for the tensor-core products (B = 1): the FP64 tables
 // of all sign vectors, an amplitude buffer when the caller wants
 // probabilities only, and the digit tensors.  Returns the bytes, -1 on overflow.
@@ -213,6 +233,7 @@ struct TcInputs {
     double* prob;                                 // or null
     void* ws;                                     // tc_workspace bytes
     int* error;                                   // device flag, or null
+    int64_t lo, hi;                               // outputs [lo, hi), stored at [o - lo]
 };
 int tc_pad_k(int K);
 int64_t tc_workspace(int m, int n, int K, int64_t total, const int64_t* lowoff, const int64_t* highoff);

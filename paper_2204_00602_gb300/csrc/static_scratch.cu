@@ -72,9 +72,13 @@ extern "C" int pcv_distribution_static(const pcv_c64* U, int m, const uint8_t* i
     for (; c < PCV_MAX_PHOTONS; ++c) p.cols[c] = 0;
     p.norm_t = 1.0 / std::sqrt(f);
 
+    // an output space or plan that does not fit in int64 is a range error, as
+    // in pcv_distribution; only problems too big for the array are ENOMEM
+    if (pcv_num_outputs(m, n) < 0) return static_fail(PCV_ERANGE, "output space C(m+n-1, n) too large");
     pcv::DistPlan dp;
     const int64_t need = pcv::dist_plan(p, 1, PCV_STATIC_SCRATCH_BYTES, amp == nullptr, &dp);
-    if (need < 0 || need > PCV_STATIC_SCRATCH_BYTES)
+    if (need < 0) return static_fail(PCV_ERANGE, "workspace size overflows");
+    if (need > PCV_STATIC_SCRATCH_BYTES)
         return static_fail(PCV_ENOMEM, "problem needs more scratch than PCV_STATIC_SCRATCH_BYTES; "
                                        "use pcv_distribution with a workspace");
     void* scratch = nullptr;

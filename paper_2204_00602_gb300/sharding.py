@@ -8,7 +8,10 @@ the data path:
   model (``circuit_cost``, ``lpt_assign``);
 * outputs of one distribution or one list of explicit outputs, and phase sets
   of a mesh batch: contiguous index ranges [r N / P, (r + 1) N / P)
-  (``index_range``).
+  (``index_range``); ``sharded_distribution`` computes a rank's range of one
+  distribution with pcv_distribution_range, and ``gather_slices`` reassembles
+  the ranges on every rank where the whole array is wanted (an all-gather,
+  the one exchange of the split).
 
 A reduction is needed only where a quantity is a sum over the split:
 
@@ -106,3 +109,39 @@ def local_stats(p_slice: torch.Tensor, q_slice: torch.Tensor) -> torch.Tensor:
 
 def sharded_stats(p_slice: torch.Tensor, q_slice: torch.Tensor) -> torch.Tensor:
     return reduce_sum(local_stats(p_slice, q_slice))
+
+
+def sharded_distribution(U: torch.Tensor, input_occ, *, want_amp: bool = True, ws: torch.Tensor | None = None):
+    """This rank's contiguous range of the distribution of U (one GPU per rank):
+    (lo, hi, prob [hi - lo], amp [hi - lo] or None), canonical outputs lo..hi-1."""
+    from . import distribution_range, num_outputs
+    world, rank = world_and_rank()
+    m = U.shape[0]
+    n = int(np.asarray(input_occ, dtype=np.int64).sum())
+    lo, hi = index_range(num_outputs(m, n), rank, world)
+    prob, amp = distribution_range(U, input_occ, lo, hi, want_amp=want_amp, ws=ws)
+    return lo, hi, prob, amp
+
+
+def gather_slices(local: torch.Tensor, N: int) -> torch.Tensor:
+    """The whole length-N array on every rank, from each rank's slice
+    [index_range(N, rank, world)] (all-gather; complex values travel as pairs
+    of reals)."""
+    world, rank = world_and_rank()
+    if world == 1:
+        return local
+    import torch.distributed as td
+    cplx = local.is_complex()
+    flat = torch.view_as_real(local).reshape(-1) if cplx else local.reshape(-1)
+    per = 2 if cplx else 1
+    cap = (N + world - 1) // world * per
+    buf = torch.zeros(cap, dtype=flat.dtype, device=flat.device)
+    buf[:flat.numel()] = flat
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    td.all_gather(parts, buf)
+    pieces = []
+    for r in range(world):
+        lo, hi = index_range(N, r, world)
+        pieces.append(parts[r][:(hi - lo) * per])
+    whole = torch.cat(pieces)
+    return torch.view_as_complex(whole.reshape(-1, 2)) if cplx else whole

@@ -205,3 +205,63 @@ def test_tensor_core_workspace_sizes(lib):
     assert _abi.pcv_distribution_tc_workspace(12, 6) > 0
     with pytest.raises(_abi.PcvError):
         _abi.pcv_distribution_tc_workspace(20, 11)              # K = 2^{n-1} <= 512
+
+
+def test_auto_algorithm_choice(lib):
+    # host-only: pcv_distribution's AUTO takes the tensor-core products for
+    # 2 <= n <= 10 when the workspace holds their plan, else the FP64 products
+    from paper_2204_00602_gb300 import _abi
+    tc = _abi.pcv_distribution_tc_workspace(20, 10)
+    assert _abi.pcv_distribution_workspace(20, 10) == tc
+    assert _abi.pcv_distribution_auto_algo(20, 10, tc) == _abi.PCV_ALGO_FACTOR_TC
+    assert _abi.pcv_distribution_auto_algo(20, 10, tc - 1) == _abi.PCV_ALGO_FACTOR
+    assert _abi.pcv_distribution_auto_algo(20, 11, 1 << 60) == _abi.PCV_ALGO_FACTOR
+    assert _abi.pcv_distribution_auto_algo(20, 1, 1 << 60) == _abi.PCV_ALGO_FACTOR
+    assert _abi.pcv_distribution_auto_algo(1, 4, 1 << 60) == _abi.PCV_ALGO_FACTOR
+    assert _abi.pcv_distribution_auto_algo(12, 6, 1 << 40) == _abi.PCV_ALGO_FACTOR_TC
+    assert _abi.pcv_distribution_workspace(20, 11) == _abi.pcv_distribution_batched_workspace(1, 20, 11)
+    with pytest.raises(_abi.PcvError):
+        _abi.pcv_distribution_auto_algo(0, 4, 0)
+
+
+def test_static_entry_point_range_errors(lib):
+    # host-only: an output space beyond int64 is a range error (as in
+    # pcv_distribution), reported before any device work
+    from paper_2204_00602_gb300 import _abi
+    fake = 1 << 40
+    with pytest.raises(_abi.PcvError) as e:
+        _abi.pcv_distribution_static(fake, 1024, np.array([1] * 30 + [0] * 994, np.uint8), fake, fake, None)
+    assert e.value.code == _abi.PCV_ERANGE
+
+
+@pytest.mark.parametrize("m,n", [(7, 3), (6, 4), (9, 2), (2, 3), (1, 3), (5, 5)])
+def test_range_plan_against_enumeration(lib, m, n):
+    # host-only: for ranges of the canonical order, the low-side multisets P
+    # (photons in modes [0, h), ranked at their size k) that the range
+    # computes are exactly those of the outputs inside it, found here by
+    # walking itertools' enumeration of S_{m,n}
+    from paper_2204_00602_gb300 import _abi
+    h = max(1, m // 2)
+    outs = list(itertools.combinations_with_replacement(range(m), n))
+    rank_of = {k: {P: i for i, P in enumerate(itertools.combinations_with_replacement(range(h), k))}
+               for k in range(n + 1)}
+    N = len(outs)
+    cuts = sorted({0, 1, N // 3, N // 2, N - 1, N, 5 % (N + 1), (7 * N) // 11})
+    ranges = [(a, b) for a in cuts for b in cuts if a <= b]
+    for begin, end in ranges:
+        want = [[None, None] for _ in range(n + 1)]
+        for S in outs[begin:end]:
+            P = tuple(x for x in S if x < h)
+            r = rank_of[len(P)][P]
+            w = want[len(P)]
+            w[0] = r if w[0] is None else min(w[0], r)
+            w[1] = r + 1 if w[1] is None else max(w[1], r + 1)
+        got = _abi.pcv_distribution_range_plan(m, n, begin, end)
+        for k in range(n + 1):
+            a, b = got[k]
+            if want[k][0] is None:
+                assert a >= b, (begin, end, k, got[k])
+            else:
+                assert (a, b) == tuple(want[k]), (begin, end, k, got[k], want[k])
+    with pytest.raises(_abi.PcvError):
+        _abi.pcv_distribution_range_plan(m, n, 0, N + 1)

@@ -105,7 +105,7 @@ def test_tc_m20_n10_against_fp64_path_and_oracle(pcv):
     m, n = 20, 10
     U = pin.haar_unitary(m, pin.BASE_SEED + 2)
     t = pin.single_photon_input(m, n)
-    p64, a64 = pcv.distribution(dev(U), t)
+    p64, a64 = pcv.distribution(dev(U), t, algo=pcv.PCV_ALGO_FACTOR)
     ptc, atc = pcv.distribution(dev(U), t, algo=pcv.PCV_ALGO_FACTOR_TC)
     torch.cuda.synchronize()
     assert abs(ptc.sum().item() - 1.0) < 1e-12
@@ -127,3 +127,25 @@ def test_tc_workspace_and_limits(pcv):
     U = dev(pin.haar_unitary(12, 7301))
     with pytest.raises(pcv.PcvError):
         pcv.distribution(U, pin.single_photon_input(12, 11), algo=pcv.PCV_ALGO_FACTOR_TC)
+
+
+@pytest.mark.parametrize("branch", ["tc", "fp64", "fp64_min"])
+def test_auto_takes_both_branches(pcv, branch):
+    """pcv_distribution (PCV_ALGO_AUTO): the tensor-core products with the
+    full workspace, the FP64 products with a smaller one (single pass, and the
+    minimum workspace, which runs the sign vectors in chunks); all three
+    against the oracle."""
+    m, n = 12, 6
+    U = pin.haar_unitary(m, 7501)
+    t = pin.single_photon_input(m, n)
+    tc = pcv.abi.pcv_distribution_tc_workspace(m, n)
+    nbytes = {"tc": tc, "fp64": min(tc - 256, pcv.abi.pcv_distribution_batched_workspace(1, m, n)),
+              "fp64_min": pcv.abi.pcv_distribution_workspace_min(m, n)}[branch]
+    want = pcv.PCV_ALGO_FACTOR_TC if branch == "tc" else pcv.PCV_ALGO_FACTOR
+    assert pcv.abi.pcv_distribution_auto_algo(m, n, nbytes) == want
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    prob, amp = pcv.distribution(dev(U), t, ws=ws)
+    torch.cuda.synchronize()
+    p_ref, a_ref = oracle.distribution(U, t)
+    assert amp_err(amp.cpu().numpy(), a_ref, m, n) <= 1e-10
+    assert 0.5 * np.abs(prob.cpu().numpy() - p_ref).sum() <= 1e-12

@@ -83,6 +83,11 @@ def _shard_worker(rank, world, port, out):
     q = pin.dirichlet_target(p.shape[0], 8102)
     lo, hi = sh.index_range(p.shape[0], rank, world)
     ps, qs = p[lo:hi], q[lo:hi]
+    # the ranges reassembled on every rank (the amplitudes as complex values)
+    _, a = oracle.distribution(U, pin.single_photon_input(m, n))
+    res["gathered_p"] = sh.gather_slices(torch.from_numpy(ps.copy()), p.shape[0]).numpy()
+    res["gathered_a"] = sh.gather_slices(torch.from_numpy(a[lo:hi].copy()), p.shape[0]).numpy()
+    res["whole"] = (p, a)
     part = torch.tensor([ps.sum(), 0.5 * np.abs(ps - qs).sum(), float(np.sum(qs * np.log(qs / ps)))],
                         dtype=torch.float64)
     res["stats"] = sh.reduce_sum(part).numpy()
@@ -109,6 +114,9 @@ def test_two_rank_sharding_host_logic():
     # additive statistics: the reduced partial sums are the whole distribution's
     for r in (r0, r1):
         assert np.allclose(r["stats"], r["full"], rtol=1e-13, atol=1e-15)
+        # the gathered ranges are the whole arrays, exactly
+        p, a = r["whole"]
+        assert np.array_equal(r["gathered_p"], p) and np.array_equal(r["gathered_a"], a)
 
 
 def test_index_ranges_cover_exactly():

@@ -54,6 +54,32 @@ def test_static_scratch_matches_workspace_entry_point(pcv, m, n, seed):
         assert abs(prob.sum().item() - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("m,n,seed", [(12, 6, 21), (14, 8, 22)])
+def test_static_scratch_probabilities_only(pcv, m, n, seed):
+    """Probabilities only: the running amplitude sums then live inside the
+    shared array too.  m=12, n=6 takes one pass over the sign vectors; at
+    m=14, n=8 the tables of all 128 sign vectors exceed the array, so the
+    sign vectors run in two passes that add into those sums.  Two calls in a
+    row with different unitaries: nothing of the first may leak into the
+    second."""
+    abi = pcv.abi
+    stream = torch.cuda.current_stream().cuda_stream
+    t = pin.single_photon_input(m, n)
+    N = math.comb(m + n - 1, n)
+    for call in range(2):
+        U = torch.from_numpy(pin.haar_unitary(m, seed + 100 * call)).cuda()
+        p_ref = torch.empty(N, dtype=torch.float64, device="cuda")
+        ws_bytes = abi.pcv_distribution_workspace(m, n)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+        abi.pcv_distribution(U, m, t, p_ref, None, ws, ws_bytes, stream)
+        prob = torch.full((N,), -1.0, dtype=torch.float64, device="cuda")
+        abi.pcv_distribution_static(U, m, t, prob, None, stream)
+        torch.cuda.synchronize()
+        assert 0.5 * (prob - p_ref).abs().sum().item() <= 1e-12
+        assert (prob - p_ref).abs().max().item() <= 1e-12
+        assert abs(prob.sum().item() - 1.0) < 1e-12
+
+
 def test_static_scratch_rejects_problems_that_do_not_fit(pcv):
     abi = pcv.abi
     m, n = 20, 10
