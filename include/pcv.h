@@ -375,28 +375,38 @@ int pcv_distribution_source(const pcv_c64* U, int m, const uint8_t* input_occ, d
 
 /* ------------------------------------------------------------ gradients */
 
-/* dL/dU from dL/da for explicit outputs of one U (n <= 8).
+/* dL/dU from dL/da for explicit outputs of one U, any n the forward calls
+ * take (n <= 30).
  *   grad_amp  device, n_out pcv_c64: dL/dRe a + i dL/dIm a per output
  *   grad_U    device, m*m pcv_c64 (overwritten): dL/dRe U + i dL/dIm U
+ *   workspace device, >= the minimum (pcv_amplitudes_backward_workspace(1, m,
+ *             n, 1)); pcv_amplitudes_backward_workspace(1, m, n, n_out) is the
+ *             default plan, and a smaller workspace runs the outputs in more
+ *             chunks.
  * a(S) is holomorphic in U, so grad_U = sum_S grad_amp_S * conj(da_S/dU), and
  * da_S/dU[k][l] = norm_S * sum over (i, j) with r_i = k, c_j = l of the
  * permanent of the minor of (i, j) (the Laplace expansion of Eq. eqperm's
- * permanent), each minor computed as a Glynn sum over the forward kernel's
- * Gray-code row sums.  The order in which per-output contributions are added
- * is not fixed (FP64 atomics), so repeated calls may differ in the last bits. */
+ * permanent), all minors of one output computed as Glynn sums over the
+ * forward kernels' Gray-code row sums (one warp per output, or per part of
+ * its sign vectors for n > 14).  Every sum is taken in one fixed order (no
+ * atomics), so repeated calls give the same bits.  Outputs whose photon number
+ * differs from the input's contribute nothing. */
+int64_t pcv_amplitudes_backward_workspace(int B, int m, int n, int64_t n_out);
 int pcv_amplitudes_backward(const pcv_c64* U, int m, const uint8_t* input_occ,
                             const uint8_t* output_occ, int64_t n_out, const pcv_c64* grad_amp,
-                            pcv_c64* grad_U, void* stream);
+                            pcv_c64* grad_U, void* workspace, int64_t workspace_bytes, void* stream);
 
-/* The same explicit outputs for B unitaries: grad_amp [B][n_out], grad_U [B][m][m]. */
+/* The same explicit outputs for B unitaries: grad_amp [B][n_out], grad_U
+ * [B][m][m]; workspace from pcv_amplitudes_backward_workspace(B, m, n, n_out). */
 int pcv_amplitudes_backward_multi(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
                                   const uint8_t* output_occ, int64_t n_out, const pcv_c64* grad_amp,
-                                  pcv_c64* grad_U, void* stream);
+                                  pcv_c64* grad_U, void* workspace, int64_t workspace_bytes, void* stream);
 
 /* The same for every output of the distributions of B unitaries (grad_amp
- * [B][C(m+n-1,n)] in canonical order, grad_U [B][m][m]); the workspace holds
- * the multiset-count table used to unrank outputs. */
-int64_t pcv_distribution_backward_workspace(int m, int n);
+ * [B][C(m+n-1,n)] in canonical order, grad_U [B][m][m]); the workspace
+ * (default plan: pcv_distribution_backward_workspace(B, m, n)) also holds the
+ * multiset-count table used to unrank outputs. */
+int64_t pcv_distribution_backward_workspace(int B, int m, int n);
 int pcv_distribution_backward(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
                               const pcv_c64* grad_amp, pcv_c64* grad_U,
                               void* workspace, int64_t workspace_bytes, void* stream);

@@ -63,8 +63,9 @@ SIGNATURES = {
     "pcv_distribution_batched": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
     "pcv_distribution_slos_workspace": (_i64, [_i, _i, _i]),
     "pcv_distribution_slos": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
-    "pcv_amplitudes_backward": (_i, [_vp, _i, _vp, _vp, _i64, _vp, _vp, _vp]),
-    "pcv_distribution_backward_workspace": (_i64, [_i, _i]),
+    "pcv_amplitudes_backward_workspace": (_i64, [_i, _i, _i, _i64]),
+    "pcv_amplitudes_backward": (_i, [_vp, _i, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp]),
+    "pcv_distribution_backward_workspace": (_i64, [_i, _i, _i]),
     "pcv_distribution_backward": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
     "pcv_mesh_unitary": (_i, [_vp, _i, _i, _vp, _vp]),
     "pcv_mesh_backward": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp]),
@@ -90,7 +91,7 @@ SIGNATURES = {
     "pcv_exp_f32_to_f64": (_i, [_vp, _i64, _vp, _vp]),
     "pcv_adam_f64": (_i, [_vp, _vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                           ctypes.c_double, _i, _vp]),
-    "pcv_amplitudes_backward_multi": (_i, [_vp, _i, _i, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "pcv_amplitudes_backward_multi": (_i, [_vp, _i, _i, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp]),
     "pcv_sample": (_i, [_vp, _i, _vp, _vp, _vp, _i64, _vp, _vp]),
     "pcv_fp64_probe": (_i, [_vp, _i, _i, _i, _vp]),
     "pcv_amplitudes_batched_workspace": (_i64, [_i, _i64]),
@@ -274,13 +275,18 @@ def pcv_distribution_batched(U, B, m, input_occ, prob, amp, workspace, workspace
                  workspace_bytes, stream)
 
 
-def pcv_amplitudes_backward(U, m, input_occ, output_occ, n_out, grad_amp, grad_U, stream):
+def pcv_amplitudes_backward_workspace(B, m, n, n_out) -> int:
+    return _call("pcv_amplitudes_backward_workspace", B, m, n, n_out)
+
+
+def pcv_amplitudes_backward(U, m, input_occ, output_occ, n_out, grad_amp, grad_U, workspace, workspace_bytes,
+                            stream):
     return _call("pcv_amplitudes_backward", ptr(U), m, ptr(input_occ), ptr(output_occ), n_out, ptr(grad_amp),
-                 ptr(grad_U), stream)
+                 ptr(grad_U), ptr(workspace), workspace_bytes, stream)
 
 
-def pcv_distribution_backward_workspace(m, n) -> int:
-    return _call("pcv_distribution_backward_workspace", m, n)
+def pcv_distribution_backward_workspace(B, m, n) -> int:
+    return _call("pcv_distribution_backward_workspace", B, m, n)
 
 
 def pcv_distribution_backward(U, B, m, input_occ, grad_amp, grad_U, workspace, workspace_bytes, stream):
@@ -381,9 +387,10 @@ def pcv_adam_f64(w, m, v, g, count, lr, beta1, beta2, eps, step, stream):
     return _call("pcv_adam_f64", ptr(w), ptr(m), ptr(v), ptr(g), count, lr, beta1, beta2, eps, step, stream)
 
 
-def pcv_amplitudes_backward_multi(U, B, m, input_occ, output_occ, n_out, grad_amp, grad_U, stream):
+def pcv_amplitudes_backward_multi(U, B, m, input_occ, output_occ, n_out, grad_amp, grad_U, workspace,
+                                  workspace_bytes, stream):
     return _call("pcv_amplitudes_backward_multi", ptr(U), B, m, ptr(input_occ), ptr(output_occ), n_out,
-                 ptr(grad_amp), ptr(grad_U), stream)
+                 ptr(grad_amp), ptr(grad_U), ptr(workspace), workspace_bytes, stream)
 
 
 def pcv_distribution_slos_workspace(B, m, n) -> int:

@@ -29,7 +29,7 @@ def distribution_backward(U: torch.Tensor, input_occ, grad_amp: torch.Tensor) ->
     B, m = U.shape[0], U.shape[1]
     t = _host_occ(input_occ, m)
     gU = torch.empty_like(U)
-    ws = workspace(abi.pcv_distribution_backward_workspace(m, int(t.sum())), U.device)
+    ws = workspace(abi.pcv_distribution_backward_workspace(B, m, int(t.sum())), U.device)
     abi.pcv_distribution_backward(U, B, m, t, grad_amp.contiguous(), gU, ws, 0 if ws is None else ws.numel(),
                                   _stream(U.device))
     return gU

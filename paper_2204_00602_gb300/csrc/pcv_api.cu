@@ -781,6 +781,15 @@ int pcv_distribution_range(const pcv_c64* U, int m, const uint8_t* input_occ, in
     int n = 0;
     if (m >= 1 && m <= PCV_MAX_MODES && input_occ)
         for (int i = 0; i < m; ++i) n += input_occ[i];
+    if (begin == end) {                           // nothing to write; the buffers may be empty (NULL)
+        pcv::Plan p;
+        const int rc = make_plan(U, m, input_occ, &p);
+        if (rc) return rc;
+        const int64_t N = msets(m, p.n);
+        if (N < 0) return fail(PCV_ERANGE, "output space too large");
+        return end <= N ? PCV_OK : fail(PCV_EINVAL, "output range [%lld, %lld) outside [0, %lld]", (long long)begin,
+                                        (long long)end, (long long)N);
+    }
     if (auto_dist_algo(m, n, workspace ? workspace_bytes : 0) == PCV_ALGO_FACTOR_TC)
         return distribution_tc(U, m, input_occ, begin, end, prob, amp, workspace, workspace_bytes, stream);
     return distribution_factor(U, 1, m, input_occ, begin, end, prob, amp, workspace, workspace_bytes, stream);
@@ -788,67 +797,77 @@ int pcv_distribution_range(const pcv_c64* U, int m, const uint8_t* input_occ, in
 
 // ------------------------------------------------------------- adjoint
 
+// Checks shared by the backward calls; fills the plan for `count` outputs.
+static int backward_common(const pcv_c64* U, int B, int m, const uint8_t* input_occ, int64_t count,
+                           const pcv_c64* grad_amp, pcv_c64* grad_U, void* workspace, int64_t workspace_bytes,
+                           pcv::Plan* p, pcv::AdjPlan* ap)
+{
+    int rc = make_plan(U, m, input_occ, p);
+    if (rc) return rc;
+    if (B < 1 || B > 65535) return fail(PCV_EINVAL, "batch %d outside [1, 65535]", B);
+    if (count < 0) return fail(PCV_EINVAL, "n_out < 0");
+    if (!grad_U || !aligned(grad_U, 16)) return fail(PCV_EINVAL, "grad_U is NULL or misaligned");
+    if (count > 0 && (!grad_amp || !aligned(grad_amp, 16))) return fail(PCV_EINVAL, "bad gradient pointer");
+    if (workspace && !aligned(workspace, 256)) return fail(PCV_EINVAL, "workspace is not 256-byte aligned");
+    *ap = pcv::adjoint_plan(m, p->n, B, count, workspace ? workspace_bytes : 0);
+    if (count > 0 && p->n > 0 && (!workspace || workspace_bytes < (int64_t)ap->min_total))
+        return fail(PCV_ENOMEM, "workspace of at least %lld bytes needed, %lld given", (long long)ap->min_total,
+                    (long long)workspace_bytes);
+    return PCV_OK;
+}
+
+int64_t pcv_amplitudes_backward_workspace(int B, int m, int n, int64_t n_out)
+{
+    if (B < 1 || m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS || n_out < 0)
+        return fail(PCV_EINVAL, "bad sizes");
+    return (int64_t)pcv::adjoint_plan(m, n, B, n_out, -1).total;
+}
+
 int pcv_amplitudes_backward(const pcv_c64* U, int m, const uint8_t* input_occ,
                             const uint8_t* output_occ, int64_t n_out, const pcv_c64* grad_amp,
-                            pcv_c64* grad_U, void* stream)
+                            pcv_c64* grad_U, void* workspace, int64_t workspace_bytes, void* stream)
 {
-    pcv::Plan p;
-    int rc = make_plan(U, m, input_occ, &p);
-    if (rc) return rc;
-    if (p.n > pcv::adjoint_max_photons()) return fail(PCV_EINVAL, "adjoint supports n <= %d (n=%d)", pcv::adjoint_max_photons(), p.n);
-    if (n_out < 0) return fail(PCV_EINVAL, "n_out < 0");
-    if (!grad_U || !aligned(grad_U, 16)) return fail(PCV_EINVAL, "grad_U is NULL or misaligned");
-    if (n_out > 0 && (!output_occ || !grad_amp || !aligned(grad_amp, 16))) return fail(PCV_EINVAL, "bad output or gradient pointer");
-    if ((n_out + 127) / 128 > INT32_MAX) return fail(PCV_ERANGE, "too many outputs");
-    cudaError_t e = pcv::launch_adjoint(p, (const double2*)U, 1, output_occ, nullptr, n_out, (const double2*)grad_amp,
-                                        (double2*)grad_U, (cudaStream_t)stream);
-    return e == cudaSuccess ? PCV_OK : cuda_fail(e, "adjoint");
+    return pcv_amplitudes_backward_multi(U, 1, m, input_occ, output_occ, n_out, grad_amp, grad_U, workspace,
+                                         workspace_bytes, stream);
 }
 
 int pcv_amplitudes_backward_multi(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
                                   const uint8_t* output_occ, int64_t n_out, const pcv_c64* grad_amp,
-                                  pcv_c64* grad_U, void* stream)
+                                  pcv_c64* grad_U, void* workspace, int64_t workspace_bytes, void* stream)
 {
     pcv::Plan p;
-    int rc = make_plan(U, m, input_occ, &p);
+    pcv::AdjPlan ap;
+    int rc = backward_common(U, B, m, input_occ, n_out, grad_amp, grad_U, workspace, workspace_bytes, &p, &ap);
     if (rc) return rc;
-    if (B < 1 || B > 65535) return fail(PCV_EINVAL, "batch %d outside [1, 65535]", B);
-    if (p.n > pcv::adjoint_max_photons()) return fail(PCV_EINVAL, "adjoint supports n <= %d (n=%d)", pcv::adjoint_max_photons(), p.n);
-    if (n_out < 0) return fail(PCV_EINVAL, "n_out < 0");
-    if (!grad_U || !aligned(grad_U, 16)) return fail(PCV_EINVAL, "grad_U is NULL or misaligned");
-    if (n_out > 0 && (!output_occ || !grad_amp || !aligned(grad_amp, 16))) return fail(PCV_EINVAL, "bad output or gradient pointer");
-    if ((n_out + 127) / 128 > INT32_MAX) return fail(PCV_ERANGE, "too many outputs");
-    cudaError_t e = pcv::launch_adjoint(p, (const double2*)U, B, output_occ, nullptr, n_out, (const double2*)grad_amp,
-                                        (double2*)grad_U, (cudaStream_t)stream);
+    if (n_out > 0 && !output_occ) return fail(PCV_EINVAL, "output_occ is NULL");
+    cudaError_t e = pcv::launch_adjoint(p, (const double2*)U, B, output_occ, n_out, (const double2*)grad_amp,
+                                        (double2*)grad_U, workspace, ap, (cudaStream_t)stream);
     return e == cudaSuccess ? PCV_OK : cuda_fail(e, "adjoint");
 }
 
-int64_t pcv_distribution_backward_workspace(int m, int n)
+int64_t pcv_distribution_backward_workspace(int B, int m, int n)
 {
-    if (m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "bad sizes");
-    return (int64_t)align256((size_t)(m + 1) * (n + 1) * sizeof(int64_t));
+    if (B < 1 || m < 1 || m > PCV_MAX_MODES || n < 0 || n > PCV_MAX_PHOTONS) return fail(PCV_EINVAL, "bad sizes");
+    const int64_t N = msets(m, n);
+    if (N < 0) return fail(PCV_ERANGE, "output space too large");
+    return (int64_t)pcv::adjoint_plan(m, n, B, N, -1).total;
 }
 
 int pcv_distribution_backward(const pcv_c64* U, int B, int m, const uint8_t* input_occ,
                               const pcv_c64* grad_amp, pcv_c64* grad_U,
                               void* workspace, int64_t workspace_bytes, void* stream)
 {
+    int n = 0;
+    if (m >= 1 && m <= PCV_MAX_MODES && input_occ)
+        for (int i = 0; i < m; ++i) n += input_occ[i];
+    const int64_t N = msets(m, std::min(n, PCV_MAX_PHOTONS));
+    if (N < 0) return fail(PCV_ERANGE, "output space too large");
     pcv::Plan p;
-    int rc = make_plan(U, m, input_occ, &p);
+    pcv::AdjPlan ap;
+    int rc = backward_common(U, B, m, input_occ, N, grad_amp, grad_U, workspace, workspace_bytes, &p, &ap);
     if (rc) return rc;
-    if (B < 1 || B > 65535) return fail(PCV_EINVAL, "batch %d outside [1, 65535]", B);
-    if (p.n > pcv::adjoint_max_photons()) return fail(PCV_EINVAL, "adjoint supports n <= %d (n=%d)", pcv::adjoint_max_photons(), p.n);
-    if (!grad_U || !aligned(grad_U, 16) || !grad_amp || !aligned(grad_amp, 16)) return fail(PCV_EINVAL, "bad gradient pointer");
-    const int64_t N = msets(m, p.n);
-    if (N < 0 || (N + 127) / 128 > INT32_MAX) return fail(PCV_ERANGE, "output space too large");
-    const int64_t need = pcv_distribution_backward_workspace(m, p.n);
-    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
-        return fail(PCV_ENOMEM, "workspace of %lld bytes (256-byte aligned) needed", (long long)need);
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = pcv::build_multiset_table((int64_t*)workspace, m, p.n, s);
-    if (e == cudaSuccess)
-        e = pcv::launch_adjoint(p, (const double2*)U, B, nullptr, (const int64_t*)workspace, N,
-                                (const double2*)grad_amp, (double2*)grad_U, s);
+    cudaError_t e = pcv::launch_adjoint(p, (const double2*)U, B, nullptr, N, (const double2*)grad_amp,
+                                        (double2*)grad_U, workspace, ap, (cudaStream_t)stream);
     return e == cudaSuccess ? PCV_OK : cuda_fail(e, "distribution adjoint");
 }
 

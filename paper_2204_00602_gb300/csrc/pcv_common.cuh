@@ -146,10 +146,25 @@ struct MultQueue {
 cudaError_t launch_glynn_mult(const pcv_batch_desc& d, int parts, int side, double2* partial, cudaStream_t s);
 cudaError_t launch_glynn_mult_persistent(const pcv_batch_desc* descs, const MultQueue& q, int sms, cudaStream_t s);
 
-// Adjoint (adjoint.cu), mesh (mesh.cu), reductions (reduce.cu)
+// Adjoint (adjoint.cu): the plan of one call (B batch entries, `count`
+// outputs each) in a workspace of ws_bytes (< 0: the default budget): Gray
+// sequence split in `parts` of part_steps, lanes per row q and columns per
+// lane cj of the G matrix, outputs per chunk, and the bytes used.
+struct AdjPlan {
+    int parts;
+    int64_t part_steps;
+    int q, cj;
+    size_t table;             // multiset table (canonical outputs)
+    int64_t chunk;
+    size_t total, min_total;  // bytes of this plan, of a one-output chunk
+};
+AdjPlan adjoint_plan(int m, int n, int B, int64_t count, int64_t ws_bytes);
 int adjoint_max_photons();
-cudaError_t launch_adjoint(const Plan& p, const double2* U, int B, const uint8_t* out_occ, const int64_t* mc_table,
-                           int64_t count, const double2* gbar, double2* gradU, cudaStream_t s);
+// out_occ: explicit outputs [count][m] (device) or null for every output of
+// S_{m,n} in canonical order; dL/dU [B][m][m] is overwritten.
+cudaError_t launch_adjoint(const Plan& p, const double2* U, int B, const uint8_t* out_occ, int64_t count,
+                           const double2* gbar, double2* gradU, void* ws, const AdjPlan& ap, cudaStream_t s);
+// Mesh (mesh.cu), reductions (reduce.cu)
 int mesh_max_modes();
 cudaError_t launch_mesh_forward(const double* phases, int B, int m, double2* U, cudaStream_t s);
 cudaError_t launch_mesh_backward(const double* phases, int B, int m, const double2* U, const double2* G,

@@ -27,7 +27,7 @@ import numpy as np
 import torch
 
 from . import _abi as abi
-from . import _stream
+from . import _stream, workspace
 from .autograd import dist_stats, mesh_backward, mesh_unitary
 from .surrogate import MLP, exact_log_probs, init_weights, output_set
 
@@ -48,6 +48,7 @@ class MeshProblem:
         self.prob = torch.empty(B, n_set, dtype=torch.float64, device=self.dev)
         self.gamp = torch.empty_like(self.amp)
         self.gU = torch.empty(B, m, m, dtype=torch.complex128, device=self.dev)
+        self.bws = workspace(abi.pcv_amplitudes_backward_workspace(B, m, n, n_set), self.dev)
 
     @property
     def stream(self):
@@ -67,7 +68,8 @@ class MeshProblem:
         U, p = self.probs(phases)
         B = phases.shape[0]
         abi.pcv_kl_grad(p, self.q, self.amp, self.n_set, B, 0, None, 1.0, self.gamp, self.stream)
-        abi.pcv_amplitudes_backward_multi(U, B, self.m, self.t, self.outs, self.n_set, self.gamp, self.gU, self.stream)
+        abi.pcv_amplitudes_backward_multi(U, B, self.m, self.t, self.outs, self.n_set, self.gamp, self.gU, self.bws,
+                                          self.bws.numel(), self.stream)
         return mesh_backward(phases, U, self.gU)
 
 

@@ -55,23 +55,68 @@ def test_mesh_backward_matches_finite_differences(ag):
             assert abs(g[b, q] - fd) < 1e-8
 
 
-@pytest.mark.parametrize("m,n", [(4, 1), (5, 3), (6, 4), (8, 6), (9, 8)])
+def backward(pcv, U, m, tin, outs, g, ws_bytes=None):
+    """pcv_amplitudes_backward through the C ABI; dL/dU as numpy."""
+    n = int(np.asarray(tin).sum())
+    if ws_bytes is None:
+        ws_bytes = pcv.abi.pcv_amplitudes_backward_workspace(1, m, n, len(outs))
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device="cuda")
+    gU = torch.empty(m, m, dtype=torch.complex128, device="cuda")
+    pcv.abi.pcv_amplitudes_backward(dev(U), m, tin, dev(outs), len(outs), dev(g), gU, ws, ws_bytes,
+                                    torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return gU.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,n", [(4, 1), (5, 3), (6, 4), (8, 6), (9, 8), (12, 10), (14, 12)])
 def test_adjoint_matches_laplace_gradient(pcv, m, n):
+    """Against the oracle's Laplace expansion (each dPerm/dA[i][j] the permanent
+    of a minor, by Ryser), single-photon and bunched inputs, bunched outputs,
+    up to n = 12."""
     U = pin.haar_unitary(m, 60 + n)
     t = pin.single_photon_input(m, n)
     t2 = t.copy()
     if n >= 3:                                  # a bunched input as well
         t2[1] = 0; t2[0] = 2
     for tin in (t, t2):
-        outs = pin.random_bunched_outputs(m, n, 12, 70 + n)
+        outs = pin.random_bunched_outputs(m, n, 12 if n <= 10 else 4, 70 + n)
         g = pin.random_complex_matrix(1, len(outs), 80 + n)[0]
         want = oracle.grad_U_from_amp_grad(U, tin, outs, g)
-        gU = torch.empty(m, m, dtype=torch.complex128, device="cuda")
-        pcv.abi.pcv_amplitudes_backward(dev(U), m, tin, dev(outs), len(outs), dev(g), gU,
-                                        torch.cuda.current_stream().cuda_stream)
-        torch.cuda.synchronize()
-        got = gU.cpu().numpy()
+        got = backward(pcv, U, m, tin, outs, g)
         assert np.abs(got - want).max() <= 1e-10 * max(1.0, np.abs(want).max())
+
+
+@pytest.mark.parametrize("m,n", [(18, 16), (22, 20)])
+def test_adjoint_large_n_split_sign_vectors(pcv, m, n):
+    """n = 16 and 20: each output's sign vectors split into parts (several
+    warps), summed in part order; against the oracle's Laplace gradient on
+    collision-free outputs (tolerance 1e-8, as the forward path's for n > 12)."""
+    U = pin.haar_unitary(m, 160 + n)
+    t = pin.single_photon_input(m, n)
+    outs = pin.random_outputs(m, n, 2, 170 + n)
+    g = pin.random_complex_matrix(1, len(outs), 180 + n)[0]
+    want = oracle.grad_U_from_amp_grad(U, t, outs, g)
+    got = backward(pcv, U, m, t, outs, g)
+    assert np.abs(got - want).max() <= 1e-8 * max(1.0, np.abs(want).max())
+
+
+def test_adjoint_is_deterministic_and_chunks_agree(pcv):
+    """The same call twice gives the same bits (fixed summation order, no
+    atomics); the smallest workspace (one output per chunk) gives the same
+    gradient up to the order in which chunks are added."""
+    m, n = 10, 7
+    U = pin.haar_unitary(m, 190)
+    t = pin.single_photon_input(m, n)
+    outs = pin.random_bunched_outputs(m, n, 600, 191)
+    g = pin.random_complex_matrix(1, len(outs), 192)[0]
+    a = backward(pcv, U, m, t, outs, g)
+    b = backward(pcv, U, m, t, outs, g)
+    assert np.array_equal(a, b)
+    small = pcv.abi.pcv_amplitudes_backward_workspace(1, m, n, 1)
+    c = backward(pcv, U, m, t, outs, g, ws_bytes=small)
+    assert np.abs(c - a).max() <= 1e-13 * np.abs(a).max()
+    with pytest.raises(pcv.PcvError):
+        backward(pcv, U, m, t, outs, g, ws_bytes=small - 256)
 
 
 def test_distribution_backward_batched(pcv, ag):
