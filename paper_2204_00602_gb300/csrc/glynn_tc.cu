@@ -42,12 +42,13 @@
 //   tc_product_kernel   one persistent CTA per SM walking 128 x N output
 //                       tiles of one block each (N = 16..64; the single-entry
 //                       columns ride in the tile of the block k = 1 or n-1
-//                       with the same rows when both fit), ten warps:
-//   warp 0  TMA producer: per 64-wide K block, the 8 digit slices of the
+//                       with the same rows when both fit), eleven warps:
+//   warp 0  row-operand TMA: per 64-wide K block, the 8 digit slices of the
+//           row operand one at a time (16 KB slots, six in flight, digits in
+//           the order 0 7 1 6 2 5 3 4), 128B swizzle;
+//   warp 10 column-operand TMA: per K block the 8 digit slices of the
 //           column operand (N rows each, packed one after the other in a
-//           64 KB set, double-buffered), then the 8 digit slices of the row
-//           operand one at a time (16 KB slots, six in flight, digits in the
-//           order 0 7 1 6 2 5 3 4), 128B swizzle;
+//           64 KB set, double-buffered);
 //   warp 1  MMA issuer: the accumulator of diagonal d sits at TMEM columns
 //           d N .. d N + N - 1, so the products of row digit i with column
 //           digits j = j0 .. j1 land on the contiguous columns (i + j0) N ..
@@ -62,7 +63,9 @@
 //           accumulators are then handed back to the MMA, and the rounding
 //           and stores follow.  t1 and t2 are stored at the output's
 //           canonical index in a [2][outputs] buffer; after t3 the thread
-//           that stored them forms the amplitude and |a|^2 in place.
+//           that stored them forms the amplitude and |a|^2 in place.  Tile
+//           rows are high-side entries wherever there are 128 of them, so a
+//           warp's 32 lanes hold consecutive outputs and its stores coalesce.
 // Every mbarrier wait is bounded; on a time-out the kernel records an error
 // code and returns after releasing its tensor memory.
 
@@ -86,7 +89,8 @@ constexpr uint32_t kRowBytes = TBK * 2;                 // one 64-wide K row of 
 constexpr uint32_t kBBytes = kDigits * TBN * kRowBytes; // 64 KB: all digit slices of the column operand
 constexpr int kBSub = 16;                               // rows per column load when N < 64
 constexpr uint32_t kSmemBytes = kBSets * kBBytes + kASlots * kABytes + 1024;
-constexpr int kThreads = 320;                            // warp 0 TMA, warp 1 MMA, warps 2-9 drain
+constexpr int kColWarp = 10;                             // its lane 0 loads the column operand
+constexpr int kThreads = 352;                            // warp 0 row loads, 1 MMA, 2-9 drain, 10 column loads
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kMaxPolls = 1ll << 26;               // default bound of one mbarrier wait
 constexpr int kNoExp = -100000;                          // an all-zero row
@@ -588,59 +592,15 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
     const long long polls = a.max_polls;
 
     if (tid == 0) {
-        // ---------------- TMA producer
-        // chunk q = (tile it, product t, K block c), in that nesting; the tile
-        // of the next chunk is looked up once, when the chunk crosses into it
-        uint32_t na = 0, nb = 0;                                      // row and column loads issued
-        auto issue_b = [&](uint32_t q, const TileInfo& tb, int t, int c) -> bool {
-            const uint32_t bs = q % kBSets;
-            if (q >= kBSets && !mbar_wait(&bempty[bs], ((q / kBSets) - 1) & 1, polls)) return false;
-            // slice j at rows j N .. j N + N - 1 of the set: one 64-row box, or
-            // N / 16 boxes of 16 rows
-            unsigned char* dst = bset + bs * kBBytes;
-            mbar_expect_tx(&bfull[bs], (uint32_t)(kDigits * tb.tn) * kRowBytes);
-            if (tb.tn == TBN && a.ecols[tb.kb] == 0) {
-                const CUtensorMap* cmap = tb.rl ? &high_cols : &low_cols;
-                for (int j = 0; j < kDigits; ++j)
-                    tma_load_4d(dst + j * TBN * kRowBytes, cmap, &bfull[bs], c * TBK, tb.centry, j, t);
-            } else {
-                // 16-row boxes; those at or past ecol0 come from the vectors
-                // of the single-entry columns (ecol0 is a multiple of 16)
-                const int e0 = a.ecol0[tb.kb];
-                const CUtensorMap* nmap = tb.rl ? &high_cols16 : &low_cols16;
-                const CUtensorMap* vmap = tb.rl ? &vlow16 : &vhigh16;
-                for (int j = 0; j < kDigits; ++j)
-                    for (int r = 0; r < tb.tn; r += kBSub) {
-                        const int lc = (int)tb.c0 + r;
-                        if (lc < e0)
-                            tma_load_4d(dst + (j * tb.tn + r) * kRowBytes, nmap, &bfull[bs], c * TBK, tb.centry + r, j, t);
-                        else
-                            tma_load_4d(dst + (j * tb.tn + r) * kRowBytes, vmap, &bfull[bs], c * TBK, lc - e0, j, t);
-                    }
-            }
-            nb = q + 1;
-            return true;
-        };
-        TileInfo ti = {}, tnext = {};
-        if (my_tiles > 0) {
-            ti = tile_info(a, blockIdx.x);
-            if (!issue_b(0, ti, 0, 0)) s_fail = 1;
-        }
-        uint32_t q = 0;
+        // ---------------- row-operand producer: for every chunk q = (tile,
+        // product t, K block c), in that nesting, the 8 digit slices of the
+        // row tile, one per slot, in the MMA's digit order
+        uint32_t na = 0;                                              // row slices issued
         for (int64_t it = 0; it < my_tiles && !s_fail; ++it) {
-            if (it > 0) ti = tnext;
+            const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
             const CUtensorMap* rmap = ti.rl ? &low_rows : &high_rows;
             for (int t = 0; t < 3 && !s_fail; ++t) {
-                for (int c = 0; c < nkb && !s_fail; ++c, ++q) {
-                    int tn1 = t, cn1 = c + 1;                       // the chunk after this one
-                    bool next_tile = false;
-                    if (cn1 == nkb) {
-                        cn1 = 0;
-                        if (++tn1 == 3) {
-                            tn1 = 0;
-                            next_tile = true;
-                        }
-                    }
+                for (int c = 0; c < nkb && !s_fail; ++c) {
                     for (int ii = 0; ii < kDigits; ++ii) {
                         const uint32_t as = na % kASlots;
                         if (na >= (uint32_t)kASlots && !mbar_wait(&aempty[as], ((na / kASlots) - 1) & 1, polls)) {
@@ -650,22 +610,57 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                         mbar_expect_tx(&afull[as], kABytes);
                         tma_load_4d(aslot + as * kABytes, rmap, &afull[as], c * TBK, ti.rentry, slice_order(ii), t);
                         ++na;
-                        if (ii == 2 && q + 1 < nchunks) {
-                            if (next_tile) tnext = tile_info(a, blockIdx.x + (it + 1) * gridDim.x);
-                            if (!issue_b(q + 1, next_tile ? tnext : ti, tn1, cn1)) {
-                                s_fail = 1;
-                                break;
-                            }
-                        }
                     }
                 }
             }
         }
         // every load issued lands in this CTA's shared memory: wait for the
         // ones no consumer waited for before the CTA may exit
-        const bool rows_in = tcx::wait_issued(afull, kASlots, na);
-        const bool cols_in = tcx::wait_issued(bfull, kBSets, nb);
-        if (!(rows_in && cols_in) && !s_fail) s_fail = 4;
+        if (!tcx::wait_issued(afull, kASlots, na) && !s_fail) s_fail = 4;
+    } else if (tid == kColWarp * 32) {
+        // ---------------- column-operand producer: for every chunk, the digit
+        // slices of the column tile packed one after the other in a set
+        // (double-buffered), so a slow set never holds up the row slices
+        uint32_t q = 0;                                               // column sets issued
+        for (int64_t it = 0; it < my_tiles && !s_fail; ++it) {
+            const TileInfo tb = tile_info(a, blockIdx.x + it * gridDim.x);
+            for (int t = 0; t < 3 && !s_fail; ++t) {
+                for (int c = 0; c < nkb && !s_fail; ++c, ++q) {
+                    const uint32_t bs = q % kBSets;
+                    if (q >= kBSets && !mbar_wait(&bempty[bs], ((q / kBSets) - 1) & 1, polls)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    // slice j at rows j N .. j N + N - 1 of the set: one 64-row
+                    // box, or N / 16 boxes of 16 rows
+                    unsigned char* dst = bset + bs * kBBytes;
+                    mbar_expect_tx(&bfull[bs], (uint32_t)(kDigits * tb.tn) * kRowBytes);
+                    if (tb.tn == TBN && a.ecols[tb.kb] == 0) {
+                        const CUtensorMap* cmap = tb.rl ? &high_cols : &low_cols;
+                        for (int j = 0; j < kDigits; ++j)
+                            tma_load_4d(dst + j * TBN * kRowBytes, cmap, &bfull[bs], c * TBK, tb.centry, j, t);
+                    } else {
+                        // 16-row boxes; those at or past ecol0 come from the
+                        // vectors of the single-entry columns (ecol0 is a
+                        // multiple of 16)
+                        const int e0 = a.ecol0[tb.kb];
+                        const CUtensorMap* nmap = tb.rl ? &high_cols16 : &low_cols16;
+                        const CUtensorMap* vmap = tb.rl ? &vlow16 : &vhigh16;
+                        for (int j = 0; j < kDigits; ++j)
+                            for (int r = 0; r < tb.tn; r += kBSub) {
+                                const int lc = (int)tb.c0 + r;
+                                if (lc < e0)
+                                    tma_load_4d(dst + (j * tb.tn + r) * kRowBytes, nmap, &bfull[bs], c * TBK,
+                                                tb.centry + r, j, t);
+                                else
+                                    tma_load_4d(dst + (j * tb.tn + r) * kRowBytes, vmap, &bfull[bs], c * TBK,
+                                                lc - e0, j, t);
+                            }
+                    }
+                }
+            }
+        }
+        if (!tcx::wait_issued(bfull, kBSets, q) && !s_fail) s_fail = 4;
     } else if (tid == 32) {
         // ---------------- MMA issuer
         uint32_t na = 0, q = 0, g = 0;                               // slices, chunks, passes
@@ -720,7 +715,7 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             mma_commit(&mma_done);
             if (!mbar_wait(&mma_done, 0, tcx::kCleanupPolls) && !s_fail) s_fail = 4;
         }
-    } else if (warp >= 2) {
+    } else if (warp >= 2 && warp < kColWarp) {
         // ---------------- drain: warp w owns TMEM lanes 32 (w mod 4) .. + 31;
         // warps 2-5 take the 16-column chunks at 0 and 32, warps 6-9 those at
         // 16 and 48 (so a 32-wide tile keeps all eight busy)
@@ -799,7 +794,26 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                 }
                 tcx::fence_before_sync();
                 mbar_arrive(&accempty);
-                if (!rv) continue;
+                // the per-column data of this warp's two 16-column chunks:
+                // lane l loads that of column l mod 16 of each chunk, and the
+                // loop below broadcasts it (no loads inside the loop)
+                int ecl[2];
+                int64_t lbl[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t col = ti.c0 + cbase + 32 * h + (lane & 15);
+                    const int64_t ce = col - e0;
+                    ecl[h] = kNoExp;
+                    lbl[h] = 0;
+                    if (cbase + 32 * h < tn) {
+                        if (col >= e0) {
+                            if (ce < necol) ecl[h] = ex_e[(int64_t)t * necol + ce];
+                        } else if (col < ncol) {
+                            ecl[h] = ex_c[(int64_t)t * wc + a.col_off[kb] + col];
+                            if (!rl) lbl[h] = a.lowbase[a.lowoff[kb] + col];
+                        }
+                    }
+                }
                 // t1 and t2 go to the workspace; with t3, the same thread
                 // forms a = (t1 - t2) + i (t3 - t1 - t2) and |a|^2
 #pragma unroll
@@ -808,18 +822,19 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                     if (cc >= tn) continue;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
+                        const int ec = __shfl_sync(0xffffffffu, ecl[h], q);
+                        const int64_t lb = __shfl_sync(0xffffffffu, lbl[h], q);
                         const int64_t col = ti.c0 + cc + q;
                         const bool is_e = col >= e0;       // a single-entry column: mode ce of this side
                         const int64_t ce = col - e0;
-                        if (is_e ? (ce >= necol || ce < emx) : (col >= ncol)) continue;
-                        const int ec = is_e ? ex_e[(int64_t)t * necol + ce] : ex_c[(int64_t)t * wc + a.col_off[kb] + col];
+                        if (!rv || (is_e ? (ce >= necol || ce < emx) : (col >= ncol))) continue;
                         double x = 0.0;
                         if (er != kNoExp && ec != kNoExp) {
                             const int sc = er + ec - 14;
                             if (!scale_packed(zh[h][q], zl[h][q], sc - 49, x))
                                 x = fma((double)zl[h][q], pow2(sc - 49), (double)zh[h][q] * pow2(sc - 21));
                         }
-                        const int64_t og = is_e ? ebase + ce : (rl ? pbase + col : a.lowbase[a.lowoff[kb] + col] + row);
+                        const int64_t og = is_e ? ebase + ce : (rl ? pbase + col : lb + row);
                         if (og < a.lo || og >= a.hi) continue;
                         const int64_t o = og - a.lo, span = a.hi - a.lo;
                         if (t < 2) {
@@ -1163,7 +1178,12 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     for (int k = 1; k < in.n; ++k) {
         const int64_t M = msets_tc(in.h, k), N = msets_tc(in.m - in.h, in.n - k);
         if (M == 0 || N == 0) continue;
-        const bool rl = M >= N;
+        // Rows are the high-side entries Q unless Q has fewer entries than a
+        // tile's 128 rows (and P more), which would leave most rows empty.
+        // With Q on the rows, the 32 lanes of a drain warp hold consecutive Q
+        // of one P, i.e. consecutive canonical outputs, so each store of the
+        // drain is one contiguous 256-byte run.
+        const bool rl = N < TBM && M > N;
         const int64_t rows = rl ? M : N, cols = rl ? N : M;
         const bool any = pr.pa[k] < pr.pb[k];
         a.rows_low[a.nk] = rl ? 1 : 0;
