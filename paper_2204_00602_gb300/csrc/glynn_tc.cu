@@ -11,11 +11,14 @@
 // into integer digits (the error-free splitting idea of Ozaki, Ogita, Oishi
 // and Rump, 2012):
 //
-//   * each row (table entry, per product t) gets an exponent E with
-//     max_d |x(d)| <= 2^{E-1}; X = round(x 2^{56-E}) is an integer with
-//     |X| <= 2^55, written as 8 balanced base-128 digits,
+//   * each row gets an exponent E with max_d |x(d)| <= 2^{E-1}; X =
+//     round(x 2^{56-E}) is an integer with |X| <= 2^55, written as 8
+//     balanced base-128 digits,
 //         X = sum_{i=0..7} D_i 128^{7-i},   |D_i| <= 64,
-//     so x = 2^E sum_i D_i 2^{-7(i+1)} up to 2^{E-56} (FP64 accuracy);
+//     so x = 2^E sum_i D_i 2^{-7(i+1)} up to 2^{E-56} (FP64 accuracy).  A
+//     table entry's re and im share one exponent one bit higher (54 bits
+//     each), and its third operand is the integer X_re + X_im; the per-mode
+//     vectors of the single-entry columns keep one exponent per product;
 //   * a digit is an integer of at most 7 bits, exact in BF16, and a product of
 //     two is at most 2^12; over K <= 512 sign vectors a digit-pair product
 //     sums to at most 2^21, and the 8 pairs (i, j) of one diagonal i + j = d
@@ -127,18 +130,18 @@ __global__ void split_exp_kernel(const double2* __restrict__ T, const double* __
 }
 
 // X = round(x 2^{56-E}) as a signed integer, |X| <= 2^55 (the magnitude
-// rounded half up; 0 for x = 0 or an all-zero row).
+// rounded half up; 0 for x = 0 or an all-zero row), for |x| <= 2^{E-1}.  With
+// the 53-bit mantissa m, X = m 2^{sh} for sh = e - 1019 - E <= 3 (e the
+// exponent field): one right shift of 16 m by s = 4 - sh >= 1, rounded half
+// up, covers every case without branches.
 __device__ __forceinline__ long long fixed_of(double x, int E)
 {
     const long long bits = __double_as_longlong(x);
     const int ef = (int)((bits >> 52) & 0x7FF);
-    unsigned long long M = 0;
-    if (ef != 0 && E != kNoExp) {
-        const unsigned long long mant = (unsigned long long)(bits & ((1ll << 52) - 1)) | (1ull << 52);
-        const int sh = ef - 1019 - E;                      // M = mant 2^{sh}, sh <= 3
-        if (sh >= 0) M = mant << sh;
-        else if (sh > -60) M = (mant + (1ull << (-sh - 1))) >> (-sh);
-    }
+    const unsigned long long m16 = ((unsigned long long)(bits & ((1ll << 52) - 1)) | (1ull << 52)) << 4;
+    const int s = min(max(4 - (ef - 1019 - E), 1), 64);
+    unsigned long long M = s < 64 ? (m16 + (1ull << (s - 1))) >> s : 0ull;
+    if (ef == 0 || E == kNoExp) M = 0;
     return bits < 0 ? -(long long)M : (long long)M;
 }
 
@@ -173,9 +176,9 @@ __device__ __forceinline__ uint32_t bf16_pair(unsigned long long P0, unsigned lo
 // sqrt(multiplicity of r in P), level 0 being sigma(d) 2^{-(n-1)} norm_t on
 // the low side and 1 on the high side.  Kpad / 128 warps per entry P (one
 // for Kpad <= 128), each lane holding 4 sign vectors (2 at Kpad = 64; those
-// >= K are zero): the three row exponents (re, im, re + im) are maxima over the
-// entry's warps, so the digits [3][8][entry][Kpad] are written in the same
-// pass.  Levels below
+// >= K are zero): the entry's exponent (one for re, im and re + im) is a
+// maximum over its warps, so the digits [3][8][entry][Kpad] are written in
+// the same pass.  Levels below
 // n - 1 also keep the complex entries, entry-major [entry][K], as the parents
 // of the next level.  Low side: writes lowbase of each entry.
 struct TcLevelArgs {
@@ -276,8 +279,7 @@ __global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
     constexpr int RUN = PER < 8 ? PER : 8;
     const int qbase = part * 32 * PER;
     double2 v[PER];
-    double sv[PER];
-    int f0 = 0, f1 = 0, f2 = 0;
+    int fc = 0;                                            // largest exponent field of re and im
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         const int q = qbase + (j / RUN) * 32 * RUN + lane * RUN + (j % RUN);
@@ -298,42 +300,38 @@ __global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
             v[j] = cmul(pv, y);
             if (a.out) a.out[e * a.K + q] = v[j];
         }
-        sv[j] = v[j].x + v[j].y;
-        f0 = max(f0, exp_field(v[j].x));
-        f1 = max(f1, exp_field(v[j].y));
-        f2 = max(f2, exp_field(sv[j]));
+        fc = max(fc, max(exp_field(v[j].x), exp_field(v[j].y)));
     }
-    f0 = __reduce_max_sync(0xffffffffu, f0);
-    f1 = __reduce_max_sync(0xffffffffu, f1);
-    f2 = __reduce_max_sync(0xffffffffu, f2);
+    fc = __reduce_max_sync(0xffffffffu, fc);
     if constexpr (WPE > 1) {
-        if (lane == 0) {
-            s_f[warp][0] = f0;
-            s_f[warp][1] = f1;
-            s_f[warp][2] = f2;
-        }
+        if (lane == 0) s_f[warp][0] = fc;
         __syncthreads();
         const int w0 = warp - part;
 #pragma unroll
-        for (int u = 0; u < WPE; ++u) {
-            f0 = max(f0, s_f[w0 + u][0]);
-            f1 = max(f1, s_f[w0 + u][1]);
-            f2 = max(f2, s_f[w0 + u][2]);
-        }
+        for (int u = 0; u < WPE; ++u) fc = max(fc, s_f[w0 + u][0]);
     }
     if (!valid) return;
     const int64_t ent = a.dig_off + e;
+    // One exponent for re, im and re + im of the entry, one bit above their
+    // largest: |re|, |im| <= 2^{E-2}, so |X_re|, |X_im| <= 2^54 and the third
+    // operand X_re + X_im (|.| <= 2^55) is formed exactly in integers; the
+    // third product then equals t1 + t2 + the imaginary part exactly.
+    const int E = fc ? fc - 1020 : kNoExp;
+    if (lane == 0 && part == 0)
+        for (int t = 0; t < 3; ++t) a.ex[(int64_t)t * a.wdig + ent] = E;
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        const int f = t == 0 ? f0 : (t == 1 ? f1 : f2);
-        const int E = f ? f - 1021 : kNoExp;
-        if (lane == 0 && part == 0) a.ex[(int64_t)t * a.wdig + ent] = E;
+    for (int j0 = 0; j0 < PER; j0 += RUN) {
+        long long xr[RUN], xi[RUN];
 #pragma unroll
-        for (int j0 = 0; j0 < PER; j0 += RUN) {
+        for (int j = 0; j < RUN; ++j) {
+            xr[j] = fixed_of(v[j0 + j].x, E);
+            xi[j] = fixed_of(v[j0 + j].y, E);
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
             unsigned long long pk[RUN];
 #pragma unroll
-            for (int j = 0; j < RUN; ++j)
-                pk[j] = digit_word(fixed_of(t == 0 ? v[j0 + j].x : (t == 1 ? v[j0 + j].y : sv[j0 + j]), E));
+            for (int j = 0; j < RUN; ++j) pk[j] = digit_word(t == 0 ? xr[j] : (t == 1 ? xi[j] : xr[j] + xi[j]));
 #pragma unroll
             for (int i = 0; i < kDigits; ++i)
                 store_digit_run<RUN>(a.digits + (((int64_t)t * kDigits + i) * a.wdig + ent) * a.Kpad + qbase + j0 * 32 +

@@ -113,3 +113,70 @@ def test_fp64_scaling_of_the_combined_diagonals():
         lo = sum(acc[d] * 128 ** (7 - d) for d in range(4, 8))
         assert abs(hi) < 1 << 46 and abs(lo) < 1 << 46
         assert hi * (1 << 28) + lo == sum(acc[d] * 128 ** (7 - d) for d in range(8))
+
+
+def fixed_by_shift(x, E):
+    """The kernels' branch-free recipe for fixed(x, E): with the 53-bit
+    mantissa m of x and sh = e - 1019 - E <= 3 (e its exponent field; any E
+    with |x| <= 2^{E-1}), one right shift by s = 4 - sh >= 1 of 16 m, rounded
+    half up."""
+    if E is None or x == 0:
+        return 0
+    bits = int.from_bytes(__import__("struct").pack(">d", x), "big")
+    e = (bits >> 52) & 0x7FF
+    m = (bits & ((1 << 52) - 1)) | (1 << 52)
+    s = 4 - (e - 1019 - E)
+    assert s >= 1
+    M = ((m << 4) + (1 << (s - 1))) >> s if s < 64 else 0
+    return -M if x < 0 else M
+
+
+def test_branch_free_fixed_point_matches_rounding_half_up():
+    rng = random.Random(11)
+    for _ in range(400):
+        row = [rng.gauss(0, 1) * 2.0 ** rng.randint(-70, 10) for _ in range(16)]
+        row.append(2.0 ** rng.randint(-20, 20))          # an exact power of two as the row maximum
+        for extra in (0, 1):                             # the row's own exponent, and one bit coarser
+            E = exponent(row) + extra
+            for x in row + [0.0, -row[0]]:
+                assert fixed_by_shift(x, E) == fixed(x, E)
+
+
+@pytest.mark.parametrize("K", [1, 64, 512])
+def test_common_exponent_for_real_and_imaginary_parts(K):
+    """One exponent per row for re and im, one bit above their largest: then
+    |X_re|, |X_im| <= 2^54, the re + im operand is the integer X_re + X_im
+    (|.| <= 2^55, so its balanced digits exist), Re = t1 - t2 and
+    Im = t3 - t1 - t2 hold exactly in integers before the single scaling, and
+    the result is within K 2^{-53} of the row x column scale."""
+    rng = random.Random(100 + K)
+    for trial in range(3):
+        ar = [rng.gauss(0, 1) * 2.0 ** rng.randint(-30, 3) for _ in range(K)]
+        ai = [rng.gauss(0, 1) * 2.0 ** rng.randint(-30, 3) for _ in range(K)]
+        br = [rng.gauss(0, 1) * 2.0 ** rng.randint(-12, 8) for _ in range(K)]
+        bi = [rng.gauss(0, 1) * 2.0 ** rng.randint(-12, 8) for _ in range(K)]
+        Ea, Eb = exponent(ar + ai) + 1, exponent(br + bi) + 1
+        Xa = [(fixed(r, Ea), fixed(i, Ea)) for r, i in zip(ar, ai)]
+        Xb = [(fixed(r, Eb), fixed(i, Eb)) for r, i in zip(br, bi)]
+        assert all(abs(v) <= 1 << 54 for p in Xa + Xb for v in p)
+
+        def product(f, g):
+            acc = [0] * 8
+            for x, y in zip(f, g):
+                dx, dy = digits(x), digits(y)
+                for i in range(8):
+                    for j in range(8 - i):
+                        acc[i + j] += dx[i] * dy[j]
+            assert all(abs(v) <= 1 << 24 for v in acc)
+            return sum(acc[d] * 128 ** (7 - d) for d in range(8))
+
+        t1 = product([x for x, _ in Xa], [y for y, _ in Xb])
+        t2 = product([x for _, x in Xa], [y for _, y in Xb])
+        t3 = product([x + y for x, y in Xa], [x + y for x, y in Xb])
+        sc = Fraction(2) ** (Ea + Eb - 63)
+        re, im = (t1 - t2) * sc, (t3 - t1 - t2) * sc
+        ex_re = sum(Fraction(p) * Fraction(q) - Fraction(r) * Fraction(s) for p, r, q, s in zip(ar, ai, br, bi))
+        ex_im = sum(Fraction(p) * Fraction(s) + Fraction(r) * Fraction(q) for p, r, q, s in zip(ar, ai, br, bi))
+        scale = Fraction(2) ** (Ea + Eb)
+        assert abs(re - ex_re) <= K * scale / 2 ** 53
+        assert abs(im - ex_im) <= K * scale / 2 ** 53
