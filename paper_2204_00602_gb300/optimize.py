@@ -387,14 +387,93 @@ def run(samples: int, epochs: int, steps: int, B: int, seed: int = 2204006025, l
     }
 
 
+def _tvd_stats(net: MLP, problem: MeshProblem, phases: torch.Tensor):
+    out = []
+    for s0 in range(0, phases.shape[0], problem.B):
+        out.append(validate(net, problem, phases[s0:s0 + problem.B]).cpu().numpy())
+    t = np.concatenate(out)
+    return {"median": float(np.median(t)), "p90": float(np.quantile(t, 0.9)), "max": float(t.max()),
+            "frac_within_1e-3": float(np.mean(t <= 1e-3))}
+
+
+def _fit(problem, ph, y, width: int, epochs: int, seed: int, lr_net: float = 1e-3):
+    dims = (288, width, width, width, 512)
+    Ws, bs = init_weights(seed, dims=dims)
+    net = MLP(Ws, bs, lr=lr_net)
+    t0 = time.perf_counter()
+    losses = train(net, ph, y, epochs)
+    torch.cuda.synchronize()
+    return net, time.perf_counter() - t0, losses[-1]
+
+
+def gate_curve(seed: int = 2204006025, B: int = 64, steps: int = 2000):
+    """Validation TVD of the surrogate on the 512-output set against the
+    training budget: samples, epochs and width on uniformly random phases, and
+    training on phases near where the optimisation runs (Gaussian patches of
+    width sigma around the 64 start points, and around points of the exact
+    loop's trajectory), each validated on held-out phases of its own
+    distribution.  Returns a list of records."""
+    problem = MeshProblem(B=B, seed=seed)
+    rec = []
+    ph_all, y_all = make_dataset(problem, 4_000_000, seed + 10)
+    val_ph = torch.from_numpy(np.random.default_rng(seed + 30).uniform(0, 2 * np.pi, (4 * B, problem.P))).to(
+        problem.dev)
+    for samples in (250_000, 500_000, 1_000_000, 2_000_000, 4_000_000):
+        net, tt, mse = _fit(problem, ph_all[:samples], y_all[:samples], 1024, 8, seed + 20)
+        rec.append({"data": "uniform", "samples": samples, "epochs": 8, "width": 1024, "train_s": tt,
+                    "final_mse": mse, "tvd": _tvd_stats(net, problem, val_ph)})
+    for epochs in (2, 4, 16, 32):
+        net, tt, mse = _fit(problem, ph_all[:2_000_000], y_all[:2_000_000], 1024, epochs, seed + 20)
+        rec.append({"data": "uniform", "samples": 2_000_000, "epochs": epochs, "width": 1024, "train_s": tt,
+                    "final_mse": mse, "tvd": _tvd_stats(net, problem, val_ph)})
+    for width in (256, 512, 2048):
+        net, tt, mse = _fit(problem, ph_all[:2_000_000], y_all[:2_000_000], width, 8, seed + 20)
+        rec.append({"data": "uniform", "samples": 2_000_000, "epochs": 8, "width": width, "train_s": tt,
+                    "final_mse": mse, "tvd": _tvd_stats(net, problem, val_ph)})
+    del ph_all, y_all
+    # local patches: around the 64 start points, and around 41 points of the
+    # exact loop's trajectory (every 50 steps)
+    g = np.random.default_rng(seed + 50)
+    phases0 = torch.from_numpy(np.random.default_rng(seed + 40).uniform(0, 2 * np.pi, (B, problem.P))).to(
+        problem.dev)
+    traj = [phases0.clone()]
+    ph = phases0.clone()
+    opt = Adam64(ph, 0.02)
+    for st in range(steps):
+        opt.step(problem.loss_and_grad(ph))
+        if (st + 1) % 50 == 0:
+            traj.append(ph.clone())
+    traj = torch.cat(traj)
+    for name, centers in (("start_points", phases0), ("trajectory", traj)):
+        for sigma in (0.3, 0.1, 0.03):
+            n = 2_000_000
+            c = centers[torch.from_numpy(g.integers(0, centers.shape[0], n)).to(problem.dev)]
+            ph_l = c + sigma * torch.from_numpy(g.standard_normal((n, problem.P))).to(problem.dev)
+            y_l = exact_log_probs(ph_l, problem.m, problem.t, problem.outs)
+            cv = centers[torch.from_numpy(g.integers(0, centers.shape[0], 4 * B)).to(problem.dev)]
+            val_l = cv + sigma * torch.from_numpy(g.standard_normal((4 * B, problem.P))).to(problem.dev)
+            net, tt, mse = _fit(problem, ph_l, y_l, 1024, 8, seed + 20)
+            rec.append({"data": f"{name}, sigma {sigma}", "samples": n, "epochs": 8, "width": 1024, "train_s": tt,
+                        "final_mse": mse, "tvd": _tvd_stats(net, problem, val_l),
+                        "tvd_at_centers": _tvd_stats(net, problem, centers)})
+            del ph_l, y_l
+    return rec
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
+    ap.add_argument("--curve", action="store_true",
+                    help="the surrogate's TVD against training budget and locality (gate_curve)")
     ap.add_argument("--samples", type=int, default=2_000_000)
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-refine", action="store_true", help="skip the online-refinement variant")
     a = ap.parse_args(argv)
+    if a.curve:
+        for r in gate_curve():
+            print(json.dumps(r), flush=True)
+        return
     print(json.dumps(run(a.samples, a.epochs, a.steps, a.batch, refine=not a.no_refine)), flush=True)
 
 
