@@ -72,7 +72,8 @@ def recorded_traffic(algo: str, m: int, n: int):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=250,
+                    help="timed steps (250 x ~4 ms: about a second, long enough for several clock samples)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="auto", choices=["auto", "factor", "factor_tc", "group", "slos"],
@@ -412,14 +413,15 @@ def run_ours(args):
         abi.pcv_profile_read()
         abi.pcv_profile_enable(True)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fsteps = min(args.steps, 20)                      # ~55 ms each
         f0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(fsteps):
             pcv.distribution(U, t, algo=pcv.PCV_ALGO_FACTOR, ws=ws_f, out=(prob, amp))
         f1.record(stream)
         torch.cuda.synchronize()
         abi.pcv_profile_enable(False)
         st = abi.pcv_profile_read()
-        ms_f = f0.elapsed_time(f1) / args.steps
+        ms_f = f0.elapsed_time(f1) / fsteps
         gms, gcalls = st["dist_products"]
         gflops = Ntot * (2 ** (N_PH - 1)) * 6
         ach = gflops * gcalls / (gms * 1e-3) / 1e12 if gms > 0 else None

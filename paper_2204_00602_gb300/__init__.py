@@ -141,6 +141,26 @@ class BatchPlan:
                                       0 if self.ws is None else self.ws.numel(), _stream(self.device))
         return self.amps, self.probs
 
+    def capture(self):
+        """Record the batched launch (queue building, routing, persistent
+        kernels) once as a CUDA graph; replay() then relaunches all of it with
+        one call.  The graph keeps the addresses of the unitaries, outputs,
+        results and workspace, so new inputs are written into those tensors
+        in place before a replay.  The queue counters are reset by the
+        launch's own kernels, so replays need no host work."""
+        self.run()                                    # loads kernels, sets attributes
+        torch.cuda.synchronize(self.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        return self.graph
+
+    def replay(self):
+        if getattr(self, "graph", None) is None:
+            self.capture()
+        self.graph.replay()
+        return self.amps, self.probs
+
 
 def amplitudes_batched(circuits, want_prob: bool = True, algo: int = PCV_ALGO_AUTO):
     """Amplitudes of many circuits of uneven size: per output the shared-row-sum

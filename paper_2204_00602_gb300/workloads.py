@@ -255,9 +255,43 @@ def source(m: int, n: int, eta: float, V: float, reps: int = 3):
             "seconds": sec, "outputs": off[-1], "pure_sets": 2 ** n, "sum": float(p.sum().item())}
 
 
+def batched_graph(n_circ: int = 64, n_out: int = 256, reps: int = 200):
+    """Small uneven batches, where launch overhead shows: the batched launch
+    issued directly each time against the same launch replayed from a CUDA
+    graph (BatchPlan.capture)."""
+    g = np.random.default_rng(SEED + 7)
+    circs = []
+    for c in range(n_circ):
+        m = int(g.integers(8, 33))
+        n = int(g.integers(3, min(9, m) + 1))
+        outs = torch.from_numpy(pin.random_outputs(m, n, n_out, SEED + 7000 + c)).cuda()
+        U = torch.from_numpy(pin.haar_unitary(m, SEED + 8000 + c)).cuda()
+        circs.append((U, pin.single_photon_input(m, n), outs))
+    plan = BatchPlan(circs)
+    plan.run()
+    plan.capture()
+    torch.cuda.synchronize()
+    res = {}
+    for name, call in (("direct", plan.run), ("graph", plan.replay)):
+        for _ in range(5):
+            call()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a, b = _events()
+        a.record()
+        for _ in range(reps):
+            call()
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = {"gpu_ms_per_call": a.elapsed_time(b) / reps,
+                     "host_ms_per_call": (time.perf_counter() - t0) * 1e3 / reps}
+    return {"workload": f"batched {n_circ} circuits x {n_out} outputs (m~U[8,32], n~U[3,9]), direct vs CUDA graph",
+            "amplitudes_per_call": n_circ * n_out, **res}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["batched", "sweep", "mesh", "sample", "pk", "source"])
+    ap.add_argument("which", choices=["batched", "batched_graph", "sweep", "mesh", "sample", "pk", "source"])
     ap.add_argument("--eta", type=float, default=0.9)
     ap.add_argument("--V", type=float, default=0.9)
     ap.add_argument("--unitaries", type=int, default=300)
@@ -277,6 +311,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     if a.which == "batched":
         r = batched(a.circuits, a.outputs or 4096, route=a.route)
+    elif a.which == "batched_graph":
+        r = batched_graph(min(a.circuits, 64), a.outputs or 256)
     elif a.which == "sweep":
         r = sweep(a.nmin, a.nmax, a.outputs or 256)
     elif a.which == "mesh":

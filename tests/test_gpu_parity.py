@@ -331,6 +331,29 @@ def test_batched_repeat_is_deterministic(pcv):
         assert torch.equal(x, y)
 
 
+def test_batched_graph_replay(pcv):
+    """The whole batched launch captured once as a CUDA graph: a replay gives
+    the direct launch's bits, and after new unitaries are copied into the
+    recorded tensors a replay gives their amplitudes (against the oracle)."""
+    circs = pin.batched_circuits(16, 8, 40, 4, 14, 200, seed=2650)
+    Us = [dev(c["U"]) for c in circs]
+    plan = pcv.BatchPlan([(U, c["input_occ"], dev(c["outputs"])) for U, c in zip(Us, circs)])
+    direct = [a.clone() for a in plan.run()[0]]
+    plan.capture()
+    replayed = plan.replay()[0]
+    torch.cuda.synchronize()
+    for x, y in zip(direct, replayed):
+        assert torch.equal(x, y)
+    new = [pin.haar_unitary(c["m"], 2700 + i) for i, c in enumerate(circs)]
+    for U, Un in zip(Us, new):
+        U.copy_(torch.from_numpy(Un))
+    amps = plan.replay()[0]
+    torch.cuda.synchronize()
+    for c, Un, a in zip(circs, new, amps):
+        a_ref = oracle.amplitudes(Un, c["input_occ"], c["outputs"])
+        assert amp_err(a.cpu().numpy(), a_ref, c["m"], c["n"]) <= tol(c["n"])
+
+
 def test_batched_skips_invalid_descriptor(pcv):
     # a descriptor with an input mode outside [0, m) gets no work; the others run
     circs = pin.batched_circuits(3, 8, 12, 3, 5, 10, seed=2700)
