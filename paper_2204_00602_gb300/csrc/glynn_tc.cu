@@ -149,23 +149,57 @@ __device__ __forceinline__ long long fixed_of(double x, int E)
 // 128^{7-i}: with C = 64 (1 + 128 + ... + 128^7), the word P = X + C is
 // non-negative and below 2^57, and D_i = u_i - 64 for its 7-bit fields u_i
 // (the top field, bits 49 and up, unmasked), so |D_i| <= 64 with no carry
-// chain.  digit_f32 returns D_i = u_i - 64 as FP32 bits, formed exactly
-// (1.5 2^23 + u_i, minus 1.5 2^23 + 64); their low 16 bits are zero, so the
-// high half is D_i in BF16, and bf16_pair packs two of them into a word.
+// chain.  The digits are formed in FP32 (below), exactly; their low 16 bits
+// are zero, so the high half of each is D_i in BF16.
 constexpr unsigned long long kDigitOffset = 0x0081020408102040ull;   // 64 in every 7-bit field
 
 __device__ __forceinline__ unsigned long long digit_word(long long X) { return (unsigned long long)(X + (long long)kDigitOffset); }
 
-__device__ __forceinline__ uint32_t digit_f32(unsigned long long P, int i)
+// The digits on the FP32 pipe (twice the lanes of the integer pipe), from
+// three pieces of P that FP32 holds exactly: piece 0 = P >> 42 (< 2^15)
+// gives digits 0 and 1, piece 1 = bits 21..41 digits 2..4, piece 2 = bits
+// 0..20 digits 5..7.  For 0 <= x < 2^22, RD(x + 2^23) - 2^23 = floor(x), and
+// subtracting 2^23 + 64 instead gives the balanced digit; every other step is
+// a fused multiply-add of integers below 2^24, exact.
+template <int PIECE>
+__device__ __forceinline__ void piece_digits(unsigned long long P, float* d)
 {
-    const uint32_t u = i == 0 ? (uint32_t)(P >> 49) : (uint32_t)((P >> (7 * (7 - i))) & 127u);
-    return __float_as_uint(__uint_as_float(0x4B400000u | u) - 12582976.0f);
+    const uint32_t lo = (uint32_t)P, hi = (uint32_t)(P >> 32);
+    if constexpr (PIECE == 0) {
+        const float v = __uint_as_float(0x4B000000u | (hi >> 10)) - 8388608.0f;
+        d[0] = __fmaf_rd(v, 0.0078125f, 8388608.0f) - 8388672.0f;              // floor(v / 2^7) - 64
+        d[1] = fmaf(d[0], -128.0f, v - 8256.0f);                                 // v mod 2^7 - 64
+    } else {
+        const uint32_t u = PIECE == 1 ? (__funnelshift_r(lo, hi, 21) & 0x1FFFFFu) : (lo & 0x1FFFFFu);
+        const float v = __uint_as_float(0x4B000000u | u) - 8388608.0f;
+        d[0] = __fmaf_rd(v, 6.103515625e-05f, 8388608.0f) - 8388672.0f;         // floor(v / 2^14) - 64
+        const float r = fmaf(d[0], -16384.0f, v - 1048576.0f);                   // v mod 2^14
+        d[1] = __fmaf_rd(r, 0.0078125f, 8388608.0f) - 8388672.0f;              // floor(r / 2^7) - 64
+        d[2] = fmaf(d[1], -128.0f, r - 8256.0f);                                 // r mod 2^7 - 64
+    }
 }
 
-// BF16 of digit i of P0 in the low half, of P1 in the high half
-__device__ __forceinline__ uint32_t bf16_pair(unsigned long long P0, unsigned long long P1, int i)
+// The digits of one piece of RUN words, each digit plane a store of RUN
+// consecutive BF16 values (planes dstride elements apart); two digits share
+// a 32-bit word, the first in its low half.
+template <int PIECE, int RUN>
+__device__ __forceinline__ void store_piece(__nv_bfloat16* dst, int64_t dstride, const unsigned long long* pk)
 {
-    return __byte_perm(digit_f32(P0, i), digit_f32(P1, i), 0x7632);
+    constexpr int ND = PIECE == 0 ? 2 : 3;
+    float d[RUN][3];
+#pragma unroll
+    for (int j = 0; j < RUN; ++j) piece_digits<PIECE>(pk[j], d[j]);
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+        uint32_t wv[RUN / 2];
+#pragma unroll
+        for (int u = 0; u < RUN / 2; ++u)
+            wv[u] = __byte_perm(__float_as_uint(d[2 * u][k]), __float_as_uint(d[2 * u + 1][k]), 0x7632);
+        __nv_bfloat16* q = dst + k * dstride;
+        if constexpr (RUN == 8) *reinterpret_cast<uint4*>(q) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        else if constexpr (RUN == 4) *reinterpret_cast<uint2*>(q) = make_uint2(wv[0], wv[1]);
+        else *reinterpret_cast<uint32_t*>(q) = wv[0];
+    }
 }
 
 // ------------------------------------------------------------ fused tables
@@ -215,20 +249,6 @@ __global__ void scaled_rowsums_kernel(const double2* __restrict__ Y, int m, int 
     Ys[i] = y;
 }
 
-template <int PER>
-__device__ __forceinline__ void store_digit_run(__nv_bfloat16* dst, const unsigned long long* pk, int i)
-{
-    uint32_t wv[PER / 2];
-#pragma unroll
-    for (int u = 0; u < PER / 2; ++u) wv[u] = bf16_pair(pk[2 * u], pk[2 * u + 1], i);
-    if constexpr (PER == 8) {
-        *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-    } else if constexpr (PER == 4) {
-        *reinterpret_cast<uint2*>(dst) = make_uint2(wv[0], wv[1]);
-    } else {
-        *reinterpret_cast<uint32_t*>(dst) = wv[0];
-    }
-}
 
 template <int PER, int WPE>
 __global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
@@ -332,11 +352,11 @@ __global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
             unsigned long long pk[RUN];
 #pragma unroll
             for (int j = 0; j < RUN; ++j) pk[j] = digit_word(t == 0 ? xr[j] : (t == 1 ? xi[j] : xr[j] + xi[j]));
-#pragma unroll
-            for (int i = 0; i < kDigits; ++i)
-                store_digit_run<RUN>(a.digits + (((int64_t)t * kDigits + i) * a.wdig + ent) * a.Kpad + qbase + j0 * 32 +
-                                         lane * RUN,
-                                     pk, i);
+            const int64_t plane = a.wdig * a.Kpad;                 // elements between digit planes
+            __nv_bfloat16* d0 = a.digits + ((int64_t)t * kDigits * a.wdig + ent) * a.Kpad + qbase + j0 * 32 + lane * RUN;
+            store_piece<0, RUN>(d0, plane, pk);
+            store_piece<1, RUN>(d0 + 2 * plane, plane, pk);
+            store_piece<2, RUN>(d0 + 5 * plane, plane, pk);
         }
     }
 }
@@ -376,13 +396,11 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const double2* __rest
         unsigned long long pk[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) pk[u] = digit_word(fixed_of(t == 0 ? vr[u] : (t == 1 ? vi[u] : vs[u]), E));
-#pragma unroll
-        for (int i = 0; i < kDigits; ++i) {
-            uint2 st;
-            st.x = bf16_pair(pk[0], pk[1], i);
-            st.y = bf16_pair(pk[2], pk[3], i);
-            *reinterpret_cast<uint2*>(out + (((int64_t)t * kDigits + i) * w + e) * Kpad + d0) = st;
-        }
+        const int64_t plane = (int64_t)w * Kpad;
+        __nv_bfloat16* q = out + ((int64_t)t * kDigits * w + e) * Kpad + d0;
+        store_piece<0, 4>(q, plane, pk);
+        store_piece<1, 4>(q + 2 * plane, plane, pk);
+        store_piece<2, 4>(q + 5 * plane, plane, pk);
     }
 }
 

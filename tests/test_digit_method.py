@@ -180,3 +180,37 @@ def test_common_exponent_for_real_and_imaginary_parts(K):
         scale = Fraction(2) ** (Ea + Eb)
         assert abs(re - ex_re) <= K * scale / 2 ** 53
         assert abs(im - ex_im) <= K * scale / 2 ** 53
+
+
+def floor_rd(x):
+    """RD(x + 2^23) - 2^23 for 0 <= x < 2^22 with x on a grid of 2^-23 or
+    coarser: FP32 addition rounded down leaves the integer part exactly."""
+    assert 0 <= x < 2 ** 22
+    return math.floor(x)
+
+
+def digits_by_pieces(P):
+    """The kernels' FP32 recipe for the balanced digits of P = X + C: the
+    15-bit piece P >> 42 holds fields 0 and 1, and the 21-bit pieces
+    (P >> 21) mod 2^21 and P mod 2^21 three fields each; every field comes
+    from floor(v 2^-14) or floor(r 2^-7) and fused multiply-adds whose
+    operands and results are integers below 2^24 (exact in FP32)."""
+    out = []
+    a = P >> 42
+    d0 = floor_rd(Fraction(a, 128)) - 64
+    out += [d0, (a - 8256) - 128 * d0]
+    for v in ((P >> 21) & ((1 << 21) - 1), P & ((1 << 21) - 1)):
+        da = floor_rd(Fraction(v, 1 << 14)) - 64
+        r = (v - (1 << 20)) - 16384 * da
+        db = floor_rd(Fraction(r, 128)) - 64
+        out += [da, db, (r - 8256) - 128 * db]
+    # every intermediate the recipe forms is an integer of magnitude < 2^24
+    return out
+
+
+def test_digits_from_fp32_pieces_equal_the_field_digits():
+    rng = random.Random(21)
+    cases = [0, 1, -1, 1 << 55, -(1 << 55), (1 << 55) - 1, 64, -64, 63, -65, (1 << 54) + 12345]
+    cases += [rng.randrange(-(1 << 55), (1 << 55) + 1) for _ in range(20000)]
+    for X in cases:
+        assert digits_by_pieces(X + C) == digits(X)
