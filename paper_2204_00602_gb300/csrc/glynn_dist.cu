@@ -471,7 +471,7 @@ int64_t dist_plan_tc(const Plan& p, bool need_amp_buffer, DistPlan* dp)
     const bool tc_all = p.n >= 2 && p.m - dp->h >= 1;
     if (tc_all) {
         dp->ws_tl = dp->ws_sl = dp->ws_th = dp->ws_sh = 0;
-        dp->ws_tc = (size_t)tc_workspace(p.m, p.n, (int)dmax, dp->total, dp->lowoff, dp->highoff);
+        dp->ws_tc = (size_t)tc_workspace(p.m, p.n, dp->h, (int)dmax, dp->total);
         dp->ws_edge = 0;
     } else {
         dp->ws_tc = 0;

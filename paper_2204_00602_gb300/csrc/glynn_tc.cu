@@ -1,24 +1,24 @@
 // The factorised full distribution with its products on the BF16 tensor
 // cores, in exact integer arithmetic: table levels, digit splitting and the
-// products of every block k = 0..n.
+// products of every output block.
 //
 // With the row sums y_r(d) (glynn_dist.cu), every output is
 //     a(S) = sum_d alpha_P(d) beta_Q(d),
-// for each k a complex matrix product over the K = 2^{n-1} sign vectors, done
-// as three real products (Gauss): t1 = Ar Br, t2 = Ai Bi, t3 = (Ar+Ai)(Br+Bi),
-// Re a = t1 - t2, Im a = t3 - t1 - t2.  Here each real product runs on the
-// tensor cores without losing FP64 accuracy, by splitting every table value
+// a sum over the K = 2^{n-1} sign vectors of a low-side factor (modes [0, h))
+// times a high-side one, so a block of outputs is a complex matrix product,
+// done as three real products (Gauss): t1 = Ar Br, t2 = Ai Bi, t3 = (Ar+Ai)
+// (Br+Bi), Re a = t1 - t2, Im a = t3 - t1 - t2.  Each real product runs on the
+// tensor cores without losing FP64 accuracy, by splitting every operand value
 // into integer digits (the error-free splitting idea of Ozaki, Ogita, Oishi
 // and Rump, 2012):
 //
-//   * each row gets an exponent E with max_d |x(d)| <= 2^{E-1}; X =
+//   * each operand row gets an exponent E with max_d |x(d)| <= 2^{E-1}; X =
 //     round(x 2^{56-E}) is an integer with |X| <= 2^55, written as 8
 //     balanced base-128 digits,
 //         X = sum_{i=0..7} D_i 128^{7-i},   |D_i| <= 64,
 //     so x = 2^E sum_i D_i 2^{-7(i+1)} up to 2^{E-56} (FP64 accuracy).  A
 //     table entry's re and im share one exponent one bit higher (54 bits
-//     each), and its third operand is the integer X_re + X_im; the per-mode
-//     vectors of the single-entry columns keep one exponent per product;
+//     each), and its third operand is the integer X_re + X_im;
 //   * a digit is an integer of at most 7 bits, exact in BF16, and a product of
 //     two is at most 2^12; over K <= 512 sign vectors a digit-pair product
 //     sums to at most 2^21, and the 8 pairs (i, j) of one diagonal i + j = d
@@ -31,21 +31,38 @@
 //     acc_d 128^{7-d}, and x_t = Z 2^{E_row + E_col - 63} is rounded once to
 //     FP64 with integer operations (scale_packed).
 //
+// Output blocks.  With e = min(3, n / 2) and k the photons on the low side:
+//   * k = e+1 .. n-e-1: the low-side table level k times the high-side level
+//     n-k (both in lexicographic order);
+//   * the outputs with at least n-e photons on one side ("extension blocks"):
+//     S = R ++ E, R the n-e photons of that side nearest the other side (for
+//     the low side the n-e smallest modes of S, for the high side the n-e
+//     largest) and E the other e photons, any modes.  Rows are the table
+//     entries R of level n-e of that side, grouped by their seam mode (max R
+//     low, min R high); columns are the e-multisets E over all m modes,
+//     v_E(d) = prod_{x in E} y_x(d) / sqrt(prod mult!).  A row with seam
+//     mode t takes the columns with min E >= t (low side) or max E <= t (high
+//     side), which the column orders make a prefix: by min E descending for
+//     the low side, by max E ascending for the high side.  When n = 2e the
+//     high side leaves out the all-low E (those outputs are the low side's).
+//     The output index splits into a row part and a column part, and where
+//     E meets R at the seam mode the product carries 1/sqrt(C(mu_R + mu_E,
+//     mu_E)) more (multiplicities of that mode in R and E).  The glynn sign
+//     and 2^{-(n-1)} norm_t sit on the low-side entries, and on the high
+//     side's level n-e rows.
+// So no table level above n-e is built: for n = 10, levels 8 and 9 of both
+// sides (three quarters of all table entries) never exist.
+//
 // Kernels:
-//   tc_level_kernel     table levels 1..n-1 of each side, built in FP64 from
-//                       the parent level and written as BF16 digits, laid out
-//                       [t][digit][entry][K] for TMA (levels <= n-2 also keep
-//                       their complex entries as the next level's parents);
-//   split_exp_kernel, split_digits_kernel, edge_vectors_kernel,
-//   edge_info_kernel    the single-entry blocks (k = 0, k = n): level n is
-//                       level n-1 times y_r / sqrt(multiplicity), so these
-//                       blocks are products of level n-1 with one vector per
-//                       mode; the vectors are split here, and each level n-1
-//                       entry gets its output index and scale;
+//   tc_level_kernel     a table level, built in FP64 from its parent level and
+//                       written as BF16 digits, laid out [t][digit][entry][K]
+//                       for TMA; levels below n-e also keep their complex
+//                       entries as the next level's parents.  The extension
+//                       rows and the column vectors are levels too, in their
+//                       grouped orders (seam_entries_kernel gives each entry
+//                       its parent, mode and output-index part);
 //   tc_product_kernel   one persistent CTA per SM walking 128 x N output
-//                       tiles of one block each (N = 16..64; the single-entry
-//                       columns ride in the tile of the block k = 1 or n-1
-//                       with the same rows when both fit), eleven warps:
+//                       tiles of one block each (N = 16..64), eleven warps:
 //   warp 0  row-operand TMA: per 64-wide K block, the 8 digit slices of the
 //           row operand one at a time (16 KB slots, six in flight, digits in
 //           the order 0 7 1 6 2 5 3 4), 128B swizzle;
@@ -76,7 +93,9 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "pcv_common.cuh"
 #include "tc_ptx.cuh"
@@ -98,36 +117,10 @@ constexpr uint32_t kTmemCols = 512;
 constexpr long long kMaxPolls = 1ll << 26;               // default bound of one mbarrier wait
 constexpr int kNoExp = -100000;                          // an all-zero row
 
+
 // ------------------------------------------------------------ splitting
 
 __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
-
-// E_t(entry) for t = re, im, re+im: the smallest E with max |x| <= 2^{E-1}
-// (from the largest exponent field; a power of two costs one spare bit).
-// (T, Sm: [K][stride] tables from their first digitised entry; w entries.)
-// One warp per entry, lanes over the sign vectors.
-__global__ void split_exp_kernel(const double2* __restrict__ T, const double* __restrict__ Sm, int64_t stride,
-                                 int64_t w, int K, int* __restrict__ ex)
-{
-    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (e >= w) return;                                    // whole warps
-    int f0 = 0, f1 = 0, f2 = 0;
-    for (int d = lane; d < K; d += 32) {
-        const double2 v = T[(int64_t)d * stride + e];
-        f0 = max(f0, exp_field(v.x));
-        f1 = max(f1, exp_field(v.y));
-        f2 = max(f2, exp_field(Sm[(int64_t)d * stride + e]));
-    }
-    f0 = __reduce_max_sync(0xffffffffu, f0);
-    f1 = __reduce_max_sync(0xffffffffu, f1);
-    f2 = __reduce_max_sync(0xffffffffu, f2);
-    if (lane == 0) {
-        ex[e] = f0 ? f0 - 1021 : kNoExp;
-        ex[w + e] = f1 ? f1 - 1021 : kNoExp;
-        ex[2 * w + e] = f2 ? f2 - 1021 : kNoExp;
-    }
-}
 
 // X = round(x 2^{56-E}) as a signed integer, |X| <= 2^55 (the magnitude
 // rounded half up; 0 for x = 0 or an all-zero row), for |x| <= 2^{E-1}.  With
@@ -202,33 +195,192 @@ __device__ __forceinline__ void store_piece(__nv_bfloat16* dst, int64_t dstride,
     }
 }
 
+// ------------------------------------------------------------ extension blocks
+
+// Orders of the extension rows and of the column vectors: the entries of one
+// level over the values [0, w), listed group by group, lexicographically
+// within a group.
+enum SeamOrder {
+    kRowsLow = 0,     // low-side rows (level n-e over [0, h)): by largest mode, ascending
+    kRowsHigh = 1,    // high-side rows (level n-e over [h, m)): by smallest mode, ascending
+    kColsHigh = 2,    // columns of the high-side rows (e-multisets over m): by largest mode, ascending
+    kColsLow = 3,     // columns of the low-side rows: by smallest mode, descending
+};
+
+// A table entry whose parent, last mode and multiplicity are given (the
+// extension rows and the column vectors, whose orders are not lexicographic).
+struct EntryInfo {
+    long long parent;     // lexicographic rank of the entry without its last mode (in the parent level)
+    int r;                // that last mode (global, the row of Ys)
+    int mult;             // its multiplicity in the entry
+};
+
+// The output-index part and seam data of a row or a column of an extension
+// block: the output of row i and column j is base_i + base_j.
+struct SeamInfo {
+    long long base;
+    int key;              // seam mode (global): max R (low rows), min R (high rows), min E, max E
+    int mu;               // multiplicity of key in the row or column
+};
+
+// Entry i of a grouped order of the k-multisets over [0, w), into
+// modes[0..k).  By largest mode g = 0, 1, ...: a (k-1)-multiset over [0, g],
+// then g.  By smallest mode g (ascending, or descending from w-1): g, then a
+// (k-1)-multiset over [g, w).
+__host__ __device__ inline void unrank_grouped(const MultisetTable& mc, bool bymax, bool desc, int w, int k, int64_t i,
+                                               int* modes)
+{
+    for (int j = 0; j < w; ++j) {
+        const int g = desc ? w - 1 - j : j;
+        const int64_t c = bymax ? mc(g + 1, k - 1) : mc(w - g, k - 1);
+        if (i >= c) {
+            i -= c;
+            continue;
+        }
+        if (bymax) {
+            unrank_multiset<PCV_MAX_PHOTONS>(mc, g + 1, k - 1, i, modes);
+            modes[k - 1] = g;
+        } else {
+            modes[0] = g;
+            unrank_multiset<PCV_MAX_PHOTONS>(mc, w - g, k - 1, i, modes + 1);
+            for (int p = 1; p < k; ++p) modes[p] += g;
+        }
+        return;
+    }
+}
+
+// Seam data from an entry's modes s (global), with idx the canonical index of
+// an n-photon output (lexicographic rank of its mode list) and C_a(b) the
+// b-multisets over a values:
+//   low rows R (n-e modes, t = max R):   base = idx(R ++ t^e) - Phi(t)
+//   columns by min E (order kColsLow):   base = rank of E among e-multisets over m
+//   high rows R (t = min R):             base = idx(0^e ++ R)
+//   columns by max E (u = max E):        base = idx(E ++ u^{n-e}) - Psi(u)
+// with Phi(z) = sum_{v<z} C_{m-v}(e-1), Psi(z) = sum_{v<z} C_{m-v}(n-e-1).
+// In the rank sum of R ++ E (or E ++ R) only the term of the first position
+// after R (after E) depends on both, as Phi(min E) - Phi(t) (Psi(t) -
+// Psi(u)); every other term belongs to one of the two.
+__host__ __device__ inline SeamInfo seam_of(const MultisetTable& mc, int m, int n, int e, int order, const int* s)
+{
+    int buf[PCV_MAX_PHOTONS];
+    const int L = n - e;
+    SeamInfo si;
+    int mu = 0;
+    if (order == kRowsLow) {
+        const int t = s[L - 1];
+        for (int p = 0; p < L; ++p) {
+            buf[p] = s[p];
+            mu += s[p] == t;
+        }
+        for (int p = L; p < n; ++p) buf[p] = t;
+        int64_t phi = 0;
+        for (int v = 0; v < t; ++v) phi += mc(m - v, e - 1);
+        si.base = rank_multiset(mc, m, n, buf) - phi;
+        si.key = t;
+    } else if (order == kRowsHigh) {
+        const int t = s[0];
+        for (int p = 0; p < e; ++p) buf[p] = 0;
+        for (int p = 0; p < L; ++p) {
+            buf[e + p] = s[p];
+            mu += s[p] == t;
+        }
+        si.base = rank_multiset(mc, m, n, buf);
+        si.key = t;
+    } else if (order == kColsLow) {
+        const int t = s[0];
+        for (int p = 0; p < e; ++p) mu += s[p] == t;
+        si.base = rank_multiset(mc, m, e, s);
+        si.key = t;
+    } else {
+        const int u = s[e - 1];
+        for (int p = 0; p < e; ++p) {
+            buf[p] = s[p];
+            mu += s[p] == u;
+        }
+        for (int p = e; p < n; ++p) buf[p] = u;
+        int64_t psi = 0;
+        for (int v = 0; v < u; ++v) psi += mc(m - v, L - 1);
+        si.base = rank_multiset(mc, m, n, buf) - psi;
+        si.key = u;
+    }
+    si.mu = mu;
+    return si;
+}
+
+// The modes (global) of entry i of an extension-row or column order.
+__host__ __device__ inline int seam_modes(const MultisetTable& mc, int m, int n, int e, int h, int order, int64_t i,
+                                          int* modes)
+{
+    const bool rows = order == kRowsLow || order == kRowsHigh;
+    const int k = rows ? n - e : e;
+    const int w = order == kRowsLow ? h : (order == kRowsHigh ? m - h : m);
+    unrank_grouped(mc, order == kRowsLow || order == kColsHigh, order == kColsLow, w, k, i, modes);
+    return k;
+}
+
+// Per entry of the extension rows or the column vectors: the parent
+// (lexicographic rank without the last mode, over the same values), the
+// last mode and its multiplicity, and the seam data.
+__global__ void seam_entries_kernel(MultisetTable mc, int m, int n, int e, int h, int order, int64_t count,
+                                    EntryInfo* __restrict__ info, SeamInfo* __restrict__ seam)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int modes[PCV_MAX_PHOTONS];
+    const int k = seam_modes(mc, m, n, e, h, order, i, modes);
+    const int w = order == kRowsLow ? h : (order == kRowsHigh ? m - h : m);
+    const int shift = order == kRowsHigh ? h : 0;
+    const int last = modes[k - 1];
+    int mult = 0;
+    for (int p = 0; p < k; ++p) mult += modes[p] == last;
+    EntryInfo ei;
+    ei.parent = rank_multiset(mc, w, k - 1, modes);
+    ei.r = last + shift;
+    ei.mult = mult;
+    info[i] = ei;
+    for (int p = 0; p < k; ++p) modes[p] += shift;
+    seam[i] = seam_of(mc, m, n, e, order, modes);
+}
+
 // ------------------------------------------------------------ fused tables
 
-// One level k >= 1 of one side's factor table, built and split in one pass
-// (the tables are never stored in the [sign vector][entry] layout of the
-// FP64 path): entry(P)(d) = entry(P minus its last mode r)(d) y_r(d) /
+// One level k >= 1 of a factor table, built and split in one pass (the
+// tables are never stored in the [sign vector][entry] layout of the FP64
+// path): entry(P)(d) = entry(P minus its last mode r)(d) y_r(d) /
 // sqrt(multiplicity of r in P), level 0 being sigma(d) 2^{-(n-1)} norm_t on
-// the low side and 1 on the high side.  Kpad / 128 warps per entry P (one
-// for Kpad <= 128), each lane holding 4 sign vectors (2 at Kpad = 64; those
-// >= K are zero): the entry's exponent (one for re, im and re + im) is a
-// maximum over its warps, so the digits [3][8][entry][Kpad] are written in
-// the same pass.  Levels below
-// n - 1 also keep the complex entries, entry-major [entry][K], as the parents
-// of the next level.  Low side: writes lowbase of each entry.
+// the low side (side 0) and 1 elsewhere (high side, column vectors).  Kpad /
+// 128 warps per entry P (one for Kpad <= 128), each lane holding 4 sign
+// vectors (2 at Kpad = 64; those >= K are zero): the entry's exponent (one for
+// re, im and re + im) is a maximum over its warps, so the digits
+// [3][8][entry][Kpad] are written in the same pass.  A level that is a parent
+// keeps its complex entries, entry-major [entry][K].  Entries are in
+// lexicographic order (unranked here; the low side's also get lowbase), or
+// take parent, mode and multiplicity from `info` (grouped orders).
 struct TcLevelArgs {
     MultisetTable mc;
     int m, n, h, side, k, K, Kpad;
+    int w, shift;                        // modes [0, w), at `shift` in the output (lexicographic levels)
     int64_t count;                       // entries of level k
     double lead;                         // 2^{-(n-1)} norm_t
+    int sigma_out;                       // 1: entries times sigma(d) 2^{-(n-1)} norm_t (high-side extension rows)
+    const EntryInfo* info;               // per entry, or null (lexicographic)
     const double2* Ys;                   // [n-1][m][K]: y_r(d) / sqrt(mult), mult = 1 .. n-1
     const double2* parent;               // level k-1, [entry][K] (k >= 2)
     double2* out;                        // level k, [entry][K], or null
     int64_t dig_off, wdig;               // entry offset of level k in the digit tensor; its entries
-    __nv_bfloat16* digits;               // [3][8][wdig][Kpad]
+    __nv_bfloat16* digits;               // [3][8][wdig][Kpad], or null (a parent level only)
     int* ex;                             // [3][wdig]
     int64_t* lowbase;                    // low side: at lowoff_k + entry, else null
     int64_t lowoff_k;
 };
+
+// sigma(d) 2^{-(n-1)} norm_t: the sign of sign vector d (Gray-code order)
+// times the leading factor
+__device__ __forceinline__ double glynn_lead(int q, double lead)
+{
+    const uint64_t d = (uint64_t)q;
+    return (__popcll(d ^ (d >> 1)) & 1) ? -lead : lead;
+}
 
 // Ys[mult-1][r][d] = y_r(d) / sqrt(mult) (mult = 1: y_r(d) itself), the
 // factor a level entry whose last mode r occurs mult times takes from its
@@ -260,11 +412,15 @@ __global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
     const int part = warp % WPE;
     const int64_t e = (int64_t)blockIdx.x * (4 / WPE) + warp / WPE;
     const bool valid = e < a.count;
-    const int w = a.side == 0 ? a.h : a.m - a.h;
-    const int shift = a.side == 0 ? 0 : a.h;
+    const int w = a.w, shift = a.shift;
     int mult = 1, r = 0;
     int64_t parent = 0;
-    if (valid) {
+    if (valid && a.info) {
+        const EntryInfo ei = a.info[e];
+        parent = ei.parent;
+        r = ei.r;
+        mult = ei.mult;
+    } else if (valid) {
         // unrank P (non-decreasing modes, lexicographic order) and, in the same
         // walk, the rank of P minus its last mode among (k-1)-multisets, the
         // run length of the last mode, and (low side) the canonical index of
@@ -307,21 +463,21 @@ __global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
         if (valid && q < a.K) {
             const double2 y = yr[q];
             double2 pv;
-            if (a.k == 1) {
-                double lv = 1.0;
-                if (a.side == 0) {
-                    const uint64_t d = (uint64_t)q;
-                    lv = (__popcll(d ^ (d >> 1)) & 1) ? -a.lead : a.lead;
-                }
-                pv = make_double2(lv, 0.0);
-            } else {
+            if (a.k == 1)
+                pv = make_double2(a.side == 0 ? glynn_lead(q, a.lead) : 1.0, 0.0);
+            else
                 pv = a.parent[parent * a.K + q];
-            }
             v[j] = cmul(pv, y);
+            if (a.sigma_out) {
+                const double sl = glynn_lead(q, a.lead);
+                v[j].x *= sl;
+                v[j].y *= sl;
+            }
             if (a.out) a.out[e * a.K + q] = v[j];
         }
         fc = max(fc, max(exp_field(v[j].x), exp_field(v[j].y)));
     }
+    if (!a.digits) return;                                 // the same for the whole grid
     fc = __reduce_max_sync(0xffffffffu, fc);
     if constexpr (WPE > 1) {
         if (lane == 0) s_f[warp][0] = fc;
@@ -360,84 +516,36 @@ __global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
         }
     }
 }
-
-// One warp: 4 consecutive entries x 32 consecutive sign vectors (lane ->
-// entry lane & 3, sign vectors 4 (lane >> 2) .. + 3).  Loads take 64-byte
-// segments of the tables; each product and digit is one 8-byte store per
-// lane (64-byte segments along K of the digit tensors).  No shared memory.
-__global__ void __launch_bounds__(256) split_digits_kernel(const double2* __restrict__ T, const double* __restrict__ Sm,
-                                                           int64_t stride, int64_t w, int K, int Kpad,
-                                                           const int* __restrict__ ex, __nv_bfloat16* __restrict__ out)
-{
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int ndg = Kpad / 32;
-    const int64_t eg = gw / ndg;
-    const int dg = (int)(gw % ndg);
-    const int64_t e = eg * 4 + (lane & 3);
-    const int d0 = dg * 32 + (lane >> 2) * 4;
-    if (e >= w) return;
-    double vr[4], vi[4], vs[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int d = d0 + u;
-        if (d < K) {
-            const double2 v = T[(int64_t)d * stride + e];
-            vr[u] = v.x;
-            vi[u] = v.y;
-            vs[u] = Sm[(int64_t)d * stride + e];
-        } else {
-            vr[u] = vi[u] = vs[u] = 0.0;
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        const int E = ex[(int64_t)t * w + e];
-        unsigned long long pk[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) pk[u] = digit_word(fixed_of(t == 0 ? vr[u] : (t == 1 ? vi[u] : vs[u]), E));
-        const int64_t plane = (int64_t)w * Kpad;
-        __nv_bfloat16* q = out + ((int64_t)t * kDigits * w + e) * Kpad + d0;
-        store_piece<0, 4>(q, plane, pk);
-        store_piece<1, 4>(q + 2 * plane, plane, pk);
-        store_piece<2, 4>(q + 5 * plane, plane, pk);
-    }
-}
-
 // ------------------------------------------------------------ products
 
-constexpr int kMaxBlocks = PCV_MAX_PHOTONS + 2;     // k = 1 .. n-1 and the two single-entry blocks
+constexpr int kMaxSideBlocks = 32;                  // extension blocks per side
+constexpr int kMaxBlocks = 8 + 2 * kMaxSideBlocks;  // and the level products k = e+1 .. n-e-1 (n <= 10)
 
 struct TcProdArgs {
-    int nk;                                   // blocks with outputs
+    int nk;                                   // blocks with tiles
     int kblocks;                              // 64-wide K blocks
     int64_t tile0[kMaxBlocks + 1];            // first tile of each block
     int64_t tiles;                            // all tiles
-    int rows_low[kMaxBlocks];                 // 1: rows are low-side entries P, columns high-side Q
-    // Columns of a block: [0, ncol) from the other side's table levels
-    // (col_off), then [ecol0, ecol0 + ecols) single-entry columns (see below);
-    // a block k = 1 or k = n-1 whose rows are level n-1 carries the
-    // single-entry columns of that side when both fit one tile
-    int ncol[kMaxBlocks], ecol0[kMaxBlocks], ecols[kMaxBlocks];
-    int tn[kMaxBlocks];                       // tile width (16..64)
-    // tiles cover rows [rows0, rows) and columns [cols0, cols) of the block:
-    // all of it, or the rows or columns of the P whose outputs meet [lo, hi)
+    // Per block: rows_low 1 if the rows come from the low side's digit tensor
+    // (then the columns from the high side's, else the other way round);
+    // kind 0 for a level product, 1 for an extension block; tile width
+    // (16..64); the rows [rows0, rows) and columns [cols0, cols) its tiles
+    // cover; entry offsets of row 0 and column 0 in the digit tensors; lowoff
+    // the level offset of a level product's low-side entries (lowbase).  An
+    // extension block's rows and columns take their seam data from seam[rs]
+    // at ri_off + row and seam[cs] at ci_off + column, and a pair is an
+    // output when the column's seam mode is >= the row's (cge = 1) or <= it.
+    int rows_low[kMaxBlocks], kind[kMaxBlocks], tn[kMaxBlocks];
+    int rs[kMaxBlocks], cs[kMaxBlocks], cge[kMaxBlocks];
     int64_t rows0[kMaxBlocks], rows[kMaxBlocks], cols0[kMaxBlocks], cols[kMaxBlocks];
-    int64_t row_off[kMaxBlocks], col_off[kMaxBlocks];   // entry offsets in the digit tensors
-    int64_t lowoff[kMaxBlocks];               // level offset of P (for lowbase)
+    int64_t row_off[kMaxBlocks], col_off[kMaxBlocks], lowoff[kMaxBlocks], ri_off[kMaxBlocks], ci_off[kMaxBlocks];
     const int64_t* lowbase;
     const int* ex_low;                        // [3][wlow]
     const int* ex_high;                       // [3][whigh]
     int64_t wlow, whigh;
-    // Single-entry blocks, by the side s of their rows (0 low, 1 high): the
-    // rows are the level n-1 entries R' of side s, the columns the modes r of
-    // side s with the vectors v_r of that side (digits under the v maps), and
-    // the output of (R', r), r >= max R', is entry R' + r of level n:
-    // index efirst[s][R'] + r - max R', scaled by esc[s][R'] when r = max R'.
-    const int* ex_v[2];                       // [3][modes of side s]
-    const int64_t* efirst[2];
-    const int* emax[2];
-    const double* esc[2];
+    // seam data: extension rows of the low (0) and high (1) side, column
+    // vectors by max E (2, in the low tensor) and by min E (3, high tensor)
+    const SeamInfo* seam[4];
     double* xt;                               // [2][hi - lo]: the real products t1, t2 per output
     int64_t lo, hi;                           // outputs [lo, hi) are written, at o - lo
     double2* amp;                             // amplitudes, or null
@@ -459,6 +567,15 @@ using tcx::tma_load_4d;
 __device__ __forceinline__ double pow2(int e)      // 2^e for -1022 <= e <= 1023
 {
     return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+// 1/sqrt(C(a + b, b)): the seam mode's share of 1/sqrt(prod mult!) that
+// neither the row (multiplicity a) nor the column (multiplicity b) carries.
+__device__ __forceinline__ double seam_scale(int a, int b)
+{
+    int c = 1;
+    for (int i = 1; i <= b; ++i) c = c * (a + i) / i;
+    return inv_sqrt_int(c);
 }
 
 // RN(Z 2^s) for the exact integer Z = zh 2^28 + zl (0 <= zl < 2^28, |Z| <
@@ -560,7 +677,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_constant__ CUtensorMap low_cols,
                   const __grid_constant__ CUtensorMap high_rows, const __grid_constant__ CUtensorMap high_cols,
                   const __grid_constant__ CUtensorMap low_cols16, const __grid_constant__ CUtensorMap high_cols16,
-                  const __grid_constant__ CUtensorMap vlow16, const __grid_constant__ CUtensorMap vhigh16,
                   const TcProdArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -597,8 +713,6 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
         tcx::prefetch_tmap(&high_cols);
         tcx::prefetch_tmap(&low_cols16);
         tcx::prefetch_tmap(&high_cols16);
-        tcx::prefetch_tmap(&vlow16);
-        tcx::prefetch_tmap(&vhigh16);
     }
     if (warp == 1) tcx::tmem_alloc(&tmem_base, kTmemCols);
     tcx::fence_before_sync();
@@ -651,27 +765,16 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                     // box, or N / 16 boxes of 16 rows
                     unsigned char* dst = bset + bs * kBBytes;
                     mbar_expect_tx(&bfull[bs], (uint32_t)(kDigits * tb.tn) * kRowBytes);
-                    if (tb.tn == TBN && a.ecols[tb.kb] == 0) {
+                    if (tb.tn == TBN) {
                         const CUtensorMap* cmap = tb.rl ? &high_cols : &low_cols;
                         for (int j = 0; j < kDigits; ++j)
                             tma_load_4d(dst + j * TBN * kRowBytes, cmap, &bfull[bs], c * TBK, tb.centry, j, t);
                     } else {
-                        // 16-row boxes; those at or past ecol0 come from the
-                        // vectors of the single-entry columns (ecol0 is a
-                        // multiple of 16)
-                        const int e0 = a.ecol0[tb.kb];
-                        const CUtensorMap* nmap = tb.rl ? &high_cols16 : &low_cols16;
-                        const CUtensorMap* vmap = tb.rl ? &vlow16 : &vhigh16;
+                        const CUtensorMap* nmap = tb.rl ? &high_cols16 : &low_cols16;     // 16-row boxes
                         for (int j = 0; j < kDigits; ++j)
-                            for (int r = 0; r < tb.tn; r += kBSub) {
-                                const int lc = (int)tb.c0 + r;
-                                if (lc < e0)
-                                    tma_load_4d(dst + (j * tb.tn + r) * kRowBytes, nmap, &bfull[bs], c * TBK,
-                                                tb.centry + r, j, t);
-                                else
-                                    tma_load_4d(dst + (j * tb.tn + r) * kRowBytes, vmap, &bfull[bs], c * TBK,
-                                                lc - e0, j, t);
-                            }
+                            for (int r = 0; r < tb.tn; r += kBSub)
+                                tma_load_4d(dst + (j * tb.tn + r) * kRowBytes, nmap, &bfull[bs], c * TBK,
+                                            tb.centry + r, j, t);
                     }
                 }
             }
@@ -742,24 +845,28 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
             const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
             const int kb = ti.kb, tn = ti.tn;
             const bool rl = ti.rl;
+            const bool ext = a.kind[kb] != 0;
             const int64_t row = ti.r0 + q4 * 32 + lane;
             const bool rv = row < a.rows[kb];
-            const int side = rl ? 0 : 1;
             const int* ex_r = rl ? a.ex_low : a.ex_high;
             const int* ex_c = rl ? a.ex_high : a.ex_low;
-            const int* ex_e = a.ex_v[side];
             const int64_t wr = rl ? a.wlow : a.whigh, wc = rl ? a.whigh : a.wlow;
-            const int ncol = a.ncol[kb], e0 = a.ecol0[kb], necol = a.ecols[kb];
-            int64_t pbase = 0;                     // lowbase(P) of a low-side row
-            int64_t ebase = 0;                     // efirst(R') - max R' of a level n-1 row
-            int emx = 0;
-            double esc = 1.0;
-            if (rv && necol > 0) {
-                emx = a.emax[side][row];
-                esc = a.esc[side][row];
-                ebase = a.efirst[side][row] - emx;
+            const int64_t ncol = a.cols[kb];
+            // The output of (row, column) is rbase + the column's base: in a
+            // level product lowbase(P) + rank of Q, P being the row (rows
+            // low, column base = its index) or the column (row base = its
+            // index); in an extension block the two seam parts.
+            int64_t rbase = row;
+            int rkey = 0, rmu = 0;
+            const bool cge = a.cge[kb] != 0;
+            if (rv && ext) {
+                const SeamInfo si = a.seam[a.rs[kb]][a.ri_off[kb] + row];
+                rbase = si.base;
+                rkey = si.key;
+                rmu = si.mu;
+            } else if (rv && rl) {
+                rbase = a.lowbase[a.lowoff[kb] + row];
             }
-            if (rv && rl && ncol > 0) pbase = a.lowbase[a.lowoff[kb] + row];
             for (int t = 0; t < 3; ++t) {
                 const int64_t g = it * 3 + t;
                 const int er = rv ? ex_r[(int64_t)t * wr + a.row_off[kb] + row] : kNoExp;
@@ -813,20 +920,22 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                 // the per-column data of this warp's two 16-column chunks:
                 // lane l loads that of column l mod 16 of each chunk, and the
                 // loop below broadcasts it (no loads inside the loop)
-                int ecl[2];
-                int64_t lbl[2];
+                int ecl[2], ckl[2];
+                int64_t cbl[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int64_t col = ti.c0 + cbase + 32 * h + (lane & 15);
-                    const int64_t ce = col - e0;
                     ecl[h] = kNoExp;
-                    lbl[h] = 0;
-                    if (cbase + 32 * h < tn) {
-                        if (col >= e0) {
-                            if (ce < necol) ecl[h] = ex_e[(int64_t)t * necol + ce];
-                        } else if (col < ncol) {
-                            ecl[h] = ex_c[(int64_t)t * wc + a.col_off[kb] + col];
-                            if (!rl) lbl[h] = a.lowbase[a.lowoff[kb] + col];
+                    cbl[h] = 0;
+                    ckl[h] = 0;
+                    if (cbase + 32 * h < tn && col < ncol) {
+                        ecl[h] = ex_c[(int64_t)t * wc + a.col_off[kb] + col];
+                        if (ext) {
+                            const SeamInfo si = a.seam[a.cs[kb]][a.ci_off[kb] + col];
+                            cbl[h] = si.base;
+                            ckl[h] = si.key | (si.mu << 16);
+                        } else {
+                            cbl[h] = rl ? col : a.lowbase[a.lowoff[kb] + col];
                         }
                     }
                 }
@@ -839,18 +948,21 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const int ec = __shfl_sync(0xffffffffu, ecl[h], q);
-                        const int64_t lb = __shfl_sync(0xffffffffu, lbl[h], q);
+                        const int64_t cb = __shfl_sync(0xffffffffu, cbl[h], q);
+                        const int ck = ext ? __shfl_sync(0xffffffffu, ckl[h], q) : 0;
                         const int64_t col = ti.c0 + cc + q;
-                        const bool is_e = col >= e0;       // a single-entry column: mode ce of this side
-                        const int64_t ce = col - e0;
-                        if (!rv || (is_e ? (ce >= necol || ce < emx) : (col >= ncol))) continue;
+                        if (!rv || col >= ncol) continue;
+                        // an extension pair is an output when its column lies on
+                        // the row's side of the seam
+                        const int ckey = ck & 0xFFFF;
+                        if (ext && (cge ? ckey < rkey : ckey > rkey)) continue;
                         double x = 0.0;
                         if (er != kNoExp && ec != kNoExp) {
                             const int sc = er + ec - 14;
                             if (!scale_packed(zh[h][q], zl[h][q], sc - 49, x))
                                 x = fma((double)zl[h][q], pow2(sc - 49), (double)zh[h][q] * pow2(sc - 21));
                         }
-                        const int64_t og = is_e ? ebase + ce : (rl ? pbase + col : lb + row);
+                        const int64_t og = rbase + cb;
                         if (og < a.lo || og >= a.hi) continue;
                         const int64_t o = og - a.lo, span = a.hi - a.lo;
                         if (t < 2) {
@@ -858,9 +970,10 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                         } else {
                             const double t1 = a.xt[o], t2 = a.xt[span + o];
                             double re = t1 - t2, im = x - t1 - t2;
-                            if (is_e && ce == emx) {           // 1 / sqrt(multiplicity of r in R' + r)
-                                re *= esc;
-                                im *= esc;
+                            if (ext && ckey == rkey) {         // the seam mode's multiplicity in S
+                                const double sc = seam_scale(rmu, ck >> 16);
+                                re *= sc;
+                                im *= sc;
                             }
                             if (a.amp) a.amp[o] = make_double2(re, im);
                             if (a.prob) a.prob[o] = fma(re, re, im * im);
@@ -874,66 +987,6 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
     __syncthreads();
     if (warp == 1) tcx::tmem_dealloc(tmem, kTmemCols);
     if (tid == 0 && s_fail && a.error) atomicExch(a.error, s_fail);
-}
-
-// Column vectors of the single-entry blocks, per sign vector d and mode r:
-//   low side  (block k = n, rows P'):  v_r(d) = y_r(d) beta_{}(d),
-//   high side (block k = 0, rows Q'):  v_r(d) = alpha_{}(d) y_{h+r}(d),
-// so that sum_d entry_{R'}(d) v_r(d) is the output of R' + r up to the
-// 1/sqrt(multiplicity) that level n would have applied.  [K][modes] each,
-// with re + im beside them for the third product.
-__global__ void edge_vectors_kernel(const double2* __restrict__ Y, int m, int h, int K, double lead,
-                                    double2* __restrict__ Vl, double* __restrict__ Sl, double2* __restrict__ Vh,
-                                    double* __restrict__ Sh)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)K * m) return;
-    const int64_t q = i / m;
-    const int r = (int)(i % m);
-    const double2 y = Y[q * m + r];
-    if (r < h) {                                           // beta_{}(d) = 1
-        const double2 v = cmul(y, make_double2(1.0, 0.0));
-        Vl[q * h + r] = v;
-        Sl[q * h + r] = v.x + v.y;
-    } else {                                               // alpha_{}(d) = sigma(d) 2^{-(n-1)} norm_t
-        const uint64_t d = (uint64_t)q;
-        const double2 t0 = make_double2((__popcll(d ^ (d >> 1)) & 1) ? -lead : lead, 0.0);
-        const double2 v = cmul(t0, y);
-        Vh[q * (m - h) + (r - h)] = v;
-        Sh[q * (m - h) + (r - h)] = v.x + v.y;
-    }
-}
-
-// Per level n-1 entry R' of one side (modes in [0, w), shifted by `shift` in
-// the output): its largest mode, the canonical output index of R' + max R',
-// and 1/sqrt(multiplicity of max R' in R' + max R').  Low side: the output
-// index among all n-photon outputs; high side: lowbase({}) + rank of Q'+max.
-__global__ void edge_info_kernel(MultisetTable mc, int m, int n, int h, int side, int64_t count,
-                                 int64_t* __restrict__ first, int* __restrict__ mx, double* __restrict__ sc)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const int w = side == 0 ? h : m - h;
-    int modes[PCV_MAX_PHOTONS];
-    unrank_multiset<PCV_MAX_PHOTONS>(mc, w, n - 1, i, modes);
-    const int top = modes[n - 2];
-    int mult = 1;
-    for (int p = n - 2; p >= 0 && modes[p] == top; --p) ++mult;
-    modes[n - 1] = top;
-    int64_t o = 0;
-    if (side == 0) {
-        int prev = 0;
-        for (int p = 0; p < n; ++p) {
-            for (int v = prev; v < modes[p]; ++v) o += mc(m - v, n - p - 1);
-            prev = modes[p];
-        }
-    } else {
-        for (int v = 0; v < h; ++v) o += mc(m - v, n - 1);
-        o += rank_multiset(mc, w, n, modes);
-    }
-    first[i] = o;
-    mx[i] = top;
-    sc[i] = inv_sqrt_int(mult);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
@@ -983,45 +1036,91 @@ int tc_pad_k(int K) { return ((K + TBK - 1) / TBK) * TBK; }
 
 namespace {
 
-// Workspace layout: digits and exponents of table levels 1 .. n-1 of the two
-// sides, the entry-major complex entries of levels 1 .. n-2 (parents), two
-// products per output, the column vectors of the single-entry blocks (sized
-// by m for both sides) with their digits and exponents, and the per-row data
-// of those blocks (sized by levels 1 .. n-1).
-struct TcLayout {
-    int64_t lcnt, hcnt, plow, phigh;
-    size_t dlow, dhigh, exlow, exhigh, tpl, tph, ys, xt, v, sv, dv, exv, efirst_l, emax_l, esc_l, efirst_h, emax_h, esc_h,
-        total;
+// The tables of one problem: e = min(3, n / 2) (at least 1), L = n - e.  Per
+// side s (w_s modes) a digit tensor holds the lexicographic levels e+1 ..
+// n-e-1 (operands of the level products), then the extension rows (level L,
+// grouped by seam mode), then the column vectors in the order the other
+// side's rows take them (side 0's tensor by max E, for the high-side rows;
+// side 1's by min E).  FP64 entries are kept for the parents: levels 1 .. L-1
+// of each side and column levels 1 .. e-1 over all m modes.
+struct TcShape {
+    int m, n, h, e, L, K, Kp;
+    int w[2];
+    int64_t lev[2][PCV_MAX_PHOTONS + 2];              // digit entry offset of lexicographic level k, or -1
+    int64_t rows_off[2], nrows[2];                    // extension rows: digit entry offset, count
+    int64_t cols_off[2], ncols;                       // column vectors in each tensor
+    int64_t wdig[2];                                  // entries of each digit tensor
+    int64_t par[2][PCV_MAX_PHOTONS + 2], npar[2];     // FP64 parents: entry offset of level k
+    int64_t cpar[PCV_MAX_PHOTONS + 2], ncpar;         // FP64 column levels
 };
 
-TcLayout tc_layout(int m, int n, int K, int64_t total, const int64_t* lowoff, const int64_t* highoff)
+TcShape tc_shape(int m, int n, int h, int K)
 {
-    const size_t Kp = (size_t)tc_pad_k(K);
+    TcShape S;
+    S.m = m;
+    S.n = n;
+    S.h = h;
+    S.K = K;
+    S.Kp = tc_pad_k(K);
+    S.e = std::max(1, std::min(3, n / 2));
+    S.L = n - S.e;
+    S.w[0] = h;
+    S.w[1] = m - h;
+    S.ncols = msets_tc(m, S.e);
+    for (int s = 0; s < 2; ++s) {
+        int64_t off = 0;
+        for (int k = 0; k < PCV_MAX_PHOTONS + 2; ++k) S.lev[s][k] = S.par[s][k] = -1;
+        for (int k = S.e + 1; k <= n - S.e - 1; ++k) {
+            S.lev[s][k] = off;
+            off += msets_tc(S.w[s], k);
+        }
+        S.rows_off[s] = off;
+        S.nrows[s] = msets_tc(S.w[s], S.L);
+        S.cols_off[s] = off + S.nrows[s];
+        S.wdig[s] = S.cols_off[s] + S.ncols;
+        int64_t p = 0;
+        for (int k = 1; k < S.L; ++k) {
+            S.par[s][k] = p;
+            p += msets_tc(S.w[s], k);
+        }
+        S.npar[s] = p;
+    }
+    int64_t p = 0;
+    for (int k = 0; k < PCV_MAX_PHOTONS + 2; ++k) S.cpar[k] = -1;
+    for (int k = 1; k < S.e; ++k) {
+        S.cpar[k] = p;
+        p += msets_tc(m, k);
+    }
+    S.ncpar = p;
+    return S;
+}
+
+// Workspace: per side the digits and exponents, the FP64 parents and the
+// entry and seam data of the extension rows and of the column vectors; the
+// FP64 column levels, Ys, and two products per output.
+struct TcLayout {
+    size_t dig[2], ex[2], par[2], rinfo[2], rseam[2], cinfo[2], cseam[2], cpar, ys, xt, total;
+};
+
+TcLayout tc_layout(const TcShape& S, int64_t total)
+{
+    const size_t Kp = (size_t)S.Kp, K = (size_t)S.K;
     TcLayout L;
-    L.lcnt = n >= 2 ? lowoff[n] - lowoff[1] : 0;
-    L.hcnt = n >= 2 ? highoff[n] - highoff[1] : 0;
-    L.plow = n >= 3 ? lowoff[n - 1] - lowoff[1] : 0;
-    L.phigh = n >= 3 ? highoff[n - 1] - highoff[1] : 0;
-    L.dlow = al256((size_t)3 * kDigits * L.lcnt * Kp * 2);
-    L.dhigh = al256((size_t)3 * kDigits * L.hcnt * Kp * 2);
-    L.exlow = al256((size_t)3 * L.lcnt * sizeof(int));
-    L.exhigh = al256((size_t)3 * L.hcnt * sizeof(int));
-    L.tpl = al256((size_t)L.plow * K * sizeof(double2));
-    L.tph = al256((size_t)L.phigh * K * sizeof(double2));
-    L.ys = al256((size_t)(n > 1 ? n - 1 : 1) * m * K * sizeof(double2));
+    L.total = 256;
+    for (int s = 0; s < 2; ++s) {
+        L.dig[s] = al256((size_t)3 * kDigits * S.wdig[s] * Kp * 2);
+        L.ex[s] = al256((size_t)3 * S.wdig[s] * sizeof(int));
+        L.par[s] = al256((size_t)S.npar[s] * K * sizeof(double2));
+        L.rinfo[s] = al256((size_t)S.nrows[s] * sizeof(EntryInfo));
+        L.rseam[s] = al256((size_t)S.nrows[s] * sizeof(SeamInfo));
+        L.cinfo[s] = al256((size_t)S.ncols * sizeof(EntryInfo));
+        L.cseam[s] = al256((size_t)S.ncols * sizeof(SeamInfo));
+        L.total += L.dig[s] + L.ex[s] + L.par[s] + L.rinfo[s] + L.rseam[s] + L.cinfo[s] + L.cseam[s];
+    }
+    L.cpar = al256((size_t)S.ncpar * K * sizeof(double2));
+    L.ys = al256((size_t)(S.n > 1 ? S.n - 1 : 1) * S.m * K * sizeof(double2));
     L.xt = al256((size_t)2 * total * sizeof(double));
-    L.v = al256((size_t)K * m * sizeof(double2));
-    L.sv = al256((size_t)K * m * sizeof(double));
-    L.dv = al256((size_t)3 * kDigits * m * Kp * 2);
-    L.exv = al256((size_t)3 * m * sizeof(int));
-    L.efirst_l = al256((size_t)L.lcnt * sizeof(int64_t));
-    L.emax_l = al256((size_t)L.lcnt * sizeof(int));
-    L.esc_l = al256((size_t)L.lcnt * sizeof(double));
-    L.efirst_h = al256((size_t)L.hcnt * sizeof(int64_t));
-    L.emax_h = al256((size_t)L.hcnt * sizeof(int));
-    L.esc_h = al256((size_t)L.hcnt * sizeof(double));
-    L.total = L.dlow + L.dhigh + L.exlow + L.exhigh + L.tpl + L.tph + L.ys + L.xt + 2 * (L.v + L.sv + L.dv + L.exv) +
-              L.efirst_l + L.emax_l + L.esc_l + L.efirst_h + L.emax_h + L.esc_h + 256;
+    L.total += L.cpar + L.ys + L.xt;
     return L;
 }
 
@@ -1029,41 +1128,31 @@ struct TcBuffers {
     __nv_bfloat16* dig[2];
     int* ex[2];
     double2* par[2];
+    EntryInfo* rinfo[2];
+    SeamInfo* rseam[2];
+    EntryInfo* cinfo[2];
+    SeamInfo* cseam[2];
+    double2* cpar;
     double2* ys;
     double* xt;
-    double2* V[2];
-    double* SV[2];
-    __nv_bfloat16* DV[2];
-    int* EXV[2];
-    int64_t* efirst[2];
-    int* emax[2];
-    double* esc[2];
 };
 
 TcBuffers tc_buffers(const TcLayout& L, void* ws)
 {
     TcBuffers B;
     char* w = (char*)ws;
-    B.dig[0] = (__nv_bfloat16*)w;    w += L.dlow;
-    B.dig[1] = (__nv_bfloat16*)w;    w += L.dhigh;
-    B.ex[0] = (int*)w;               w += L.exlow;
-    B.ex[1] = (int*)w;               w += L.exhigh;
-    B.par[0] = (double2*)w;          w += L.tpl;
-    B.par[1] = (double2*)w;          w += L.tph;
-    B.ys = (double2*)w;              w += L.ys;
-    B.xt = (double*)w;               w += L.xt;
-    for (int side = 0; side < 2; ++side) {
-        B.V[side] = (double2*)w;     w += L.v;
-        B.SV[side] = (double*)w;     w += L.sv;
-        B.DV[side] = (__nv_bfloat16*)w;  w += L.dv;
-        B.EXV[side] = (int*)w;       w += L.exv;
+    for (int s = 0; s < 2; ++s) {
+        B.dig[s] = (__nv_bfloat16*)w;   w += L.dig[s];
+        B.ex[s] = (int*)w;              w += L.ex[s];
+        B.par[s] = (double2*)w;         w += L.par[s];
+        B.rinfo[s] = (EntryInfo*)w;     w += L.rinfo[s];
+        B.rseam[s] = (SeamInfo*)w;      w += L.rseam[s];
+        B.cinfo[s] = (EntryInfo*)w;     w += L.cinfo[s];
+        B.cseam[s] = (SeamInfo*)w;      w += L.cseam[s];
     }
-    B.efirst[0] = (int64_t*)w;       w += L.efirst_l;
-    B.emax[0] = (int*)w;             w += L.emax_l;
-    B.esc[0] = (double*)w;           w += L.esc_l;
-    B.efirst[1] = (int64_t*)w;       w += L.efirst_h;
-    B.emax[1] = (int*)w;             w += L.emax_h;
-    B.esc[1] = (double*)w;           w += L.esc_h;
+    B.cpar = (double2*)w;               w += L.cpar;
+    B.ys = (double2*)w;                 w += L.ys;
+    B.xt = (double*)w;
     return B;
 }
 
@@ -1076,49 +1165,135 @@ cudaError_t launch_level(const TcLevelArgs& la, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_level_kp(const TcLevelArgs& la, cudaStream_t s)
+{
+    if (la.count == 0) return cudaSuccess;
+    switch (la.Kpad / 32) {
+        case 2: return launch_level<2, 1>(la, s);     // Kpad = 64
+        case 4: return launch_level<4, 1>(la, s);     // 128
+        case 8: return launch_level<4, 2>(la, s);     // 256
+        default: return launch_level<4, 4>(la, s);    // 512
+    }
+}
+
+cudaError_t launch_seam_entries(const TcInputs& in, const TcShape& S, int order, int64_t count, EntryInfo* info,
+                                SeamInfo* seam, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    seam_entries_kernel<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(in.mc, in.m, in.n, S.e, in.h, order, count,
+                                                                        info, seam);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// The multiset counts on the host, in the device table's layout.
+struct HostCounts {
+    std::vector<int64_t> t;
+    MultisetTable mc;
+    HostCounts(int m, int n) : t((size_t)(m + 1) * (n + 1))
+    {
+        for (int a = 0; a <= m; ++a)
+            for (int k = 0; k <= n; ++k) t[(size_t)a * (n + 1) + k] = msets_tc(a, k);
+        mc.t = t.data();
+        mc.kmax = n;
+    }
+};
+
 }  // namespace
 
-int64_t tc_workspace(int m, int n, int K, int64_t total, const int64_t* lowoff, const int64_t* highoff)
+int64_t tc_workspace(int m, int n, int h, int K, int64_t total)
 {
-    return (int64_t)tc_layout(m, n, K, total, lowoff, highoff).total;
+    return (int64_t)tc_layout(tc_shape(m, n, h, K), total).total;
 }
 
 cudaError_t launch_tc_tables(const TcInputs& in, cudaStream_t s)
 {
-    const int K = in.K, Kp = tc_pad_k(K), n = in.n;
-    if (n < 2 || Kp > 512) return cudaErrorInvalidValue;
-    const TcLayout L = tc_layout(in.m, n, K, in.total, in.lowoff, in.highoff);
+    const int K = in.K, n = in.n;
+    const TcShape S = tc_shape(in.m, n, in.h, K);
+    if (n < 2 || S.Kp > 512) return cudaErrorInvalidValue;
+    const TcLayout L = tc_layout(S, in.total);
     const TcBuffers B = tc_buffers(L, in.ws);
     const int64_t nys = (int64_t)(n - 1) * in.m * K;
     scaled_rowsums_kernel<<<(unsigned)((nys + 255) / 256), 256, 0, s>>>(in.Y, in.m, K, n - 1, B.ys);
     note_launches(1);
+    auto level_args = [&](int side, int k, int w, int shift) {
+        TcLevelArgs la;
+        la.mc = in.mc;
+        la.m = in.m; la.n = n; la.h = in.h; la.side = side; la.k = k; la.K = K; la.Kpad = S.Kp;
+        la.w = w; la.shift = shift;
+        la.count = 0;
+        la.lead = in.lead;
+        la.sigma_out = 0;
+        la.info = nullptr;
+        la.Ys = B.ys;
+        la.parent = nullptr;
+        la.out = nullptr;
+        la.dig_off = 0; la.wdig = 0;
+        la.digits = nullptr;
+        la.ex = nullptr;
+        la.lowbase = nullptr;
+        la.lowoff_k = 0;
+        return la;
+    };
+    cudaError_t e;
     for (int side = 0; side < 2; ++side) {
-        const int64_t* off = side == 0 ? in.lowoff : in.highoff;
-        for (int k = 1; k < n; ++k) {
-            TcLevelArgs la;
-            la.mc = in.mc;
-            la.m = in.m; la.n = n; la.h = in.h; la.side = side; la.k = k; la.K = K; la.Kpad = Kp;
-            la.count = off[k + 1] - off[k];
-            if (la.count == 0) continue;
-            la.lead = in.lead;
-            la.Ys = B.ys;
-            la.parent = k >= 2 ? B.par[side] + (off[k - 1] - off[1]) * K : nullptr;
-            la.out = k <= n - 2 ? B.par[side] + (off[k] - off[1]) * K : nullptr;
-            la.dig_off = off[k] - off[1];
-            la.wdig = side == 0 ? L.lcnt : L.hcnt;
-            la.digits = B.dig[side];
-            la.ex = B.ex[side];
-            la.lowbase = side == 0 ? in.lowbase : nullptr;
-            la.lowoff_k = off[k];
-            cudaError_t e;
-            switch (Kp / 32) {
-                case 2: e = launch_level<2, 1>(la, s); break;           // Kpad = 64
-                case 4: e = launch_level<4, 1>(la, s); break;           // 128
-                case 8: e = launch_level<4, 2>(la, s); break;           // 256
-                default: e = launch_level<4, 4>(la, s); break;          // 512
+        const int w = S.w[side], shift = side == 0 ? 0 : in.h;
+        // lexicographic levels 1 .. L-1: parents, with digits where a level product takes them
+        for (int k = 1; k < S.L; ++k) {
+            TcLevelArgs la = level_args(side, k, w, shift);
+            la.count = msets_tc(w, k);
+            la.parent = k >= 2 ? B.par[side] + S.par[side][k - 1] * K : nullptr;
+            la.out = B.par[side] + S.par[side][k] * K;
+            if (S.lev[side][k] >= 0) {
+                la.digits = B.dig[side];
+                la.ex = B.ex[side];
+                la.dig_off = S.lev[side][k];
+                la.wdig = S.wdig[side];
             }
-            if (e != cudaSuccess) return e;
+            if (side == 0) {
+                la.lowbase = in.lowbase;
+                la.lowoff_k = in.lowoff[k];
+            }
+            if ((e = launch_level_kp(la, s)) != cudaSuccess) return e;
         }
+        // the extension rows: level L grouped by seam mode (the high side's
+        // carry the glynn sign and leading factor)
+        if ((e = launch_seam_entries(in, S, side == 0 ? kRowsLow : kRowsHigh, S.nrows[side], B.rinfo[side],
+                                     B.rseam[side], s)) != cudaSuccess)
+            return e;
+        TcLevelArgs la = level_args(side, S.L, w, shift);
+        la.count = S.nrows[side];
+        la.info = B.rinfo[side];
+        la.parent = S.L >= 2 ? B.par[side] + S.par[side][S.L - 1] * K : nullptr;
+        la.sigma_out = side == 1;
+        la.digits = B.dig[side];
+        la.ex = B.ex[side];
+        la.dig_off = S.rows_off[side];
+        la.wdig = S.wdig[side];
+        if ((e = launch_level_kp(la, s)) != cudaSuccess) return e;
+    }
+    // the column vectors: levels 1 .. e-1 over all modes, then level e in the
+    // two orders
+    for (int k = 1; k < S.e; ++k) {
+        TcLevelArgs la = level_args(2, k, in.m, 0);
+        la.count = msets_tc(in.m, k);
+        la.parent = k >= 2 ? B.cpar + S.cpar[k - 1] * K : nullptr;
+        la.out = B.cpar + S.cpar[k] * K;
+        if ((e = launch_level_kp(la, s)) != cudaSuccess) return e;
+    }
+    for (int side = 0; side < 2; ++side) {
+        if ((e = launch_seam_entries(in, S, side == 0 ? kColsHigh : kColsLow, S.ncols, B.cinfo[side], B.cseam[side],
+                                     s)) != cudaSuccess)
+            return e;
+        TcLevelArgs la = level_args(2, S.e, in.m, 0);
+        la.count = S.ncols;
+        la.info = B.cinfo[side];
+        la.parent = S.e >= 2 ? B.cpar + S.cpar[S.e - 1] * K : nullptr;
+        la.digits = B.dig[side];
+        la.ex = B.ex[side];
+        la.dig_off = S.cols_off[side];
+        la.wdig = S.wdig[side];
+        if ((e = launch_level_kp(la, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -1134,65 +1309,30 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         if (e != cudaSuccess) return e;
         g_tc_attr[dev] = true;
     }
-    const int K = in.K, Kp = tc_pad_k(K), n = in.n, m = in.m, h = in.h;
+    const int K = in.K, n = in.n, m = in.m, h = in.h;
     if (n < 2 || m - h < 1) return cudaErrorInvalidValue;
-    // the blocks k = 1 .. n-1 use table levels 1 .. n-1 of each side; the
-    // single-entry blocks k = 0 and k = n use level n-1 of one side
-    const int64_t lb = in.lowoff[1], hb = in.highoff[1];
-    const TcLayout L = tc_layout(m, n, K, in.total, in.lowoff, in.highoff);
+    const TcShape S = tc_shape(m, n, h, K);
+    const TcLayout L = tc_layout(S, in.total);
     const TcBuffers B = tc_buffers(L, in.ws);
-    const int64_t lcnt = L.lcnt, hcnt = L.hcnt;
-    __nv_bfloat16* dlow = B.dig[0];
-    __nv_bfloat16* dhigh = B.dig[1];
-    int* exlow = B.ex[0];
-    int* exhigh = B.ex[1];
-    double* xt = B.xt;
-    double2* const* V = B.V;
-    double* const* SV = B.SV;
-    __nv_bfloat16* const* DV = B.DV;
-    int* const* EXV = B.EXV;
-    int64_t* const* efirst = B.efirst;
-    int* const* emax = B.emax;
-    double* const* esc = B.esc;
-    // single-entry blocks: the column vectors of both sides, their digits, and
-    // the output data of every level n-1 entry (timed as the split stage)
-    stage_begin(kStageSplit, s);
-    edge_vectors_kernel<<<(unsigned)(((int64_t)K * m + 255) / 256), 256, 0, s>>>(in.Y, m, h, K, in.lead, V[0], SV[0],
-                                                                                    V[1], SV[1]);
-    note_launches(1);
-    for (int side = 0; side < 2; ++side) {
-        const int64_t ww = side == 0 ? h : m - h;
-        split_exp_kernel<<<(unsigned)((ww * 32 + 255) / 256), 256, 0, s>>>(V[side], SV[side], ww, ww, K, EXV[side]);
-        const int64_t warps = ((ww + 3) / 4) * (Kp / 32);
-        split_digits_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(V[side], SV[side], ww, ww, K, Kp, EXV[side],
-                                                                          DV[side]);
-        const int64_t cnt = side == 0 ? in.lowoff[n] - in.lowoff[n - 1] : in.highoff[n] - in.highoff[n - 1];
-        edge_info_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(in.mc, m, n, h, side, cnt, efirst[side],
-                                                                         emax[side], esc[side]);
-        note_launches(3);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    stage_end(kStageSplit, s);
+    if (S.wdig[0] + TBM > INT32_MAX || S.wdig[1] + TBM > INT32_MAX) return cudaErrorInvalidConfiguration;
     stage_begin(kStageGemm, s);
-    CUtensorMap lr, lc, hr, hc, lc16, hc16, vl16, vh16;
-    if ((e = make_digit_map(&vl16, DV[0], h, Kp, kBSub)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&vh16, DV[1], m - h, Kp, kBSub)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&lr, dlow, lcnt, Kp, TBM)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&lc, dlow, lcnt, Kp, TBN)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&hr, dhigh, hcnt, Kp, TBM)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&hc, dhigh, hcnt, Kp, TBN)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&lc16, dlow, lcnt, Kp, kBSub)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&hc16, dhigh, hcnt, Kp, kBSub)) != cudaSuccess) return e;
+    CUtensorMap lr, lc, hr, hc, lc16, hc16;
+    if ((e = make_digit_map(&lr, B.dig[0], S.wdig[0], S.Kp, TBM)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&lc, B.dig[0], S.wdig[0], S.Kp, TBN)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&hr, B.dig[1], S.wdig[1], S.Kp, TBM)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&hc, B.dig[1], S.wdig[1], S.Kp, TBN)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&lc16, B.dig[0], S.wdig[0], S.Kp, kBSub)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&hc16, B.dig[1], S.wdig[1], S.Kp, kBSub)) != cudaSuccess) return e;
     TcProdArgs a;
     a.nk = 0;
-    a.kblocks = Kp / TBK;
-    auto round16 = [](int64_t x) { return (int)((x + 15) / 16) * 16; };
+    a.kblocks = S.Kp / TBK;
+    auto width = [](int64_t cols) { return cols >= TBN ? TBN : (int)((cols + 15) / 16) * 16; };
     // outputs [lo, hi): per k the ranks of the P whose outputs meet the range
     PRanges pr;
     p_ranges(m, n, h, in.lo, in.hi, &pr);
-    int64_t fullcols[kMaxBlocks];                 // columns of each block before any restriction
-    for (int k = 1; k < in.n; ++k) {
-        const int64_t M = msets_tc(in.h, k), N = msets_tc(in.m - in.h, in.n - k);
+    // level products k = e+1 .. n-e-1
+    for (int k = S.e + 1; k <= n - S.e - 1; ++k) {
+        const int64_t M = msets_tc(h, k), N = msets_tc(m - h, n - k);
         if (M == 0 || N == 0) continue;
         // Rows are the high-side entries Q unless Q has fewer entries than a
         // tile's 128 rows (and P more), which would leave most rows empty.
@@ -1202,83 +1342,147 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         const bool rl = N < TBM && M > N;
         const int64_t rows = rl ? M : N, cols = rl ? N : M;
         const bool any = pr.pa[k] < pr.pb[k];
-        a.rows_low[a.nk] = rl ? 1 : 0;
-        a.tn[a.nk] = cols >= TBN ? TBN : round16(cols);
+        const int b = a.nk++;
+        a.rows_low[b] = rl ? 1 : 0;
+        a.kind[b] = 0;
+        a.tn[b] = width(cols);
         // the P side (rows when rl, else columns) restricted to [pa, pb)
-        a.rows0[a.nk] = rl ? pr.pa[k] : 0;
-        a.rows[a.nk] = !any ? a.rows0[a.nk] : (rl ? pr.pb[k] : rows);
-        a.cols0[a.nk] = rl ? 0 : pr.pa[k];
-        a.cols[a.nk] = !any ? a.cols0[a.nk] : (rl ? cols : pr.pb[k]);
-        a.ncol[a.nk] = (int)std::min<int64_t>(a.cols[a.nk], INT32_MAX);
-        a.ecol0[a.nk] = (int)std::min<int64_t>(cols, INT32_MAX);
-        a.ecols[a.nk] = 0;
-        fullcols[a.nk] = cols;
-        a.row_off[a.nk] = rl ? in.lowoff[k] - lb : in.highoff[in.n - k] - hb;
-        a.col_off[a.nk] = rl ? in.highoff[in.n - k] - hb : in.lowoff[k] - lb;
-        a.lowoff[a.nk] = in.lowoff[k];
-        a.nk++;
+        a.rows0[b] = rl ? pr.pa[k] : 0;
+        a.rows[b] = !any ? a.rows0[b] : (rl ? pr.pb[k] : rows);
+        a.cols0[b] = rl ? 0 : pr.pa[k];
+        a.cols[b] = !any ? a.cols0[b] : (rl ? cols : pr.pb[k]);
+        a.row_off[b] = rl ? S.lev[0][k] : S.lev[1][n - k];
+        a.col_off[b] = rl ? S.lev[1][n - k] : S.lev[0][k];
+        a.lowoff[b] = in.lowoff[k];
+        a.rs[b] = a.cs[b] = a.cge[b] = 0;
+        a.ri_off[b] = a.ci_off[b] = 0;
     }
-    // the single-entry columns: rows = level n-1 of a side, columns = its
-    // modes (side 0: outputs with every photon low, k = n; side 1: k = 0),
-    // merged into the block with the same rows when both fit one tile.  The
-    // rows that reach [lo, hi): side 0, the parents (level n-1) of the level-n
-    // P in range; side 1, the parents of the Q of the block P = {} in range.
+    // Extension blocks, per side: runs of seam groups (consecutive groups
+    // merged until a run holds at least `thr` extension entries; a run takes
+    // the vectors E of its widest group, and each pair checks its own seam).
+    // High side: the entries are the tile rows and the vectors E the columns.
+    // Low side the other way round, so that there too the 32 lanes of a drain
+    // warp hold consecutive outputs (consecutive E) and its stores coalesce.
+    // For a part [lo, hi) of the outputs the entries and vectors are cut to
+    // those with an output in range (seam data on the host: a group's
+    // entries have increasing bases, so each vector's entries in range are
+    // found by bisection).
+    const bool whole = in.lo <= 0 && in.hi >= in.total;
+    std::vector<SeamInfo> hrow, hcol;
+    HostCounts hc_tab(whole ? 0 : m, whole ? 0 : n);
     for (int side = 0; side < 2; ++side) {
-        const int64_t rows = side == 0 ? in.lowoff[n] - in.lowoff[n - 1] : in.highoff[n] - in.highoff[n - 1];
-        const int ecols = side == 0 ? h : m - h;
-        if (rows == 0 || ecols == 0) continue;
-        int64_t r0 = 0, r1 = 0;
-        if (side == 0) {
-            if (pr.pa[n] < pr.pb[n]) {
-                r0 = host_parent_rank(h, n, pr.pa[n]);
-                r1 = host_parent_rank(h, n, pr.pb[n] - 1) + 1;
+        const int w = S.w[side];
+        auto gsize = [&](int g) { return side == 0 ? msets_tc(g + 1, S.L - 1) : msets_tc(w - g, S.L - 1); };
+        auto gcols = [&](int g) { return side == 0 ? msets_tc(m - g, S.e) : msets_tc(g + h + 1, S.e); };
+        if (!whole) {
+            int modes[PCV_MAX_PHOTONS];
+            const int order = side == 0 ? kRowsLow : kRowsHigh;
+            const int corder = side == 0 ? kColsLow : kColsHigh;     // the vectors this side's entries take
+            hrow.resize((size_t)S.nrows[side]);
+            for (int64_t i = 0; i < S.nrows[side]; ++i) {
+                const int k = seam_modes(hc_tab.mc, m, n, S.e, h, order, i, modes);
+                if (side == 1)
+                    for (int p = 0; p < k; ++p) modes[p] += h;
+                hrow[(size_t)i] = seam_of(hc_tab.mc, m, n, S.e, order, modes);
             }
-        } else {
-            const int64_t base = host_lowbase(m, n, h, 0, 0);
-            const int64_t c = std::max(in.lo, base) - base, d = std::min(in.hi, in.total) - base;
-            if (c < d) {
-                r0 = host_parent_rank(m - h, n, c);
-                r1 = host_parent_rank(m - h, n, d - 1) + 1;
+            hcol.resize((size_t)S.ncols);
+            for (int64_t i = 0; i < S.ncols; ++i) {
+                seam_modes(hc_tab.mc, m, n, S.e, h, corder, i, modes);
+                hcol[(size_t)i] = seam_of(hc_tab.mc, m, n, S.e, corder, modes);
             }
         }
-        if (r0 >= r1) continue;
-        const int64_t roff = side == 0 ? in.lowoff[n - 1] - lb : in.highoff[n - 1] - hb;
-        int host = -1;
-        for (int b = 0; b < a.nk; ++b)
-            if (a.rows_low[b] == (side == 0 ? 1 : 0) && a.row_off[b] == roff && a.ecols[b] == 0 &&
-                round16(fullcols[b]) + round16(ecols) <= TBN)
-                host = b;
-        if (host >= 0) {
-            // one column tile: every column of the host block, then the modes
-            a.ecol0[host] = round16(fullcols[host]);
-            a.ecols[host] = ecols;
-            a.ncol[host] = (int)fullcols[host];
-            a.cols0[host] = 0;
-            a.cols[host] = a.ecol0[host] + ecols;
-            a.tn[host] = a.ecol0[host] + round16(ecols);
-            if (a.rows[host] <= a.rows0[host]) {
-                a.rows0[host] = r0;
-                a.rows[host] = r1;
+        // the shortest run length that keeps the runs within kMaxSideBlocks
+        int64_t thr = TBM;
+        for (;; thr *= 2) {
+            int runs = 0;
+            int64_t r = 0;
+            for (int g = 0; g < w; ++g) {
+                r += gsize(g);
+                if (r >= thr || g + 1 == w) {
+                    ++runs;
+                    r = 0;
+                }
+            }
+            if (runs <= kMaxSideBlocks) break;
+        }
+        const int64_t c0 = (side == 1 && n == 2 * S.e) ? msets_tc(h, S.e) : 0;   // all-low E: the low side's
+        int64_t rb = 0, r = 0, cend = 0;
+        int g0 = 0;
+        for (int g = 0; g < w; ++g) {
+            r += gsize(g);
+            cend = std::max(cend, gcols(g));
+            if (r - rb < thr && g + 1 < w) continue;
+            // entries [ea, ez) (from rb) and vectors [va, vz) of the block
+            int64_t ea = 0, ez = r - rb, va = c0, vz = cend;
+            if (!whole) {
+                int64_t ra = INT64_MAX, rz = -1, ca = INT64_MAX, cz = -1;
+                int64_t gb = rb;
+                for (int gg = g0; gg <= g; ++gg) {
+                    const int64_t gs = gsize(gg), nc = gcols(gg);
+                    for (int64_t c = c0; c < nc && gs > 0; ++c) {
+                        const int64_t cb = hcol[(size_t)c].base;
+                        auto first_at_least = [&](int64_t v) {     // first entry of the group with base >= v
+                            int64_t x = gb, y = gb + gs;
+                            while (x < y) {
+                                const int64_t mid = (x + y) / 2;
+                                if (hrow[(size_t)mid].base < v) x = mid + 1; else y = mid;
+                            }
+                            return x;
+                        };
+                        const int64_t x0 = first_at_least(in.lo - cb), x1 = first_at_least(in.hi - cb);
+                        if (x0 >= x1) continue;
+                        ra = std::min(ra, x0);
+                        rz = std::max(rz, x1);
+                        ca = std::min(ca, c);
+                        cz = std::max(cz, c);
+                    }
+                    gb += gs;
+                }
+                if (rz < 0) {
+                    ez = ea;
+                } else {
+                    ea = ra - rb;
+                    ez = rz - rb;
+                    va = ca;
+                    vz = cz + 1;
+                }
+            }
+            if (a.nk >= kMaxBlocks) return cudaErrorInvalidConfiguration;
+            const int b = a.nk++;
+            a.kind[b] = 1;
+            a.lowoff[b] = 0;
+            a.rows_low[b] = 0;
+            // a pair is an output when max E <= min R (high side; rows R,
+            // columns E) or max R <= min E (low side; rows E, columns R)
+            a.cge[b] = 0;
+            if (side == 1) {
+                a.rows0[b] = ea;
+                a.rows[b] = ez;
+                a.cols0[b] = va;
+                a.cols[b] = vz;
+                a.row_off[b] = S.rows_off[1] + rb;
+                a.col_off[b] = S.cols_off[0];
+                a.rs[b] = 1;
+                a.ri_off[b] = rb;
+                a.cs[b] = 2;
+                a.ci_off[b] = 0;
             } else {
-                a.rows0[host] = std::min(a.rows0[host], r0);
-                a.rows[host] = std::max(a.rows[host], r1);
+                a.rows0[b] = va;
+                a.rows[b] = vz;
+                a.cols0[b] = ea;
+                a.cols[b] = ez;
+                a.row_off[b] = S.cols_off[1];
+                a.col_off[b] = S.rows_off[0] + rb;
+                a.rs[b] = 3;
+                a.ri_off[b] = 0;
+                a.cs[b] = 0;
+                a.ci_off[b] = rb;
             }
-            continue;
+            a.tn[b] = width(a.cols[b] - a.cols0[b]);
+            rb = r;
+            cend = 0;
+            g0 = g + 1;
         }
-        a.rows_low[a.nk] = side == 0 ? 1 : 0;
-        a.tn[a.nk] = ecols >= TBN ? TBN : round16(ecols);
-        a.rows0[a.nk] = r0;
-        a.rows[a.nk] = r1;
-        a.cols0[a.nk] = 0;
-        a.cols[a.nk] = ecols;
-        a.ncol[a.nk] = 0;
-        a.ecol0[a.nk] = 0;
-        a.ecols[a.nk] = ecols;
-        fullcols[a.nk] = ecols;
-        a.row_off[a.nk] = roff;
-        a.col_off[a.nk] = 0;
-        a.lowoff[a.nk] = 0;
-        a.nk++;
     }
     // blocks without tiles are dropped
     int64_t tiles = 0;
@@ -1289,17 +1493,20 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         if (rt * ct == 0) continue;
         if (nb != b) {
             a.rows_low[nb] = a.rows_low[b];
+            a.kind[nb] = a.kind[b];
             a.tn[nb] = a.tn[b];
             a.rows0[nb] = a.rows0[b];
             a.rows[nb] = a.rows[b];
             a.cols0[nb] = a.cols0[b];
             a.cols[nb] = a.cols[b];
-            a.ncol[nb] = a.ncol[b];
-            a.ecol0[nb] = a.ecol0[b];
-            a.ecols[nb] = a.ecols[b];
             a.row_off[nb] = a.row_off[b];
             a.col_off[nb] = a.col_off[b];
             a.lowoff[nb] = a.lowoff[b];
+            a.rs[nb] = a.rs[b];
+            a.cs[nb] = a.cs[b];
+            a.cge[nb] = a.cge[b];
+            a.ri_off[nb] = a.ri_off[b];
+            a.ci_off[nb] = a.ci_off[b];
         }
         a.tile0[nb] = tiles;
         tiles += rt * ct;
@@ -1311,31 +1518,28 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         stage_end(kStageGemm, s);
         return cudaSuccess;
     }
-    if (tiles * 3 * a.kblocks > INT32_MAX || lcnt + TBM > INT32_MAX || hcnt + TBM > INT32_MAX)
-        return cudaErrorInvalidConfiguration;
+    if (tiles * 3 * a.kblocks > INT32_MAX) return cudaErrorInvalidConfiguration;
     a.lowbase = in.lowbase;
-    a.ex_low = exlow;
-    a.ex_high = exhigh;
-    a.wlow = lcnt;                            // entries of the digit tensors (exponent stride)
-    a.whigh = hcnt;
-    a.xt = xt;
+    a.ex_low = B.ex[0];
+    a.ex_high = B.ex[1];
+    a.wlow = S.wdig[0];                       // entries of the digit tensors (exponent stride)
+    a.whigh = S.wdig[1];
+    a.seam[0] = B.rseam[0];
+    a.seam[1] = B.rseam[1];
+    a.seam[2] = B.cseam[0];
+    a.seam[3] = B.cseam[1];
+    a.xt = B.xt;
     a.lo = in.lo;
     a.hi = in.hi;
     a.amp = in.amp;
     a.prob = in.prob;
-    for (int side = 0; side < 2; ++side) {
-        a.ex_v[side] = EXV[side];
-        a.efirst[side] = efirst[side];
-        a.emax[side] = emax[side];
-        a.esc[side] = esc[side];
-    }
     a.error = in.error;
     a.max_polls = wait_limit(kMaxPolls);
     a.tiles = tiles;
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const unsigned grid = (unsigned)(tiles < (int64_t)sms ? tiles : sms);
-    tc_product_kernel<<<grid, kThreads, kSmemBytes, s>>>(lr, lc, hr, hc, lc16, hc16, vl16, vh16, a);
+    tc_product_kernel<<<grid, kThreads, kSmemBytes, s>>>(lr, lc, hr, hc, lc16, hc16, a);
     note_launches(1);
     stage_end(kStageGemm, s);
     return cudaGetLastError();

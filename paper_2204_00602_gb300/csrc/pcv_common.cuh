@@ -47,13 +47,13 @@ __device__ __forceinline__ double2 ld(const double2* p) { return __ldg(p); }
 struct MultisetTable {
     const int64_t* t;
     int kmax;
-    __device__ __forceinline__ int64_t operator()(int a, int k) const { return t[a * (kmax + 1) + k]; }
+    __host__ __device__ __forceinline__ int64_t operator()(int a, int k) const { return t[a * (kmax + 1) + k]; }
 };
 
 // Canonical order of S_{w,k}: lexicographic order of the non-decreasing
 // photon->mode list.  Unrank `idx` into modes[0..k) (values in [0, w)).
 template <int KMAX>
-__device__ __forceinline__ void unrank_multiset(MultisetTable mc, int w, int k, int64_t idx, int* modes)
+__host__ __device__ __forceinline__ void unrank_multiset(MultisetTable mc, int w, int k, int64_t idx, int* modes)
 {
     int v = 0;
     for (int p = 0; p < k; ++p) {
@@ -69,7 +69,7 @@ __device__ __forceinline__ void unrank_multiset(MultisetTable mc, int w, int k, 
 }
 
 // Rank of a non-decreasing mode list of length k over w modes.
-__device__ __forceinline__ int64_t rank_multiset(MultisetTable mc, int w, int k, const int* modes)
+__host__ __device__ __forceinline__ int64_t rank_multiset(MultisetTable mc, int w, int k, const int* modes)
 {
     int64_t r = 0;
     int prev = 0;
@@ -232,10 +232,10 @@ int64_t dist_plan(const Plan& p, int B, int64_t ws_bytes, bool need_acc, DistPla
 
 // Tables and products on the tensor cores with exact digit splitting
 // (glynn_tc.cu): one batch entry, all K = 2^{n-1} <= 512 sign vectors in one
-// pass, n >= 2 and both sides non-empty.  launch_tc_tables builds table
-// levels 1 .. n-1 of both sides from the row sums and writes their digits
-// (and lowbase of the low side); launch_tc_products runs every output block,
-// k = 0 .. n, and writes amp / prob.
+// pass, n >= 2 and both sides non-empty.  launch_tc_tables builds the table
+// levels 1 .. n-e of both sides (e = min(3, n/2)) and the e-photon column
+// vectors from the row sums and writes their digits (and lowbase of the low
+// side); launch_tc_products runs every output block and writes amp / prob.
 struct TcInputs {
     int K, n, m, h;
     int64_t lowoff[PCV_MAX_PHOTONS + 2], highoff[PCV_MAX_PHOTONS + 2];
@@ -251,7 +251,7 @@ struct TcInputs {
     int64_t lo, hi;                               // outputs [lo, hi), stored at [o - lo]
 };
 int tc_pad_k(int K);
-int64_t tc_workspace(int m, int n, int K, int64_t total, const int64_t* lowoff, const int64_t* highoff);
+int64_t tc_workspace(int m, int n, int h, int K, int64_t total);
 cudaError_t launch_tc_tables(const TcInputs& in, cudaStream_t s);
 cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s);
 cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* U,

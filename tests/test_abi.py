@@ -133,9 +133,12 @@ def test_distribution_workspace_sizes():
     full = _abi.pcv_distribution_workspace(20, 10)
     small = _abi.pcv_distribution_workspace_min(20, 10)
     assert 0 < small < full < 8 << 30
-    n = 10
-    lo = math.comb(10 + n, n)
-    assert full >= 512 * 2 * lo * 16      # alpha and beta tables for all 512 sign vectors
+    # the tensor-core plan: two real products per output, and 48 bytes of
+    # digits per sign vector for each extension row (level n - 3 = 7 of the
+    # ten modes of each side)
+    N = math.comb(20 + 10 - 1, 10)
+    rows = math.comb(10 + 7 - 1, 7)
+    assert full >= 2 * N * 8 + 2 * rows * 512 * 48
     with pytest.raises(_abi.PcvError) as e:
         fake = 1 << 40
         _abi.pcv_distribution(fake, 20, np.array([1] * 10 + [0] * 10, np.uint8), fake, None, fake, small - 1024, None)
@@ -195,12 +198,17 @@ def test_distinguishability_arguments_are_checked():
 
 def test_tensor_core_workspace_sizes(lib):
     # host-only: the factorised tensor-core path's workspace (digit tensors of
-    # table levels 1..n-1, parents, two products per output, single-entry data)
+    # the table levels 4..6 and the extension rows (level 7) of each side and
+    # of the 3-photon column vectors, FP64 parents (levels 1..6), two products
+    # per output, entry and seam data)
     from paper_2204_00602_gb300 import _abi
     ws = _abi.pcv_distribution_tc_workspace(20, 10)
-    # 2 sides x 92,377 entries x 3 products x 8 digits x 512 sign vectors x 2 B
-    digits = 2 * 92377 * 3 * 8 * 512 * 2
-    assert digits < ws < digits + 1.1e9, ws
+    c = math.comb
+    entries = sum(c(10 + k - 1, k) for k in (4, 5, 6, 7)) + c(20 + 3 - 1, 3)
+    digits = 2 * entries * 3 * 8 * 512 * 2      # per side; 3 products x 8 digits x 512 sign vectors x 2 B
+    parents = 2 * sum(c(10 + k - 1, k) for k in range(1, 7)) * 512 * 16
+    products = 2 * c(29, 10) * 8
+    assert digits + parents + products < ws < digits + parents + products + 0.1e9, ws
     assert _abi.pcv_distribution_tc_workspace(20, 9) < ws
     assert _abi.pcv_distribution_tc_workspace(12, 6) > 0
     with pytest.raises(_abi.PcvError):
