@@ -634,6 +634,35 @@ __device__ __forceinline__ bool scale_packed(long long zh, uint32_t zl, int s, d
     return true;
 }
 
+// The rounding and stores of one output of one product: x_t = RN(Z 2^{sc -
+// 49}) (sc = E_row + E_col - 14, kNoExp for an all-zero row or column); t1
+// and t2 go to the workspace at o, and with t3 the amplitude and |a|^2 are
+// formed, times the seam factor 1/sqrt(C(a + b, b)) when smu = a << 8 | b is
+// set.  Not inlined: the drain calls it for each of its 32 outputs per
+// product, and a single copy keeps the kernel's code, which the MMA and TMA
+// warps share the instruction cache with, small (measured: products 2.51 ->
+// 2.28 ms at m=20, n=10).
+__device__ __noinline__ void drain_output(double* __restrict__ xt, double2* amp, double* prob, int64_t span, int64_t o,
+                                         int t, long long zh, uint32_t zl, int sc, int smu)
+{
+    double x = 0.0;
+    if (sc != kNoExp && !scale_packed(zh, zl, sc - 49, x))
+        x = fma((double)zl, pow2(sc - 49), (double)zh * pow2(sc - 21));
+    if (t < 2) {
+        xt[(int64_t)t * span + o] = x;
+        return;
+    }
+    const double t1 = xt[o], t2 = xt[span + o];
+    double re = t1 - t2, im = x - t1 - t2;
+    if (smu) {
+        const double f = seam_scale(smu >> 8, smu & 255);
+        re *= f;
+        im *= f;
+    }
+    if (amp) amp[o] = make_double2(re, im);
+    if (prob) prob[o] = fma(re, re, im * im);
+}
+
 // Row digits in the order 0, 7, 1, 6, 2, 5, 3, 4: digit i is multiplied by
 // 8 - i column digits, so alternating long and short products keeps the MMA
 // time between consecutive row-digit loads even (the slots then stay about
@@ -956,28 +985,11 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
                         // the row's side of the seam
                         const int ckey = ck & 0xFFFF;
                         if (ext && (cge ? ckey < rkey : ckey > rkey)) continue;
-                        double x = 0.0;
-                        if (er != kNoExp && ec != kNoExp) {
-                            const int sc = er + ec - 14;
-                            if (!scale_packed(zh[h][q], zl[h][q], sc - 49, x))
-                                x = fma((double)zl[h][q], pow2(sc - 49), (double)zh[h][q] * pow2(sc - 21));
-                        }
                         const int64_t og = rbase + cb;
                         if (og < a.lo || og >= a.hi) continue;
-                        const int64_t o = og - a.lo, span = a.hi - a.lo;
-                        if (t < 2) {
-                            a.xt[(int64_t)t * span + o] = x;
-                        } else {
-                            const double t1 = a.xt[o], t2 = a.xt[span + o];
-                            double re = t1 - t2, im = x - t1 - t2;
-                            if (ext && ckey == rkey) {         // the seam mode's multiplicity in S
-                                const double sc = seam_scale(rmu, ck >> 16);
-                                re *= sc;
-                                im *= sc;
-                            }
-                            if (a.amp) a.amp[o] = make_double2(re, im);
-                            if (a.prob) a.prob[o] = fma(re, re, im * im);
-                        }
+                        const int sc = (er != kNoExp && ec != kNoExp) ? er + ec - 14 : kNoExp;
+                        const int smu = (ext && ckey == rkey) ? ((rmu << 8) | (ck >> 16)) : 0;
+                        drain_output(a.xt, a.amp, a.prob, a.hi - a.lo, og - a.lo, t, zh[h][q], zl[h][q], sc, smu);
                     }
                 }
             }
