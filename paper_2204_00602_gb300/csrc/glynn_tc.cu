@@ -48,19 +48,20 @@
 //     The output index splits into a row part and a column part, and where
 //     E meets R at the seam mode the product carries 1/sqrt(C(mu_R + mu_E,
 //     mu_E)) more (multiplicities of that mode in R and E).  The glynn sign
-//     and 2^{-(n-1)} norm_t sit on the low-side entries, and on the high
-//     side's level n-e rows.
+//     and 2^{-(n-1)} norm_t sit on the low-side entries, and on the column
+//     vectors the high side's rows take.
 // So no table level above n-e is built: for n = 10, levels 8 and 9 of both
 // sides (three quarters of all table entries) never exist.
 //
 // Kernels:
-//   tc_level_kernel     a table level, built in FP64 from its parent level and
-//                       written as BF16 digits, laid out [t][digit][entry][K]
-//                       for TMA; levels below n-e also keep their complex
+//   tc_level_kernel     table levels, built in FP64 from their parent levels
+//                       and written as BF16 digits, laid out [t][digit][entry]
+//                       [K] for TMA; levels below n-e also keep their complex
 //                       entries as the next level's parents.  The extension
 //                       rows and the column vectors are levels too, in their
 //                       grouped orders (seam_entries_kernel gives each entry
-//                       its parent, mode and output-index part);
+//                       its parent, mode and output-index part).  One launch
+//                       per level number covers both sides and the columns;
 //   tc_product_kernel   one persistent CTA per SM walking 128 x N output
 //                       tiles of one block each (N = 16..64), eleven warps:
 //   warp 0  row-operand TMA: per 64-wide K block, the 8 digit slices of the
@@ -318,14 +319,29 @@ __host__ __device__ inline int seam_modes(const MultisetTable& mc, int m, int n,
     return k;
 }
 
+// The four entry lists of the extension blocks (rows of both sides, the
+// column vectors in both orders), one launch: list j holds threads
+// [start[j], start[j+1]).
+struct SeamLists {
+    int order[4];
+    EntryInfo* info[4];
+    SeamInfo* seam[4];
+    int64_t start[5];
+};
+
 // Per entry of the extension rows or the column vectors: the parent
 // (lexicographic rank without the last mode, over the same values), the
 // last mode and its multiplicity, and the seam data.
-__global__ void seam_entries_kernel(MultisetTable mc, int m, int n, int e, int h, int order, int64_t count,
-                                    EntryInfo* __restrict__ info, SeamInfo* __restrict__ seam)
+__global__ void seam_entries_kernel(MultisetTable mc, int m, int n, int e, int h, const SeamLists sl)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= sl.start[4]) return;
+    int j = 0;
+    while (j < 3 && g >= sl.start[j + 1]) ++j;
+    const int order = sl.order[j];
+    const int64_t i = g - sl.start[j];
+    EntryInfo* __restrict__ info = sl.info[j];
+    SeamInfo* __restrict__ seam = sl.seam[j];
     int modes[PCV_MAX_PHOTONS];
     const int k = seam_modes(mc, m, n, e, h, order, i, modes);
     const int w = order == kRowsLow ? h : (order == kRowsHigh ? m - h : m);
@@ -362,7 +378,7 @@ struct TcLevelArgs {
     int w, shift;                        // modes [0, w), at `shift` in the output (lexicographic levels)
     int64_t count;                       // entries of level k
     double lead;                         // 2^{-(n-1)} norm_t
-    int sigma_out;                       // 1: entries times sigma(d) 2^{-(n-1)} norm_t (high-side extension rows)
+    int sigma_out;                       // 1: entries times sigma(d) 2^{-(n-1)} norm_t (the high side's columns)
     const EntryInfo* info;               // per entry, or null (lexicographic)
     const double2* Ys;                   // [n-1][m][K]: y_r(d) / sqrt(mult), mult = 1 .. n-1
     const double2* parent;               // level k-1, [entry][K] (k >= 2)
@@ -402,15 +418,28 @@ __global__ void scaled_rowsums_kernel(const double2* __restrict__ Y, int m, int 
 }
 
 
+// Up to four independent levels in one launch (the same level of both sides
+// and of the column vectors, which need only their own parents): job j takes
+// the blocks [block0[j], block0[j+1]).
+constexpr int kLevelJobs = 4;
+struct TcLevelBatch {
+    TcLevelArgs job[kLevelJobs];
+    int njobs;
+    int64_t block0[kLevelJobs + 1];
+};
+
 template <int PER, int WPE>
-__global__ void __launch_bounds__(128) tc_level_kernel(const TcLevelArgs a)
+__global__ void __launch_bounds__(128) tc_level_kernel(const __grid_constant__ TcLevelBatch b)
 {
+    int jb = 0;
+    while (jb + 1 < b.njobs && (int64_t)blockIdx.x >= b.block0[jb + 1]) ++jb;
+    const TcLevelArgs& a = b.job[jb];
     // WPE warps per entry (4 / WPE entries per block), warp `part` holding
     // sign vectors part 32 PER .. (part + 1) 32 PER - 1
     __shared__ int s_f[4][3];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int part = warp % WPE;
-    const int64_t e = (int64_t)blockIdx.x * (4 / WPE) + warp / WPE;
+    const int64_t e = ((int64_t)blockIdx.x - b.block0[jb]) * (4 / WPE) + warp / WPE;
     const bool valid = e < a.count;
     const int w = a.w, shift = a.shift;
     int mult = 1, r = 0;
@@ -1169,33 +1198,30 @@ TcBuffers tc_buffers(const TcLayout& L, void* ws)
 }
 
 template <int PER, int WPE>
-cudaError_t launch_level(const TcLevelArgs& la, cudaStream_t s)
+cudaError_t launch_level(TcLevelBatch& b, cudaStream_t s)
 {
-    const int64_t blocks = (la.count + (4 / WPE) - 1) / (4 / WPE);
-    tc_level_kernel<PER, WPE><<<(unsigned)blocks, 128, 0, s>>>(la);
-    note_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_level_kp(const TcLevelArgs& la, cudaStream_t s)
-{
-    if (la.count == 0) return cudaSuccess;
-    switch (la.Kpad / 32) {
-        case 2: return launch_level<2, 1>(la, s);     // Kpad = 64
-        case 4: return launch_level<4, 1>(la, s);     // 128
-        case 8: return launch_level<4, 2>(la, s);     // 256
-        default: return launch_level<4, 4>(la, s);    // 512
+    int64_t blocks = 0;
+    for (int j = 0; j < b.njobs; ++j) {
+        b.block0[j] = blocks;
+        blocks += (b.job[j].count + (4 / WPE) - 1) / (4 / WPE);
     }
-}
-
-cudaError_t launch_seam_entries(const TcInputs& in, const TcShape& S, int order, int64_t count, EntryInfo* info,
-                                SeamInfo* seam, cudaStream_t s)
-{
-    if (count == 0) return cudaSuccess;
-    seam_entries_kernel<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(in.mc, in.m, in.n, S.e, in.h, order, count,
-                                                                        info, seam);
+    b.block0[b.njobs] = blocks;
+    if (blocks == 0) return cudaSuccess;
+    tc_level_kernel<PER, WPE><<<(unsigned)blocks, 128, 0, s>>>(b);
     note_launches(1);
     return cudaGetLastError();
+}
+
+// One launch for the jobs in b (all with the same Kpad).
+cudaError_t launch_levels(TcLevelBatch& b, cudaStream_t s)
+{
+    if (b.njobs == 0) return cudaSuccess;
+    switch (b.job[0].Kpad / 32) {
+        case 2: return launch_level<2, 1>(b, s);     // Kpad = 64
+        case 4: return launch_level<4, 1>(b, s);     // 128
+        case 8: return launch_level<4, 2>(b, s);     // 256
+        default: return launch_level<4, 4>(b, s);    // 512
+    }
 }
 
 // The multiset counts on the host, in the device table's layout.
@@ -1248,11 +1274,34 @@ cudaError_t launch_tc_tables(const TcInputs& in, cudaStream_t s)
         return la;
     };
     cudaError_t e;
-    for (int side = 0; side < 2; ++side) {
-        const int w = S.w[side], shift = side == 0 ? 0 : in.h;
-        // lexicographic levels 1 .. L-1: parents, with digits where a level product takes them
-        for (int k = 1; k < S.L; ++k) {
-            TcLevelArgs la = level_args(side, k, w, shift);
+    // the entry lists of the extension blocks (they need only the multiset
+    // counts): rows of both sides, column vectors by max E (side 0's tensor)
+    // and by min E (side 1's)
+    {
+        SeamLists sl;
+        const int orders[4] = {kRowsLow, kRowsHigh, kColsHigh, kColsLow};
+        const int64_t counts[4] = {S.nrows[0], S.nrows[1], S.ncols, S.ncols};
+        EntryInfo* infos[4] = {B.rinfo[0], B.rinfo[1], B.cinfo[0], B.cinfo[1]};
+        SeamInfo* seams[4] = {B.rseam[0], B.rseam[1], B.cseam[0], B.cseam[1]};
+        sl.start[0] = 0;
+        for (int j = 0; j < 4; ++j) {
+            sl.order[j] = orders[j];
+            sl.info[j] = infos[j];
+            sl.seam[j] = seams[j];
+            sl.start[j + 1] = sl.start[j] + counts[j];
+        }
+        seam_entries_kernel<<<(unsigned)((sl.start[4] + 127) / 128), 128, 0, s>>>(in.mc, in.m, n, S.e, in.h, sl);
+        note_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // lexicographic levels k = 1 .. L-1 of both sides (parents, with digits
+    // where a level product takes them) and, for k < e, of the column vectors
+    for (int k = 1; k < S.L; ++k) {
+        TcLevelBatch b;
+        b.njobs = 0;
+        for (int side = 0; side < 2; ++side) {
+            const int w = S.w[side];
+            TcLevelArgs la = level_args(side, k, w, side == 0 ? 0 : in.h);
             la.count = msets_tc(w, k);
             la.parent = k >= 2 ? B.par[side] + S.par[side][k - 1] * K : nullptr;
             la.out = B.par[side] + S.par[side][k] * K;
@@ -1266,48 +1315,47 @@ cudaError_t launch_tc_tables(const TcInputs& in, cudaStream_t s)
                 la.lowbase = in.lowbase;
                 la.lowoff_k = in.lowoff[k];
             }
-            if ((e = launch_level_kp(la, s)) != cudaSuccess) return e;
+            b.job[b.njobs++] = la;
         }
-        // the extension rows: level L grouped by seam mode (the high side's
-        // carry the glynn sign and leading factor)
-        if ((e = launch_seam_entries(in, S, side == 0 ? kRowsLow : kRowsHigh, S.nrows[side], B.rinfo[side],
-                                     B.rseam[side], s)) != cudaSuccess)
-            return e;
-        TcLevelArgs la = level_args(side, S.L, w, shift);
+        if (k < S.e) {
+            TcLevelArgs la = level_args(2, k, in.m, 0);
+            la.count = msets_tc(in.m, k);
+            la.parent = k >= 2 ? B.cpar + S.cpar[k - 1] * K : nullptr;
+            la.out = B.cpar + S.cpar[k] * K;
+            b.job[b.njobs++] = la;
+        }
+        if ((e = launch_levels(b, s)) != cudaSuccess) return e;
+    }
+    // the extension rows (level L of each side, grouped by seam mode) and
+    // the column vectors (level e over all modes) in both orders.  The glynn
+    // sign and leading factor, on the low side from level 0 on, go to the
+    // high side's products through their columns (side 0's tensor).
+    TcLevelBatch b;
+    b.njobs = 0;
+    for (int side = 0; side < 2; ++side) {
+        TcLevelArgs la = level_args(side, S.L, S.w[side], side == 0 ? 0 : in.h);
         la.count = S.nrows[side];
         la.info = B.rinfo[side];
         la.parent = S.L >= 2 ? B.par[side] + S.par[side][S.L - 1] * K : nullptr;
-        la.sigma_out = side == 1;
         la.digits = B.dig[side];
         la.ex = B.ex[side];
         la.dig_off = S.rows_off[side];
         la.wdig = S.wdig[side];
-        if ((e = launch_level_kp(la, s)) != cudaSuccess) return e;
-    }
-    // the column vectors: levels 1 .. e-1 over all modes, then level e in the
-    // two orders
-    for (int k = 1; k < S.e; ++k) {
-        TcLevelArgs la = level_args(2, k, in.m, 0);
-        la.count = msets_tc(in.m, k);
-        la.parent = k >= 2 ? B.cpar + S.cpar[k - 1] * K : nullptr;
-        la.out = B.cpar + S.cpar[k] * K;
-        if ((e = launch_level_kp(la, s)) != cudaSuccess) return e;
+        b.job[b.njobs++] = la;
     }
     for (int side = 0; side < 2; ++side) {
-        if ((e = launch_seam_entries(in, S, side == 0 ? kColsHigh : kColsLow, S.ncols, B.cinfo[side], B.cseam[side],
-                                     s)) != cudaSuccess)
-            return e;
         TcLevelArgs la = level_args(2, S.e, in.m, 0);
         la.count = S.ncols;
         la.info = B.cinfo[side];
         la.parent = S.e >= 2 ? B.cpar + S.cpar[S.e - 1] * K : nullptr;
+        la.sigma_out = side == 0;
         la.digits = B.dig[side];
         la.ex = B.ex[side];
         la.dig_off = S.cols_off[side];
         la.wdig = S.wdig[side];
-        if ((e = launch_level_kp(la, s)) != cudaSuccess) return e;
+        b.job[b.njobs++] = la;
     }
-    return cudaSuccess;
+    return launch_levels(b, s);
 }
 
 cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)

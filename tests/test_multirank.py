@@ -38,7 +38,7 @@ def _worker(rank, world, port, out):
 def test_two_cpu_ranks():
     import torch.multiprocessing as mp
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     for r in (0, 1):
@@ -99,7 +99,7 @@ def _shard_worker(rank, world, port, out):
 def test_two_rank_sharding_host_logic():
     import torch.multiprocessing as mp
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_shard_worker, args=(2, port, out), nprocs=2, join=True)
     r0, r1 = out[0], out[1]
