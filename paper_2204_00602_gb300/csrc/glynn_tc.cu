@@ -82,11 +82,12 @@
 //           diagonals (warp w owns TMEM lanes 32 (w mod 4) .., two warps per
 //           lane group split the columns) and the integer combination; the
 //           accumulators are then handed back to the MMA, and the rounding
-//           and stores follow.  t1 and t2 are stored at the output's
-//           canonical index in a [2][outputs] buffer; after t3 the thread
-//           that stored them forms the amplitude and |a|^2 in place.  Tile
-//           rows are high-side entries wherever there are 128 of them, so a
-//           warp's 32 lanes hold consecutive outputs and its stores coalesce.
+//           and stores follow (one non-inlined function per output).  t1 is
+//           stored at the output's canonical index in a [2][outputs] buffer;
+//           with t2 the same thread turns it into Re a and t1 + t2, and with
+//           t3 it forms Im a and |a|^2.  Tiles are oriented so that a warp's
+//           32 lanes hold consecutive outputs wherever a block allows it, so
+//           its stores coalesce.
 // Every mbarrier wait is bounded; on a time-out the kernel records an error
 // code and returns after releasing its tensor memory.
 
@@ -575,7 +576,7 @@ struct TcProdArgs {
     // seam data: extension rows of the low (0) and high (1) side, column
     // vectors by max E (2, in the low tensor) and by min E (3, high tensor)
     const SeamInfo* seam[4];
-    double* xt;                               // [2][hi - lo]: the real products t1, t2 per output
+    double* xt;                               // [2][hi - lo]: per output t1, then Re a and t1 + t2
     int64_t lo, hi;                           // outputs [lo, hi) are written, at o - lo
     double2* amp;                             // amplitudes, or null
     double* prob;                             // probabilities, or null
@@ -664,25 +665,33 @@ __device__ __forceinline__ bool scale_packed(long long zh, uint32_t zl, int s, d
 }
 
 // The rounding and stores of one output of one product: x_t = RN(Z 2^{sc -
-// 49}) (sc = E_row + E_col - 14, kNoExp for an all-zero row or column); t1
-// and t2 go to the workspace at o, and with t3 the amplitude and |a|^2 are
-// formed, times the seam factor 1/sqrt(C(a + b, b)) when smu = a << 8 | b is
-// set.  Not inlined: the drain calls it for each of its 32 outputs per
-// product, and a single copy keeps the kernel's code, which the MMA and TMA
-// warps share the instruction cache with, small (measured: products 2.51 ->
-// 2.28 ms at m=20, n=10).
+// 49}) (sc = E_row + E_col - 14, kNoExp for an all-zero row or column).  t1
+// goes to the workspace at o; with t2 the same thread replaces it by Re a =
+// t1 - t2 and stores t1 + t2 beside it, so that with t3 only Im a = t3 - (t1
+// + t2) and |a|^2 remain (FP64 is scarce on this part, and the work after
+// the third product is the one that holds up the next tile); the amplitude
+// takes the seam factor 1/sqrt(C(a + b, b)) when smu = a << 8 | b is set.
+// Not inlined: the drain calls it for each of its 32 outputs per product, and
+// a single copy keeps the kernel's code, which the MMA and TMA warps share
+// the instruction cache with, small (measured at m=20, n=10: products 2.51
+// -> 2.28 ms; the split of the combination, 2.27 -> 2.22 ms).
 __device__ __noinline__ void drain_output(double* __restrict__ xt, double2* amp, double* prob, int64_t span, int64_t o,
                                          int t, long long zh, uint32_t zl, int sc, int smu)
 {
     double x = 0.0;
     if (sc != kNoExp && !scale_packed(zh, zl, sc - 49, x))
         x = fma((double)zl, pow2(sc - 49), (double)zh * pow2(sc - 21));
-    if (t < 2) {
-        xt[(int64_t)t * span + o] = x;
+    if (t == 0) {
+        xt[o] = x;
         return;
     }
-    const double t1 = xt[o], t2 = xt[span + o];
-    double re = t1 - t2, im = x - t1 - t2;
+    if (t == 1) {
+        const double t1 = xt[o];
+        xt[o] = t1 - x;
+        xt[span + o] = t1 + x;
+        return;
+    }
+    double re = xt[o], im = x - xt[span + o];
     if (smu) {
         const double f = seam_scale(smu >> 8, smu & 255);
         re *= f;
