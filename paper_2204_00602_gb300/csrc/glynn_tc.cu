@@ -708,9 +708,12 @@ __device__ __noinline__ void drain_output(double* __restrict__ xt, double2* amp,
 // every diagonal.
 __device__ __forceinline__ int slice_order(int ii) { return (ii & 1) ? kDigits - 1 - (ii >> 1) : (ii >> 1); }
 
-// A tile's place: k block, first row and column, width, and which side the
-// rows come from.  Tiles are numbered k block by k block, column tiles
-// fastest, so CTAs that run at the same time share row digits.
+// A tile's place: block, first row and column, width, and which side the
+// rows come from.  Tiles are numbered block by block; within a block the
+// tiles along the longer side come slowest (column tiles fastest when the
+// block has at least as many rows as columns), so CTAs that run at the same
+// time share the operand tile of the longer side, which is read from memory
+// once, and cycle through the shorter side's operand, which stays in L2.
 struct TileInfo {
     int kb, tn;
     int64_t r0, c0;
@@ -726,9 +729,11 @@ __device__ __forceinline__ TileInfo tile_info(const TcProdArgs& a, int64_t tile)
     ti.kb = kb;
     ti.tn = a.tn[kb];
     const int64_t ctiles = (a.cols[kb] - a.cols0[kb] + ti.tn - 1) / ti.tn;
+    const int64_t rtiles = (a.rows[kb] - a.rows0[kb] + TBM - 1) / TBM;
     const int64_t lt = tile - a.tile0[kb];
-    ti.r0 = a.rows0[kb] + (lt / ctiles) * TBM;
-    ti.c0 = a.cols0[kb] + (lt % ctiles) * ti.tn;
+    const bool cfast = a.cols[kb] - a.cols0[kb] <= a.rows[kb] - a.rows0[kb];
+    ti.r0 = a.rows0[kb] + (cfast ? lt / ctiles : lt % rtiles) * TBM;
+    ti.c0 = a.cols0[kb] + (cfast ? lt % ctiles : lt / rtiles) * ti.tn;
     ti.rl = a.rows_low[kb] != 0;
     ti.rentry = (int)(a.row_off[kb] + ti.r0);
     ti.centry = (int)(a.col_off[kb] + ti.c0);
