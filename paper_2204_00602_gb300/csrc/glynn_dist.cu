@@ -502,7 +502,7 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
 
     // the status word starts each call at zero; a tensor-core kernel whose
     // bounded wait gives up writes its role code there
-    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(status, 0, 16, s);     // time-out word, tensor-core tile counter
     if (e != cudaSuccess) return e;
     if ((e = build_multiset_table(table, m, n, s)) != cudaSuccess) return e;
     MultisetTable mc{table, n};
@@ -581,6 +581,7 @@ cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* 
             ti.prob = prob;
             ti.ws = tcws;
             ti.error = status;
+            ti.next_tile = (unsigned long long*)((char*)status + 8);
             ti.lo = lo;
             ti.hi = hi;
             if ((e = launch_tc_tables(ti, s)) != cudaSuccess) return e;

@@ -582,6 +582,7 @@ struct TcProdArgs {
     double* prob;                             // probabilities, or null
     int* error;                               // set to the role that gave up (1 producer, 2 MMA, 3 drain,
                                               // 4 clean-up), or null
+    unsigned long long* next_tile;            // tile counter, zero at launch: CTAs take tiles in order
     long long max_polls;                      // bound of one mbarrier wait
 };
 
@@ -740,11 +741,30 @@ __device__ __forceinline__ TileInfo tile_info(const TcProdArgs& a, int64_t tile)
     return ti;
 }
 
-// Persistent: CTA b takes tiles b, b + grid, b + 2 grid, ...  The work of a
-// CTA is a sequence of chunks q = (tile, product t, 64-wide K block c); the
-// producer issues chunk q + 1's column digits after chunk q's third row digit
-// (by then chunk q - 1, the last user of that buffer, is nearly done), and
-// the next tile's loads while the drain finishes the last one.
+constexpr int kTileRing = 4;     // tiles a CTA's row producer has taken ahead of the other roles
+
+// The next tile of this CTA from the tile ring (-1: no more tiles, -2: the
+// wait gave up); every role takes every tile and hands the slot back once
+// (a warp role: its lane 0 waits and reads, and the warp learns the tile by
+// a shuffle, so all its lanes leave with the same answer).
+__device__ __forceinline__ int64_t take_tile(uint64_t* tfull, uint64_t* tempty, const int64_t* s_tile, uint32_t it,
+                                             long long polls, bool warp_role)
+{
+    const uint32_t slot = it % kTileRing;
+    const bool leader = !warp_role || (threadIdx.x & 31) == 0;
+    long long tile = -2;
+    if (leader && tcx::mbar_wait(&tfull[slot], (it / kTileRing) & 1, polls)) tile = s_tile[slot];
+    if (warp_role) tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (leader && tile != -2) tcx::mbar_arrive(&tempty[slot]);
+    return tile;
+}
+
+// Persistent, one CTA per SM, tiles handed out in order by a global counter
+// (the row producer takes them, a few ahead, and passes them to the other
+// roles through a ring in shared memory), so a CTA that runs fast takes more
+// tiles.  The work of a CTA is a sequence of chunks q = (tile, product t,
+// 64-wide K block c); the row and column producers run ahead of the MMA by
+// their slot rings.
 __global__ void __launch_bounds__(kThreads, 1)
 tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_constant__ CUtensorMap low_cols,
                   const __grid_constant__ CUtensorMap high_rows, const __grid_constant__ CUtensorMap high_cols,
@@ -757,13 +777,13 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
     unsigned char* aslot = base + kBSets * kBBytes;            // kASlots x 16 KB
     __shared__ __align__(8) uint64_t bfull[kBSets], bempty[kBSets], afull[kASlots], aempty[kASlots];
     __shared__ __align__(8) uint64_t accfull, accempty, mma_done;
+    __shared__ __align__(8) uint64_t tfull[kTileRing], tempty[kTileRing];
+    __shared__ int64_t s_tile[kTileRing];
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nkb = a.kblocks;
-    const int64_t my_tiles = a.tiles > (int64_t)blockIdx.x ? (a.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const uint32_t nchunks = (uint32_t)(my_tiles * 3 * nkb);      // < 2^31 (checked on the host)
 
     if (tid == 0) {
         for (int s = 0; s < kBSets; ++s) {
@@ -777,6 +797,10 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
         mbar_init(&accfull, 1);
         mbar_init(&accempty, 256);
         mbar_init(&mma_done, 1);
+        for (int s = 0; s < kTileRing; ++s) {
+            mbar_init(&tfull[s], 1);
+            mbar_init(&tempty[s], 2 + (kColWarp - 2));    // column producer, MMA, one per drain warp
+        }
         s_fail = 0;
         tcx::mbar_fence_init();
         tcx::prefetch_tmap(&low_rows);
@@ -798,8 +822,19 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
         // product t, K block c), in that nesting, the 8 digit slices of the
         // row tile, one per slot, in the MMA's digit order
         uint32_t na = 0;                                              // row slices issued
-        for (int64_t it = 0; it < my_tiles && !s_fail; ++it) {
-            const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
+        for (uint32_t it = 0; !s_fail; ++it) {
+            // take the next tile and pass it on (-1: none left)
+            const uint32_t slot = it % kTileRing;
+            if (it >= (uint32_t)kTileRing && !mbar_wait(&tempty[slot], ((it / kTileRing) - 1) & 1, polls)) {
+                s_fail = 1;
+                break;
+            }
+            int64_t tile = (int64_t)atomicAdd(a.next_tile, 1ull);
+            if (tile >= a.tiles) tile = -1;
+            s_tile[slot] = tile;
+            mbar_arrive(&tfull[slot]);
+            if (tile < 0) break;
+            const TileInfo ti = tile_info(a, tile);
             const CUtensorMap* rmap = ti.rl ? &low_rows : &high_rows;
             for (int t = 0; t < 3 && !s_fail; ++t) {
                 for (int c = 0; c < nkb && !s_fail; ++c) {
@@ -824,8 +859,11 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
         // slices of the column tile packed one after the other in a set
         // (double-buffered), so a slow set never holds up the row slices
         uint32_t q = 0;                                               // column sets issued
-        for (int64_t it = 0; it < my_tiles && !s_fail; ++it) {
-            const TileInfo tb = tile_info(a, blockIdx.x + it * gridDim.x);
+        for (uint32_t it = 0; !s_fail; ++it) {
+            const int64_t tile = take_tile(tfull, tempty, s_tile, it, polls, false);
+            if (tile == -2) s_fail = 1;
+            if (tile < 0) break;
+            const TileInfo tb = tile_info(a, tile);
             for (int t = 0; t < 3 && !s_fail; ++t) {
                 for (int c = 0; c < nkb && !s_fail; ++c, ++q) {
                     const uint32_t bs = q % kBSets;
@@ -855,8 +893,11 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
     } else if (tid == 32) {
         // ---------------- MMA issuer
         uint32_t na = 0, q = 0, g = 0;                               // slices, chunks, passes
-        for (int64_t it = 0; it < my_tiles && !s_fail; ++it) {
-            const int tn = tile_info(a, blockIdx.x + it * gridDim.x).tn;
+        for (uint32_t it = 0; !s_fail; ++it) {
+            const int64_t tile = take_tile(tfull, tempty, s_tile, it, polls, false);
+            if (tile == -2) s_fail = 2;
+            if (tile < 0) break;
+            const int tn = tile_info(a, tile).tn;
             const int per = min(kDigits, 256 / tn);                      // column slices per MMA
             for (int t = 0; t < 3 && !s_fail; ++t, ++g) {
                 if (g > 0 && !mbar_wait(&accempty, (g - 1) & 1, polls)) {
@@ -913,8 +954,11 @@ tc_product_kernel(const __grid_constant__ CUtensorMap low_rows, const __grid_con
         const int q4 = warp & 3;
         const int cbase = warp < 6 ? 0 : 16;
         bool alive = true;
-        for (int64_t it = 0; it < my_tiles && alive; ++it) {
-            const TileInfo ti = tile_info(a, blockIdx.x + it * gridDim.x);
+        for (uint32_t it = 0; alive; ++it) {
+            const int64_t tile = take_tile(tfull, tempty, s_tile, it, polls, true);
+            if (tile == -2 && lane == 0) s_fail = 3;
+            if (tile < 0) break;
+            const TileInfo ti = tile_info(a, tile);
             const int kb = ti.kb, tn = ti.tn;
             const bool rl = ti.rl;
             const bool ext = a.kind[kb] != 0;
@@ -1608,6 +1652,7 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     a.amp = in.amp;
     a.prob = in.prob;
     a.error = in.error;
+    a.next_tile = in.next_tile;
     a.max_polls = wait_limit(kMaxPolls);
     a.tiles = tiles;
     int sms = 0;

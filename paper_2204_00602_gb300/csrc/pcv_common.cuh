@@ -248,6 +248,7 @@ struct TcInputs {
     double* prob;                                 // or null
     void* ws;                                     // tc_workspace bytes
     int* error;                                   // device flag, or null
+    unsigned long long* next_tile;                // the products' tile counter, zero at the call's start
     int64_t lo, hi;                               // outputs [lo, hi), stored at [o - lo]
 };
 int tc_pad_k(int K);
