@@ -190,10 +190,12 @@ int pcv_amplitudes_batched(const pcv_batch_desc* descs, int n_circ, int64_t tota
 int pcv_amplitudes_batched_ex(const pcv_batch_desc* descs, int n_circ, int64_t total_outputs, int algo,
                               void* workspace, int64_t workspace_bytes, void* stream);
 
-/* Workspace bytes of pcv_distribution_ex with PCV_ALGO_FACTOR_TC (1 <= n <= 10):
- * the FP64 factor tables of all sign vectors, the digit tensors (48 bytes
- * per table entry and sign vector), two FP64 products per output, and the
- * vectors and per-row data of the single-entry blocks. */
+/* Workspace bytes of pcv_distribution_ex with PCV_ALGO_FACTOR_TC (1 <= n <= 10;
+ * e = min(3, n/2)): per side the digit tensor (48 bytes per entry and sign
+ * vector) of the table levels e+1 .. n-e-1, of the level n-e entries and of
+ * the e-photon column vectors, their exponents, the FP64 entries of the
+ * parent levels 1 .. n-e-1, the entry and seam data of the level n-e entries
+ * and column vectors, and two FP64 values per output. */
 int64_t pcv_distribution_tc_workspace(int m, int n);
 
 /* Workspace bytes pcv_distribution needs for m modes and n photons with the
@@ -289,11 +291,14 @@ int pcv_distribution_slos(const pcv_c64* U, int B, int m, const uint8_t* input_o
  * each diagonal of digit pairs sums to at most 2^24, so its FP32 tensor-core
  * accumulation is exact; the diagonals are recombined in 64-bit integers and
  * rounded once to FP64 (round to nearest even) with integer operations.
- * The blocks with every photon on one side (k = 0, k = n) are products of
- * that side's level n-1 with one vector per mode, y_r(d) times the other
- * side's single entry; the output of R' + r is kept for r >= max R'.  With
- * n = 1 or m = 1 those two blocks run in FP64.  Results agree with the FP64
- * path to double precision.  The paper has no such variant (its back-ends
+ * With k photons on the low side (modes [0, h)) and e = min(3, n/2), the
+ * outputs with k = e+1 .. n-e-1 are products of table levels k and n-k; an
+ * output with at least n-e photons on one side is R ++ E, R its n-e photons
+ * of that side nearest the other side (a level n-e entry) and E the other e
+ * (an e-multiset over all modes, v_E = prod y_x / sqrt(prod mult!)), so no
+ * table level above n-e is built.  With n = 1 or m = 1 the outputs with
+ * every photon on one side run in FP64.  Results agree with the FP64 path
+ * to double precision.  The paper has no such variant (its back-ends
  * run on CPUs).  n <= 10 (2^{n-1} <= 512 keeps each diagonal sum below 2^24). */
 int pcv_distribution_ex(const pcv_c64* U, int m, const uint8_t* input_occ,
                         double* prob, pcv_c64* amp, int algo, int param,
@@ -562,9 +567,8 @@ int pcv_fp64_probe(double* out, int blocks, int threads, int iters, void* stream
  * record CUDA events on the launching stream around each stage of a call
  * (stage 0: factorised-distribution tables, with PCV_ALGO_FACTOR_TC their
  * digits too, 1: factorised-distribution products, 2: plain Glynn kernels,
- * 3: PCV_ALGO_FACTOR_TC's per-mode vectors of the single-entry columns and
- * their digits, 4: the FP64 single-entry blocks of PCV_ALGO_FACTOR_TC,
- * n = 1 or m = 1 only).  pcv_profile_read waits for the recorded
+ * 3: not recorded any more (kept so that stage numbers stay), 4: the FP64
+ * single-entry blocks of PCV_ALGO_FACTOR_TC, n = 1 or m = 1 only).  pcv_profile_read waits for the recorded
  * events, writes the accumulated milliseconds and call counts of the first
  * `nstages` stages to ms[] and calls[] (host) and resets them.
  * pcv_launch_count returns the number of kernels the library has launched
