@@ -1509,27 +1509,52 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
                 hcol[(size_t)i] = seam_of(hc_tab.mc, m, n, S.e, corder, modes);
             }
         }
-        // the shortest run length that keeps the runs within kMaxSideBlocks
-        int64_t thr = TBM;
-        for (;; thr *= 2) {
-            int runs = 0;
-            int64_t r = 0;
-            for (int g = 0; g < w; ++g) {
-                r += gsize(g);
-                if (r >= thr || g + 1 == w) {
-                    ++runs;
-                    r = 0;
+        const int64_t c0 = (side == 1 && n == 2 * S.e) ? msets_tc(h, S.e) : 0;   // all-low E: the low side's
+        // The runs of groups: fewest tiles over at most kMaxSideBlocks runs
+        // (f[i][j]: groups i.. in j runs; a run's tiles follow from its
+        // entries and its widest group's vectors, in this side's orientation).
+        auto run_tiles = [&](int64_t entries, int64_t vectors) {
+            const int64_t rows = side == 0 ? vectors : entries, cols = side == 0 ? entries : vectors;
+            const int64_t tn = width(cols);
+            return ((rows + TBM - 1) / TBM) * ((cols + tn - 1) / tn);
+        };
+        const int64_t kInf = INT64_MAX / 4;
+        const int J = kMaxSideBlocks;
+        std::vector<int64_t> f((size_t)(w + 1) * (J + 1), kInf);
+        std::vector<int> cut((size_t)(w + 1) * (J + 1), -1);
+        f[(size_t)w * (J + 1)] = 0;
+        for (int i = w - 1; i >= 0; --i) {
+            int64_t ent = 0, vec = 0;
+            for (int b = i; b < w; ++b) {
+                ent += gsize(b);
+                vec = std::max(vec, gcols(b));
+                const int64_t t = run_tiles(ent, vec - c0);
+                for (int j = 1; j <= J; ++j) {
+                    const int64_t rest = f[(size_t)(b + 1) * (J + 1) + j - 1];
+                    if (rest < kInf && t + rest < f[(size_t)i * (J + 1) + j]) {
+                        f[(size_t)i * (J + 1) + j] = t + rest;
+                        cut[(size_t)i * (J + 1) + j] = b;
+                    }
                 }
             }
-            if (runs <= kMaxSideBlocks) break;
         }
-        const int64_t c0 = (side == 1 && n == 2 * S.e) ? msets_tc(h, S.e) : 0;   // all-low E: the low side's
+        int jbest = 1;
+        for (int j = 1; j <= J; ++j)
+            if (f[(size_t)j] < f[(size_t)jbest]) jbest = j;
+        std::vector<int> run_end;                                    // last group of each run
+        for (int i = 0, j = jbest; i < w; --j) {
+            const int b = cut[(size_t)i * (J + 1) + j];
+            run_end.push_back(b);
+            i = b + 1;
+        }
         int64_t rb = 0, r = 0, cend = 0;
         int g0 = 0;
+        size_t ri = 0;
         for (int g = 0; g < w; ++g) {
             r += gsize(g);
             cend = std::max(cend, gcols(g));
-            if (r - rb < thr && g + 1 < w) continue;
+            if (g != run_end[ri]) continue;
+            ++ri;
             // entries [ea, ez) (from rb) and vectors [va, vz) of the block
             int64_t ea = 0, ez = r - rb, va = c0, vz = cend;
             if (!whole) {
