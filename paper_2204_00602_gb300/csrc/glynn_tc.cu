@@ -1627,6 +1627,39 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
             g0 = g + 1;
         }
     }
+    // A block whose last row tile holds at most 64 rows gives those rows to
+    // a block of the other orientation (its columns as rows, the leftover
+    // rows as one narrow column tile) when that takes fewer tiles: the
+    // leftover rows of a 286-vector group, say, take 79 tiles as a row tile
+    // and 40 as a column tile.  Whole distributions only; a part keeps its
+    // blocks as they are (the results are the same either way).
+    if (whole) {
+        const int nb0 = a.nk;
+        for (int b = 0; b < nb0 && a.nk < kMaxBlocks; ++b) {
+            const int64_t rows = a.rows[b] - a.rows0[b], cols = a.cols[b] - a.cols0[b];
+            const int64_t tail = rows % TBM;
+            if (rows < TBM || tail == 0 || tail > TBN || cols <= 0) continue;
+            const int64_t now = (cols + a.tn[b] - 1) / a.tn[b];          // tiles of the last row tile
+            if ((cols + TBM - 1) / TBM >= now) continue;
+            const int t = a.nk++;
+            a.kind[t] = a.kind[b];
+            a.rows_low[t] = a.rows_low[b] ? 0 : 1;
+            a.rows0[t] = a.cols0[b];
+            a.rows[t] = a.cols[b];
+            a.cols0[t] = a.rows[b] - tail;
+            a.cols[t] = a.rows[b];
+            a.tn[t] = width(tail);
+            a.row_off[t] = a.col_off[b];
+            a.col_off[t] = a.row_off[b];
+            a.lowoff[t] = a.lowoff[b];
+            a.rs[t] = a.cs[b];
+            a.cs[t] = a.rs[b];
+            a.ri_off[t] = a.ci_off[b];
+            a.ci_off[t] = a.ri_off[b];
+            a.cge[t] = a.cge[b] ? 0 : 1;
+            a.rows[b] -= tail;
+        }
+    }
     // blocks without tiles are dropped
     int64_t tiles = 0;
     int nb = 0;
