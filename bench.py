@@ -364,10 +364,10 @@ def run_ours(args):
         # BF16 tensor-core work: 3 real products x 36 digit pairs x 2 flops per
         # output and sign vector (useful outputs only)
         ms, calls = stages["dist_products"]
-        # every output goes through the tensor cores when n >= 2 and m >= 2 (the
-        # single-entry blocks k = 0 and k = n as products of level n-1 with one
-        # vector per mode; products whose mode is below the row's largest are
-        # computed and dropped, not counted); else those two blocks run in FP64
+        # every output goes through the tensor cores when n >= 2 and m >= 2
+        # (tile padding and the pairs of merged seam groups that are not
+        # outputs are computed but not counted); else the outputs with every
+        # photon on one side run in FP64
         h = max(1, M // 2)
         n_tc = (hi - lo) if (N_PH >= 2 and M - h >= 1) else \
             Ntot - math.comb(M - h + N_PH - 1, N_PH) - math.comb(h + N_PH - 1, N_PH)
