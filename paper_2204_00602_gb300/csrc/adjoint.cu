@@ -43,6 +43,7 @@ constexpr int kSeg = 256;                   // outputs per segment of the reduct
 constexpr int64_t kPartSteps = 1 << 13;     // Gray steps per part when a sequence is split
 constexpr int kMaxParts = 1024;
 constexpr uint16_t kBadOutput = 0xFFFF;     // rows marker of an output whose photon number differs
+constexpr int kThreadMaxN = 6;              // n up to this: one thread per output (G in registers)
 
 struct ColList32 { int c[PCV_MAX_PHOTONS]; };
 
@@ -223,6 +224,81 @@ __global__ void __launch_bounds__(kWarpsA * 32) adjoint_part_kernel(const AdjArg
     }
 }
 
+// Small n: one thread per output walks all 2^{n-1} sign vectors in Gray
+// order with the n x n Glynn sums of the minors in registers, and writes H as
+// adjoint_part_kernel does with one part.  Every lane does useful FP64 work
+// (FP64 is scarce on this part; the warp form leaves lanes idle when n is
+// small).
+template <int N>
+__global__ void __launch_bounds__(128) adjoint_thread_kernel(const AdjArgs a)
+{
+    const int64_t oc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (oc >= a.chunk) return;
+    const int b = blockIdx.y;
+    const int64_t o = a.o0 + oc;
+    const int m = a.m;
+    uint16_t rows[N];
+    double norm_s = 1.0;
+    const bool ok = decode_rows(a, o, rows, norm_s);
+    if (b == 0)
+        for (int i = 0; i < N; ++i) a.rows[oc * N + i] = ok ? rows[i] : kBadOutput;
+    double2* H = a.H + ((size_t)b * a.chunk + oc) * N * N;
+    const double2 g = ok ? a.gbar[(int64_t)b * a.count + o] : make_double2(0.0, 0.0);
+    if (g.x == 0.0 && g.y == 0.0) {
+        for (int e = 0; e < N * N; ++e) H[e] = make_double2(0.0, 0.0);
+        return;
+    }
+    const double2* U = a.U + (size_t)b * m * m;
+    double2 x[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {                         // sign vector 0: every sign +1
+        double2 sum = __ldg(U + (size_t)rows[i] * m + a.cols[0]);
+        for (int j = 1; j < N; ++j) sum = cadd(sum, __ldg(U + (size_t)rows[i] * m + a.cols[j]));
+        x[i] = sum;
+    }
+    double2 G[N][N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) G[i][j] = make_double2(0.0, 0.0);
+    uint32_t gc = 0;
+    double sg = 1.0;                                      // sigma(d)
+    const uint32_t steps = 1u << (N - 1);
+    for (uint32_t st = 0; st < steps; ++st) {
+        // w_i = sigma prod_{i' != i} x_i': prefix products, then suffixes
+        double2 pre[N];
+        pre[0] = make_double2(1.0, 0.0);
+#pragma unroll
+        for (int i = 1; i < N; ++i) pre[i] = cmul(pre[i - 1], x[i - 1]);
+        double2 sfx = make_double2(sg, 0.0);
+#pragma unroll
+        for (int i = N - 1; i >= 0; --i) {
+            const double2 w = cmul(pre[i], sfx);
+            sfx = cmul(sfx, x[i]);
+            G[i][0] = cadd(G[i][0], w);
+#pragma unroll
+            for (int j = 1; j < N; ++j) caxpy(G[i][j], ((gc >> (j - 1)) & 1u) ? -1.0 : 1.0, w);
+        }
+        if (st + 1 < steps) {                             // Gray step to the next sign vector
+            const uint32_t kk = st + 1;
+            const int bb = __ffs((int)kk) - 1;
+            const uint32_t gn = kk ^ (kk >> 1);
+            const double sd = ((gn >> bb) & 1u) ? -2.0 : 2.0;
+            const int col = a.cols[bb + 1];
+#pragma unroll
+            for (int i = 0; i < N; ++i) caxpy(x[i], sd, __ldg(U + (size_t)rows[i] * m + col));
+            gc = gn;
+            sg = -sg;
+        }
+    }
+    // H = gbar conj(c G), c = norm_S norm_T 2^{-(n-1)}
+    const double c = ldexp(norm_s * a.norm_t, -(N - 1));
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) H[i * N + j] = cmul(g, make_double2(c * G[i][j].x, -c * G[i][j].y));
+}
+
 // H of each output summed over its parts, in part order, into part 0's place
 // of a [B][chunk][n][n] array.
 __global__ void adjoint_parts_kernel(const double2* __restrict__ H, int64_t chunk, int parts, int nn, int B,
@@ -290,6 +366,15 @@ __global__ void adjoint_final_kernel(const double2* __restrict__ seg, int B, int
 }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <int N>
+cudaError_t launch_thread(const AdjArgs& a, int B, cudaStream_t s)
+{
+    dim3 grid((unsigned)((a.chunk + 127) / 128), (unsigned)B);
+    adjoint_thread_kernel<N><<<grid, 128, 0, s>>>(a);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 template <int CJ>
 cudaError_t launch_part(const AdjArgs& a, int B, cudaStream_t s)
@@ -405,7 +490,16 @@ cudaError_t launch_adjoint(const Plan& pl, const double2* U, int B, const uint8_
         const int64_t cc = std::min<int64_t>(C, count - o0);
         a.o0 = o0;
         a.chunk = cc;
-        switch (ap.cj) {
+        if (ap.parts == 1 && n <= kThreadMaxN) {
+            switch (n) {
+            case 1: e = launch_thread<1>(a, B, s); break;
+            case 2: e = launch_thread<2>(a, B, s); break;
+            case 3: e = launch_thread<3>(a, B, s); break;
+            case 4: e = launch_thread<4>(a, B, s); break;
+            case 5: e = launch_thread<5>(a, B, s); break;
+            default: e = launch_thread<6>(a, B, s); break;
+            }
+        } else switch (ap.cj) {
         case 1: e = launch_part<1>(a, B, s); break;
         case 2: e = launch_part<2>(a, B, s); break;
         case 3: case 4: e = launch_part<4>(a, B, s); break;
