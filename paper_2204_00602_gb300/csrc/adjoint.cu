@@ -12,6 +12,9 @@
 //     dL/dU[k][l] = sum_S gbar_S conj(norm_S sum_{r_i = k, c_j = l} G_S[i][j]).
 //
 // Kernels:
+//   adjoint_thread_kernel  n <= 6: one thread per (output, batch entry) walks
+//                          the whole Gray sequence with G in registers and
+//                          writes H (below);
 //   adjoint_part_kernel    one warp per (output, part of its Gray sequence,
 //                          batch entry).  Each round every lane takes one sign
 //                          vector (lane l walks its own run of the part),
@@ -22,7 +25,7 @@
 //                          lane order.  The scaled partial matrix
 //                          H = gbar conj(c G) goes to the workspace.
 //   adjoint_parts_kernel   (several parts per output) their H added in part order;
-//   adjoint_segment_kernel per (batch entry, segment of 256 outputs, mode k,
+//   adjoint_segment_kernel per (batch entry, segment of 64 outputs, mode k,
 //                          input mode l): the H entries of (k, l) summed over
 //                          the segment's outputs in index order;
 //   adjoint_final_kernel   per (batch entry, k, l): the segments added in
@@ -39,7 +42,7 @@ namespace pcv {
 namespace {
 
 constexpr int kWarpsA = 4;                  // warps per block of adjoint_part_kernel
-constexpr int kSeg = 256;                   // outputs per segment of the reduction
+constexpr int kSeg = 64;                    // outputs per segment of the reduction
 constexpr int64_t kPartSteps = 1 << 13;     // Gray steps per part when a sequence is split
 constexpr int kMaxParts = 1024;
 constexpr uint16_t kBadOutput = 0xFFFF;     // rows marker of an output whose photon number differs
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(kWarpsA * 32) adjoint_part_kernel(const AdjArg
 // order with the n x n Glynn sums of the minors in registers, and writes H as
 // adjoint_part_kernel does with one part.  Every lane does useful FP64 work
 // (FP64 is scarce on this part; the warp form leaves lanes idle when n is
-// small).
+// small): measured at n = 6, 2.4x faster over 792K outputs and 1.3x over 32K.
 template <int N>
 __global__ void __launch_bounds__(128) adjoint_thread_kernel(const AdjArgs a)
 {
