@@ -254,6 +254,30 @@ int pcv_distribution_range(const pcv_c64* U, int m, const uint8_t* input_occ, in
  * n + 1 entries (written).  Errors as pcv_distribution_range. */
 int pcv_distribution_range_plan(int m, int n, int64_t begin, int64_t end, int64_t* pa, int64_t* pb);
 
+/* Host-only view of the output blocks PCV_ALGO_FACTOR_TC's products run for
+ * the outputs [begin, end) (end < 0: all), for inspection and tests.  With
+ * h = max(1, m/2) and e = min(3, n/2), each side s (0: modes [0, h), 1:
+ * [h, m)) has a digit tensor whose entries are, in order, the table levels
+ * e+1 .. n-e-1 (each lexicographic), the level n-e entries (side 0 grouped
+ * by largest mode ascending, side 1 by smallest mode ascending, each group
+ * lexicographic) and the e-photon vectors over all m modes (side 0's tensor
+ * grouped by largest mode ascending, side 1's by smallest mode descending).
+ * out (host int64): 48 header values, then 16 per block.  Header: e, n-e, h,
+ * blocks, tiles, vectors per tensor, level-(n-e) offsets [2], counts [2],
+ * vector offsets [2], entries per tensor [2], then at 16 + 16 s + k the offset
+ * of level k in side s's tensor (-1: not in it).  Block: kind (0: level
+ * product, 1: extension block), rows_low (1: rows from side 0's tensor,
+ * columns from side 1's), tile width, rows [rows0, rows) and columns [cols0,
+ * cols) of the block, entry offsets of row 0 and column 0, lowoff, seam list
+ * of the rows and of the columns (0, 1: level n-e of side 0, 1; 2, 3: the
+ * vectors in side 0's, 1's tensor), cge (1: a pair is an output when the
+ * column's seam mode >= the row's; 0: <=), seam index of row 0 and of column
+ * 0, first tile.  needed (host, or NULL) receives the values out must hold;
+ * out may be NULL to ask for it.  PCV_EINVAL outside 2 <= n <= 10, m >= 2,
+ * or for a bad range or a short out.  No counterpart in the paper. */
+int pcv_distribution_tc_blocks(int m, int n, int64_t begin, int64_t end, int64_t* out, int64_t out_len,
+                               int64_t* needed);
+
 /* Full distributions of B unitaries with the same input state (the
  * factorised algorithm of pcv_distribution, all B in the same launches).
  *   U     device, B*m*m pcv_c64 (entry b at U + b*m*m)

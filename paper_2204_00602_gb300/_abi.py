@@ -59,6 +59,7 @@ SIGNATURES = {
     "pcv_distribution_ex": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _vp, _i64, _vp]),
     "pcv_distribution_range": (_i, [_vp, _i, _vp, _i64, _i64, _vp, _vp, _vp, _i64, _vp]),
     "pcv_distribution_range_plan": (_i, [_i, _i, _i64, _i64, _vp, _vp]),
+    "pcv_distribution_tc_blocks": (_i, [_i, _i, _i64, _i64, _vp, _i64, _vp]),
     "pcv_distribution_batched_workspace": (_i64, [_i, _i, _i]),
     "pcv_distribution_batched": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _i64, _vp]),
     "pcv_distribution_slos_workspace": (_i64, [_i, _i, _i]),
@@ -212,6 +213,26 @@ def pcv_distribution_range_plan(m, n, begin, end):
     pb = np.zeros(n + 1, dtype=np.int64)
     _call("pcv_distribution_range_plan", m, n, begin, end, pa.ctypes.data, pb.ctypes.data)
     return list(zip(pa.tolist(), pb.tolist()))
+
+
+TC_BLOCK_FIELDS = ("kind", "rows_low", "tn", "rows0", "rows", "cols0", "cols", "row_off", "col_off", "lowoff",
+                   "rs", "cs", "cge", "ri_off", "ci_off", "tile0")
+
+
+def pcv_distribution_tc_blocks(m, n, begin=0, end=-1):
+    """(header dict, [block dicts]): the output blocks of the tensor-core
+    products for the outputs [begin, end) (host only; layout in include/pcv.h)."""
+    import numpy as np
+    need = ctypes.c_int64(0)
+    _call("pcv_distribution_tc_blocks", m, n, begin, end, None, 0, ctypes.addressof(need))
+    out = np.zeros(need.value, dtype=np.int64)
+    _call("pcv_distribution_tc_blocks", m, n, begin, end, out.ctypes.data, out.size, None)
+    h = out[:48].tolist()
+    head = {"e": h[0], "L": h[1], "h": h[2], "blocks": h[3], "tiles": h[4], "ncols": h[5],
+            "rows_off": h[6:8], "nrows": h[8:10], "cols_off": h[10:12], "wdig": h[12:14],
+            "lev": [h[16:32], h[32:48]]}
+    blocks = [dict(zip(TC_BLOCK_FIELDS, out[48 + 16 * b: 64 + 16 * b].tolist())) for b in range(h[3])]
+    return head, blocks
 
 
 def pcv_distribution(U, m, input_occ, prob, amp, workspace, workspace_bytes, stream):

@@ -1416,38 +1416,21 @@ cudaError_t launch_tc_tables(const TcInputs& in, cudaStream_t s)
     return launch_levels(b, s);
 }
 
-cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
+namespace {
+
+// The output blocks of one call, the outputs [lo, hi) of `total`: a's
+// per-block fields, nk, tile0 and tiles (host only; lowoff: offset of each
+// low-side level in lowbase).
+cudaError_t plan_tc_blocks(const TcShape& S, int64_t total, const int64_t* lowoff, int64_t lo, int64_t hi,
+                           TcProdArgs& a)
 {
-    cudaError_t e = get_enc();
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64 && !g_tc_attr[dev]) {
-        e = cudaFuncSetAttribute(tc_product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-        if (e != cudaSuccess) return e;
-        g_tc_attr[dev] = true;
-    }
-    const int K = in.K, n = in.n, m = in.m, h = in.h;
-    if (n < 2 || m - h < 1) return cudaErrorInvalidValue;
-    const TcShape S = tc_shape(m, n, h, K);
-    const TcLayout L = tc_layout(S, in.total);
-    const TcBuffers B = tc_buffers(L, in.ws);
-    if (S.wdig[0] + TBM > INT32_MAX || S.wdig[1] + TBM > INT32_MAX) return cudaErrorInvalidConfiguration;
-    stage_begin(kStageGemm, s);
-    CUtensorMap lr, lc, hr, hc, lc16, hc16;
-    if ((e = make_digit_map(&lr, B.dig[0], S.wdig[0], S.Kp, TBM)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&lc, B.dig[0], S.wdig[0], S.Kp, TBN)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&hr, B.dig[1], S.wdig[1], S.Kp, TBM)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&hc, B.dig[1], S.wdig[1], S.Kp, TBN)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&lc16, B.dig[0], S.wdig[0], S.Kp, kBSub)) != cudaSuccess) return e;
-    if ((e = make_digit_map(&hc16, B.dig[1], S.wdig[1], S.Kp, kBSub)) != cudaSuccess) return e;
-    TcProdArgs a;
+    const int m = S.m, n = S.n, h = S.h;
     a.nk = 0;
     a.kblocks = S.Kp / TBK;
     auto width = [](int64_t cols) { return cols >= TBN ? TBN : (int)((cols + 15) / 16) * 16; };
     // outputs [lo, hi): per k the ranks of the P whose outputs meet the range
     PRanges pr;
-    p_ranges(m, n, h, in.lo, in.hi, &pr);
+    p_ranges(m, n, h, lo, hi, &pr);
     // level products k = e+1 .. n-e-1
     for (int k = S.e + 1; k <= n - S.e - 1; ++k) {
         const int64_t M = msets_tc(h, k), N = msets_tc(m - h, n - k);
@@ -1471,7 +1454,7 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
         a.cols[b] = !any ? a.cols0[b] : (rl ? cols : pr.pb[k]);
         a.row_off[b] = rl ? S.lev[0][k] : S.lev[1][n - k];
         a.col_off[b] = rl ? S.lev[1][n - k] : S.lev[0][k];
-        a.lowoff[b] = in.lowoff[k];
+        a.lowoff[b] = lowoff[k];
         a.rs[b] = a.cs[b] = a.cge[b] = 0;
         a.ri_off[b] = a.ci_off[b] = 0;
     }
@@ -1485,7 +1468,7 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     // those with an output in range (seam data on the host: a group's
     // entries have increasing bases, so each vector's entries in range are
     // found by bisection).
-    const bool whole = in.lo <= 0 && in.hi >= in.total;
+    const bool whole = lo <= 0 && hi >= total;
     std::vector<SeamInfo> hrow, hcol;
     HostCounts hc_tab(whole ? 0 : m, whole ? 0 : n);
     for (int side = 0; side < 2; ++side) {
@@ -1572,7 +1555,7 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
                             }
                             return x;
                         };
-                        const int64_t x0 = first_at_least(in.lo - cb), x1 = first_at_least(in.hi - cb);
+                        const int64_t x0 = first_at_least(lo - cb), x1 = first_at_least(hi - cb);
                         if (x0 >= x1) continue;
                         ra = std::min(ra, x0);
                         rz = std::max(rz, x1);
@@ -1690,6 +1673,40 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     }
     a.nk = nb;
     a.tile0[a.nk] = tiles;
+    a.tiles = tiles;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
+{
+    cudaError_t e = get_enc();
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !g_tc_attr[dev]) {
+        e = cudaFuncSetAttribute(tc_product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        g_tc_attr[dev] = true;
+    }
+    const int K = in.K, n = in.n, m = in.m, h = in.h;
+    if (n < 2 || m - h < 1) return cudaErrorInvalidValue;
+    const TcShape S = tc_shape(m, n, h, K);
+    const TcLayout L = tc_layout(S, in.total);
+    const TcBuffers B = tc_buffers(L, in.ws);
+    if (S.wdig[0] + TBM > INT32_MAX || S.wdig[1] + TBM > INT32_MAX) return cudaErrorInvalidConfiguration;
+    stage_begin(kStageGemm, s);
+    CUtensorMap lr, lc, hr, hc, lc16, hc16;
+    if ((e = make_digit_map(&lr, B.dig[0], S.wdig[0], S.Kp, TBM)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&lc, B.dig[0], S.wdig[0], S.Kp, TBN)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&hr, B.dig[1], S.wdig[1], S.Kp, TBM)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&hc, B.dig[1], S.wdig[1], S.Kp, TBN)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&lc16, B.dig[0], S.wdig[0], S.Kp, kBSub)) != cudaSuccess) return e;
+    if ((e = make_digit_map(&hc16, B.dig[1], S.wdig[1], S.Kp, kBSub)) != cudaSuccess) return e;
+    TcProdArgs a;
+    if ((e = plan_tc_blocks(S, in.total, in.lowoff, in.lo, in.hi, a)) != cudaSuccess) return e;
+    const int64_t tiles = a.tiles;
     if (tiles == 0) {
         stage_end(kStageGemm, s);
         return cudaSuccess;
@@ -1720,6 +1737,48 @@ cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s)
     note_launches(1);
     stage_end(kStageGemm, s);
     return cudaGetLastError();
+}
+
+// The products' output blocks for m modes, n photons and the outputs [lo,
+// hi), written to out (host only): kTcPlanHeader values describing the digit
+// tensors, then kTcPlanBlock values per block.  Returns the values needed (out
+// is written only when cap holds them), or -1 if the plan fails.
+int64_t tc_block_list(int m, int n, int64_t lo, int64_t hi, int64_t* out, int64_t cap)
+{
+    const int h = std::max(1, m / 2);
+    int64_t lowoff[PCV_MAX_PHOTONS + 2];
+    int64_t acc = 0;
+    for (int k = 0; k < PCV_MAX_PHOTONS + 2; ++k) {
+        lowoff[k] = acc;
+        if (k <= n) acc += msets_tc(h, k);
+    }
+    const TcShape S = tc_shape(m, n, h, 1 << (n - 1));
+    TcProdArgs a;
+    if (plan_tc_blocks(S, msets_tc(m, n), lowoff, lo, hi, a) != cudaSuccess) return -1;
+    const int64_t need = kTcPlanHeader + (int64_t)a.nk * kTcPlanBlock;
+    if (!out || cap < need) return need;
+    for (int64_t i = 0; i < kTcPlanHeader; ++i) out[i] = -1;
+    out[0] = S.e;
+    out[1] = S.L;
+    out[2] = h;
+    out[3] = a.nk;
+    out[4] = a.tiles;
+    out[5] = S.ncols;
+    for (int sd = 0; sd < 2; ++sd) {
+        out[6 + sd] = S.rows_off[sd];
+        out[8 + sd] = S.nrows[sd];
+        out[10 + sd] = S.cols_off[sd];
+        out[12 + sd] = S.wdig[sd];
+        for (int k = 0; k <= n && k <= 15; ++k) out[16 + 16 * sd + k] = S.lev[sd][k];
+    }
+    for (int b = 0; b < a.nk; ++b) {
+        int64_t* o = out + kTcPlanHeader + (int64_t)b * kTcPlanBlock;
+        const int64_t v[kTcPlanBlock] = {a.kind[b], a.rows_low[b], a.tn[b], a.rows0[b], a.rows[b], a.cols0[b],
+                                         a.cols[b], a.row_off[b], a.col_off[b], a.lowoff[b], a.rs[b], a.cs[b],
+                                         a.cge[b], a.ri_off[b], a.ci_off[b], a.tile0[b]};
+        for (int i = 0; i < kTcPlanBlock; ++i) o[i] = v[i];
+    }
+    return need;
 }
 
 }  // namespace pcv

@@ -795,6 +795,23 @@ int pcv_distribution_range(const pcv_c64* U, int m, const uint8_t* input_occ, in
     return distribution_factor(U, 1, m, input_occ, begin, end, prob, amp, workspace, workspace_bytes, stream);
 }
 
+int pcv_distribution_tc_blocks(int m, int n, int64_t begin, int64_t end, int64_t* out, int64_t out_len,
+                               int64_t* needed)
+{
+    if (m < 2 || m > PCV_MAX_MODES || n < 2 || n > 10) return fail(PCV_EINVAL, "m %d, n %d outside the tensor-core plan", m, n);
+    const int64_t N = msets(m, n);
+    if (N < 0) return fail(PCV_ERANGE, "output space too large");
+    if (end < 0) end = N;
+    if (begin < 0 || begin > end || end > N) return fail(PCV_EINVAL, "range [%lld, %lld) outside [0, %lld)",
+                                                         (long long)begin, (long long)end, (long long)N);
+    const int64_t need = pcv::tc_block_list(m, n, begin, end, out, out_len);
+    if (need < 0) return fail(PCV_ERANGE, "the plan needs more blocks than the products kernel takes");
+    if (needed) *needed = need;
+    if (out && out_len < need) return fail(PCV_EINVAL, "out holds %lld values, %lld needed", (long long)out_len,
+                                           (long long)need);
+    return PCV_OK;
+}
+
 // ------------------------------------------------------------- adjoint
 
 // Checks shared by the backward calls; fills the plan for `count` outputs.

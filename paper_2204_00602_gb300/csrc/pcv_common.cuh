@@ -254,6 +254,8 @@ struct TcInputs {
 int tc_pad_k(int K);
 int64_t tc_workspace(int m, int n, int h, int K, int64_t total);
 cudaError_t launch_tc_tables(const TcInputs& in, cudaStream_t s);
+constexpr int kTcPlanHeader = 48, kTcPlanBlock = 16;   // tc_block_list's record sizes
+int64_t tc_block_list(int m, int n, int64_t lo, int64_t hi, int64_t* out, int64_t cap);
 cudaError_t launch_tc_products(const TcInputs& in, cudaStream_t s);
 cudaError_t launch_glynn_dist(const Plan& p, const DistPlan& dp, const double2* U,
                               double* prob, double2* amp, void* ws, cudaStream_t s);
