@@ -135,3 +135,21 @@ def test_bench_workload_layout(pcv):
     assert [head["lev"][0][k] for k in range(4, 7)] == [0, 715, 715 + 2002]
     useful = math.comb(29, 10) / (TBM * 64)
     assert useful <= head["tiles"] <= 1.14 * useful
+
+
+def test_range_split_tile_counts_at_bench_size(pcv):
+    """m=20, n=10 split into P equal ranges: the level blocks keep close to
+    their share, the extension blocks run 1.6x / 2.7x / 5.0x the whole call's
+    tiles in total at P = 2 / 4 / 8 (the high side's e-photon vectors are in
+    max-grouped order, so a range's lexicographic run of them is scattered)."""
+    N = math.comb(29, 10)
+
+    def tiles(blocks, kind):
+        return sum(-(-(b["rows"] - b["rows0"]) // TBM) * -(-(b["cols"] - b["cols0"]) // b["tn"])
+                   for b in blocks if b["kind"] == kind)
+
+    _, whole = pcv.abi.pcv_distribution_tc_blocks(20, 10)
+    for P, lev_max, ext_ratio in ((2, 1.01, 1.60), (4, 1.09, 2.74), (8, 1.16, 5.02)):
+        parts = [pcv.abi.pcv_distribution_tc_blocks(20, 10, N * r // P, N * (r + 1) // P)[1] for r in range(P)]
+        assert sum(tiles(b, 0) for b in parts) <= lev_max * tiles(whole, 0)
+        assert sum(tiles(b, 1) for b in parts) == pytest.approx(ext_ratio * tiles(whole, 1), rel=0.01)
