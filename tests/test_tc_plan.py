@@ -153,3 +153,21 @@ def test_range_split_tile_counts_at_bench_size(pcv):
         parts = [pcv.abi.pcv_distribution_tc_blocks(20, 10, N * r // P, N * (r + 1) // P)[1] for r in range(P)]
         assert sum(tiles(b, 0) for b in parts) <= lev_max * tiles(whole, 0)
         assert sum(tiles(b, 1) for b in parts) == pytest.approx(ext_ratio * tiles(whole, 1), rel=0.01)
+
+
+def test_every_output_once_in_seeded_random_ranges(pcv):
+    """Seeded random sizes (n = 2 .. 10, at most 30,000 outputs) and random
+    ranges, including empty and one-output ranges."""
+    import random
+    rng = random.Random(2204)
+    cases = 0
+    while cases < 12:
+        n = rng.randint(2, 10)
+        m = rng.randint(2, 14)
+        N = msets(m, n)
+        if N > 30_000:
+            continue
+        a, b = sorted(rng.randrange(N + 1) for _ in range(2))
+        for lo, hi in ((a, b), (a, a), (a, min(N, a + 1))):
+            check(pcv, m, n, lo, hi)
+        cases += 1
