@@ -273,3 +273,26 @@ def test_range_plan_against_enumeration(lib, m, n):
                 assert (a, b) == tuple(want[k]), (begin, end, k, got[k], want[k])
     with pytest.raises(_abi.PcvError):
         _abi.pcv_distribution_range_plan(m, n, 0, N + 1)
+
+
+def test_tc_block_view_errors(lib):
+    # host-only: sizes outside the tensor-core plan, a bad range and a short
+    # output array are argument errors; end < 0 means the whole space
+    import ctypes
+    from paper_2204_00602_gb300 import _abi
+    for m, n in ((1, 4), (6, 1), (6, 11), (1025, 3)):
+        with pytest.raises(_abi.PcvError) as e:
+            _abi.pcv_distribution_tc_blocks(m, n)
+        assert e.value.code == _abi.PCV_EINVAL
+    N = _abi.pcv_num_outputs(7, 4)
+    for begin, end in ((-1, 5), (6, 5), (0, N + 1)):
+        with pytest.raises(_abi.PcvError) as e:
+            _abi.pcv_distribution_tc_blocks(7, 4, begin, end)
+        assert e.value.code == _abi.PCV_EINVAL
+    f = _abi._lib.pcv_distribution_tc_blocks          # argument types set by the binding
+    need = ctypes.c_int64(0)
+    assert f(7, 4, 0, -1, None, 0, ctypes.addressof(need)) == 0
+    out = (ctypes.c_int64 * need.value)()
+    assert f(7, 4, 0, -1, ctypes.addressof(out), need.value - 1, None) == _abi.PCV_EINVAL
+    assert f(7, 4, 0, N, ctypes.addressof(out), need.value, None) == 0
+    assert out[3] >= 1 and need.value - 48 == 16 * out[3]
