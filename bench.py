@@ -15,7 +15,9 @@ Prints one JSON line (rank 0).  `value` is amplitudes/s over all ranks with
 inputs resident in HBM; `e2e` is the same metric through the public API with
 host buffers (pinned H2D of U, D2H of probabilities and amplitudes inside the
 timed region).  Multi-GPU (torchrun) runs independent unitaries per rank
-(weak scaling, no collective on the data path).
+(weak scaling), or with --shard one distribution split into contiguous output
+ranges, one per rank (pcv_distribution_range, strong scaling); neither has a
+collective on the data path.
 """
 from __future__ import annotations
 
@@ -73,7 +75,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=250,
-                    help="timed steps (250 x ~4 ms: about a second, long enough for several clock samples)")
+                    help="timed steps (250 x ~2.4 ms: about a second with the copies, long enough for several clock samples)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="auto", choices=["auto", "factor", "factor_tc", "group", "slos"],
