@@ -411,6 +411,13 @@ def test_tvd_and_kl_basics():
     assert oracle.tvd(p, p) == 0 and 0 < oracle.tvd(p, q) <= 1
     assert abs(oracle.tvd(np.eye(2)[0], np.eye(2)[1]) - 1.0) < 1e-15
     assert abs(oracle.kl(p, p)) < 1e-15 and oracle.kl(q, p) > 0
+    # worked by hand: KL(q || p) = sum q log(q / p), the first argument the
+    # target.  q = (1/2, 1/2), p = (1/4, 3/4): 1/2 log 2 + 1/2 log(2/3) = 1/2 log(4/3);
+    # an outcome with q = 0 adds nothing, one with p = 0 < q makes it infinite
+    assert abs(oracle.kl([0.5, 0.5], [0.25, 0.75]) - 0.5 * math.log(4 / 3)) < 1e-15
+    assert abs(oracle.kl([0.5, 0.5, 0.0], [0.25, 0.5, 0.25]) - 0.5 * math.log(2)) < 1e-15
+    with np.errstate(divide="ignore"):
+        assert oracle.kl([0.5, 0.5], [1.0, 0.0]) == math.inf
 
 
 # ------------------------------------------------ surrogate MLP reference
@@ -422,6 +429,15 @@ def test_mlp_oracle_bf16_rounding_matches_torch():
     x = np.random.default_rng(3).standard_normal(10000) * np.logspace(-30, 30, 10000)
     want = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(mlp.bf16(x), want)
+    # exact ties (the dropped 16 bits are 0x8000) go to the even neighbour:
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 and rounds down to 1;
+    # 1 + 3 * 2^-8 lies halfway between 1 + 2^-7 and 1 + 2^-6 and rounds up
+    ties = np.array([0x3F808000, 0x3F818000, 0xBF808000, 0xBF818000, 0x00008000, 0x00018000], np.uint32)
+    tv = ties.view(np.float32).astype(np.float64)
+    even = np.array([1.0, 1 + 2 ** -6, -1.0, -(1 + 2 ** -6), 0.0, 2.0 ** -132], np.float64)
+    assert np.array_equal(mlp.bf16(tv), even)
+    assert np.array_equal(mlp.bf16(tv), torch.from_numpy(tv.astype(np.float32)).to(torch.bfloat16)
+                          .to(torch.float64).numpy())
     bits = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
     assert np.array_equal(mlp.bf16_bits_to_f64(bits), want)
 
@@ -469,3 +485,49 @@ def test_mlp_oracle_forward_backward_by_finite_differences():
         for j in range(8):
             E = np.zeros_like(Ws[0]); E[i, j] = h
             assert abs((f(Ws[0] + E) - f(Ws[0] - E)) / (2 * h) - gW0[i, j]) < 1e-7
+
+
+def test_mlp_oracle_mse_gradient_by_finite_differences():
+    from oracle import mlp
+    g = np.random.default_rng(6)
+    pred, target = g.standard_normal((4, 5)), g.standard_normal((4, 5))
+    loss, grad = mlp.mse(pred, target)
+    assert abs(loss - float(np.mean((pred - target) ** 2))) < 1e-15
+    h = 1e-6
+    for i in range(4):
+        for j in range(5):
+            E = np.zeros_like(pred); E[i, j] = h
+            fd = (mlp.mse(pred + E, target)[0] - mlp.mse(pred - E, target)[0]) / (2 * h)
+            assert abs(fd - grad[i, j]) < 1e-9
+
+
+def test_mlp_oracle_features_invariants():
+    # rows [sin phi, cos phi, 1, 0 ...] in bf16: sin^2 + cos^2 = 1 and the
+    # angle comes back up to bf16 rounding; the constant column carries the
+    # first layer's bias; the padding is zero
+    from oracle import mlp
+    phases = np.random.default_rng(8).uniform(0, 2 * np.pi, (6, 5))
+    X = mlp.features(phases, 16)
+    s, c = X[:, :5], X[:, 5:10]
+    assert np.abs(s * s + c * c - 1).max() < 2 ** -7
+    d = np.angle(np.exp(1j * (np.arctan2(s, c) - phases)))
+    assert np.abs(d).max() < 2 ** -7
+    assert np.all(X[:, 10] == 1.0) and np.all(X[:, 11:] == 0.0)
+
+
+def test_mlp_oracle_forward_computes_a_known_function():
+    # gelu(x) - gelu(-x) = x Phi(x) + x (1 - Phi(x)) = x, so a network whose
+    # layers map x to (x, -x), then (h1 - h2, h2 - h1) twice, then h1 - h2 + c
+    # computes x + c whatever the depth; the hidden activations are stored in
+    # bf16, so the result holds to a few bf16 rounding errors of |x|
+    from oracle import mlp
+    x = np.linspace(-4, 4, 33)[:, None]
+    X = mlp.bf16(x)
+    pm = np.array([[1.0, -1.0], [-1.0, 1.0]])
+    Ws = [np.array([[1.0], [-1.0]]), pm, pm, np.array([[1.0, -1.0]])]
+    c = 3.0
+    bs = [np.zeros(2), np.zeros(2), np.zeros(2), np.array([c])]
+    ins, pres, out = mlp.forward(X, Ws, bs)
+    assert len(ins) == 4 and len(pres) == 3 and out.shape == (33, 1)
+    assert np.abs(out - (X + c)).max() < 0.05
+    assert np.abs(pres[0] - np.hstack([X, -X])).max() == 0.0
