@@ -265,6 +265,20 @@ def test_partial_certificate_equals_gram_permanent():
     assert abs(_pk_gram(U, range(n), m) - 1.0) < 1e-13
 
 
+def test_haar_generator_moments():
+    # the seeded input generator draws from the Haar measure: every entry has
+    # mean 0, E|u|^2 = 1/m and E|u|^4 = 2 / (m (m + 1)); a QR without the
+    # phase fix of R's diagonal leaves Re U[0][0] of one sign
+    m, N = 4, 4000
+    Us = np.array([pin.haar_unitary(m, 90_000 + k) for k in range(N)])
+    assert np.abs(np.einsum("kij,kil->kjl", Us.conj(), Us) - np.eye(m)).max() < 1e-13
+    for i, j in ((0, 0), (1, 2), (3, 1)):
+        u = Us[:, i, j]
+        assert abs(u.mean()) < 5 * math.sqrt(1 / m / N)
+        assert abs(np.mean(np.abs(u) ** 2) - 1 / m) < 0.02
+        assert abs(np.mean(np.abs(u) ** 4) - 2 / (m * (m + 1))) < 0.02
+
+
 def test_haar_average_formula_matches_printed_table():
     # Eq. eqhaarpk against the analytical row of Table figtablebs (n=14, m=60)
     n, m = 14, 60

@@ -1,13 +1,14 @@
 """Planted mistakes in the oracle are caught by its pins.
 
-Each case copies ``oracle/`` into a scratch directory, plants one plausible
-mistake in the copy by an exact text substitution (a dropped term, a wrong
-sign or index, a transposed operand, a swapped convention), and runs the
-oracle's pin tests (tests/test_oracle.py, tests/test_oracle_distinguishable.py)
-against the copy in a child process: at least one pin must fail.  The copy
-builds its own C library; the repository's oracle is not modified.  A case
-whose text no longer occurs exactly once in the oracle fails loudly, so the
-list follows the oracle's source.
+Each case copies ``oracle/`` and the seeded input generator into a scratch
+directory, plants one plausible mistake in the copy by an exact text
+substitution (a dropped term, a wrong sign or index, a transposed operand, a
+swapped convention), and runs the oracle's pin tests (tests/test_oracle.py,
+tests/test_oracle_distinguishable.py) against the copy in a child process: at
+least one pin must fail, while the unchanged copy passes them all.  The copy
+builds its own C library; the repository's files are not modified.  A case
+whose text no longer occurs exactly once fails loudly, so the list follows the
+oracle's source.
 """
 import concurrent.futures as cf
 import os
@@ -18,7 +19,9 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = [os.path.join(ROOT, "tests", f) for f in ("test_oracle.py", "test_oracle_distinguishable.py")]
 
-C, PY, DIST, MLP = "pcv_oracle.c", "__init__.py", "distinguishable.py", "mlp.py"
+# files of the scratch copy: the oracle package and the seeded input generator
+C, PY, DIST, MLP = "oracle/pcv_oracle.c", "oracle/__init__.py", "oracle/distinguishable.py", "oracle/mlp.py"
+INPUTS = "pcv_inputs.py"
 
 # (name, file, text, replacement)
 MUTATIONS = [
@@ -96,6 +99,12 @@ MUTATIONS = [
     ("features_without_constant", MLP, "    X[:, 2 * P] = 1.0\n", ""),
     ("forward_bias_dropped", MLP, "pre = gemm(h, W) + b", "pre = gemm(h, W)"),
     ("forward_hidden_layer_linear", MLP, "h = bf16(gelu(pre))", "h = bf16(pre)"),
+    # the Haar unitaries both sides are fed
+    ("haar_without_phase_fix", INPUTS, "return np.ascontiguousarray(q * ph[None, :], dtype=np.complex128)",
+     "return np.ascontiguousarray(q, dtype=np.complex128)"),
+    ("haar_from_real_gaussians", INPUTS,
+     "z = (g.standard_normal((m, m)) + 1j * g.standard_normal((m, m))) / np.sqrt(2.0)\n    q, r",
+     "z = g.standard_normal((m, m)) + 0j\n    q, r"),
 ]
 
 
@@ -121,17 +130,19 @@ def plant(scratch, name, fname, text, repl):
     scratch.mkdir()
     copy = scratch / "oracle"
     shutil.copytree(os.path.join(ROOT, "oracle"), copy, ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    shutil.copy(os.path.join(ROOT, INPUTS), scratch / INPUTS)
     if fname is not None:
-        src = (copy / fname).read_text()
+        src = (scratch / fname).read_text()
         if src.count(text) != 1:
             return None, f"{name}: the text to change occurs {src.count(text)} times in {fname}"
-        (copy / fname).write_text(src.replace(text, repl))
+        (scratch / fname).write_text(src.replace(text, repl))
     # the unchanged copy runs every pin, the longest case: give it more threads
     env = child_env(scratch, 1 if fname is not None else max(1, (os.cpu_count() or 2) // 2))
     # the child imports the copy, and the copy builds
-    probe = subprocess.run([sys.executable, "-c", "import oracle; oracle.build(); print(oracle.__file__)"],
+    probe = subprocess.run([sys.executable, "-c", "import oracle, pcv_inputs; oracle.build(); "
+                            "print(oracle.__file__); print(pcv_inputs.__file__)"],
                            cwd=str(scratch), env=env, capture_output=True, text=True, timeout=300)
-    if probe.returncode != 0 or not probe.stdout.strip().startswith(str(copy)):
+    if probe.returncode != 0 or not all(f.startswith(str(scratch)) for f in probe.stdout.split()):
         return None, f"{name}: the copy did not load: {probe.stdout[-300:]} {probe.stderr[-1500:]}"
     # the quick pins first; all of them only when those pass
     for phase, extra in enumerate((QUICK, FULL)):
