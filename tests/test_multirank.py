@@ -1,9 +1,10 @@
 """The multi-GPU host logic on CPU ranks (gloo, world size 2): in the bench
 each rank simulates its own unitary, the slowest rank's time is the job's
 time and the rate counts the work of every rank; in sharding.py both ranks
-see the same LPT assignment of uneven circuits, the reduced partial
-statistics (sum p, TVD, KL) and gradients equal the whole distribution's, the
-gathered ranges equal the whole arrays, and the index ranges tile [0, N)."""
+see the same LPT assignment of uneven circuits (within Graham's bound), the
+partial statistics (sum p, TVD, KL) reduced over the ranks equal the whole
+distribution's, the gathered ranges equal the whole arrays, and the index
+ranges tile [0, N)."""
 import os
 import socket
 
