@@ -2,9 +2,9 @@
 each rank simulates its own unitary, the slowest rank's time is the job's
 time and the rate counts the work of every rank; in sharding.py both ranks
 see the same LPT assignment of uneven circuits (within Graham's bound), the
-partial statistics (sum p, TVD, KL) reduced over the ranks equal the whole
-distribution's, the gathered ranges equal the whole arrays, and the index
-ranges tile [0, N)."""
+partial statistics (sum p, TVD, KL) and the partial grad_U of a loss over
+the outputs, reduced over the ranks, equal the whole distribution's, the
+gathered ranges equal the whole arrays, and the index ranges tile [0, N)."""
 import os
 import socket
 
@@ -96,6 +96,14 @@ def _shard_worker(rank, world, port, out):
                         dtype=torch.float64)
     res["stats"] = sh.reduce_sum(part).numpy()
     res["full"] = (p.sum(), oracle.tvd(p, q), oracle.kl(q, p))
+    # a loss over the outputs: each rank's grad_U from its own outputs, summed
+    # over the ranks, is the whole gradient (the all-reduce of grad_U)
+    outs = oracle.enumerate_outputs(m, n)
+    ga = pin.random_complex_matrix(1, outs.shape[0], 8103)[0]
+    t = pin.single_photon_input(m, n)
+    mine_g = oracle.grad_U_from_amp_grad(U, t, outs[lo:hi], ga[lo:hi])
+    res["grad"] = sh.reduce_sum(torch.from_numpy(mine_g.copy())).numpy()
+    res["grad_whole"] = oracle.grad_U_from_amp_grad(U, t, outs, ga)
     td.destroy_process_group()
     out[rank] = res
 
@@ -121,6 +129,7 @@ def test_two_rank_sharding_host_logic():
         # the gathered ranges are the whole arrays, exactly
         p, a = r["whole"]
         assert np.array_equal(r["gathered_p"], p) and np.array_equal(r["gathered_a"], a)
+        assert np.abs(r["grad"] - r["grad_whole"]).max() <= 1e-13 * np.abs(r["grad_whole"]).max()
 
 
 def test_index_ranges_cover_exactly():
