@@ -81,9 +81,18 @@ def check(pcv, m, n, lo, hi):
     hi = N if hi < 0 else hi
     seen = {}
     tiles = 0
+    assert len(blocks) == head["blocks"] <= 72                 # the kernel's block table
     for b in blocks:
         rt, ct = ts[0 if b["rows_low"] else 1], ts[1 if b["rows_low"] else 0]
         assert b["tile0"] == tiles
+        # what the kernel reads stays inside the tensors and the seam lists
+        assert b["tn"] in (16, 32, 48, 64)
+        assert 0 <= b["rows0"] < b["rows"] and 0 <= b["cols0"] < b["cols"]
+        assert 0 <= b["row_off"] and b["row_off"] + b["rows"] <= len(rt)
+        assert 0 <= b["col_off"] and b["col_off"] + b["cols"] <= len(ct)
+        if b["kind"] == 1:
+            assert 0 <= b["ri_off"] and b["ri_off"] + b["rows"] <= len(seam_lists[b["rs"]])
+            assert 0 <= b["ci_off"] and b["ci_off"] + b["cols"] <= len(seam_lists[b["cs"]])
         tiles += -(-(b["rows"] - b["rows0"]) // TBM) * -(-(b["cols"] - b["cols0"]) // b["tn"])
         for r in range(b["rows0"], b["rows"]):
             R = rt[b["row_off"] + r]
